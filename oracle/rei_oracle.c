@@ -1,0 +1,1342 @@
+/*
+ * rei_oracle.c -- plain, slow CPU oracle for precise and minimal regular
+ * expression inference (Valizadeh & Berger, "Search-Based Regular Expression
+ * Inference on a GPU", PLDI 2023).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline of the benchmark may load this file.  It shares no code, header,
+ * table or helper with the CUDA library; the two are checked against each
+ * other, never built from each other.
+ *
+ * What it computes, and where the paper defines it:
+ *   - the specification and precision test            Def. "specification" (Sec. 3)
+ *   - the cost homomorphism (c_sym, c_?, c_*, c_., c_+) Def. "cost function" (Sec. 3)
+ *   - the infix closure ic(P u N), shortlex ordered     Sec. 2 (infix-closed, shortlex),
+ *                                                       Example 1
+ *   - languages restricted to ic, by the plain set      Def. "infix power series"
+ *     definitions of +, ., *, ? (strings are split      (Sec. 3): (r.s)(w) ranges over
+ *     on the fly; no bitvectors, no guide table)        splits w = s1 s2 with s1, s2 in ic
+ *   - the main loop over costs, in the order ?, *, .,   Alg. 1
+ *     + per level, and the per-candidate step           Alg. 2: build, uniqueness
+ *     insert, precision check on unique languages       check, precision, append
+ *   - trivial answers for P = {} and P = {eps}          Alg. 1 (first two tests)
+ *   - OnTheFly mode after the cache is full             Sec. 3, "OnTheFly mode"
+ *   - REI with an allowed number of errors              Sec. 6, "Future Work"
+ *
+ * Independent cross-checks it also carries:
+ *   - a Brzozowski-derivative matcher (Brzozowski 1964) on regex trees, used to
+ *     re-derive every cached language word by word (flag ORACLE_F_SELFCHECK);
+ *   - a brute force over all syntax trees by cost with no deduplication,
+ *     matched with the derivative matcher, for the minimal cost on tiny inputs.
+ *
+ * Readings of the paper fixed here (the CUDA library follows the same ones):
+ *   - eps and the empty set are answers only through the trivial cases; the
+ *     leaves of the search are the alphabet symbols (Alg. 1 seeds only them);
+ *   - leaf languages are checked for precision like any other candidate;
+ *   - the level order: ? over level c-c2, * over level c-c3, then . over
+ *     splits cl = c1 .. in ascending order (left index outer, right inner),
+ *     then + likewise, visiting only cl <= cr and, when cl == cr, pairs i < j
+ *     (the skipped pairs always repeat an earlier candidate's language);
+ *   - the first candidate in that order with a given language is the one kept,
+ *     and the first precise unique candidate is the answer;
+ *   - the cache holds at most cap = floor(budget / (4*W + 28)) languages with W
+ *     the 32-bit words of a padded characteristic sequence (1 for n <= 32, 2
+ *     for n <= 64, else 4*ceil(n/128)); a level whose survivors would exceed it
+ *     without yielding an answer ends the search with "out of memory".
+ */
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#include <time.h>
+
+#define OR_OK 0
+#define OR_NOT_FOUND 1
+#define OR_OOM 2
+#define OR_EINVAL 3
+#define OR_LIMIT 4
+#define OR_SELFCHECK 5
+#define OR_EBUF 6
+
+#define ORACLE_F_SELFCHECK 1u
+#define ORACLE_F_ONTHEFLY 2u
+
+/* operators of a cached entry / candidate */
+enum { OP_LEAF = 0, OP_OPT = 1, OP_STAR = 2, OP_CAT = 3, OP_ALT = 4 };
+
+/* postfix token kinds of the regex-tree encoding (2 bytes per token) */
+#define TK_SYM 'a'
+#define TK_EPS 'e'
+#define TK_EMPTY '0'
+#define TK_OPT '?'
+#define TK_STAR '*'
+#define TK_CAT '.'
+#define TK_ALT '+'
+
+/* Planted mistakes, used only by the test that shows the pins have teeth:
+ * 0 = none; 1 = concatenation drops its last split; 2 = concatenation reads
+ * its operands swapped; 3 = star stops after r^1; 4 = precision ignores N;
+ * 5 = stars enumerated before questions; 6 = shortlex compares symbols in
+ * reverse alphabet order; 7 = union skips pairs with cl == cr. */
+static int g_mutation = 0;
+void oracle_set_mutation(int m) { g_mutation = m; }
+
+typedef struct {
+    int status;
+    int cost;
+    uint64_t candidates;
+    uint64_t unique;
+    int levels;
+    int n_ic;
+    double seconds;
+} oracle_stats;
+
+/* ------------------------------------------------------------------------- */
+/* strings of ic                                                              */
+
+typedef struct {
+    const unsigned char *s;
+    int len;
+} ostr;
+
+typedef struct {
+    int rank[256]; /* symbol byte -> position in the caller's alphabet, or -1 */
+    int n_sym;
+    unsigned char alpha[256];
+} alphabet_t;
+
+/* shortlex: shorter first; equal lengths by the alphabet order of symbols */
+static int shortlex_cmp(const alphabet_t *A, const unsigned char *a, int la,
+                        const unsigned char *b, int lb)
+{
+    if (la != lb) return la < lb ? -1 : 1;
+    for (int i = 0; i < la; i++) {
+        int ra = A->rank[a[i]], rb = A->rank[b[i]];
+        if (g_mutation == 6) {
+            ra = -ra;
+            rb = -rb;
+        }
+        if (ra != rb) return ra < rb ? -1 : 1;
+    }
+    return 0;
+}
+
+static const alphabet_t *g_sort_alpha;
+static int ostr_qcmp(const void *x, const void *y)
+{
+    const ostr *a = (const ostr *)x, *b = (const ostr *)y;
+    return shortlex_cmp(g_sort_alpha, a->s, a->len, b->s, b->len);
+}
+
+typedef struct {
+    int n;
+    ostr *w; /* words of ic in shortlex order; w[0] is eps */
+} ic_t;
+
+/* ic(S): every infix of every string in S, including eps (Sec. 2) */
+static int build_ic(const alphabet_t *A, const unsigned char *bytes, const uint32_t *offs,
+                    int n_str, ic_t *out)
+{
+    size_t m = 1;
+    for (int k = 0; k < n_str; k++) {
+        size_t L = offs[k + 1] - offs[k];
+        m += L * (L + 1) / 2;
+    }
+    ostr *all = (ostr *)malloc(m * sizeof(ostr));
+    if (!all) return -1;
+    size_t t = 0;
+    all[t].s = bytes;
+    all[t].len = 0;
+    t++;
+    for (int k = 0; k < n_str; k++) {
+        const unsigned char *s = bytes + offs[k];
+        int L = (int)(offs[k + 1] - offs[k]);
+        for (int i = 0; i < L; i++)
+            for (int j = i + 1; j <= L; j++) {
+                all[t].s = s + i;
+                all[t].len = j - i;
+                t++;
+            }
+    }
+    g_sort_alpha = A;
+    qsort(all, t, sizeof(ostr), ostr_qcmp);
+    size_t u = 0;
+    for (size_t k = 0; k < t; k++) {
+        if (u > 0 && shortlex_cmp(A, all[u - 1].s, all[u - 1].len, all[k].s, all[k].len) == 0)
+            continue;
+        all[u++] = all[k];
+    }
+    out->n = (int)u;
+    out->w = all;
+    return 0;
+}
+
+/* index of a string in ic, or -1 (binary search in shortlex order) */
+static int ic_lookup(const alphabet_t *A, const ic_t *ic, const unsigned char *s, int len)
+{
+    int lo = 0, hi = ic->n - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) / 2;
+        int c = shortlex_cmp(A, ic->w[mid].s, ic->w[mid].len, s, len);
+        if (c == 0) return mid;
+        if (c < 0) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return -1;
+}
+
+/* ------------------------------------------------------------------------- */
+/* languages restricted to ic: one byte per word (1 = member)                 */
+
+static void lang_leaf(const alphabet_t *A, const ic_t *ic, int sym, unsigned char *out)
+{
+    memset(out, 0, (size_t)ic->n);
+    unsigned char a = A->alpha[sym];
+    int k = ic_lookup(A, ic, &a, 1);
+    if (k >= 0) out[k] = 1;
+}
+
+/* (r + s)(w) = r(w) or s(w) */
+static void lang_union(int n, const unsigned char *r, const unsigned char *s, unsigned char *out)
+{
+    for (int w = 0; w < n; w++) out[w] = (unsigned char)(r[w] | s[w]);
+}
+
+/* r? has the language of eps + r (Sec. 2, last line of the denotation) */
+static void lang_opt(int n, const unsigned char *r, unsigned char *out)
+{
+    memcpy(out, r, (size_t)n);
+    out[0] = 1; /* ic word 0 is eps */
+}
+
+/* (r . s)(w) = OR over w = s1 s2, s1 and s2 in ic, of r(s1) and s(s2) */
+static void lang_concat(const alphabet_t *A, const ic_t *ic, const unsigned char *r,
+                        const unsigned char *s, unsigned char *out)
+{
+    for (int w = 0; w < ic->n; w++) {
+        const unsigned char *str = ic->w[w].s;
+        int L = ic->w[w].len;
+        out[w] = 0;
+        for (int k = 0; k <= L - (g_mutation == 1); k++) {
+            int u = ic_lookup(A, ic, str, k);
+            int v = ic_lookup(A, ic, str + k, L - k);
+            const unsigned char *x = g_mutation == 2 ? s : r, *y = g_mutation == 2 ? r : s;
+            /* ic is infix-closed, so both halves are always found */
+            if (u >= 0 && v >= 0 && x[u] && y[v]) {
+                out[w] = 1;
+                break;
+            }
+        }
+    }
+}
+
+/* r*(w) = OR over n >= 0 of r^n(w), r^0 = 1 (eps only), r^(n+1) = r^n . r.
+ * The union stops growing after finitely many powers because ic is finite:
+ * once r^(n+1) adds nothing to r^0 + .. + r^n, no later power does. */
+static void lang_star(const alphabet_t *A, const ic_t *ic, const unsigned char *r,
+                      unsigned char *out, unsigned char *pw, unsigned char *nx)
+{
+    int n = ic->n;
+    memset(pw, 0, (size_t)n);
+    pw[0] = 1;
+    memcpy(out, pw, (size_t)n);
+    for (;;) {
+        lang_concat(A, ic, pw, r, nx);
+        int grew = 0;
+        for (int w = 0; w < n; w++)
+            if (nx[w] && !out[w]) {
+                out[w] = 1;
+                grew = 1;
+            }
+        if (!grew || g_mutation == 3) break;
+        memcpy(pw, nx, (size_t)n);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* regex trees, postfix token encoding, cost, printing, parsing               */
+
+typedef struct {
+    char k; /* TK_* */
+    int a;  /* symbol index for TK_SYM */
+    int l, r;
+} tnode;
+
+typedef struct {
+    tnode *v;
+    int n, cap;
+} tarena;
+
+static int tnew(tarena *T, char k, int a, int l, int r)
+{
+    if (T->n == T->cap) {
+        int nc = T->cap ? 2 * T->cap : 256;
+        tnode *nv = (tnode *)realloc(T->v, (size_t)nc * sizeof(tnode));
+        if (!nv) return -1;
+        T->v = nv;
+        T->cap = nc;
+    }
+    T->v[T->n].k = k;
+    T->v[T->n].a = a;
+    T->v[T->n].l = l;
+    T->v[T->n].r = r;
+    return T->n++;
+}
+
+/* postfix tokens -> tree; returns the root or -1 */
+static int tree_from_postfix(tarena *T, const unsigned char *tok, int ntok)
+{
+    int *st = (int *)malloc((size_t)(ntok + 1) * sizeof(int));
+    int sp = 0, root = -1;
+    if (!st) return -1;
+    for (int i = 0; i < ntok; i++) {
+        char k = (char)tok[2 * i];
+        int a = tok[2 * i + 1];
+        if (k == TK_SYM || k == TK_EPS || k == TK_EMPTY) {
+            st[sp++] = tnew(T, k, a, -1, -1);
+        } else if (k == TK_OPT || k == TK_STAR) {
+            if (sp < 1) goto bad;
+            st[sp - 1] = tnew(T, k, 0, st[sp - 1], -1);
+        } else if (k == TK_CAT || k == TK_ALT) {
+            if (sp < 2) goto bad;
+            int r = st[--sp];
+            st[sp - 1] = tnew(T, k, 0, st[sp - 1], r);
+        } else {
+            goto bad;
+        }
+    }
+    if (sp == 1) root = st[0];
+bad:
+    free(st);
+    return root;
+}
+
+static int tree_cost(const tarena *T, int x, const int *c)
+{
+    const tnode *t = &T->v[x];
+    switch (t->k) {
+    case TK_SYM: case TK_EPS: case TK_EMPTY: return c[0];
+    case TK_OPT: return tree_cost(T, t->l, c) + c[1];
+    case TK_STAR: return tree_cost(T, t->l, c) + c[2];
+    case TK_CAT: return tree_cost(T, t->l, c) + tree_cost(T, t->r, c) + c[3];
+    case TK_ALT: return tree_cost(T, t->l, c) + tree_cost(T, t->r, c) + c[4];
+    }
+    return -1;
+}
+
+/* printing: * and ? bind tighter than concatenation, which binds tighter than +;
+ * a child is parenthesised only when its operator binds looser than its
+ * position needs.  eps prints as "ε" and the empty set as "∅" (UTF-8). */
+static int prec_of(char k)
+{
+    if (k == TK_ALT) return 0;
+    if (k == TK_CAT) return 1;
+    return 2;
+}
+
+typedef struct {
+    char *buf;
+    size_t cap, len;
+} sbuf;
+
+static void sput(sbuf *b, const char *s, size_t n)
+{
+    if (b->len + n < b->cap) memcpy(b->buf + b->len, s, n);
+    b->len += n;
+}
+
+static void print_tree(const tarena *T, int x, const alphabet_t *A, sbuf *b, int need)
+{
+    const tnode *t = &T->v[x];
+    int p = prec_of(t->k);
+    int par = p < need;
+    if (par) sput(b, "(", 1);
+    switch (t->k) {
+    case TK_SYM: { char ch = (char)A->alpha[t->a]; sput(b, &ch, 1); break; }
+    case TK_EPS: sput(b, "\xce\xb5", 2); break;
+    case TK_EMPTY: sput(b, "\xe2\x88\x85", 3); break;
+    case TK_OPT: print_tree(T, t->l, A, b, 2); sput(b, "?", 1); break;
+    case TK_STAR: print_tree(T, t->l, A, b, 2); sput(b, "*", 1); break;
+    case TK_CAT: print_tree(T, t->l, A, b, 1); print_tree(T, t->r, A, b, 1); break;
+    case TK_ALT: print_tree(T, t->l, A, b, 0); sput(b, "+", 1); print_tree(T, t->r, A, b, 0); break;
+    }
+    if (par) sput(b, ")", 1);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Brzozowski derivatives (independent matcher)                              */
+
+typedef struct {
+    tarena T;
+    int empty, eps;
+} dctx;
+
+static int d_cat(dctx *D, int a, int b)
+{
+    if (a == D->empty || b == D->empty) return D->empty;
+    if (a == D->eps) return b;
+    if (b == D->eps) return a;
+    return tnew(&D->T, TK_CAT, 0, a, b);
+}
+
+static int d_alt(dctx *D, int a, int b)
+{
+    if (a == D->empty) return b;
+    if (b == D->empty) return a;
+    if (a == b) return a;
+    return tnew(&D->T, TK_ALT, 0, a, b);
+}
+
+static int nullable(const tarena *T, int x)
+{
+    const tnode *t = &T->v[x];
+    switch (t->k) {
+    case TK_SYM: case TK_EMPTY: return 0;
+    case TK_EPS: case TK_STAR: case TK_OPT: return 1;
+    case TK_CAT: return nullable(T, t->l) && nullable(T, t->r);
+    case TK_ALT: return nullable(T, t->l) || nullable(T, t->r);
+    }
+    return 0;
+}
+
+/* d_a(x): the language { w | a w in L(x) } */
+static int deriv(dctx *D, int x, int a)
+{
+    tnode t = D->T.v[x];
+    switch (t.k) {
+    case TK_SYM: return t.a == a ? D->eps : D->empty;
+    case TK_EPS: case TK_EMPTY: return D->empty;
+    case TK_OPT: return deriv(D, t.l, a);
+    case TK_STAR: return d_cat(D, deriv(D, t.l, a), x);
+    case TK_ALT: {
+        int l = deriv(D, t.l, a);
+        int r = deriv(D, t.r, a);
+        return d_alt(D, l, r);
+    }
+    case TK_CAT: {
+        int l = d_cat(D, deriv(D, t.l, a), t.r);
+        if (nullable(&D->T, t.l)) return d_alt(D, l, deriv(D, t.r, a));
+        return l;
+    }
+    }
+    return D->empty;
+}
+
+/* copy the subtree of `src` rooted at x into D's arena */
+static int copy_subtree(dctx *D, const tarena *src, int x)
+{
+    const tnode t = src->v[x];
+    int l = t.l >= 0 ? copy_subtree(D, src, t.l) : -1;
+    int r = t.r >= 0 ? copy_subtree(D, src, t.r) : -1;
+    return tnew(&D->T, t.k, t.a, l, r);
+}
+
+/* does the tree rooted at `root` of arena `src` accept s (symbol ranks)? */
+static int d_match(const tarena *src, int root, const int *ranks, int len)
+{
+    dctx D;
+    memset(&D, 0, sizeof D);
+    D.empty = tnew(&D.T, TK_EMPTY, 0, -1, -1);
+    D.eps = tnew(&D.T, TK_EPS, 0, -1, -1);
+    /* eps / empty-set leaves of the source keep their own ids: they mean the
+     * same as D.eps / D.empty, only the simplifications skip them */
+    int x = copy_subtree(&D, src, root);
+    for (int i = 0; i < len && x != D.empty; i++) x = deriv(&D, x, ranks[i]);
+    int ok = (x != D.empty) && nullable(&D.T, x);
+    free(D.T.v);
+    return ok;
+}
+
+/* ------------------------------------------------------------------------- */
+/* the search (Alg. 1 and Alg. 2)                                            */
+
+typedef struct {
+    alphabet_t A;
+    ic_t ic;
+    int n;
+    int c[5];
+    int max_cost;
+    uint64_t cap;
+    unsigned flags;
+    uint64_t max_candidates;
+    uint32_t max_errors;
+    unsigned char *is_pos, *is_neg;
+    int n_pos, n_neg; /* distinct examples */
+
+    /* language cache: write-once, ordered by cost */
+    uint64_t size, alloc;
+    unsigned char *lang;
+    unsigned char *bp_op;
+    int64_t *bp_l, *bp_r;
+    int64_t *lvl_start, *lvl_count; /* per cost 0..max_cost */
+
+    /* uniqueness set: open addressing over cache indices */
+    uint64_t hcap, hused;
+    int64_t *slot;
+
+    /* scratch */
+    unsigned char *tmp, *s1, *s2;
+
+    /* progress */
+    uint64_t candidates;
+    uint64_t unique_done; /* languages in completed levels */
+    int levels;
+    int otf;              /* 1 while in OnTheFly mode */
+    int partial_level;    /* first level not completely cached */
+    int found;
+    int ans_cost;
+    int ans_op;
+    int64_t ans_l, ans_r;
+    int err;
+} search_t;
+
+static uint64_t lang_hash(const unsigned char *x, int n)
+{
+    uint64_t h = 1469598103934665603ull; /* FNV-1a */
+    for (int i = 0; i < n; i++) {
+        h ^= x[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+static int set_grow(search_t *S)
+{
+    uint64_t nc = S->hcap ? 2 * S->hcap : 1024;
+    int64_t *ns = (int64_t *)malloc(nc * sizeof(int64_t));
+    if (!ns) return -1;
+    for (uint64_t i = 0; i < nc; i++) ns[i] = -1;
+    for (uint64_t i = 0; i < S->hcap; i++) {
+        int64_t e = S->slot[i];
+        if (e < 0) continue;
+        uint64_t p = lang_hash(S->lang + (uint64_t)e * S->n, S->n) & (nc - 1);
+        while (ns[p] >= 0) p = (p + 1) & (nc - 1);
+        ns[p] = e;
+    }
+    free(S->slot);
+    S->slot = ns;
+    S->hcap = nc;
+    return 0;
+}
+
+/* is x already a cached language? */
+static int set_contains(search_t *S, const unsigned char *x)
+{
+    if (!S->hcap) return 0;
+    uint64_t p = lang_hash(x, S->n) & (S->hcap - 1);
+    while (S->slot[p] >= 0) {
+        if (memcmp(S->lang + (uint64_t)S->slot[p] * S->n, x, (size_t)S->n) == 0) return 1;
+        p = (p + 1) & (S->hcap - 1);
+    }
+    return 0;
+}
+
+static int cache_append(search_t *S, const unsigned char *x, int op, int64_t l, int64_t r)
+{
+    if (S->size == S->alloc) {
+        uint64_t na = S->alloc ? 2 * S->alloc : 1024;
+        unsigned char *nl = (unsigned char *)realloc(S->lang, na * (uint64_t)S->n);
+        unsigned char *no = (unsigned char *)realloc(S->bp_op, na);
+        int64_t *nL = (int64_t *)realloc(S->bp_l, na * sizeof(int64_t));
+        int64_t *nR = (int64_t *)realloc(S->bp_r, na * sizeof(int64_t));
+        if (nl) S->lang = nl;
+        if (no) S->bp_op = no;
+        if (nL) S->bp_l = nL;
+        if (nR) S->bp_r = nR;
+        if (!nl || !no || !nL || !nR) return -1;
+        S->alloc = na;
+    }
+    if (2 * (S->hused + 1) > S->hcap && set_grow(S)) return -1;
+    uint64_t k = S->size++;
+    memcpy(S->lang + k * S->n, x, (size_t)S->n);
+    S->bp_op[k] = (unsigned char)op;
+    S->bp_l[k] = l;
+    S->bp_r[k] = r;
+    uint64_t p = lang_hash(x, S->n) & (S->hcap - 1);
+    while (S->slot[p] >= 0) p = (p + 1) & (S->hcap - 1);
+    S->slot[p] = (int64_t)k;
+    S->hused++;
+    return 0;
+}
+
+/* Def. specification: P in L and N disjoint from L; with an allowed error,
+ * at most max_errors examples may be misclassified (Sec. 6). */
+static int precise(const search_t *S, const unsigned char *x)
+{
+    uint32_t errs = 0;
+    for (int w = 0; w < S->n; w++) {
+        if (S->is_pos[w] && !x[w]) errs++;
+        if (S->is_neg[w] && x[w] && g_mutation != 4) errs++;
+    }
+    return errs <= S->max_errors;
+}
+
+/* regex tree of cache entry e (or of a candidate), appended to the arena */
+static int entry_tree(const search_t *S, tarena *T, int op, int64_t l, int64_t r)
+{
+    if (op == OP_LEAF) return tnew(T, TK_SYM, (int)l, -1, -1);
+    int a = entry_tree(S, T, S->bp_op[l], S->bp_l[l], S->bp_r[l]);
+    if (op == OP_OPT) return tnew(T, TK_OPT, 0, a, -1);
+    if (op == OP_STAR) return tnew(T, TK_STAR, 0, a, -1);
+    int b = entry_tree(S, T, S->bp_op[r], S->bp_l[r], S->bp_r[r]);
+    return tnew(T, op == OP_CAT ? TK_CAT : TK_ALT, 0, a, b);
+}
+
+/* derivative matcher re-derives the language of a cached entry on all of ic */
+static int selfcheck_entry(search_t *S, uint64_t k)
+{
+    tarena T;
+    memset(&T, 0, sizeof T);
+    int root = entry_tree(S, &T, S->bp_op[k], S->bp_l[k], S->bp_r[k]);
+    int ok = 1;
+    int ranks[4096];
+    for (int w = 0; w < S->n && ok; w++) {
+        int L = S->ic.w[w].len;
+        int *rk = L <= 4096 ? ranks : (int *)malloc((size_t)L * sizeof(int));
+        for (int i = 0; i < L; i++) rk[i] = S->A.rank[S->ic.w[w].s[i]];
+        int m = d_match(&T, root, rk, L);
+        if (rk != ranks) free(rk);
+        if (m != (S->lang[k * S->n + w] ? 1 : 0)) ok = 0;
+    }
+    free(T.v);
+    return ok;
+}
+
+/* Alg. 2, one candidate: build it, insert it, test precision if new */
+static void candidate(search_t *S, int cost, int op, int64_t l, int64_t r)
+{
+    if (S->found || S->err) return;
+    if (S->max_candidates && S->candidates >= S->max_candidates) {
+        S->err = OR_LIMIT;
+        return;
+    }
+    int n = S->n;
+    unsigned char *x = S->tmp;
+    switch (op) {
+    case OP_LEAF: lang_leaf(&S->A, &S->ic, (int)l, x); break;
+    case OP_OPT: lang_opt(n, S->lang + (uint64_t)l * n, x); break;
+    case OP_STAR: lang_star(&S->A, &S->ic, S->lang + (uint64_t)l * n, x, S->s1, S->s2); break;
+    case OP_CAT: lang_concat(&S->A, &S->ic, S->lang + (uint64_t)l * n, S->lang + (uint64_t)r * n, x); break;
+    case OP_ALT: lang_union(n, S->lang + (uint64_t)l * n, S->lang + (uint64_t)r * n, x); break;
+    }
+    S->candidates++;
+    if (S->otf) {
+        /* OnTheFly: neither cached nor checked for uniqueness */
+        if (precise(S, x)) {
+            S->found = 1;
+            S->ans_cost = cost;
+            S->ans_op = op;
+            S->ans_l = l;
+            S->ans_r = r;
+        }
+        return;
+    }
+    if (set_contains(S, x)) return;
+    if (precise(S, x)) {
+        S->found = 1;
+        S->ans_cost = cost;
+        S->ans_op = op;
+        S->ans_l = l;
+        S->ans_r = r;
+        return;
+    }
+    if (cache_append(S, x, op, l, r)) {
+        S->err = OR_OOM;
+        return;
+    }
+    if ((S->flags & ORACLE_F_SELFCHECK) && !selfcheck_entry(S, S->size - 1)) S->err = OR_SELFCHECK;
+}
+
+static void level_range(const search_t *S, int c, int64_t *st, int64_t *cnt)
+{
+    if (c < 0 || c > S->max_cost) {
+        *st = 0;
+        *cnt = 0;
+        return;
+    }
+    *st = S->lvl_start[c];
+    *cnt = S->lvl_count[c];
+}
+
+/* the highest operand level that level c refers to (OnTheFly feasibility) */
+static int max_operand_level(const search_t *S, int c)
+{
+    int m = -1;
+    const int *k = S->c;
+    if (c - k[1] >= k[0] && c - k[1] > m) m = c - k[1];
+    if (c - k[2] >= k[0] && c - k[2] > m) m = c - k[2];
+    if (c - k[3] >= 2 * k[0] && c - k[3] - k[0] > m) m = c - k[3] - k[0];
+    if (c - k[4] >= 2 * k[0] && c - k[4] - k[0] > m) m = c - k[4] - k[0];
+    return m;
+}
+
+/* Alg. 1 main loop body for one cost level c > c1 */
+static void build_level(search_t *S, int c)
+{
+    const int *k = S->c;
+    int64_t st, cnt, st2, cnt2;
+    /* questions, then stars */
+    for (int pass = 0; pass < 2; pass++) {
+        int star = (pass == 1) != (g_mutation == 5);
+        int d = star ? k[2] : k[1];
+        level_range(S, c - d, &st, &cnt);
+        if (c - d >= k[0])
+            for (int64_t i = 0; i < cnt; i++) candidate(S, c, star ? OP_STAR : OP_OPT, st + i, -1);
+    }
+    /* concatenations: every split cl + cr = c - c4 */
+    int rem = c - k[3];
+    for (int cl = k[0]; cl <= rem - k[0]; cl++) {
+        level_range(S, cl, &st, &cnt);
+        level_range(S, rem - cl, &st2, &cnt2);
+        for (int64_t i = 0; i < cnt; i++)
+            for (int64_t j = 0; j < cnt2; j++) candidate(S, c, OP_CAT, st + i, st2 + j);
+    }
+    /* unions: splits cl + cr = c - c5 with cl <= cr, and i < j when cl == cr */
+    rem = c - k[4];
+    for (int cl = k[0]; cl <= rem - k[0] && cl <= rem - cl; cl++) {
+        int cr = rem - cl;
+        if (g_mutation == 7 && cl == cr) continue;
+        level_range(S, cl, &st, &cnt);
+        level_range(S, cr, &st2, &cnt2);
+        for (int64_t i = 0; i < cnt; i++)
+            for (int64_t j = (cl == cr ? i + 1 : 0); j < cnt2; j++)
+                candidate(S, c, OP_ALT, st + i, st2 + j);
+    }
+}
+
+/* words per padded characteristic sequence, in 32-bit units (the memory
+ * accounting shared with the library's documented budget rule) */
+static uint64_t padded_words(int n)
+{
+    if (n <= 32) return 1;
+    if (n <= 64) return 2;
+    return 4ull * (uint64_t)((n + 127) / 128);
+}
+
+static uint64_t budget_cap(uint64_t budget, int n)
+{
+    uint64_t per = 4 * padded_words(n) + 28;
+    uint64_t cap = budget / per;
+    if (cap > 0x7FFF0000ull) cap = 0x7FFF0000ull;
+    return cap;
+}
+
+typedef struct oracle_run {
+    search_t S;
+    oracle_stats st;
+    tarena T;
+    int root;
+} oracle_run;
+
+static void search_free(search_t *S)
+{
+    free(S->ic.w);
+    free(S->is_pos);
+    free(S->is_neg);
+    free(S->lang);
+    free(S->bp_op);
+    free(S->bp_l);
+    free(S->bp_r);
+    free(S->lvl_start);
+    free(S->lvl_count);
+    free(S->slot);
+    free(S->tmp);
+    free(S->s1);
+    free(S->s2);
+    memset(S, 0, sizeof *S);
+}
+
+/* emit a tree as postfix tokens */
+static int emit_postfix(const tarena *T, int x, unsigned char *out, int cap, int *len)
+{
+    const tnode *t = &T->v[x];
+    if (t->l >= 0 && emit_postfix(T, t->l, out, cap, len)) return -1;
+    if (t->r >= 0 && emit_postfix(T, t->r, out, cap, len)) return -1;
+    if (out && 2 * (*len + 1) <= cap) {
+        out[2 * *len] = (unsigned char)t->k;
+        out[2 * *len + 1] = (unsigned char)(t->k == TK_SYM ? t->a : 0);
+    }
+    (*len)++;
+    return 0;
+}
+
+oracle_run *oracle_new(void)
+{
+    oracle_run *R = (oracle_run *)calloc(1, sizeof(oracle_run));
+    if (R) R->root = -1;
+    return R;
+}
+
+void oracle_free(oracle_run *R)
+{
+    if (!R) return;
+    search_free(&R->S);
+    free(R->T.v);
+    free(R);
+}
+
+static double now_s(void)
+{
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
+/*
+ * Solve one instance.  Examples are strings over `alphabet`, P first then N,
+ * string k being bytes[offs[k] .. offs[k+1]).  costs = (c_sym, c_?, c_*, c_., c_+).
+ * Returns the status (also in R->st.status).
+ */
+int oracle_solve(oracle_run *R, const unsigned char *alphabet, int n_sym,
+                 const unsigned char *bytes, const uint32_t *offs, int n_pos, int n_neg,
+                 const int *costs, int max_cost, uint64_t mem_budget, unsigned flags,
+                 uint32_t max_errors, uint64_t max_candidates)
+{
+    double t0 = now_s();
+    search_free(&R->S);
+    free(R->T.v);
+    memset(&R->T, 0, sizeof R->T);
+    R->root = -1;
+    memset(&R->st, 0, sizeof R->st);
+    search_t *S = &R->S;
+    int status = OR_OK;
+
+    /* validation */
+    for (int i = 0; i < 5; i++)
+        if (costs[i] < 1) return R->st.status = OR_EINVAL;
+    if (n_sym < 0 || n_sym > 256 || max_cost < 0) return R->st.status = OR_EINVAL;
+    for (int i = 0; i < 256; i++) S->A.rank[i] = -1;
+    for (int i = 0; i < n_sym; i++) {
+        if (S->A.rank[alphabet[i]] >= 0) return R->st.status = OR_EINVAL;
+        S->A.rank[alphabet[i]] = i;
+        S->A.alpha[i] = alphabet[i];
+    }
+    S->A.n_sym = n_sym;
+    int n_str = n_pos + n_neg;
+    for (int k = 0; k < n_str; k++)
+        for (uint32_t i = offs[k]; i < offs[k + 1]; i++)
+            if (S->A.rank[bytes[i]] < 0) return R->st.status = OR_EINVAL;
+    memcpy(S->c, costs, sizeof S->c);
+    S->max_cost = max_cost;
+    S->flags = flags;
+    S->max_candidates = max_candidates;
+    S->max_errors = max_errors;
+
+    if (build_ic(&S->A, bytes, offs, n_str, &S->ic)) return R->st.status = OR_OOM;
+    S->n = S->ic.n;
+    int n = S->n;
+    R->st.n_ic = n;
+    S->is_pos = (unsigned char *)calloc((size_t)n, 1);
+    S->is_neg = (unsigned char *)calloc((size_t)n, 1);
+    for (int k = 0; k < n_str; k++) {
+        int w = ic_lookup(&S->A, &S->ic, bytes + offs[k], (int)(offs[k + 1] - offs[k]));
+        if (k < n_pos) S->is_pos[w] = 1;
+        else S->is_neg[w] = 1;
+    }
+    for (int w = 0; w < n; w++) {
+        if (S->is_pos[w] && S->is_neg[w]) {
+            status = OR_EINVAL;
+            goto done;
+        }
+        S->n_pos += S->is_pos[w];
+        S->n_neg += S->is_neg[w];
+    }
+
+    /* trivial specifications (Alg. 1): the empty set, then eps */
+    {
+        uint32_t e_empty = (uint32_t)S->n_pos;
+        uint32_t e_eps = (uint32_t)(S->n_pos - S->is_pos[0]) + S->is_neg[0];
+        if (e_empty <= max_errors || e_eps <= max_errors) {
+            int k = e_empty <= max_errors ? TK_EMPTY : TK_EPS;
+            R->root = tnew(&R->T, (char)k, 0, -1, -1);
+            R->st.cost = costs[0];
+            status = OR_OK;
+            goto done;
+        }
+    }
+
+    S->cap = budget_cap(mem_budget, n);
+    S->lvl_start = (int64_t *)calloc((size_t)max_cost + 1, sizeof(int64_t));
+    S->lvl_count = (int64_t *)calloc((size_t)max_cost + 1, sizeof(int64_t));
+    S->tmp = (unsigned char *)malloc((size_t)n);
+    S->s1 = (unsigned char *)malloc((size_t)n);
+    S->s2 = (unsigned char *)malloc((size_t)n);
+    S->partial_level = max_cost + 1;
+    status = OR_NOT_FOUND;
+    for (int c = costs[0]; c <= max_cost; c++) {
+        if (S->otf && max_operand_level(S, c) >= S->partial_level) {
+            status = OR_OOM;
+            break;
+        }
+        S->lvl_start[c] = (int64_t)S->size;
+        uint64_t before = S->size;
+        if (c == costs[0])
+            for (int a = 0; a < n_sym; a++) candidate(S, c, OP_LEAF, a, -1);
+        else
+            build_level(S, c);
+        S->lvl_count[c] = (int64_t)(S->size - before);
+        S->levels = c;
+        if (S->err) {
+            status = S->err;
+            break;
+        }
+        if (S->found) {
+            status = OR_OK;
+            break;
+        }
+        if (!S->otf) {
+            if (S->size > S->cap) {
+                if (!(flags & ORACLE_F_ONTHEFLY)) {
+                    status = OR_OOM;
+                    break;
+                }
+                S->otf = 1;
+                S->partial_level = c;
+            } else {
+                S->unique_done = S->size;
+            }
+        }
+    }
+    if (status == OR_OK) {
+        R->root = entry_tree(S, &R->T, S->ans_op, S->ans_l, S->ans_r);
+        R->st.cost = S->ans_cost;
+    }
+done:
+    R->st.status = status;
+    R->st.candidates = S->candidates;
+    R->st.unique = S->unique_done;
+    R->st.levels = S->levels;
+    R->st.seconds = now_s() - t0;
+    return status;
+}
+
+const oracle_stats *oracle_stats_of(const oracle_run *R) { return &R->st; }
+
+/* postfix tokens of the answer; returns the token count or -1 if none */
+int oracle_answer_tree(const oracle_run *R, unsigned char *out, int cap)
+{
+    if (R->root < 0) return -1;
+    int len = 0;
+    emit_postfix(&R->T, R->root, out, cap, &len);
+    return len;
+}
+
+/* pretty string of the answer; returns the byte length (written if it fits) */
+int oracle_answer_text(const oracle_run *R, char *out, int cap)
+{
+    if (R->root < 0) return -1;
+    sbuf b = {out, (size_t)cap, 0};
+    print_tree(&R->T, R->root, &R->S.A, &b, 0);
+    if (b.len < (size_t)cap) out[b.len] = 0;
+    return (int)b.len;
+}
+
+/* ic of the last run: n, and each word's bytes (concatenated) + offsets */
+int oracle_ic_words(const oracle_run *R, unsigned char *bytes, int bcap, uint32_t *offs, int ocap)
+{
+    const ic_t *ic = &R->S.ic;
+    int pos = 0;
+    for (int w = 0; w < ic->n; w++) {
+        if (w < ocap) offs[w] = (uint32_t)pos;
+        for (int i = 0; i < ic->w[w].len; i++) {
+            if (pos < bcap) bytes[pos] = ic->w[w].s[i];
+            pos++;
+        }
+    }
+    if (ic->n < ocap) offs[ic->n] = (uint32_t)pos;
+    return ic->n;
+}
+
+/* cache introspection: number of cached languages, one entry, one level */
+uint64_t oracle_cache_size(const oracle_run *R) { return R->S.size; }
+
+int oracle_cache_entry(const oracle_run *R, uint64_t k, unsigned char *lang, int *op,
+                       int64_t *l, int64_t *r)
+{
+    const search_t *S = &R->S;
+    if (k >= S->size) return -1;
+    if (lang) memcpy(lang, S->lang + k * S->n, (size_t)S->n);
+    *op = S->bp_op[k];
+    *l = S->bp_l[k];
+    *r = S->bp_r[k];
+    return 0;
+}
+
+int oracle_level(const oracle_run *R, int c, int64_t *start, int64_t *count)
+{
+    const search_t *S = &R->S;
+    if (!S->lvl_start || c < 0 || c > S->max_cost) return -1;
+    *start = S->lvl_start[c];
+    *count = S->lvl_count[c];
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* standalone helpers for pins                                               */
+
+static int setup_alpha(alphabet_t *A, const unsigned char *alphabet, int n_sym)
+{
+    for (int i = 0; i < 256; i++) A->rank[i] = -1;
+    for (int i = 0; i < n_sym; i++) {
+        if (A->rank[alphabet[i]] >= 0) return -1;
+        A->rank[alphabet[i]] = i;
+        A->alpha[i] = alphabet[i];
+    }
+    A->n_sym = n_sym;
+    return 0;
+}
+
+/* derivative matcher: does the postfix tree accept string s? (1/0, -1 on error) */
+int oracle_match(const unsigned char *tok, int ntok, const unsigned char *alphabet, int n_sym,
+                 const unsigned char *s, int len)
+{
+    alphabet_t A;
+    if (setup_alpha(&A, alphabet, n_sym)) return -1;
+    tarena T;
+    memset(&T, 0, sizeof T);
+    int root = tree_from_postfix(&T, tok, ntok);
+    if (root < 0) {
+        free(T.v);
+        return -1;
+    }
+    int *rk = (int *)malloc((size_t)(len + 1) * sizeof(int));
+    int bad = 0;
+    for (int i = 0; i < len; i++) {
+        rk[i] = A.rank[s[i]];
+        if (rk[i] < 0) bad = 1; /* a foreign byte can never be matched */
+    }
+    int m = bad ? 0 : d_match(&T, root, rk, len);
+    free(rk);
+    free(T.v);
+    return m;
+}
+
+int oracle_tree_cost(const unsigned char *tok, int ntok, const int *costs)
+{
+    tarena T;
+    memset(&T, 0, sizeof T);
+    int root = tree_from_postfix(&T, tok, ntok);
+    int c = root < 0 ? -1 : tree_cost(&T, root, costs);
+    free(T.v);
+    return c;
+}
+
+int oracle_tree_text(const unsigned char *tok, int ntok, const unsigned char *alphabet,
+                     int n_sym, char *out, int cap)
+{
+    alphabet_t A;
+    if (setup_alpha(&A, alphabet, n_sym)) return -1;
+    tarena T;
+    memset(&T, 0, sizeof T);
+    int root = tree_from_postfix(&T, tok, ntok);
+    if (root < 0) {
+        free(T.v);
+        return -1;
+    }
+    sbuf b = {out, (size_t)cap, 0};
+    print_tree(&T, root, &A, &b, 0);
+    if (b.len < (size_t)cap) out[b.len] = 0;
+    free(T.v);
+    return (int)b.len;
+}
+
+/* language of a tree on ic(P u N) by the set definitions (the IPS operations,
+ * evaluated bottom-up on the tree); out has one byte per ic word */
+static int eval_set(const alphabet_t *A, const ic_t *ic, const tarena *T, int x,
+                    unsigned char *out)
+{
+    int n = ic->n;
+    const tnode *t = &T->v[x];
+    unsigned char *a = NULL, *b = NULL, *p = NULL, *q = NULL;
+    int rc = 0;
+    switch (t->k) {
+    case TK_SYM: lang_leaf(A, ic, t->a, out); break;
+    case TK_EPS: memset(out, 0, (size_t)n); out[0] = 1; break;
+    case TK_EMPTY: memset(out, 0, (size_t)n); break;
+    case TK_OPT:
+        a = (unsigned char *)malloc((size_t)n);
+        rc = eval_set(A, ic, T, t->l, a);
+        lang_opt(n, a, out);
+        break;
+    case TK_STAR:
+        a = (unsigned char *)malloc((size_t)n);
+        p = (unsigned char *)malloc((size_t)n);
+        q = (unsigned char *)malloc((size_t)n);
+        rc = eval_set(A, ic, T, t->l, a);
+        lang_star(A, ic, a, out, p, q);
+        break;
+    case TK_CAT:
+    case TK_ALT:
+        a = (unsigned char *)malloc((size_t)n);
+        b = (unsigned char *)malloc((size_t)n);
+        rc = eval_set(A, ic, T, t->l, a) | eval_set(A, ic, T, t->r, b);
+        if (t->k == TK_CAT) lang_concat(A, ic, a, b, out);
+        else lang_union(n, a, b, out);
+        break;
+    default: rc = -1;
+    }
+    free(a);
+    free(b);
+    free(p);
+    free(q);
+    return rc;
+}
+
+/* language of a postfix tree over ic(strings), one byte per ic word in
+ * shortlex order; returns n = |ic| (the output is written if n <= cap) */
+int oracle_tree_lang(const unsigned char *tok, int ntok, const unsigned char *alphabet,
+                     int n_sym, const unsigned char *bytes, const uint32_t *offs, int n_str,
+                     unsigned char *out, int cap)
+{
+    alphabet_t A;
+    if (setup_alpha(&A, alphabet, n_sym)) return -1;
+    ic_t ic;
+    if (build_ic(&A, bytes, offs, n_str, &ic)) return -1;
+    tarena T;
+    memset(&T, 0, sizeof T);
+    int root = tree_from_postfix(&T, tok, ntok);
+    int n = ic.n;
+    if (root >= 0 && n <= cap) {
+        if (eval_set(&A, &ic, &T, root, out)) n = -1;
+    }
+    if (root < 0) n = -1;
+    free(T.v);
+    free(ic.w);
+    return n;
+}
+
+/* ic of a set of strings, without a search */
+int oracle_ic(const unsigned char *alphabet, int n_sym, const unsigned char *bytes,
+              const uint32_t *offs, int n_str, unsigned char *wbytes, int bcap, uint32_t *woffs,
+              int ocap)
+{
+    alphabet_t A;
+    if (setup_alpha(&A, alphabet, n_sym)) return -1;
+    ic_t ic;
+    if (build_ic(&A, bytes, offs, n_str, &ic)) return -1;
+    int pos = 0;
+    for (int w = 0; w < ic.n; w++) {
+        if (w < ocap) woffs[w] = (uint32_t)pos;
+        for (int i = 0; i < ic.w[w].len; i++) {
+            if (pos < bcap) wbytes[pos] = ic.w[w].s[i];
+            pos++;
+        }
+    }
+    if (ic.n < ocap) woffs[ic.n] = (uint32_t)pos;
+    int n = ic.n;
+    free(ic.w);
+    return n;
+}
+
+/* ------------------------------------------------------------------------- */
+/* brute force: all syntax trees by exact cost, no deduplication              */
+
+/*
+ * Smallest cost <= max_cost of a tree over the grammar (symbols, ?, *, ., +)
+ * whose language, decided by the derivative matcher on every example, accepts
+ * all of P and none of N; trivial answers (empty set, eps) first as in Alg. 1.
+ * Returns the cost, 0 if none up to max_cost, -1 if the tree count exceeds
+ * node_limit.  Trees are built by cost: every tree of cost c is a symbol
+ * (c == c1), or t?, t* over trees of cost c-c2, c-c3, or t.u, t+u over all
+ * pairs with cost(t) + cost(u) = c - c4 (resp. c - c5), both orders.
+ */
+int oracle_brute_min_cost(const unsigned char *alphabet, int n_sym, const unsigned char *bytes,
+                          const uint32_t *offs, int n_pos, int n_neg, const int *costs,
+                          int max_cost, long node_limit, unsigned char *tok_out, int tok_cap,
+                          int *tok_len)
+{
+    alphabet_t A;
+    if (setup_alpha(&A, alphabet, n_sym)) return -1;
+    int n_str = n_pos + n_neg;
+    /* ranks of every example */
+    int **rk = (int **)malloc((size_t)(n_str + 1) * sizeof(int *));
+    int *lens = (int *)malloc((size_t)(n_str + 1) * sizeof(int));
+    int only_eps = 1, any_pos = 0;
+    for (int k = 0; k < n_str; k++) {
+        lens[k] = (int)(offs[k + 1] - offs[k]);
+        rk[k] = (int *)malloc((size_t)(lens[k] + 1) * sizeof(int));
+        for (int i = 0; i < lens[k]; i++) rk[k][i] = A.rank[bytes[offs[k] + i]];
+        if (k < n_pos) {
+            any_pos = 1;
+            if (lens[k] != 0) only_eps = 0;
+        }
+    }
+    int result = 0;
+    tarena T;
+    memset(&T, 0, sizeof T);
+    int found_root = -1;
+    if (!any_pos) {
+        found_root = tnew(&T, TK_EMPTY, 0, -1, -1);
+        result = costs[0];
+    } else if (only_eps) {
+        found_root = tnew(&T, TK_EPS, 0, -1, -1);
+        result = costs[0];
+    }
+    /* trees of each exact cost: list of root ids */
+    int **by = (int **)calloc((size_t)max_cost + 1, sizeof(int *));
+    long *cnt = (long *)calloc((size_t)max_cost + 1, sizeof(long));
+    for (int c = 1; c <= max_cost && !result; c++) {
+        long cap = 64, m = 0;
+        int *lst = (int *)malloc((size_t)cap * sizeof(int));
+#define PUSH(x)                                                                \
+    do {                                                                       \
+        if (m == cap) {                                                        \
+            cap *= 2;                                                          \
+            lst = (int *)realloc(lst, (size_t)cap * sizeof(int));              \
+        }                                                                      \
+        lst[m++] = (x);                                                        \
+    } while (0)
+        if (c == costs[0])
+            for (int a = 0; a < n_sym; a++) PUSH(tnew(&T, TK_SYM, a, -1, -1));
+        if (c - costs[1] >= 1)
+            for (long i = 0; i < cnt[c - costs[1]]; i++) PUSH(tnew(&T, TK_OPT, 0, by[c - costs[1]][i], -1));
+        if (c - costs[2] >= 1)
+            for (long i = 0; i < cnt[c - costs[2]]; i++) PUSH(tnew(&T, TK_STAR, 0, by[c - costs[2]][i], -1));
+        for (int op = 3; op <= 4; op++) {
+            int rem = c - costs[op];
+            for (int cl = 1; cl < rem; cl++) {
+                int cr = rem - cl;
+                for (long i = 0; i < cnt[cl]; i++)
+                    for (long j = 0; j < cnt[cr]; j++)
+                        PUSH(tnew(&T, op == 3 ? TK_CAT : TK_ALT, 0, by[cl][i], by[cr][j]));
+            }
+        }
+#undef PUSH
+        by[c] = lst;
+        cnt[c] = m;
+        if (T.n > node_limit) {
+            result = -1;
+            break;
+        }
+        for (long i = 0; i < m && !result; i++) {
+            int ok = 1;
+            for (int k = 0; k < n_str && ok; k++) {
+                int acc = d_match(&T, lst[i], rk[k], lens[k]);
+                if ((k < n_pos) != (acc == 1)) ok = 0;
+            }
+            if (ok) {
+                result = c;
+                found_root = lst[i];
+            }
+        }
+    }
+    if (tok_len) {
+        *tok_len = 0;
+        if (found_root >= 0) emit_postfix(&T, found_root, tok_out, tok_cap, tok_len);
+    }
+    for (int c = 0; c <= max_cost; c++) free(by[c]);
+    free(by);
+    free(cnt);
+    free(T.v);
+    for (int k = 0; k < n_str; k++) free(rk[k]);
+    free(rk);
+    free(lens);
+    return result;
+}
+
+/* parser for the paper's regex syntax: + (union), juxtaposition
+ * (concatenation), postfix ? and *, parentheses; "ε" / "∅" (UTF-8) or the
+ * ASCII stand-ins '_' (eps) and '#' (empty set).  Returns the token count
+ * (written if it fits), or -1 on a syntax error. */
+typedef struct {
+    const unsigned char *s;
+    int len, pos;
+    const alphabet_t *A;
+    tarena *T;
+    int err;
+} pstate;
+
+static int p_alt(pstate *P);
+
+static int p_atom(pstate *P)
+{
+    if (P->pos >= P->len) {
+        P->err = 1;
+        return -1;
+    }
+    unsigned char ch = P->s[P->pos];
+    if (ch == '(') {
+        P->pos++;
+        int x = p_alt(P);
+        if (P->pos >= P->len || P->s[P->pos] != ')') {
+            P->err = 1;
+            return -1;
+        }
+        P->pos++;
+        return x;
+    }
+    if (ch == '_') {
+        P->pos++;
+        return tnew(P->T, TK_EPS, 0, -1, -1);
+    }
+    if (ch == '#') {
+        P->pos++;
+        return tnew(P->T, TK_EMPTY, 0, -1, -1);
+    }
+    if (P->pos + 1 < P->len && ch == 0xce && P->s[P->pos + 1] == 0xb5) {
+        P->pos += 2;
+        return tnew(P->T, TK_EPS, 0, -1, -1);
+    }
+    if (P->pos + 2 < P->len && ch == 0xe2 && P->s[P->pos + 1] == 0x88 && P->s[P->pos + 2] == 0x85) {
+        P->pos += 3;
+        return tnew(P->T, TK_EMPTY, 0, -1, -1);
+    }
+    if (P->A->rank[ch] >= 0) {
+        P->pos++;
+        return tnew(P->T, TK_SYM, P->A->rank[ch], -1, -1);
+    }
+    P->err = 1;
+    return -1;
+}
+
+static int p_post(pstate *P)
+{
+    int x = p_atom(P);
+    while (!P->err && P->pos < P->len && (P->s[P->pos] == '?' || P->s[P->pos] == '*')) {
+        x = tnew(P->T, P->s[P->pos] == '?' ? TK_OPT : TK_STAR, 0, x, -1);
+        P->pos++;
+    }
+    return x;
+}
+
+static int p_cat(pstate *P)
+{
+    int x = p_post(P);
+    while (!P->err && P->pos < P->len && P->s[P->pos] != '+' && P->s[P->pos] != ')') {
+        int y = p_post(P);
+        x = tnew(P->T, TK_CAT, 0, x, y);
+    }
+    return x;
+}
+
+static int p_alt(pstate *P)
+{
+    int x = p_cat(P);
+    while (!P->err && P->pos < P->len && P->s[P->pos] == '+') {
+        P->pos++;
+        int y = p_cat(P);
+        x = tnew(P->T, TK_ALT, 0, x, y);
+    }
+    return x;
+}
+
+int oracle_parse(const char *text, const unsigned char *alphabet, int n_sym, unsigned char *tok,
+                 int cap)
+{
+    alphabet_t A;
+    if (setup_alpha(&A, alphabet, n_sym)) return -1;
+    tarena T;
+    memset(&T, 0, sizeof T);
+    pstate P = {(const unsigned char *)text, (int)strlen(text), 0, &A, &T, 0};
+    int root = p_alt(&P);
+    int len = -1;
+    if (!P.err && P.pos == P.len && root >= 0) {
+        len = 0;
+        emit_postfix(&T, root, tok, cap, &len);
+    }
+    free(T.v);
+    return len;
+}
+
+/* the budget rule, exported so tests can check both sides state the same one */
+uint64_t oracle_budget_cap(uint64_t budget, int n) { return budget_cap(budget, n); }
