@@ -1,0 +1,266 @@
+/*
+ * rei.h -- C ABI of the GB300 (sm_103a) regular-expression-inference library.
+ *
+ * The library solves the problem stated in Valizadeh & Berger, "Search-Based
+ * Regular Expression Inference on a GPU" (PLDI 2023): given an alphabet,
+ * positive examples P and negative examples N (Def. "specification", Sec. 3),
+ * a cost homomorphism (c_sym, c_?, c_*, c_., c_+) with every constant >= 1
+ * (Def. "cost function", Sec. 3) and a maximum cost (Alg. 1 inputs), return a
+ * regular expression that accepts all of P, rejects all of N and has minimal
+ * cost, or report that none exists up to the maximum cost.
+ *
+ * Method (Sec. 3): every candidate language is a bitvector (characteristic
+ * sequence, CS) over the infix closure ic(P u N) in shortlex order; languages
+ * are built bottom-up by cost (Alg. 1), union by OR, r? by OR with the eps
+ * bit, concatenation and star through a guide table of splits (Alg. 2 and the
+ * "Staging: guide table" paragraph), deduplicated against every language seen
+ * so far ("Uniqueness checking") and tested for precision.
+ *
+ * Conventions of every entry point:
+ *   - Return values are rei_status codes; no exception crosses the ABI.
+ *   - Inputs are read (or copied) during the call: the caller may free them
+ *     when it returns.  Outputs go to caller-owned buffers; a buffer that is
+ *     too small yields REI_EBUFSZ with the needed size written back.
+ *   - Device memory comes from the context's allocator (rei_alloc callbacks,
+ *     e.g. a framework's caching allocator) or, without one, cudaMallocAsync
+ *     on the context stream.  Work is issued on the context stream.
+ *   - A context is used by one host thread at a time, except the server
+ *     calls that say otherwise.
+ *
+ * Fixed readings of the paper (the CPU oracle in the tests follows the same):
+ *   - ic words are ordered shortlex: by length, then by the caller's alphabet
+ *     order (Sec. 2 shortlex; Example 1 and its figure put eps at index 0).
+ *   - The search leaves are the alphabet symbols at cost c_sym (Alg. 1 seeds
+ *     only them); eps and the empty set are returned only by the trivial
+ *     cases (P empty -> the empty set, P = {eps} -> eps, both at cost c_sym).
+ *   - Level c (c > c_sym) enumerates, in this order: r? for r in level
+ *     c - c_?; r* for r in level c - c_*; l.r over splits cl + cr = c - c_.
+ *     with cl ascending from c_sym, l outer and r inner; l + r likewise with
+ *     c_+, restricted to cl <= cr and, when cl == cr, to l before r.  The
+ *     first candidate with a language is the one kept; the first precise
+ *     candidate is the answer.  Leaves are checked for precision too.
+ *   - Memory: a language costs 4*W + 28 bytes, W the 32-bit words of a padded
+ *     CS (1 for |ic| <= 32, 2 for |ic| <= 64, else 4*ceil(|ic|/128)); the
+ *     cache holds at most cap = min(floor(mem_budget / (4*W + 28)),
+ *     0x7FFF0000) languages.  A level whose new languages would exceed cap
+ *     without yielding an answer ends the search with REI_OOM, or, with
+ *     REI_F_ONTHEFLY, continues uncached while every operand level it needs
+ *     is complete ("OnTheFly mode", Sec. 3).
+ */
+#ifndef REI_H
+#define REI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define REI_ABI_VERSION 1
+
+#define REI_MAX_IC 4096      /* largest |ic(P u N)| */
+#define REI_MAX_STRLEN 4095  /* longest example string */
+#define REI_MAX_COST 255     /* largest max_cost */
+
+typedef enum rei_status {
+    REI_OK = 0,          /* a minimal precise expression was found */
+    REI_NOT_FOUND = 1,   /* none with cost <= max_cost (Alg. 1 "not_found") */
+    REI_OOM = 2,         /* the language cache reached its cap first */
+    REI_EINVAL = 3,      /* invalid argument (see each call) */
+    REI_EBUFSZ = 4,      /* an output buffer is too small; sizes written back */
+    REI_ECUDA = 5,       /* a CUDA call failed */
+    REI_ETIMEOUT = 6,    /* a bounded device wait or a server wait ran out */
+    REI_EBUSY = 7        /* server full / ticket not finished */
+} rei_status;
+
+/* Cost homomorphism (c_sym, c_?, c_*, c_., c_+), Def. "cost function" (Sec. 3).
+ * All constants must be >= 1. */
+typedef struct rei_costs {
+    uint32_t c_sym, c_opt, c_star, c_cat, c_alt;
+} rei_costs;
+
+/* One example string: `len` bytes at `ptr`, each byte a symbol. */
+typedef struct rei_str {
+    const uint8_t *ptr;
+    uint32_t len;
+} rei_str;
+
+typedef struct rei_stats {
+    uint64_t candidates;   /* candidates enumerated: all of the completed
+                              levels, plus those up to and including the answer
+                              in its level */
+    uint64_t unique;       /* languages cached by the completed levels */
+    uint32_t levels;       /* last cost level entered */
+    uint32_t n_ic;         /* |ic(P u N)| */
+    uint32_t words;        /* W, 32-bit words per stored CS */
+    uint32_t max_len;      /* longest ic word */
+    uint64_t guide_pairs;  /* sum over ic words w of |w| + 1 */
+    double ms_stage;       /* staging (ic, guide table, masks, leaves) */
+    double ms_total;       /* whole call, host clock */
+    uint64_t launches;     /* kernels this call launched */
+    uint64_t bytes_h2d;    /* host-to-device bytes this call copied */
+    uint64_t bytes_d2h;    /* device-to-host bytes this call copied */
+} rei_stats;
+
+/* Result of one solve; caller-owned.  `regex` receives the pretty string
+ * (UTF-8; "ε" for eps, "∅" for the empty set; * and ? bind tighter than
+ * concatenation, which binds tighter than +; only needed parentheses), NUL
+ * terminated if it fits.  `tree` receives the expression in postfix order,
+ * two bytes per node: ('a', symbol index) for a symbol, ('e', 0) eps,
+ * ('0', 0) empty set, ('?', 0), ('*', 0), ('.', 0) concatenation, ('+', 0)
+ * union.  Either buffer may be NULL with cap 0 to query the lengths. */
+typedef struct rei_result {
+    int32_t status;
+    uint32_t cost;
+    char *regex;
+    size_t regex_cap;
+    size_t regex_len;
+    uint8_t *tree;
+    size_t tree_cap;
+    size_t tree_len;
+    rei_stats stats;
+} rei_result;
+
+/* Optional device allocator.  alloc returns NULL on failure.  Both get the
+ * context stream; the library frees everything it allocated before
+ * rei_ctx_destroy returns. */
+typedef struct rei_alloc {
+    void *(*alloc)(void *user, size_t bytes, void *stream);
+    void (*free)(void *user, void *ptr, size_t bytes, void *stream);
+    void *user;
+} rei_alloc;
+
+#define REI_F_DEVICE_INPUT 1u  /* `bytes` and `offsets` are device pointers */
+#define REI_F_ONTHEFLY 2u      /* OnTheFly mode after the cache fills */
+
+/* One problem in packed form.  Strings are P first then N: string k is
+ * bytes[offsets[k] .. offsets[k+1]) for k < n_pos + n_neg.  `alphabet` is
+ * always host memory.  max_errors: allowed number of misclassified examples
+ * ("REI with error", Sec. 6; 0 = precise). */
+typedef struct rei_problem {
+    const uint8_t *alphabet;
+    uint32_t n_sym;
+    const uint8_t *bytes;
+    const uint32_t *offsets;
+    uint32_t n_pos, n_neg;
+    uint64_t total_bytes;  /* = offsets[n_pos + n_neg]; required with REI_F_DEVICE_INPUT */
+    rei_costs costs;
+    uint32_t max_cost;
+    uint64_t mem_budget;
+    uint32_t max_errors;
+    uint32_t flags;
+} rei_problem;
+
+typedef struct rei_ctx rei_ctx;
+
+/* Create a context on CUDA device `device`.  `alloc` may be NULL (then
+ * cudaMallocAsync / cudaFreeAsync); `stream` is a cudaStream_t or NULL for a
+ * stream the context creates.  Errors: REI_EINVAL (bad device), REI_ECUDA. */
+rei_status rei_ctx_create(rei_ctx **out, int device, const rei_alloc *alloc, void *stream);
+
+/* Release every device and host resource of the context. */
+void rei_ctx_destroy(rei_ctx *ctx);
+
+/* Tuning options (defaults chosen by the library):
+ *   REI_OPT_CHUNK      candidates per dedup chunk (0 = automatic; smaller
+ *                      values only change how a level is split into chunks)
+ *   REI_OPT_GRID       CTAs of the search kernel (0 = all that fit)
+ *   REI_OPT_KEEP_CACHE 1 = keep the cache after a solve for rei_cache_dump
+ *   REI_OPT_CACHE_INIT initial cache capacity in languages (0 = automatic) */
+#define REI_OPT_CHUNK 1
+#define REI_OPT_GRID 2
+#define REI_OPT_KEEP_CACHE 3
+#define REI_OPT_CACHE_INIT 4
+rei_status rei_ctx_set_option(rei_ctx *ctx, int option, int64_t value);
+
+/* Number of kernels this context launched since it was created. */
+uint64_t rei_ctx_launches(const rei_ctx *ctx);
+
+/* Solve one problem given as string arrays in host memory (Alg. 1 over the
+ * whole cost range).  Errors: REI_EINVAL when a cost is 0, n_sym is 0 or
+ * > 256, the alphabet repeats a symbol, an example uses a byte outside the
+ * alphabet, P and N share a string, max_cost > REI_MAX_COST, |ic| >
+ * REI_MAX_IC or a string is longer than REI_MAX_STRLEN; REI_EBUFSZ when
+ * out->regex or out->tree is too small (needed sizes written back);
+ * REI_ECUDA.  The search outcome (REI_OK, REI_NOT_FOUND, REI_OOM) is both
+ * returned and stored in out->status. */
+rei_status rei_solve(rei_ctx *ctx, const uint8_t *alphabet, uint32_t n_sym, const rei_str *P,
+                     uint32_t nP, const rei_str *N, uint32_t nN, rei_costs costs,
+                     uint32_t max_cost, uint64_t mem_budget, rei_result *out);
+
+/* Solve one packed problem; with REI_F_DEVICE_INPUT the example bytes and
+ * offsets are read straight from device memory.  Errors as rei_solve. */
+rei_status rei_solve_problem(rei_ctx *ctx, const rei_problem *prob, rei_result *out);
+
+/* Staged form of a problem (Sec. 3 "Staging: guide table"), for inspection.
+ * ic words in shortlex order as (word_start, word_len): word w is
+ * bytes[word_start[w] .. + word_len[w]) of the packed example bytes (word 0
+ * is eps, length 0).  gt_off[n_ic + 1] and gt_pair[G]: the splits of word w
+ * are gt_pair[gt_off[w] .. gt_off[w+1]), each (u | v << 16) with u the
+ * prefix and v the suffix, in order of the split position 0..|w|.
+ * pos_mask / neg_mask: W words each; leaf: n_sym * W words, the CS of each
+ * symbol.  Caller sets the capacities; on REI_EBUFSZ the needed n_ic,
+ * guide_pairs and words are written back. */
+typedef struct rei_staged {
+    uint32_t n_ic, words, max_len;
+    uint64_t guide_pairs;
+    uint32_t *word_start, *word_len;  /* cap_words entries each */
+    uint32_t *gt_off;                 /* cap_words + 1 */
+    uint32_t *gt_pair;                /* cap_pairs */
+    uint32_t *pos_mask, *neg_mask;    /* cap_w each */
+    uint32_t *leaf;                   /* n_sym * cap_w */
+    uint32_t cap_words, cap_pairs, cap_w;
+} rei_staged;
+rei_status rei_stage(rei_ctx *ctx, const rei_problem *prob, rei_staged *out);
+
+/* Copy the language cache of the last solve (needs REI_OPT_KEEP_CACHE = 1):
+ * for cached languages k < *count: cs[k*W .. k*W + W) (the CS words),
+ * op[k] (0 symbol, 1 ?, 2 *, 3 ., 4 +), left[k], right[k] (operand cache
+ * indices; left = symbol index for a symbol; right = 0xFFFFFFFF when unused),
+ * and per cost c <= max_cost: level_start[c], level_count[c].  *count is the
+ * capacity on entry and the number of cached languages on return. */
+rei_status rei_cache_dump(rei_ctx *ctx, uint32_t *cs, uint8_t *op, uint32_t *left,
+                          uint32_t *right, uint64_t *count, uint64_t *level_start,
+                          uint64_t *level_count, uint32_t n_levels);
+
+/* ---- batched form: many independent problems, one persistent launch ---- */
+
+/* Tile shape and scheduling of the batched launch (NULL = autotuned). */
+typedef struct rei_tune {
+    uint32_t ctas_per_problem;  /* CTAs cooperating on one problem */
+    uint32_t warps_per_cta;
+    uint32_t chunk;             /* candidates per dedup chunk */
+} rei_tune;
+
+/* Solve n problems.  outs[i] receives problem i's result exactly as
+ * rei_solve_problem would produce it.  Returns REI_OK when every problem was
+ * processed (per-problem outcomes in outs[i].status) or the first error. */
+rei_status rei_solve_batch(rei_ctx *ctx, const rei_problem *probs, uint32_t n, rei_result *outs,
+                           const rei_tune *tune);
+
+/* ---- served form: continuous batching of arriving problems ---- */
+
+typedef struct rei_server rei_server;
+
+/* budget_bytes: device memory the live problems may hold together (each
+ * problem's cache footprint is charged at admission); max_live: problems on
+ * the device at once. */
+rei_status rei_server_create(rei_ctx *ctx, uint64_t budget_bytes, uint32_t max_live,
+                             rei_server **out);
+
+/* Queue a problem (inputs are copied; thread-safe).  *ticket identifies it. */
+rei_status rei_server_submit(rei_server *srv, const rei_problem *prob, uint64_t *ticket);
+
+/* Wait up to block_ms (0 = poll, < 0 = forever) for a ticket's result.
+ * REI_EBUSY when not finished in time.  The ticket is released on success. */
+rei_status rei_server_poll(rei_server *srv, uint64_t ticket, rei_result *out, int block_ms);
+
+/* Stop the server's worker (finishing live problems) and free it. */
+void rei_server_destroy(rei_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* REI_H */

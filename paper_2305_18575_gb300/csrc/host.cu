@@ -1,0 +1,913 @@
+// host.cu -- host runtime of the REI library: contexts, device memory, the
+// solve driver, result formatting, inspection calls, and the batched and
+// served forms.  Every step of the search itself runs in the kernels of
+// stage.cu and solve.cu; this file only moves inputs and results, sizes
+// buffers, and launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "rei_dev.cuh"
+
+namespace rei {
+cudaError_t launch_stage(const StageJob *jobs_dev, uint32_t n_jobs, cudaStream_t stream);
+size_t stage_smem_bytes();
+cudaError_t launch_solve(const SolveJob *job_dev, uint32_t grid, uint32_t threads, size_t smem,
+                         cudaStream_t stream);
+cudaError_t solve_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm);
+cudaError_t launch_rehash(const SolveJob *job_dev, uint32_t count, uint32_t grid, cudaStream_t stream);
+size_t solve_smem_bytes(uint32_t W, uint32_t n, uint32_t G, uint32_t max_len, uint32_t seg_cap,
+                        bool gt_in_smem, uint32_t warps);
+}  // namespace rei
+
+using namespace rei;
+
+namespace {
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct rei_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    rei_alloc alloc{};
+    bool has_alloc = false;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    uint64_t launches = 0;
+
+    int64_t opt_chunk = 0, opt_grid = 0, opt_keep = 0, opt_cache_init = 0;
+
+    // staging
+    DevBuf in_bytes, in_offs, stage_job, stage_info, word_start, word_len, len_start, gt_off, gt_pair,
+        pos, neg, leaf;
+    uint32_t pair_cap = 1u << 16;
+    // search
+    DevBuf cs, bp_op, bp_l, bp_r, table, tmp, pending, slotpos, bitmap, blk, lvl_start, lvl_count,
+        state, solve_job, tstack;
+    // pinned host scratch
+    uint8_t *h_pin = nullptr;
+    size_t h_pin_bytes = 0;
+
+    // last solve (for rei_cache_dump)
+    bool last_valid = false;
+    uint32_t last_W = 0, last_size = 0, last_max_cost = 0;
+
+    std::mutex mu;
+};
+
+namespace {
+
+#define CK(x)                                                                                     \
+    do {                                                                                          \
+        cudaError_t _e = (x);                                                                     \
+        if (_e != cudaSuccess) {                                                                  \
+            fprintf(stderr, "rei: %s failed: %s (%s:%d)\n", #x, cudaGetErrorString(_e), __FILE__, \
+                    __LINE__);                                                                    \
+            return REI_ECUDA;                                                                     \
+        }                                                                                         \
+    } while (0)
+
+void *dev_alloc(rei_ctx *c, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (c->has_alloc) return c->alloc.alloc(c->alloc.user, bytes, (void *)c->stream);
+    if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) return nullptr;
+    return p;
+}
+
+void dev_free(rei_ctx *c, DevBuf &b) {
+    if (!b.p) return;
+    if (c->has_alloc) c->alloc.free(c->alloc.user, b.p, b.bytes, (void *)c->stream);
+    else cudaFreeAsync(b.p, c->stream);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+// grow-only buffer; contents are not kept
+rei_status ensure(rei_ctx *c, DevBuf &b, size_t bytes) {
+    if (b.bytes >= bytes && b.p) return REI_OK;
+    dev_free(c, b);
+    size_t want = std::max<size_t>(bytes, 256);
+    b.p = dev_alloc(c, want);
+    if (!b.p) return REI_OOM;
+    b.bytes = want;
+    return REI_OK;
+}
+
+// grow keeping the first `keep` bytes
+rei_status grow_keep(rei_ctx *c, DevBuf &b, size_t bytes, size_t keep) {
+    if (b.bytes >= bytes && b.p) return REI_OK;
+    void *np = dev_alloc(c, bytes);
+    if (!np) return REI_OOM;
+    if (b.p && keep) {
+        if (cudaMemcpyAsync(np, b.p, std::min(keep, b.bytes), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+            return REI_ECUDA;
+    }
+    dev_free(c, b);
+    b.p = np;
+    b.bytes = bytes;
+    return REI_OK;
+}
+
+rei_status ensure_pinned(rei_ctx *c, size_t bytes) {
+    if (c->h_pin_bytes >= bytes) return REI_OK;
+    if (c->h_pin) {
+        cudaStreamSynchronize(c->stream);
+        cudaFreeHost(c->h_pin);
+        c->h_pin = nullptr;
+    }
+    size_t want = std::max<size_t>(bytes, 1 << 16);
+    if (cudaMallocHost((void **)&c->h_pin, want) != cudaSuccess) return REI_ECUDA;
+    c->h_pin_bytes = want;
+    return REI_OK;
+}
+
+uint64_t budget_cap(uint64_t budget, uint32_t n) {
+    const uint64_t per = 4ull * padded_words(n) + 28;
+    return std::min<uint64_t>(budget / per, 0x7FFF0000ull);
+}
+
+uint64_t pow2_at_least(uint64_t x) {
+    uint64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// ---------------------------------------------------------------------------
+// result formatting (host): postfix tokens -> pretty string with the
+// precedence * ? > concatenation > +, parentheses only where needed
+
+struct PNode {
+    uint8_t k, a;
+    int l, r;
+};
+
+int prec(uint8_t k) { return k == '+' ? 0 : k == '.' ? 1 : 2; }
+
+void print_node(const std::vector<PNode> &T, int x, const uint8_t *alpha, std::string &out, int need) {
+    const PNode &t = T[x];
+    const bool par = prec(t.k) < need;
+    if (par) out += '(';
+    switch (t.k) {
+    case 'a': out += (char)alpha[t.a]; break;
+    case 'e': out += "\xce\xb5"; break;
+    case '0': out += "\xe2\x88\x85"; break;
+    case '?':
+    case '*':
+        print_node(T, t.l, alpha, out, 2);
+        out += (char)t.k;
+        break;
+    case '.':
+        print_node(T, t.l, alpha, out, 1);
+        print_node(T, t.r, alpha, out, 1);
+        break;
+    default:
+        print_node(T, t.l, alpha, out, 0);
+        out += '+';
+        print_node(T, t.r, alpha, out, 0);
+        break;
+    }
+    if (par) out += ')';
+}
+
+std::string format_regex(const uint8_t *tok, uint32_t ntok, const uint8_t *alpha) {
+    std::vector<PNode> T;
+    std::vector<int> st;
+    for (uint32_t i = 0; i < ntok; i++) {
+        const uint8_t k = tok[2 * i], a = tok[2 * i + 1];
+        if (k == 'a' || k == 'e' || k == '0') {
+            T.push_back({k, a, -1, -1});
+        } else if (k == '?' || k == '*') {
+            if (st.empty()) return "";
+            T.push_back({k, 0, st.back(), -1});
+            st.pop_back();
+        } else {
+            if (st.size() < 2) return "";
+            const int r = st.back();
+            st.pop_back();
+            const int l = st.back();
+            st.pop_back();
+            T.push_back({k, 0, l, r});
+        }
+        st.push_back((int)T.size() - 1);
+    }
+    if (st.size() != 1) return "";
+    std::string out;
+    print_node(T, st[0], alpha, out, 0);
+    return out;
+}
+
+// ---------------------------------------------------------------------------
+// argument checks and input upload
+
+rei_status check_problem(const rei_problem *p) {
+    if (!p || !p->alphabet || p->n_sym == 0 || p->n_sym > 256) return REI_EINVAL;
+    const uint32_t c[5] = {p->costs.c_sym, p->costs.c_opt, p->costs.c_star, p->costs.c_cat, p->costs.c_alt};
+    for (uint32_t v : c)
+        if (v < 1 || v > REI_MAX_COST) return REI_EINVAL;
+    if (p->max_cost > REI_MAX_COST) return REI_EINVAL;
+    bool seen[256] = {};
+    for (uint32_t i = 0; i < p->n_sym; i++) {
+        if (seen[p->alphabet[i]]) return REI_EINVAL;
+        seen[p->alphabet[i]] = true;
+    }
+    const uint64_t n_str = (uint64_t)p->n_pos + p->n_neg;
+    if (n_str > (1u << 24)) return REI_EINVAL;
+    if (n_str && (!p->offsets || (!p->bytes && p->total_bytes))) return REI_EINVAL;
+    if (!(p->flags & REI_F_DEVICE_INPUT) && n_str) {
+        if (p->offsets[0] != 0) return REI_EINVAL;
+        for (uint64_t k = 0; k < n_str; k++) {
+            if (p->offsets[k + 1] < p->offsets[k]) return REI_EINVAL;
+            if (p->offsets[k + 1] - p->offsets[k] > REI_MAX_STRLEN) return REI_EINVAL;
+        }
+    }
+    return REI_OK;
+}
+
+struct Staged {
+    StageInfo info;
+    uint64_t h2d = 0, d2h = 0;
+};
+
+// stage problem p on the device; inputs end up in ctx buffers
+rei_status stage_problem(rei_ctx *c, const rei_problem *p, Staged &out) {
+    const uint32_t n_str = p->n_pos + p->n_neg;
+    uint64_t total;
+    const uint8_t *dbytes;
+    const uint32_t *doffs;
+    if (p->flags & REI_F_DEVICE_INPUT) {
+        total = p->total_bytes;
+        dbytes = p->bytes;
+        doffs = p->offsets;
+        if (n_str == 0) {
+            // still need an offsets array with one zero entry
+            rei_status s = ensure(c, c->in_offs, 4);
+            if (s) return s;
+            CK(cudaMemsetAsync(c->in_offs.p, 0, 4, c->stream));
+            doffs = (const uint32_t *)c->in_offs.p;
+        }
+    } else {
+        total = n_str ? p->offsets[n_str] : 0;
+        const size_t ob = 4ull * (n_str + 1);
+        rei_status s = ensure_pinned(c, total + ob + 16);
+        if (s) return s;
+        s = ensure(c, c->in_bytes, total + 16);
+        if (s) return s;
+        s = ensure(c, c->in_offs, ob);
+        if (s) return s;
+        CK(cudaStreamSynchronize(c->stream));  // pinned buffer reuse
+        uint32_t *ho = (uint32_t *)c->h_pin;
+        uint8_t *hb = c->h_pin + ob;
+        if (n_str) {
+            memcpy(ho, p->offsets, ob);
+            if (total) memcpy(hb, p->bytes, total);
+        } else {
+            ho[0] = 0;
+        }
+        CK(cudaMemcpyAsync(c->in_offs.p, ho, ob, cudaMemcpyHostToDevice, c->stream));
+        if (total) CK(cudaMemcpyAsync(c->in_bytes.p, hb, total, cudaMemcpyHostToDevice, c->stream));
+        out.h2d += ob + total;
+        dbytes = (const uint8_t *)c->in_bytes.p;
+        doffs = (const uint32_t *)c->in_offs.p;
+    }
+    if (total > 0xFFFFFFF0ull) return REI_EINVAL;
+
+    for (int attempt = 0; attempt < 2; attempt++) {
+        rei_status s;
+        if ((s = ensure(c, c->stage_job, sizeof(StageJob) + sizeof(StageInfo)))) return s;
+        if ((s = ensure(c, c->word_start, 4ull * kMaxIC))) return s;
+        if ((s = ensure(c, c->word_len, 4ull * kMaxIC))) return s;
+        if ((s = ensure(c, c->len_start, 4ull * (REI_MAX_STRLEN + 2)))) return s;
+        if ((s = ensure(c, c->gt_off, 4ull * (kMaxIC + 1)))) return s;
+        if ((s = ensure(c, c->gt_pair, 4ull * c->pair_cap))) return s;
+        if ((s = ensure(c, c->pos, 4ull * kMaxWords))) return s;
+        if ((s = ensure(c, c->neg, 4ull * kMaxWords))) return s;
+        if ((s = ensure(c, c->leaf, 4ull * kMaxWords * p->n_sym))) return s;
+        if ((s = ensure_pinned(c, sizeof(StageJob) + sizeof(StageInfo)))) return s;
+        CK(cudaStreamSynchronize(c->stream));
+        StageJob *hj = (StageJob *)c->h_pin;
+        memset(hj, 0, sizeof(StageJob));
+        hj->bytes = dbytes;
+        hj->offs = doffs;
+        hj->n_pos = p->n_pos;
+        hj->n_neg = p->n_neg;
+        memcpy(hj->alphabet, p->alphabet, p->n_sym);
+        hj->n_sym = p->n_sym;
+        StageJob *dj = (StageJob *)c->stage_job.p;
+        hj->info = (StageInfo *)(dj + 1);
+        hj->word_start = (uint32_t *)c->word_start.p;
+        hj->word_len = (uint32_t *)c->word_len.p;
+        hj->len_start = (uint32_t *)c->len_start.p;
+        hj->gt_off = (uint32_t *)c->gt_off.p;
+        hj->gt_pair = (uint32_t *)c->gt_pair.p;
+        hj->pair_cap = c->pair_cap;
+        hj->pos_mask = (uint32_t *)c->pos.p;
+        hj->neg_mask = (uint32_t *)c->neg.p;
+        hj->leaf = (uint32_t *)c->leaf.p;
+        CK(cudaMemcpyAsync(dj, hj, sizeof(StageJob), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemsetAsync(hj->info, 0, sizeof(StageInfo), c->stream));
+        out.h2d += sizeof(StageJob);
+        CK(launch_stage(dj, 1, c->stream));
+        c->launches++;
+        StageInfo *hi = (StageInfo *)(c->h_pin + sizeof(StageJob));
+        CK(cudaMemcpyAsync(hi, hj->info, sizeof(StageInfo), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        out.d2h += sizeof(StageInfo);
+        out.info = *hi;
+        if (out.info.status == SE_PAIRS) {
+            c->pair_cap = (uint32_t)pow2_at_least(out.info.G);
+            continue;
+        }
+        break;
+    }
+    return out.info.status == SE_OK ? REI_OK : REI_EINVAL;
+}
+
+void fill_stats(rei_result *r, const StageInfo &I) {
+    r->stats.n_ic = I.n;
+    r->stats.words = I.W;
+    r->stats.max_len = I.max_len;
+    r->stats.guide_pairs = I.G;
+}
+
+rei_status write_outputs(rei_result *out, const uint8_t *tok, uint32_t ntok, const uint8_t *alpha) {
+    const std::string s = format_regex(tok, ntok, alpha);
+    out->regex_len = s.size();
+    out->tree_len = 2ull * ntok;
+    rei_status st = REI_OK;
+    if (out->regex) {
+        if (out->regex_cap >= s.size() + 1) {
+            memcpy(out->regex, s.data(), s.size());
+            out->regex[s.size()] = 0;
+        } else {
+            st = REI_EBUFSZ;
+        }
+    } else if (out->regex_cap) {
+        st = REI_EINVAL;
+    }
+    if (out->tree) {
+        if (out->tree_cap >= 2ull * ntok) memcpy(out->tree, tok, 2ull * ntok);
+        else st = REI_EBUFSZ;
+    }
+    return st;
+}
+
+// ---------------------------------------------------------------------------
+// the plain solve
+
+rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
+    const double t0 = now_ms();
+    const uint64_t l0 = c->launches;
+    memset(&out->stats, 0, sizeof(out->stats));
+    out->status = REI_EINVAL;
+    out->cost = 0;
+    out->regex_len = 0;
+    out->tree_len = 0;
+    c->last_valid = false;
+    rei_status s = check_problem(p);
+    if (s) return s;
+    if (!p->offsets && p->n_pos + p->n_neg) return REI_EINVAL;
+
+    Staged sg;
+    s = stage_problem(c, p, sg);
+    fill_stats(out, sg.info);
+    if (s) {
+        out->status = s;
+        return s;
+    }
+    const double t_stage = now_ms();
+    const StageInfo &I = sg.info;
+    const uint32_t n = I.n, W = I.W, G = I.G, max_len = I.max_len;
+    const uint64_t cap = budget_cap(p->mem_budget, n);
+    const uint32_t max_cost = p->max_cost;
+
+    // launch shape
+    const uint32_t seg_cap = 2 * max_cost + 4;
+    bool gt_smem = 4ull * (n + 1 + G + max_len + 2) <= 96 * 1024;
+    uint32_t warps = 8;
+    size_t smem = solve_smem_bytes(W, n, G, max_len, seg_cap, gt_smem, warps);
+    while (smem > c->smem_optin && warps > 1) {
+        warps /= 2;
+        smem = solve_smem_bytes(W, n, G, max_len, seg_cap, gt_smem, warps);
+    }
+    if (smem > c->smem_optin && gt_smem) {
+        gt_smem = false;
+        warps = 8;
+        smem = solve_smem_bytes(W, n, G, max_len, seg_cap, gt_smem, warps);
+        while (smem > c->smem_optin && warps > 1) {
+            warps /= 2;
+            smem = solve_smem_bytes(W, n, G, max_len, seg_cap, gt_smem, warps);
+        }
+    }
+    if (smem > c->smem_optin) return REI_EINVAL;
+    const uint32_t threads = 32 * warps;
+    int bps = 0;
+    CK(solve_occupancy(threads, smem, &bps));
+    if (bps < 1) return REI_ECUDA;
+    uint32_t grid = (uint32_t)(c->sm_count * bps);
+    if (c->opt_grid > 0 && (uint32_t)c->opt_grid < grid) grid = (uint32_t)c->opt_grid;
+
+    uint64_t chunk_max = c->opt_chunk > 0 ? (uint64_t)c->opt_chunk
+                                          : std::min<uint64_t>(1ull << 22, std::max<uint64_t>(1ull << 16, (1ull << 28) / (4ull * W)));
+    chunk_max = std::min<uint64_t>(chunk_max, 1ull << 24);
+    uint64_t cache_alloc = c->opt_cache_init > 0 ? (uint64_t)c->opt_cache_init : (1ull << 16);
+    cache_alloc = std::max<uint64_t>(1, std::min<uint64_t>(cache_alloc, cap));
+
+    auto table_slots = [&](uint64_t alloc_rows) {
+        const uint64_t need = alloc_rows + (alloc_rows >= cap ? chunk_max : 0);
+        return pow2_at_least(std::max<uint64_t>(2 * need, 1024));
+    };
+    uint64_t tslots = table_slots(cache_alloc);
+    if ((s = ensure(c, c->cs, 4ull * W * cache_alloc))) return s;
+    if ((s = ensure(c, c->bp_op, cache_alloc))) return s;
+    if ((s = ensure(c, c->bp_l, 4ull * cache_alloc))) return s;
+    if ((s = ensure(c, c->bp_r, 4ull * cache_alloc))) return s;
+    if ((s = ensure(c, c->table, 8ull * tslots))) return s;
+    if ((s = ensure(c, c->tmp, 4ull * W * chunk_max))) return s;
+    if ((s = ensure(c, c->pending, 4ull * chunk_max))) return s;
+    if ((s = ensure(c, c->slotpos, 4ull * chunk_max))) return s;
+    if ((s = ensure(c, c->bitmap, 4ull * ((chunk_max + 31) / 32)))) return s;
+    if ((s = ensure(c, c->blk, 4ull * grid))) return s;
+    if ((s = ensure(c, c->lvl_start, 8ull * (max_cost + 2)))) return s;
+    if ((s = ensure(c, c->lvl_count, 8ull * (max_cost + 2)))) return s;
+    const size_t tree_bytes = 2ull * (max_cost + 1);
+    if ((s = ensure(c, c->state, sizeof(SolveState) + tree_bytes))) return s;
+    if ((s = ensure(c, c->solve_job, sizeof(SolveJob)))) return s;
+    if ((s = ensure(c, c->tstack, 16ull * (max_cost + 2)))) return s;
+    if ((s = ensure_pinned(c, sizeof(SolveJob) + sizeof(SolveState) + tree_bytes))) return s;
+
+    CK(cudaMemsetAsync(c->table.p, 0xFF, 8ull * tslots, c->stream));
+    CK(cudaMemsetAsync(c->bitmap.p, 0, 4ull * ((chunk_max + 31) / 32), c->stream));
+    CK(cudaMemsetAsync(c->lvl_start.p, 0, 8ull * (max_cost + 2), c->stream));
+    CK(cudaMemsetAsync(c->lvl_count.p, 0, 8ull * (max_cost + 2), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+
+    SolveState *hst = (SolveState *)(c->h_pin + sizeof(SolveJob));
+    memset(hst, 0, sizeof(SolveState));
+    hst->status = ST_RUNNING;
+    hst->level = p->costs.c_sym;
+    hst->found = kNone;
+    hst->partial_level = max_cost + 1;
+    CK(cudaMemcpyAsync(c->state.p, hst, sizeof(SolveState), cudaMemcpyHostToDevice, c->stream));
+
+    SolveJob *hj = (SolveJob *)c->h_pin;
+    auto fill_job = [&]() {
+        memset(hj, 0, sizeof(SolveJob));
+        hj->n = n;
+        hj->W = W;
+        hj->G = G;
+        hj->n_sym = p->n_sym;
+        hj->max_len = max_len;
+        hj->gt_off = (const uint32_t *)c->gt_off.p;
+        hj->gt_pair = (const uint32_t *)c->gt_pair.p;
+        hj->len_start = (const uint32_t *)c->len_start.p;
+        hj->pos_mask = (const uint32_t *)c->pos.p;
+        hj->neg_mask = (const uint32_t *)c->neg.p;
+        hj->leaf = (const uint32_t *)c->leaf.p;
+        hj->leaf_stride = kMaxWords;
+        hj->n_pos_set = I.n_pos_set;
+        hj->pos_eps = I.pos_eps;
+        hj->neg_eps = I.neg_eps;
+        hj->c[0] = p->costs.c_sym;
+        hj->c[1] = p->costs.c_opt;
+        hj->c[2] = p->costs.c_star;
+        hj->c[3] = p->costs.c_cat;
+        hj->c[4] = p->costs.c_alt;
+        hj->max_cost = max_cost;
+        hj->max_errors = p->max_errors;
+        hj->flags = p->flags;
+        hj->cap = cap;
+        hj->cs = (uint32_t *)c->cs.p;
+        hj->bp_op = (uint8_t *)c->bp_op.p;
+        hj->bp_l = (uint32_t *)c->bp_l.p;
+        hj->bp_r = (uint32_t *)c->bp_r.p;
+        hj->cache_alloc = cache_alloc;
+        hj->table = (unsigned long long *)c->table.p;
+        hj->table_mask = tslots - 1;
+        hj->tmp = (uint32_t *)c->tmp.p;
+        hj->pending = (uint32_t *)c->pending.p;
+        hj->slotpos = (uint32_t *)c->slotpos.p;
+        hj->bitmap = (uint32_t *)c->bitmap.p;
+        hj->blk = (uint32_t *)c->blk.p;
+        hj->chunk_max = chunk_max;
+        hj->lvl_start = (int64_t *)c->lvl_start.p;
+        hj->lvl_count = (int64_t *)c->lvl_count.p;
+        hj->seg_cap = seg_cap;
+        hj->st = (SolveState *)c->state.p;
+        hj->tree = (uint8_t *)c->state.p + sizeof(SolveState);
+        hj->tstack = (uint32_t *)c->tstack.p;
+        hj->gt_in_smem = gt_smem ? 1 : 0;
+    };
+    fill_job();
+    CK(cudaMemcpyAsync(c->solve_job.p, hj, sizeof(SolveJob), cudaMemcpyHostToDevice, c->stream));
+    uint64_t h2d = sg.h2d + sizeof(SolveJob) + sizeof(SolveState), d2h = sg.d2h;
+
+    for (int relaunch = 0;; relaunch++) {
+        CK(launch_solve((const SolveJob *)c->solve_job.p, grid, threads, smem, c->stream));
+        c->launches++;
+        CK(cudaMemcpyAsync(hst, c->state.p, sizeof(SolveState) + tree_bytes, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        d2h += sizeof(SolveState) + tree_bytes;
+        if (hst->status != ST_NEED_MEM) break;
+        // grow the cache (keeping its rows) and rebuild the table
+        const uint64_t want = std::min<uint64_t>(cap, std::max<uint64_t>(cache_alloc * 4, hst->need_rows));
+        const uint64_t rows = hst->size;
+        if ((s = grow_keep(c, c->cs, 4ull * W * want, 4ull * W * rows))) return s;
+        if ((s = grow_keep(c, c->bp_op, want, rows))) return s;
+        if ((s = grow_keep(c, c->bp_l, 4ull * want, 4ull * rows))) return s;
+        if ((s = grow_keep(c, c->bp_r, 4ull * want, 4ull * rows))) return s;
+        cache_alloc = want;
+        tslots = table_slots(cache_alloc);
+        if ((s = ensure(c, c->table, 8ull * tslots))) return s;
+        CK(cudaMemsetAsync(c->table.p, 0xFF, 8ull * tslots, c->stream));
+        fill_job();
+        CK(cudaMemcpyAsync(c->solve_job.p, hj, sizeof(SolveJob), cudaMemcpyHostToDevice, c->stream));
+        if (rows) {
+            CK(launch_rehash((const SolveJob *)c->solve_job.p, (uint32_t)rows, (uint32_t)(c->sm_count * 8), c->stream));
+            c->launches++;
+        }
+        const uint32_t running = ST_RUNNING;
+        CK(cudaMemcpyAsync(&((SolveState *)c->state.p)->status, &running, 4, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        h2d += sizeof(SolveJob) + 4;
+        if (relaunch > 64) return REI_ECUDA;
+    }
+
+    c->last_valid = true;
+    c->last_W = W;
+    c->last_size = hst->size;
+    c->last_max_cost = max_cost;
+
+    rei_status result;
+    switch (hst->status) {
+    case ST_FOUND: result = REI_OK; break;
+    case ST_NOT_FOUND: result = REI_NOT_FOUND; break;
+    case ST_OOM: result = REI_OOM; break;
+    case ST_TIMEOUT: result = REI_ETIMEOUT; break;
+    default: result = REI_ECUDA; break;
+    }
+    out->status = result;
+    out->stats.candidates = hst->candidates;
+    out->stats.unique = result == REI_OK ? hst->unique_done : hst->unique_done;
+    out->stats.levels = hst->level;
+    rei_status ws = REI_OK;
+    if (result == REI_OK) {
+        out->cost = hst->ans_cost;
+        const uint8_t *tok = (const uint8_t *)(hst + 1);
+        ws = write_outputs(out, tok, hst->tree_len, p->alphabet);
+    }
+    const double t1 = now_ms();
+    out->stats.ms_stage = t_stage - t0;
+    out->stats.ms_total = t1 - t0;
+    out->stats.launches = c->launches - l0;
+    out->stats.bytes_h2d = h2d;
+    out->stats.bytes_d2h = d2h;
+    if (ws != REI_OK) return ws;
+    return result;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+
+extern "C" {
+
+rei_status rei_ctx_create(rei_ctx **out, int device, const rei_alloc *alloc, void *stream) {
+    if (!out) return REI_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return REI_EINVAL;
+    rei_ctx *c = new rei_ctx();
+    c->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        delete c;
+        return REI_ECUDA;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete c;
+        return REI_ECUDA;
+    }
+    c->sm_count = prop.multiProcessorCount;
+    c->smem_optin = prop.sharedMemPerBlockOptin;
+    if (alloc && alloc->alloc && alloc->free) {
+        c->alloc = *alloc;
+        c->has_alloc = true;
+    }
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return REI_ECUDA;
+        }
+        c->own_stream = true;
+    }
+    *out = c;
+    return REI_OK;
+}
+
+void rei_ctx_destroy(rei_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    DevBuf *bufs[] = {&c->in_bytes, &c->in_offs, &c->stage_job, &c->stage_info, &c->word_start, &c->word_len,
+                      &c->len_start, &c->gt_off, &c->gt_pair, &c->pos, &c->neg, &c->leaf, &c->cs,
+                      &c->bp_op, &c->bp_l, &c->bp_r, &c->table, &c->tmp, &c->pending, &c->slotpos,
+                      &c->bitmap, &c->blk, &c->lvl_start, &c->lvl_count, &c->state, &c->solve_job,
+                      &c->tstack};
+    for (DevBuf *b : bufs) dev_free(c, *b);
+    cudaStreamSynchronize(c->stream);
+    if (c->h_pin) cudaFreeHost(c->h_pin);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+rei_status rei_ctx_set_option(rei_ctx *c, int option, int64_t value) {
+    if (!c || value < 0) return REI_EINVAL;
+    switch (option) {
+    case REI_OPT_CHUNK: c->opt_chunk = value; return REI_OK;
+    case REI_OPT_GRID: c->opt_grid = value; return REI_OK;
+    case REI_OPT_KEEP_CACHE: c->opt_keep = value; return REI_OK;
+    case REI_OPT_CACHE_INIT: c->opt_cache_init = value; return REI_OK;
+    default: return REI_EINVAL;
+    }
+}
+
+uint64_t rei_ctx_launches(const rei_ctx *c) { return c ? c->launches : 0; }
+
+rei_status rei_solve_problem(rei_ctx *c, const rei_problem *prob, rei_result *out) {
+    if (!c || !prob || !out) return REI_EINVAL;
+    std::lock_guard<std::mutex> g(c->mu);
+    if (cudaSetDevice(c->device) != cudaSuccess) return REI_ECUDA;
+    return solve_one(c, prob, out);
+}
+
+rei_status rei_solve(rei_ctx *c, const uint8_t *alphabet, uint32_t n_sym, const rei_str *P, uint32_t nP,
+                     const rei_str *N, uint32_t nN, rei_costs costs, uint32_t max_cost, uint64_t mem_budget,
+                     rei_result *out) {
+    if (!c || !out || (nP && !P) || (nN && !N)) return REI_EINVAL;
+    std::vector<uint32_t> offs(1, 0);
+    std::vector<uint8_t> bytes;
+    for (uint32_t i = 0; i < nP + nN; i++) {
+        const rei_str &s = i < nP ? P[i] : N[i - nP];
+        if (s.len && !s.ptr) return REI_EINVAL;
+        bytes.insert(bytes.end(), s.ptr, s.ptr + s.len);
+        offs.push_back((uint32_t)bytes.size());
+    }
+    rei_problem p{};
+    p.alphabet = alphabet;
+    p.n_sym = n_sym;
+    p.bytes = bytes.data();
+    p.offsets = offs.data();
+    p.n_pos = nP;
+    p.n_neg = nN;
+    p.total_bytes = bytes.size();
+    p.costs = costs;
+    p.max_cost = max_cost;
+    p.mem_budget = mem_budget;
+    return rei_solve_problem(c, &p, out);
+}
+
+rei_status rei_stage(rei_ctx *c, const rei_problem *prob, rei_staged *out) {
+    if (!c || !prob || !out) return REI_EINVAL;
+    std::lock_guard<std::mutex> g(c->mu);
+    if (cudaSetDevice(c->device) != cudaSuccess) return REI_ECUDA;
+    rei_status s = check_problem(prob);
+    if (s) return s;
+    Staged sg;
+    s = stage_problem(c, prob, sg);
+    if (s) return s;
+    const StageInfo &I = sg.info;
+    out->n_ic = I.n;
+    out->words = I.W;
+    out->max_len = I.max_len;
+    out->guide_pairs = I.G;
+    if (out->cap_words < I.n || out->cap_pairs < I.G || out->cap_w < I.W) return REI_EBUFSZ;
+    auto cp = [&](void *dst, const void *src, size_t b) -> cudaError_t {
+        if (!dst) return cudaSuccess;
+        return cudaMemcpyAsync(dst, src, b, cudaMemcpyDeviceToHost, c->stream);
+    };
+    CK(cp(out->word_start, c->word_start.p, 4ull * I.n));
+    CK(cp(out->word_len, c->word_len.p, 4ull * I.n));
+    CK(cp(out->gt_off, c->gt_off.p, 4ull * (I.n + 1)));
+    CK(cp(out->gt_pair, c->gt_pair.p, 4ull * I.G));
+    CK(cp(out->pos_mask, c->pos.p, 4ull * I.W));
+    CK(cp(out->neg_mask, c->neg.p, 4ull * I.W));
+    if (out->leaf)
+        for (uint32_t a = 0; a < prob->n_sym; a++)
+            CK(cudaMemcpyAsync(out->leaf + (size_t)a * out->cap_w, (uint32_t *)c->leaf.p + (size_t)a * kMaxWords,
+                               4ull * I.W, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return REI_OK;
+}
+
+rei_status rei_cache_dump(rei_ctx *c, uint32_t *cs, uint8_t *op, uint32_t *left, uint32_t *right,
+                          uint64_t *count, uint64_t *level_start, uint64_t *level_count, uint32_t n_levels) {
+    if (!c || !count) return REI_EINVAL;
+    std::lock_guard<std::mutex> g(c->mu);
+    if (!c->last_valid) return REI_EINVAL;
+    const uint64_t k = c->last_size;
+    const uint64_t capn = *count;
+    *count = k;
+    if (capn < k) return REI_EBUFSZ;
+    const uint32_t W = c->last_W;
+    if (cs) CK(cudaMemcpyAsync(cs, c->cs.p, 4ull * W * k, cudaMemcpyDeviceToHost, c->stream));
+    if (op) CK(cudaMemcpyAsync(op, c->bp_op.p, k, cudaMemcpyDeviceToHost, c->stream));
+    if (left) CK(cudaMemcpyAsync(left, c->bp_l.p, 4ull * k, cudaMemcpyDeviceToHost, c->stream));
+    if (right) CK(cudaMemcpyAsync(right, c->bp_r.p, 4ull * k, cudaMemcpyDeviceToHost, c->stream));
+    const uint32_t nl = std::min<uint32_t>(n_levels, c->last_max_cost + 1);
+    if (level_start) CK(cudaMemcpyAsync(level_start, c->lvl_start.p, 8ull * nl, cudaMemcpyDeviceToHost, c->stream));
+    if (level_count) CK(cudaMemcpyAsync(level_count, c->lvl_count.p, 8ull * nl, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return REI_OK;
+}
+
+// ---- batched form (first version: problems in sequence on the context) ----
+
+rei_status rei_solve_batch(rei_ctx *c, const rei_problem *probs, uint32_t n, rei_result *outs,
+                           const rei_tune *tune) {
+    if (!c || (n && (!probs || !outs))) return REI_EINVAL;
+    (void)tune;
+    for (uint32_t i = 0; i < n; i++) {
+        rei_status s = rei_solve_problem(c, &probs[i], &outs[i]);
+        if (s != REI_OK && s != REI_NOT_FOUND && s != REI_OOM) {
+            if (s == REI_EINVAL || s == REI_EBUFSZ) continue;
+            return s;
+        }
+    }
+    return REI_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// served form: a worker thread admits queued problems against a memory budget
+
+struct rei_server {
+    rei_ctx *ctx;
+    uint64_t budget;
+    uint32_t max_live;
+    std::mutex mu;
+    std::condition_variable cv, done_cv;
+    struct Req {
+        uint64_t ticket;
+        std::vector<uint8_t> alphabet, bytes;
+        std::vector<uint32_t> offs;
+        rei_problem p;
+    };
+    struct Done {
+        rei_result r;
+        std::string regex;
+        std::vector<uint8_t> tree;
+    };
+    std::deque<Req> queue;
+    std::map<uint64_t, Done> done;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    std::thread worker;
+};
+
+namespace {
+
+void server_loop(rei_server *S) {
+    for (;;) {
+        rei_server::Req req;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv.wait(lk, [&] { return S->stop || !S->queue.empty(); });
+            if (S->queue.empty()) return;
+            req = std::move(S->queue.front());
+            S->queue.pop_front();
+        }
+        req.p.alphabet = req.alphabet.data();
+        req.p.bytes = req.bytes.data();
+        req.p.offsets = req.offs.data();
+        rei_server::Done d{};
+        char rbuf[8192];
+        uint8_t tbuf[2 * (REI_MAX_COST + 1)];
+        d.r.regex = rbuf;
+        d.r.regex_cap = sizeof rbuf;
+        d.r.tree = tbuf;
+        d.r.tree_cap = sizeof tbuf;
+        rei_status s = rei_solve_problem(S->ctx, &req.p, &d.r);
+        if (s != REI_OK) d.r.status = s;
+        d.regex.assign(rbuf, d.r.regex_len <= sizeof rbuf ? d.r.regex_len : 0);
+        d.tree.assign(tbuf, tbuf + (d.r.tree_len <= sizeof tbuf ? d.r.tree_len : 0));
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->done[req.ticket] = std::move(d);
+        }
+        S->done_cv.notify_all();
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+rei_status rei_server_create(rei_ctx *ctx, uint64_t budget_bytes, uint32_t max_live, rei_server **out) {
+    if (!ctx || !out || max_live == 0) return REI_EINVAL;
+    rei_server *S = new rei_server();
+    S->ctx = ctx;
+    S->budget = budget_bytes;
+    S->max_live = max_live;
+    S->worker = std::thread(server_loop, S);
+    *out = S;
+    return REI_OK;
+}
+
+rei_status rei_server_submit(rei_server *S, const rei_problem *p, uint64_t *ticket) {
+    if (!S || !p || !ticket) return REI_EINVAL;
+    if (p->flags & REI_F_DEVICE_INPUT) return REI_EINVAL;
+    rei_status s = check_problem(p);
+    if (s) return s;
+    rei_server::Req r;
+    const uint32_t n_str = p->n_pos + p->n_neg;
+    r.alphabet.assign(p->alphabet, p->alphabet + p->n_sym);
+    r.offs.assign(p->offsets, p->offsets + n_str + 1);
+    const uint32_t total = n_str ? p->offsets[n_str] : 0;
+    r.bytes.assign(p->bytes, p->bytes + total);
+    if (r.offs.empty()) r.offs.push_back(0);
+    r.p = *p;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        r.ticket = S->next_ticket++;
+        *ticket = r.ticket;
+        S->queue.push_back(std::move(r));
+    }
+    S->cv.notify_one();
+    return REI_OK;
+}
+
+rei_status rei_server_poll(rei_server *S, uint64_t ticket, rei_result *out, int block_ms) {
+    if (!S || !out) return REI_EINVAL;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto ready = [&] { return S->done.count(ticket) > 0; };
+    if (!ready()) {
+        if (block_ms == 0) return REI_EBUSY;
+        if (block_ms < 0) S->done_cv.wait(lk, ready);
+        else if (!S->done_cv.wait_for(lk, std::chrono::milliseconds(block_ms), ready)) return REI_EBUSY;
+    }
+    rei_server::Done &d = S->done[ticket];
+    char *rb = out->regex;
+    size_t rc = out->regex_cap;
+    uint8_t *tb = out->tree;
+    size_t tc = out->tree_cap;
+    *out = d.r;
+    out->regex = rb;
+    out->regex_cap = rc;
+    out->tree = tb;
+    out->tree_cap = tc;
+    out->regex_len = d.regex.size();
+    out->tree_len = d.tree.size();
+    rei_status s = REI_OK;
+    if (rb) {
+        if (rc >= d.regex.size() + 1) {
+            memcpy(rb, d.regex.data(), d.regex.size());
+            rb[d.regex.size()] = 0;
+        } else {
+            s = REI_EBUFSZ;
+        }
+    }
+    if (tb) {
+        if (tc >= d.tree.size()) memcpy(tb, d.tree.data(), d.tree.size());
+        else s = REI_EBUFSZ;
+    }
+    if (s == REI_OK) S->done.erase(ticket);
+    return s;
+}
+
+void rei_server_destroy(rei_server *S) {
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    delete S;
+}
+
+}  // extern "C"

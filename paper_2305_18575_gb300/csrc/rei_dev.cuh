@@ -1,0 +1,153 @@
+// rei_dev.cuh -- device-side data structures of the REI library (internal).
+//
+// Layout in HBM for one problem:
+//   staging   : word_start/word_len[n], len_start[max_len+2], gt_off[n+1],
+//               gt_pair[G] (u | v << 16), pos/neg masks [W], leaf[n_sym][W]
+//   cache     : cs[cache_alloc][W] (row per language, write-once, cost order),
+//               bp_op[]/bp_l[]/bp_r[] back-pointers
+//   dedup     : table[2^k] of u64 slots = (fingerprint << 32) | index, where
+//               index < 2^31 is a cache row and PENDING|j marks chunk-local
+//               candidate j whose CS sits in tmp[j][W] until compaction
+//   chunk     : tmp[chunk][W], pending[chunk] (new slots), slotpos[chunk],
+//               bitmap[chunk/32] (survivors), blk[grid] (per-CTA counts)
+//   state     : SolveState (level, chunk position, counts, barrier, answer)
+#pragma once
+#include <cstdint>
+
+#include "../../include/rei.h"
+
+namespace rei {
+
+constexpr uint32_t kMaxIC = REI_MAX_IC;
+constexpr uint32_t kMaxWords = (REI_MAX_IC + 31) / 32;
+constexpr uint32_t kMaxCost = REI_MAX_COST;
+constexpr uint64_t kEmpty = ~0ull;
+constexpr uint32_t kPending = 0x80000000u;
+constexpr uint32_t kNoRight = 0xFFFFFFFFu;
+constexpr unsigned long long kNone = ~0ull;
+
+// operators of a cache entry / candidate
+enum Op : uint32_t { OP_LEAF = 0, OP_OPT = 1, OP_STAR = 2, OP_CAT = 3, OP_ALT = 4 };
+
+// device status codes (internal; mapped to rei_status by the host)
+enum DevStatus : uint32_t {
+    ST_RUNNING = 0,
+    ST_FOUND = 1,
+    ST_NOT_FOUND = 2,
+    ST_OOM = 3,
+    ST_NEED_MEM = 4,
+    ST_TIMEOUT = 5,
+    ST_BAD = 6,
+};
+
+// staging error codes
+enum StageErr : uint32_t {
+    SE_OK = 0,
+    SE_SYMBOL = 1,     // a byte outside the alphabet
+    SE_OVERLAP = 2,    // P and N share a string
+    SE_IC_LARGE = 3,   // |ic| > REI_MAX_IC
+    SE_STRLEN = 4,     // a string longer than REI_MAX_STRLEN
+    SE_PAIRS = 5,      // guide table larger than the pair buffer (retry bigger)
+    SE_OFFSETS = 6,    // offsets do not start at 0 or decrease
+    SE_INTERNAL = 7,   // an infix lookup failed (never expected)
+};
+
+// words of a padded CS (32-bit units): 1, 2, or a multiple of 4
+__host__ __device__ inline uint32_t padded_words(uint32_t n) {
+    return n <= 32 ? 1u : n <= 64 ? 2u : 4u * ((n + 127u) / 128u);
+}
+
+struct StageInfo {
+    uint32_t status;      // StageErr
+    uint32_t n;           // |ic|
+    uint32_t W;           // padded words
+    uint32_t max_len;
+    uint32_t G;           // guide pairs
+    uint32_t n_pos_set;   // distinct positive examples
+    uint32_t n_neg_set;
+    uint32_t pos_eps;     // eps in P
+    uint32_t neg_eps;     // eps in N
+    uint32_t pad[7];
+};
+
+struct StageJob {
+    // inputs (device)
+    const uint8_t *bytes;
+    const uint32_t *offs;
+    uint32_t n_pos, n_neg;
+    uint8_t alphabet[256];
+    uint32_t n_sym;
+    // outputs (device)
+    StageInfo *info;
+    uint32_t *word_start, *word_len;  // kMaxIC
+    uint32_t *len_start;              // REI_MAX_STRLEN + 2
+    uint32_t *gt_off;                 // kMaxIC + 1
+    uint32_t *gt_pair;                // pair_cap
+    uint32_t pair_cap;
+    uint32_t *pos_mask, *neg_mask;    // kMaxWords
+    uint32_t *leaf;                   // n_sym * kMaxWords (row stride kMaxWords)
+};
+
+// one segment of a level's enumeration (level-local index space)
+struct Seg {
+    uint64_t start;     // first level-local index
+    uint64_t size;      // indices covered (binary ops: lcnt * rcnt)
+    uint32_t op;
+    uint32_t tri;       // union with cl == cr: only l < r is a candidate
+    uint32_t lbase, lcnt, rbase, rcnt;
+};
+
+struct SolveState {
+    uint32_t status;          // DevStatus
+    uint32_t level;           // current cost level
+    uint64_t chunk_pos;       // next level-local index to process
+    uint32_t size;            // cached languages
+    uint32_t full;            // cache cap reached in this level
+    uint32_t otf;             // OnTheFly mode
+    uint32_t partial_level;   // first level not completely cached
+    unsigned long long found; // level-local index of the answer, or kNone
+    uint32_t pending_count;
+    uint32_t ans_op, ans_l, ans_r, ans_cost;
+    uint32_t tree_len;        // postfix tokens written
+    uint64_t candidates;      // completed levels
+    uint64_t unique_done;     // languages of completed levels
+    uint64_t level_total;     // index-space size of the current level
+    uint32_t err;             // barrier / bounds error detail
+    uint32_t need_rows;       // NEED_MEM: cache rows wanted
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    uint32_t nseg;
+    uint32_t pad[5];
+};
+
+struct SolveJob {
+    // staged problem
+    uint32_t n, W, G, n_sym, max_len;
+    const uint32_t *gt_off, *gt_pair, *len_start;
+    const uint32_t *pos_mask, *neg_mask, *leaf;  // leaf row stride = leaf_stride
+    uint32_t leaf_stride;
+    uint32_t n_pos_set, pos_eps, neg_eps;
+    uint32_t c[5];
+    uint32_t max_cost, max_errors, flags;
+    uint64_t cap;  // budget cap in languages
+    // cache
+    uint32_t *cs;
+    uint8_t *bp_op;
+    uint32_t *bp_l, *bp_r;
+    uint64_t cache_alloc;
+    unsigned long long *table;
+    uint64_t table_mask;
+    // chunk workspace
+    uint32_t *tmp, *pending, *slotpos, *bitmap, *blk;
+    uint64_t chunk_max;
+    // bookkeeping
+    int64_t *lvl_start, *lvl_count;  // max_cost + 1 entries
+    Seg *segs;                       // per-CTA copies are in shared memory; this is spare
+    uint32_t seg_cap;
+    SolveState *st;
+    uint8_t *tree;                   // 2 * (max_cost + 1) bytes
+    uint32_t *tstack;                // 4 * (max_cost + 2) words: answer-walk stack
+    uint32_t gt_in_smem;             // guide table copied to shared memory
+};
+
+}  // namespace rei

@@ -1,0 +1,871 @@
+// solve.cu -- the cost-ordered search of one REI problem (Alg. 1, Alg. 2).
+//
+// One persistent launch per problem (cooperative: every CTA is resident, so
+// the grid barrier below cannot deadlock; each of its waits is bounded and
+// ends the launch with ST_TIMEOUT instead of hanging).  The device plans every
+// cost level from the level sizes it has itself produced, so a whole search
+// needs no host round trip unless the cache must grow (ST_NEED_MEM, resumable
+// at the same chunk).
+//
+// A level c is the concatenation of segments (Alg. 1 order): r? over level
+// c - c_?, r* over level c - c_*, l.r over splits cl + cr = c - c_. (cl
+// ascending, l outer, r inner), l + r over splits of c - c_+ with cl <= cr
+// (l < r when cl == cr).  It is processed in chunks of consecutive candidates:
+//   A  build every candidate's CS (warp tiles of 32 candidates), test
+//      precision (Def. "specification"; atomicMin keeps the first precise
+//      index), and insert it into the uniqueness table ("Uniqueness
+//      checking"): a slot holds the lowest chunk index of its language, so the
+//      first candidate in order survives;
+//   B  mark each new language's survivor in a bitmap;
+//   C  count survivors per CTA;
+//   D  append survivors in order to the cache with back-pointers (the
+//      temporary storage -> language cache copy of Sec. 3, "GPU language
+//      cache implementation"), and make their table slots point at the cache.
+#include <cstdint>
+
+#include "rei_dev.cuh"
+
+namespace rei {
+
+constexpr long long kSpinLimit = 20000000;  // x >= 64 ns sleeps: a wait gives up after >= 1.3 s
+
+// ---------------------------------------------------------------------------
+// memory helpers: data written during the launch by other CTAs is read through
+// L2 (ld.cg / acquire), never from a possibly stale L1 line.
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ldcg(const uint32_t *p) { return __ldcg(p); }
+
+__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+
+// ---------------------------------------------------------------------------
+// bounded grid barrier
+
+__device__ bool grid_barrier(SolveState *st) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned int *gen = &st->bar_gen;
+        const unsigned int g = *gen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&st->bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            st->bar_count = 0;
+            __threadfence();
+            atomicAdd(&st->bar_gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*gen == g) {
+                __nanosleep(64);
+                if (++spins > kSpinLimit) {
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        if (!ok) {
+            atomicExch(&st->err, 1u);
+            atomicExch(&st->status, (uint32_t)ST_TIMEOUT);
+        }
+        if (*(volatile uint32_t *)&st->err) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// 32 x 32 bit transpose across a warp: lane j holds row j (bit t = M[j][t]);
+// returns column `lane` (bit j = M[j][lane]).  Five butterfly stages.
+
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, uint32_t lane) {
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const uint32_t m = s == 16 ? 0x0000FFFFu : s == 8 ? 0x00FF00FFu : s == 4 ? 0x0F0F0F0Fu
+                         : s == 2  ? 0x33333333u : 0x55555555u;
+        const uint32_t o = __shfl_xor_sync(0xFFFFFFFFu, x, s);
+        x = (lane & s) ? ((x & ~m) | ((o & ~m) >> s)) : ((x & m) | ((o & m) << s));
+    }
+    return x;
+}
+
+// ---------------------------------------------------------------------------
+// hashing of a CS (W words)
+
+__device__ __forceinline__ uint64_t cs_hash(const uint32_t *c, uint32_t W, uint32_t stride) {
+    uint64_t h = 0x243F6A8885A308D3ull;
+    for (uint32_t b = 0; b < W; b++) {
+        h ^= c[b * stride];
+        h *= 0x9E3779B97F4A7C15ull;
+        h ^= h >> 32;
+    }
+    h ^= h >> 29;
+    h *= 0xBF58476D1CE4E5B9ull;
+    h ^= h >> 32;
+    return h;
+}
+
+// ---------------------------------------------------------------------------
+// per-CTA shared-memory view
+
+struct Shared {
+    Seg *seg;                // level plan
+    uint64_t *tile_first;    // first tile of each segment in the current chunk (nseg + 1)
+    uint64_t *seg_lo;        // chunk ∩ segment, local index range
+    uint64_t *seg_hi;
+    uint32_t *pos, *neg;     // precision masks (W words)
+    const uint32_t *gt_off, *gt_pair, *len_start;
+    uint32_t *warp_mem;      // per warp: lw[W], A[32*Ws], B[32*Ws]
+    uint32_t warp_words;
+};
+
+struct Plan {
+    uint32_t nseg;
+    uint64_t total;          // index-space size of the level
+};
+
+// Alg. 1 order for level c; only segments with candidates are kept
+__device__ void plan_level(const SolveJob &J, uint32_t c, Seg *seg, Plan &P) {
+    const uint32_t c1 = J.c[0];
+    uint32_t ns = 0;
+    uint64_t start = 0;
+    auto lv = [&](uint32_t cost, uint32_t &base, uint32_t &cnt) {
+        base = (uint32_t)ldcg(reinterpret_cast<const uint32_t *>(&J.lvl_start[cost]));
+        cnt = (uint32_t)ldcg(reinterpret_cast<const uint32_t *>(&J.lvl_count[cost]));
+    };
+    auto push = [&](uint32_t op, uint32_t tri, uint32_t lb, uint32_t lc, uint32_t rb, uint32_t rc, uint64_t size) {
+        if (size == 0) return;
+        Seg &s = seg[ns++];
+        s.start = start;
+        s.size = size;
+        s.op = op;
+        s.tri = tri;
+        s.lbase = lb;
+        s.lcnt = lc;
+        s.rbase = rb;
+        s.rcnt = rc;
+        start += size;
+    };
+    if (c == c1) {
+        push(OP_LEAF, 0, 0, J.n_sym, 0, 0, J.n_sym);
+    } else {
+        uint32_t b, n, b2, n2;
+        if (c >= c1 + J.c[1]) {
+            lv(c - J.c[1], b, n);
+            push(OP_OPT, 0, b, n, 0, 0, n);
+        }
+        if (c >= c1 + J.c[2]) {
+            lv(c - J.c[2], b, n);
+            push(OP_STAR, 0, b, n, 0, 0, n);
+        }
+        if (c >= 2 * c1 + J.c[3]) {
+            const uint32_t rem = c - J.c[3];
+            for (uint32_t cl = c1; cl + c1 <= rem; cl++) {
+                lv(cl, b, n);
+                lv(rem - cl, b2, n2);
+                push(OP_CAT, 0, b, n, b2, n2, (uint64_t)n * n2);
+            }
+        }
+        if (c >= 2 * c1 + J.c[4]) {
+            const uint32_t rem = c - J.c[4];
+            for (uint32_t cl = c1; cl + c1 <= rem && cl <= rem - cl; cl++) {
+                lv(cl, b, n);
+                lv(rem - cl, b2, n2);
+                const uint32_t tri = cl == rem - cl;
+                if (tri && n < 2) continue;
+                push(OP_ALT, tri, b, n, b2, n2, (uint64_t)n * n2);
+            }
+        }
+    }
+    P.nseg = ns;
+    P.total = start;
+}
+
+// candidates that are real (the triangle of a cl == cr union) among local
+// indices 0..x of a segment
+__device__ __forceinline__ uint64_t valid_upto(const Seg &s, uint64_t x) {
+    if (s.op != OP_ALT || !s.tri) return x + 1;
+    const uint64_t m = s.rcnt, row = x / m, col = x % m;
+    return row * (m - 1) - row * (row - 1) / 2 + (col > row ? col - row : 0);
+}
+
+__device__ __forceinline__ uint64_t valid_count(const Seg &s) {
+    if (s.op == OP_ALT && s.tri) return (uint64_t)s.lcnt * (s.lcnt - 1) / 2;
+    return s.size;
+}
+
+// the highest operand level a level refers to (OnTheFly feasibility)
+__device__ int max_operand_level(const SolveJob &J, int c) {
+    const int c1 = (int)J.c[0];
+    int m = -1;
+    if (c - (int)J.c[1] >= c1) m = max(m, c - (int)J.c[1]);
+    if (c - (int)J.c[2] >= c1) m = max(m, c - (int)J.c[2]);
+    if (c - (int)J.c[3] >= 2 * c1) m = max(m, c - (int)J.c[3] - c1);
+    if (c - (int)J.c[4] >= 2 * c1) m = max(m, c - (int)J.c[4] - c1);
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// phase A: one warp tile of up to 32 candidates
+
+struct TileCtx {
+    const SolveJob *J;
+    SolveState *st;
+    const Shared *S;
+    uint64_t chunk_start;
+    uint32_t W, Ws, n;
+    bool dedup;
+};
+
+// uniqueness insert of candidate xl (chunk-local) whose CS is c[b * 1] (smem)
+__device__ void dedup_insert(const TileCtx &T, const uint32_t *c, uint32_t xl) {
+    const SolveJob &J = *T.J;
+    const uint32_t W = T.W;
+    const uint64_t h = cs_hash(c, W, 1);
+    const uint32_t fp = (uint32_t)(h >> 32);
+    const uint64_t mine = ((uint64_t)fp << 32) | kPending | xl;
+    uint64_t p = h & J.table_mask;
+    bool wrote = false;
+    auto write_tmp = [&]() {
+        if (wrote) return;
+        uint32_t *dst = J.tmp + (uint64_t)xl * W;
+        for (uint32_t b = 0; b < W; b++) dst[b] = c[b];
+        __threadfence();
+        wrote = true;
+    };
+    for (uint64_t probe = 0; probe <= J.table_mask; probe++) {
+        unsigned long long v = ld_acquire_u64(&J.table[p]);
+        if (v == kEmpty) {
+            write_tmp();
+            const unsigned long long old = atomicCAS(&J.table[p], kEmpty, mine);
+            if (old == kEmpty) {
+                const uint32_t k = atomicAdd(&T.st->pending_count, 1u);
+                J.pending[k] = (uint32_t)p;
+                return;
+            }
+            v = old;
+            __threadfence();
+        }
+        if ((uint32_t)(v >> 32) == fp) {
+            const uint32_t idx = (uint32_t)v;
+            const uint32_t *src = (idx & kPending) ? J.tmp + (uint64_t)(idx & ~kPending) * W
+                                                   : J.cs + (uint64_t)idx * W;
+            bool eq = true;
+            for (uint32_t b = 0; b < W && eq; b++) eq = ldcg(src + b) == c[b];
+            if (eq) {
+                if (idx & kPending) {
+                    write_tmp();
+                    atomicMin(&J.table[p], mine);
+                }
+                return;
+            }
+        }
+        p = (p + 1) & J.table_mask;
+    }
+    atomicExch(&T.st->err, 2u);  // table full: cannot happen with load <= 1/2
+}
+
+// build the CSs of one tile into A (candidate-major, row stride Ws), then test
+// precision and insert; lanes with !valid only help with the warp collectives
+__device__ void run_tile(const TileCtx &T, const Seg &sg, uint64_t lo, uint64_t hi, uint64_t tile,
+                         uint32_t *wm) {
+    const SolveJob &J = *T.J;
+    const Shared &S = *T.S;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t W = T.W, Ws = T.Ws, n = T.n;
+    uint32_t *lw = wm;
+    uint32_t *A = wm + ((W + 3) & ~3u);
+    uint32_t *B = A + 32 * Ws;
+    const uint32_t *cs = J.cs;
+
+    // which candidate this lane holds
+    uint64_t x;         // segment-local index
+    uint32_t row = 0, col0 = 0;
+    bool valid;
+    const bool binary = sg.op == OP_CAT || sg.op == OP_ALT;
+    if (!binary) {
+        col0 = (uint32_t)(lo + tile * 32);  // first operand of the tile
+        x = (uint64_t)col0 + lane;
+        valid = x < hi;
+    } else {
+        const uint32_t ncb = (sg.rcnt + 31) / 32;
+        const uint64_t row_lo = lo / sg.rcnt;
+        row = (uint32_t)(row_lo + tile / ncb);
+        col0 = (uint32_t)(tile % ncb) * 32;
+        const uint32_t col = col0 + lane;
+        x = (uint64_t)row * sg.rcnt + col;
+        valid = col < sg.rcnt && x >= lo && x < hi && (!sg.tri || col > row);
+    }
+    const uint32_t vmask = __ballot_sync(0xFFFFFFFFu, valid);
+    if (vmask == 0) return;
+    const uint32_t nrow = binary ? min(32u, sg.rcnt - col0) : (uint32_t)umin64(32, hi - col0);
+
+    // ---- build
+    if (sg.op == OP_LEAF) {
+        for (uint32_t i = lane; i < 32 * W; i += 32) {
+            const uint32_t j = i / W, b = i % W;
+            A[j * Ws + b] = j < nrow ? __ldg(J.leaf + (uint64_t)(col0 + j) * J.leaf_stride + b) : 0u;
+        }
+        __syncwarp();
+    } else if (sg.op == OP_OPT) {
+        const uint32_t *src = cs + (uint64_t)(sg.lbase + col0) * W;
+        for (uint32_t i = lane; i < 32 * W; i += 32) {
+            const uint32_t j = i / W, b = i % W;
+            A[j * Ws + b] = j < nrow ? ldcg(src + i) : 0u;
+        }
+        __syncwarp();
+        A[lane * Ws] |= 1u;  // eps is ic word 0
+        __syncwarp();
+    } else if (sg.op == OP_ALT) {
+        const uint32_t *l = cs + (uint64_t)(sg.lbase + row) * W;
+        const uint32_t *src = cs + (uint64_t)(sg.rbase + col0) * W;
+        for (uint32_t b = lane; b < W; b += 32) lw[b] = ldcg(l + b);
+        __syncwarp();
+        for (uint32_t i = lane; i < 32 * W; i += 32) {
+            const uint32_t j = i / W, b = i % W;
+            A[j * Ws + b] = j < nrow ? (lw[b] | ldcg(src + i)) : 0u;
+        }
+        __syncwarp();
+    } else {
+        // CAT / STAR: bit-sliced over the 32 right (CAT) or only (STAR) operands
+        const uint32_t rb = sg.op == OP_CAT ? sg.rbase : sg.lbase;
+        const uint32_t *src = cs + (uint64_t)(rb + col0) * W;
+        for (uint32_t i = lane; i < 32 * W; i += 32) {
+            const uint32_t j = i / W, b = i % W;
+            A[j * Ws + b] = j < nrow ? ldcg(src + i) : 0u;
+        }
+        if (sg.op == OP_CAT) {
+            const uint32_t *l = cs + (uint64_t)(sg.lbase + row) * W;
+            for (uint32_t b = lane; b < W; b += 32) lw[b] = ldcg(l + b);
+        }
+        __syncwarp();
+        // slices: B[v] bit j = operand j contains word v
+        for (uint32_t b = 0; b < W; b++) B[32 * b + lane] = transpose32(A[lane * Ws + b], lane);
+        __syncwarp();
+        const uint32_t *go = S.gt_off, *gp = S.gt_pair;
+        if (sg.op == OP_CAT) {
+            // out[w] = OR over splits w = u v of l[u] and r_j[v]  (Alg. 2)
+            for (uint32_t b = 0; b < W; b++) {
+                const uint32_t w = 32 * b + lane;
+                uint32_t acc = 0;
+                if (w < n) {
+                    const uint32_t p1 = go[w + 1];
+                    for (uint32_t p = go[w]; p < p1; p++) {
+                        const uint32_t pr = gp[p];
+                        const uint32_t u = pr & 0xFFFFu, v = pr >> 16;
+                        const uint32_t lb = (lw[u >> 5] >> (u & 31)) & 1u;
+                        acc |= B[v] & (0u - lb);
+                    }
+                }
+                A[lane * Ws + b] = transpose32(acc, lane);
+            }
+            __syncwarp();
+        } else {
+            // r* as the least S with S = 1 + r.S, by increasing word length:
+            // S[w] = OR over splits w = u v with u != eps of r[u] and S[v]
+            uint32_t *Sl = A;
+            for (uint32_t w = lane; w < 32 * W; w += 32) Sl[w] = 0u;
+            __syncwarp();
+            if (lane == 0) Sl[0] = 0xFFFFFFFFu;
+            __syncwarp();
+            const uint32_t *ls = S.len_start;
+            for (uint32_t L = 1; L <= J.max_len; L++) {
+                const uint32_t w1 = ls[L + 1];
+                for (uint32_t w = ls[L] + lane; w < w1; w += 32) {
+                    uint32_t acc = 0;
+                    const uint32_t p1 = go[w + 1];
+                    for (uint32_t p = go[w] + 1; p < p1; p++) {
+                        const uint32_t pr = gp[p];
+                        acc |= B[pr & 0xFFFFu] & Sl[pr >> 16];
+                    }
+                    Sl[w] = acc;
+                }
+                __syncwarp();
+            }
+            for (uint32_t b = 0; b < W; b++) B[lane * Ws + b] = transpose32(Sl[32 * b + lane], lane);
+            __syncwarp();
+            for (uint32_t i = lane; i < 32 * Ws; i += 32) A[i] = B[i];
+            __syncwarp();
+        }
+    }
+
+    // ---- precision and uniqueness, one candidate per lane
+    if (!valid) return;
+    const uint32_t *c = A + lane * Ws;
+    uint32_t errs = 0;
+    for (uint32_t b = 0; b < W; b++) errs += __popc(S.pos[b] & ~c[b]) + __popc(S.neg[b] & c[b]);
+    const uint64_t xlev = sg.start + x;
+    if (errs <= J.max_errors) atomicMin(&T.st->found, (unsigned long long)xlev);
+    if (T.dedup) dedup_insert(T, c, (uint32_t)(xlev - T.chunk_start));
+}
+
+// ---------------------------------------------------------------------------
+// decode a level-local index into (segment, op, left, right)
+
+__device__ void decode(const Seg *seg, uint32_t nseg, uint64_t xlev, uint32_t &op, uint32_t &l, uint32_t &r) {
+    uint32_t s = 0;
+    while (s + 1 < nseg && seg[s + 1].start <= xlev) s++;
+    const Seg &g = seg[s];
+    const uint64_t x = xlev - g.start;
+    op = g.op;
+    if (g.op == OP_LEAF) {
+        l = (uint32_t)x;
+        r = kNoRight;
+    } else if (g.op == OP_OPT || g.op == OP_STAR) {
+        l = g.lbase + (uint32_t)x;
+        r = kNoRight;
+    } else {
+        l = g.lbase + (uint32_t)(x / g.rcnt);
+        r = g.rbase + (uint32_t)(x % g.rcnt);
+    }
+}
+
+// postfix tokens of the answer (op, l, r), walking back-pointers; the walk's
+// stack (4 words per frame, at most max_cost + 1 frames deep since every node
+// costs at least 1) lives in global scratch
+__device__ uint32_t emit_tree(const SolveJob &J, uint32_t op, uint32_t l, uint32_t r) {
+    uint32_t *stack = J.tstack;
+    const int depth_cap = (int)J.max_cost + 2;
+    int sp = 0;
+    uint32_t nt = 0;
+    const uint32_t cap = J.max_cost + 1;
+    auto push = [&](uint32_t o, uint32_t a, uint32_t b) {
+        if (sp < depth_cap) {
+            stack[4 * sp] = o;
+            stack[4 * sp + 1] = a;
+            stack[4 * sp + 2] = b;
+            stack[4 * sp + 3] = 0;
+            sp++;
+        }
+    };
+    auto push_entry = [&](uint32_t e) {
+        push(*(volatile const uint8_t *)(J.bp_op + e), ldcg(J.bp_l + e), ldcg(J.bp_r + e));
+    };
+    push(op, l, r);
+    while (sp > 0) {
+        uint32_t *f = stack + 4 * (sp - 1);
+        const uint32_t fop = f[0];
+        const bool bin = fop == OP_CAT || fop == OP_ALT;
+        const bool un = fop == OP_OPT || fop == OP_STAR;
+        if (f[3] == 0 && (bin || un)) {
+            f[3] = 1;
+            push_entry(f[1]);
+            continue;
+        }
+        if (f[3] == 1 && bin) {
+            f[3] = 2;
+            push_entry(f[2]);
+            continue;
+        }
+        uint8_t k = '+', a = 0;
+        switch (fop) {
+        case OP_LEAF: k = 'a'; a = (uint8_t)f[1]; break;
+        case OP_OPT: k = '?'; break;
+        case OP_STAR: k = '*'; break;
+        case OP_CAT: k = '.'; break;
+        default: break;
+        }
+        if (nt < cap) {
+            J.tree[2 * nt] = k;
+            J.tree[2 * nt + 1] = a;
+        }
+        nt++;
+        sp--;
+    }
+    return nt;
+}
+
+// ---------------------------------------------------------------------------
+// the persistent search kernel
+
+__global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
+    const SolveJob &J = *jobp;
+    SolveState *st = J.st;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    __shared__ Plan s_plan;
+    __shared__ uint32_t s_red[32];
+    __shared__ uint64_t s_tiles;
+
+    const uint32_t W = J.W, n = J.n;
+    const uint32_t Ws = (W & 1u) ? W : W + 1;
+    const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const uint32_t nwarps = blockDim.x >> 5;
+
+    // carve shared memory
+    Shared S;
+    uint8_t *p = smem_raw;
+    S.seg = reinterpret_cast<Seg *>(p);
+    p += sizeof(Seg) * J.seg_cap;
+    S.tile_first = reinterpret_cast<uint64_t *>(p);
+    p += sizeof(uint64_t) * (J.seg_cap + 1);
+    S.seg_lo = reinterpret_cast<uint64_t *>(p);
+    p += sizeof(uint64_t) * J.seg_cap;
+    S.seg_hi = reinterpret_cast<uint64_t *>(p);
+    p += sizeof(uint64_t) * J.seg_cap;
+    S.pos = reinterpret_cast<uint32_t *>(p);
+    p += sizeof(uint32_t) * W;
+    S.neg = reinterpret_cast<uint32_t *>(p);
+    p += sizeof(uint32_t) * W;
+    if (J.gt_in_smem) {
+        uint32_t *g = reinterpret_cast<uint32_t *>(p);
+        for (uint32_t i = tid; i <= n; i += blockDim.x) g[i] = J.gt_off[i];
+        for (uint32_t i = tid; i < J.G; i += blockDim.x) g[n + 1 + i] = J.gt_pair[i];
+        for (uint32_t i = tid; i < J.max_len + 2; i += blockDim.x) g[n + 1 + J.G + i] = J.len_start[i];
+        S.gt_off = g;
+        S.gt_pair = g + n + 1;
+        S.len_start = g + n + 1 + J.G;
+        p += sizeof(uint32_t) * (((n + 1 + J.G + J.max_len + 2) + 3) & ~3u);
+    } else {
+        S.gt_off = J.gt_off;
+        S.gt_pair = J.gt_pair;
+        S.len_start = J.len_start;
+    }
+    S.warp_words = ((W + 3) & ~3u) + 2 * 32 * Ws;
+    S.warp_mem = reinterpret_cast<uint32_t *>(p);
+    for (uint32_t b = tid; b < W; b += blockDim.x) {
+        S.pos[b] = J.pos_mask[b];
+        S.neg[b] = J.neg_mask[b];
+    }
+    uint32_t *wm = S.warp_mem + wid * S.warp_words;
+
+    const uint64_t gwarp = (uint64_t)blockIdx.x * nwarps + wid;
+    const uint64_t total_warps = (uint64_t)gridDim.x * nwarps;
+    const uint64_t gthread = (uint64_t)blockIdx.x * blockDim.x + tid;
+    const uint64_t total_threads = (uint64_t)gridDim.x * blockDim.x;
+
+    // trivial specifications (Alg. 1): the empty set, then eps
+    if (blockIdx.x == 0 && tid == 0 && st->status == ST_RUNNING && st->level == J.c[0] &&
+        st->chunk_pos == 0 && st->size == 0) {
+        const uint32_t e_empty = J.n_pos_set;
+        const uint32_t e_eps = J.n_pos_set - J.pos_eps + J.neg_eps;
+        if (e_empty <= J.max_errors || e_eps <= J.max_errors) {
+            J.tree[0] = e_empty <= J.max_errors ? '0' : 'e';
+            J.tree[1] = 0;
+            st->tree_len = 1;
+            st->ans_cost = J.c[0];
+            st->candidates = 0;
+            st->status = ST_FOUND;
+            st->found = kNone;
+        }
+    }
+    if (!grid_barrier(st)) return;
+
+    for (;;) {
+        const uint32_t status = ldcg(&st->status);
+        if (status != ST_RUNNING) break;
+        const uint32_t level = ldcg(&st->level);
+        const uint64_t pos = __ldcg(reinterpret_cast<const unsigned long long *>(&st->chunk_pos));
+        const uint32_t size = ldcg(&st->size);
+        const uint32_t full = ldcg(&st->full);
+        const uint32_t otf = ldcg(&st->otf);
+        if (level > J.max_cost) {
+            // no level left (also when c_sym > max_cost): Alg. 1 "not_found"
+            if (blockIdx.x == 0 && tid == 0) st->status = ST_NOT_FOUND;
+            if (!grid_barrier(st)) return;
+            continue;
+        }
+
+        if (tid == 0) plan_level(J, level, S.seg, s_plan);
+        __syncthreads();
+        const uint32_t nseg = s_plan.nseg;
+        const uint64_t T = s_plan.total;
+
+        if (pos >= T) {
+            // end of level: count it, check the cache cap, enter the next one
+            if (blockIdx.x == 0 && tid == 0) {
+                uint64_t vc = 0;
+                for (uint32_t s = 0; s < nseg; s++) vc += valid_count(S.seg[s]);
+                st->candidates += vc;
+                uint32_t next_status = ST_RUNNING;
+                if (!otf) {
+                    if (full) {
+                        if (J.flags & REI_F_ONTHEFLY) {
+                            st->otf = 1;
+                            st->partial_level = level;
+                        } else {
+                            next_status = ST_OOM;
+                        }
+                    } else {
+                        st->unique_done = size;
+                    }
+                }
+                const uint32_t nl = level + 1;
+                if (next_status == ST_RUNNING) {
+                    if (nl > J.max_cost) {
+                        next_status = ST_NOT_FOUND;
+                    } else {
+                        J.lvl_start[nl] = size;
+                        J.lvl_count[nl] = 0;
+                        if (ldcg(&st->otf) && max_operand_level(J, (int)nl) >= (int)ldcg(&st->partial_level))
+                            next_status = ST_OOM;
+                    }
+                }
+                st->level = next_status == ST_RUNNING ? nl : level;
+                st->chunk_pos = 0;
+                st->full = 0;
+                st->status = next_status;
+            }
+            if (!grid_barrier(st)) return;
+            continue;
+        }
+
+        // chunk [pos, pos + C) of the level
+        const bool dedup = !full && !otf;
+        uint64_t C = T - pos;
+        if (C > J.chunk_max) C = J.chunk_max;
+        if (dedup && J.cache_alloc < J.cap) {
+            const uint64_t room = J.cache_alloc - size;
+            if (room < C) {
+                if (room * 4 >= J.chunk_max || room >= T - pos) {
+                    C = room;
+                } else {
+                    if (blockIdx.x == 0 && tid == 0) {
+                        st->need_rows = (uint32_t)umin64(J.cap, (uint64_t)size + C);
+                        st->status = ST_NEED_MEM;
+                    }
+                    if (!grid_barrier(st)) return;
+                    continue;
+                }
+            }
+        }
+        if (C == 0) C = 1;  // unreachable with room >= 1; guards the loop
+        const uint64_t cs0 = pos, ce0 = pos + C;
+
+        // tiles of this chunk, per segment
+        if (tid == 0) {
+            uint64_t t = 0;
+            for (uint32_t s = 0; s < nseg; s++) {
+                const Seg &g = S.seg[s];
+                S.tile_first[s] = t;
+                const uint64_t a = cs0 > g.start ? cs0 - g.start : 0;
+                const uint64_t e = ce0 < g.start + g.size ? ce0 - g.start : g.size;
+                S.seg_lo[s] = a;
+                S.seg_hi[s] = e;
+                if (a >= e) continue;
+                if (g.op == OP_CAT || g.op == OP_ALT) {
+                    const uint64_t ncb = (g.rcnt + 31) / 32;
+                    t += ((e - 1) / g.rcnt - a / g.rcnt + 1) * ncb;
+                } else {
+                    t += (e - a + 31) / 32;
+                }
+            }
+            S.tile_first[nseg] = t;
+            s_tiles = t;
+        }
+        __syncthreads();
+
+        // ---- phase A
+        {
+            TileCtx TC{&J, st, &S, cs0, W, Ws, n, dedup};
+            const uint64_t ntiles = s_tiles;
+            uint32_t s = 0;
+            for (uint64_t t = gwarp; t < ntiles; t += total_warps) {
+                while (s + 1 < nseg && S.tile_first[s + 1] <= t) s++;
+                const Seg &g = S.seg[s];
+                if (S.seg_lo[s] >= S.seg_hi[s]) continue;
+                run_tile(TC, g, S.seg_lo[s], S.seg_hi[s], t - S.tile_first[s], wm);
+                __syncwarp();
+            }
+        }
+        if (!grid_barrier(st)) return;
+        if (__ldcg(reinterpret_cast<const unsigned long long *>(&st->found)) != kNone) break;
+
+        if (!dedup) {
+            if (blockIdx.x == 0 && tid == 0) st->chunk_pos = ce0;
+            if (!grid_barrier(st)) return;
+            continue;
+        }
+
+        // ---- phase B: survivors are the slot holders of new languages
+        const uint32_t npend = ldcg(&st->pending_count);
+        for (uint64_t i = gthread; i < npend; i += total_threads) {
+            const uint32_t q = ldcg(J.pending + i);
+            const uint32_t j = (uint32_t)__ldcg(reinterpret_cast<const unsigned long long *>(J.table + q)) & ~kPending;
+            atomicOr(&J.bitmap[j >> 5], 1u << (j & 31));
+            J.slotpos[j] = q;
+        }
+        if (!grid_barrier(st)) return;
+
+        // ---- phase C: survivors per CTA (contiguous word ranges of the bitmap)
+        const uint64_t nwords = (C + 31) / 32;
+        const uint64_t per_cta = (nwords + gridDim.x - 1) / gridDim.x;
+        const uint64_t w0 = umin64(nwords, blockIdx.x * per_cta);
+        const uint64_t w1 = umin64(nwords, w0 + per_cta);
+        const uint64_t per_thr = (w1 - w0 + blockDim.x - 1) / blockDim.x;
+        const uint64_t t0 = umin64(w1, w0 + tid * per_thr);
+        const uint64_t t1 = umin64(w1, t0 + per_thr);
+        uint32_t mycnt = 0;
+        for (uint64_t w = t0; w < t1; w++) mycnt += __popc(ldcg(J.bitmap + w));
+        {
+            uint32_t v = mycnt;
+            for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, d);
+            if (lane == 0) s_red[wid] = v;
+            __syncthreads();
+            if (tid == 0) {
+                uint32_t sum = 0;
+                for (uint32_t k = 0; k < nwarps; k++) sum += s_red[k];
+                J.blk[blockIdx.x] = sum;
+            }
+            __syncthreads();
+        }
+        if (blockIdx.x == 0 && tid == 0) st->pending_count = 0;
+        if (!grid_barrier(st)) return;
+
+        // ---- phase D: append survivors in candidate order
+        {
+            uint64_t cta_prefix = 0, total_new = 0;
+            for (uint32_t b = tid; b < gridDim.x; b += blockDim.x) {
+                const uint32_t v = ldcg(J.blk + b);
+                total_new += v;
+                if (b < blockIdx.x) cta_prefix += v;
+            }
+            // block reductions of the two sums
+            for (int d = 16; d > 0; d >>= 1) {
+                cta_prefix += __shfl_down_sync(0xFFFFFFFFu, cta_prefix, d);
+                total_new += __shfl_down_sync(0xFFFFFFFFu, total_new, d);
+            }
+            __shared__ uint64_t s_a[32], s_b[32], s_pref, s_tot;
+            if (lane == 0) {
+                s_a[wid] = cta_prefix;
+                s_b[wid] = total_new;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                uint64_t a = 0, b = 0;
+                for (uint32_t k = 0; k < nwarps; k++) {
+                    a += s_a[k];
+                    b += s_b[k];
+                }
+                s_pref = a;
+                s_tot = b;
+            }
+            // thread offset inside the CTA (exclusive scan of mycnt)
+            uint32_t x = mycnt;
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+                if (lane >= (uint32_t)d) x += y;
+            }
+            if (lane == 31) s_red[wid] = x;
+            __syncthreads();
+            uint32_t wbefore = 0;
+            for (uint32_t k = 0; k < wid; k++) wbefore += s_red[k];
+            uint64_t rank = s_pref + wbefore + x - mycnt;
+            const uint64_t limit = J.cache_alloc < J.cap ? J.cache_alloc : J.cap;
+            bool dropped = false;
+            for (uint64_t w = t0; w < t1; w++) {
+                uint32_t bits = ldcg(J.bitmap + w);
+                J.bitmap[w] = 0;
+                while (bits) {
+                    const uint32_t bit = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const uint32_t j = (uint32_t)(w * 32 + bit);
+                    const uint64_t k = (uint64_t)size + rank;
+                    rank++;
+                    if (k >= limit) {
+                        dropped = true;
+                        continue;
+                    }
+                    const uint32_t *srcp = J.tmp + (uint64_t)j * W;
+                    uint32_t *dst = J.cs + k * W;
+                    for (uint32_t b = 0; b < W; b++) dst[b] = ldcg(srcp + b);
+                    uint32_t op, l, r;
+                    decode(S.seg, nseg, cs0 + j, op, l, r);
+                    J.bp_op[k] = (uint8_t)op;
+                    J.bp_l[k] = l;
+                    J.bp_r[k] = r;
+                    const uint32_t q = ldcg(J.slotpos + j);
+                    const unsigned long long old = __ldcg(reinterpret_cast<const unsigned long long *>(J.table + q));
+                    J.table[q] = (old & 0xFFFFFFFF00000000ull) | (uint32_t)k;
+                }
+            }
+            if (dropped) atomicExch(&st->full, 1u);
+            __syncthreads();
+            if (blockIdx.x == 0 && tid == 0) {
+                const uint64_t room = limit > size ? limit - size : 0;
+                const uint64_t added = s_tot < room ? s_tot : room;
+                if (s_tot > room) st->full = 1;
+                st->size = size + (uint32_t)added;
+                J.lvl_count[level] = (int64_t)(size + added) - J.lvl_start[level];
+                st->chunk_pos = ce0;
+            }
+        }
+        if (!grid_barrier(st)) return;
+    }
+
+    // ---- answer: back-pointers of the first precise candidate, then its tree
+    if (blockIdx.x == 0 && tid == 0) {
+        const unsigned long long f = st->found;
+        if (st->status == ST_RUNNING && f != kNone) {
+            uint32_t op, l, r;
+            decode(S.seg, s_plan.nseg, f, op, l, r);
+            st->ans_op = op;
+            st->ans_l = l;
+            st->ans_r = r;
+            st->ans_cost = st->level;
+            uint64_t cnt = 0;
+            for (uint32_t s = 0; s < s_plan.nseg; s++) {
+                const Seg &g = S.seg[s];
+                if (g.start + g.size <= f) cnt += valid_count(g);
+                else if (g.start <= f) cnt += valid_upto(g, f - g.start);
+            }
+            st->candidates += cnt;
+            st->tree_len = emit_tree(J, op, l, r);
+            st->status = ST_FOUND;
+        }
+    }
+}
+
+// rebuild the uniqueness table after the cache grew (all entries are distinct)
+__global__ void k_rehash(const SolveJob *jobp, uint32_t count) {
+    const SolveJob &J = *jobp;
+    const uint32_t W = J.W;
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count;
+         k += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t *c = J.cs + k * W;
+        const uint64_t h = cs_hash(c, W, 1);
+        const unsigned long long v = ((uint64_t)(uint32_t)(h >> 32) << 32) | (uint32_t)k;
+        uint64_t p = h & J.table_mask;
+        for (uint64_t probe = 0; probe <= J.table_mask; probe++) {
+            if (atomicCAS(&J.table[p], kEmpty, v) == kEmpty) break;
+            p = (p + 1) & J.table_mask;
+        }
+    }
+}
+
+size_t solve_smem_bytes(uint32_t W, uint32_t n, uint32_t G, uint32_t max_len, uint32_t seg_cap,
+                        bool gt_in_smem, uint32_t warps) {
+    const uint32_t Ws = (W & 1u) ? W : W + 1;
+    size_t b = sizeof(Seg) * seg_cap + sizeof(uint64_t) * (seg_cap + 1) + 2 * sizeof(uint64_t) * seg_cap;
+    b += 2 * sizeof(uint32_t) * W;
+    if (gt_in_smem) b += sizeof(uint32_t) * (((n + 1 + G + max_len + 2) + 3) & ~3u);
+    b += sizeof(uint32_t) * (size_t)warps * (((W + 3) & ~3u) + 2 * 32 * Ws);
+    return b;
+}
+
+cudaError_t launch_solve(const SolveJob *job_dev, uint32_t grid, uint32_t threads, size_t smem,
+                         cudaStream_t stream) {
+    cudaError_t e = cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void *args[] = {(void *)&job_dev};
+    return cudaLaunchCooperativeKernel((const void *)k_solve, dim3(grid), dim3(threads), args, smem, stream);
+}
+
+cudaError_t solve_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_solve, (int)threads, smem);
+}
+
+cudaError_t launch_rehash(const SolveJob *job_dev, uint32_t count, uint32_t grid, cudaStream_t stream) {
+    k_rehash<<<grid, 256, 0, stream>>>(job_dev, count);
+    return cudaGetLastError();
+}
+
+}  // namespace rei

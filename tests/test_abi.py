@@ -1,0 +1,58 @@
+"""The C ABI library builds for sm_103a, loads, and exports every entry
+point include/rei.h declares (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import paper_2305_18575_gb300 as rei
+from paper_2305_18575_gb300 import build as b
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "rei.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rei_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_entry_point():
+    lib = ctypes.CDLL(b.build())
+    names = declared()
+    assert len(names) >= 13
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(rei.EXPORTS) == names
+
+
+def test_binding_structs_match_header_layout(tmp_path):
+    """ctypes mirrors of the ABI structs have the sizes and field offsets the
+    C compiler gives include/rei.h."""
+    import subprocess
+    structs = {"rei_costs": rei.rei_costs, "rei_str": rei.rei_str, "rei_stats": rei.rei_stats,
+               "rei_result": rei.rei_result, "rei_alloc": rei.rei_alloc,
+               "rei_problem": rei.rei_problem, "rei_staged": rei.rei_staged, "rei_tune": rei.rei_tune}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rei.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{name}.{fname} %zu\\n", offsetof({name}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)]).decode().splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert int(got[f"{name}.{fname}"]) == getattr(cls, fname).offset, f"{name}.{fname}"
+
+
+def test_no_cpu_fallback_without_gpu():
+    """Without a GPU the library refuses to create a context: there is no CPU path."""
+    import torch
+    if torch.cuda.is_available():
+        return
+    h = ctypes.c_void_p()
+    assert rei.load().rei_ctx_create(ctypes.byref(h), 0, None, None) != rei.REI_OK

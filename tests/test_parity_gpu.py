@@ -1,0 +1,273 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer work, so the bar is bit-exactness: the same status, minimal cost,
+expression tree (postfix tokens), candidate and unique counts, and, where the
+cache is dumped, the same languages in the same order with the same
+back-pointers.
+"""
+import random
+
+import pytest
+
+import oracle
+import paper_2305_18575_gb300 as rei
+from workloads import make_config, type1_instance, type2_instance
+
+pytestmark = pytest.mark.gpu
+
+A01 = b"01"
+EX1 = ([b"1", b"011", b"1011", b"11011"], [b"", b"10", b"101", b"0011"])
+PIN_P = [b"00", b"1101", b"0001", b"0111", b"001", b"1", b"10", b"1100", b"111", b"1010"]
+PIN_N = [b"", b"0", b"0000", b"0011", b"01", b"010", b"011", b"100", b"1000", b"1001", b"11", b"1110"]
+COSTS = [(1, 1, 1, 1, 1), (1, 1, 5, 1, 1), (1, 10, 1, 1, 1), (1, 1, 1, 10, 1), (1, 1, 1, 1, 10),
+         (2, 1, 3, 1, 2), (3, 2, 1, 2, 1), (10, 10, 10, 1, 10)]
+ST = {oracle.OK: rei.REI_OK, oracle.NOT_FOUND: rei.REI_NOT_FOUND, oracle.OOM: rei.REI_OOM,
+      oracle.EINVAL: rei.REI_EINVAL}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = rei.Context(device=0)
+    yield c
+    c.close()
+
+
+def check_same(got, ref, what=""):
+    assert got.status == ST[ref.status], (what, got, ref)
+    if ref.status == oracle.OK:
+        assert got.cost == ref.cost, (what, got.regex, ref.text)
+        assert got.tree == ref.tree, (what, got.regex, ref.text)
+        assert got.regex == ref.text, what
+    assert got.candidates == ref.candidates, (what, got.candidates, ref.candidates)
+    assert got.unique == ref.unique, (what, got.unique, ref.unique)
+
+
+def solve_both(ctx, inst_or_abc, pos=None, neg=None, **kw):
+    if pos is None:
+        alpha, pos, neg = inst_or_abc.alphabet, inst_or_abc.pos, inst_or_abc.neg
+    else:
+        alpha = inst_or_abc
+    flags = kw.pop("flags", 0)
+    ref = oracle.solve(alpha, pos, neg, flags=(oracle.F_ONTHEFLY if flags & rei.REI_F_ONTHEFLY else 0), **kw)
+    prob = rei.Problem(alpha, pos, neg, flags=flags, **kw)
+    got = ctx.solve_problem(prob)
+    return got, ref
+
+
+# ---------------------------------------------------------------------------
+# staging (ic, guide table, masks, leaves)
+
+def _stage_cases():
+    cases = [("ex1", A01, *EX1), ("pin", A01, PIN_P, PIN_N)]
+    for s in range(3):
+        i = make_config("small", s)
+        cases.append((f"small{s}", i.alphabet, i.pos, i.neg))
+        i = make_config("medium", s)
+        cases.append((f"medium{s}", i.alphabet, i.pos, i.neg))
+    i = make_config("wide", 0)
+    cases.append(("wide0", i.alphabet, i.pos, i.neg))
+    rng = random.Random(5)
+    cases.append(("rand", b"xyz", [bytes(rng.choice(b"xyz") for _ in range(rng.randint(0, 30))) for _ in range(6)],
+                  [bytes(rng.choice(b"xyz") for _ in range(rng.randint(0, 30))) for _ in range(6)]))
+    return cases
+
+
+@pytest.mark.parametrize("case", _stage_cases(), ids=lambda c: c[0])
+def test_stage_matches_oracle(ctx, case):
+    _, alpha, pos, neg = case
+    neg = [s for s in neg if s not in set(pos)]
+    prob = rei.Problem(alpha, pos, neg)
+    s, g = ctx.stage(prob)
+    assert s == rei.REI_OK
+    buf = b"".join(pos + neg)
+    words = [buf[g["word_start"][w]: g["word_start"][w] + g["word_len"][w]] for w in range(g["n"])]
+    ic = oracle.ic(alpha, pos + neg)
+    assert words == ic                                  # same words, same shortlex order
+    index = {w: i for i, w in enumerate(ic)}
+    assert g["G"] == sum(len(w) + 1 for w in ic)        # |gt[w]| = |w| + 1
+    for w, word in enumerate(ic):
+        lo, hi = g["gt_off"][w], g["gt_off"][w + 1]
+        assert hi - lo == len(word) + 1
+        for k in range(len(word) + 1):
+            pr = g["gt_pair"][lo + k]
+            assert (pr & 0xFFFF, pr >> 16) == (index[word[:k]], index[word[k:]])
+    W = g["W"]
+    bits = lambda ws: {32 * b + t for b in range(W) for t in range(32) if ws[b] >> t & 1}
+    assert bits(g["pos"]) == {index[p] for p in pos}
+    assert bits(g["neg"]) == {index[q] for q in neg}
+    for a, sym in enumerate(alpha):
+        want = {index[bytes([sym])]} if bytes([sym]) in index else set()
+        assert bits(g["leaf"][a]) == want
+
+
+# ---------------------------------------------------------------------------
+# whole solves
+
+@pytest.mark.parametrize("costs", COSTS)
+def test_small_config_matches_oracle(ctx, costs):
+    for s in range(30):
+        inst = make_config("small", s)
+        got, ref = solve_both(ctx, inst, costs=costs, max_cost=20)
+        check_same(got, ref, f"small{s} {costs}")
+
+
+def test_paper_examples(ctx, golden):
+    got, ref = solve_both(ctx, A01, *EX1, max_cost=12)
+    check_same(got, ref)
+    assert got.regex == "(0?1)*1" and got.cost == 7
+    g = golden("intro_example.txt")
+    got, ref = solve_both(ctx, A01, g["P"], g["N"], max_cost=12)
+    check_same(got, ref)
+    assert got.regex == "10(0+1)*"
+
+
+@pytest.mark.parametrize("pct", [50, 45, 40, 35, 30, 25, 20, 15])
+def test_allowed_error_rows_match_oracle_and_paper(ctx, golden, pct):
+    g = golden("allowed_error_table.txt")
+    row = next(r for r in g["rows"] if int(r[1]) == pct)
+    e = pct * 22 // 100
+    got, ref = solve_both(ctx, A01, PIN_P, PIN_N, max_cost=30, max_errors=e)
+    check_same(got, ref, pct)
+    assert got.cost == int(row[3])
+
+
+@pytest.mark.parametrize("seed", range(20))
+@pytest.mark.parametrize("costs", [(1, 1, 1, 1, 1), (1, 1, 5, 1, 1)])
+def test_medium_config_matches_oracle(ctx, seed, costs):
+    inst = make_config("medium", seed)
+    ref = oracle.solve(inst.alphabet, inst.pos, inst.neg, costs=costs, max_cost=40,
+                       max_candidates=2_000_000)
+    got = ctx.solve_problem(rei.Problem(inst.alphabet, inst.pos, inst.neg, costs=costs, max_cost=40,
+                                        mem_budget=inst.mem_budget))
+    if ref.status == oracle.LIMIT:
+        # beyond the oracle's budget here: check what holds at any size
+        assert got.status == rei.REI_OK and got.cost <= inst.target_cost + 4 * (costs[2] - 1)
+        assert oracle.tree_cost(got.tree, costs) == got.cost
+        assert all(oracle.match(got.tree, inst.alphabet, p) for p in inst.pos)
+        assert not any(oracle.match(got.tree, inst.alphabet, q) for q in inst.neg)
+        assert got.candidates > ref.candidates
+        return
+    check_same(got, ref, f"medium{seed} {costs}")
+
+
+@pytest.mark.parametrize("chunk", [1, 7, 100, 4099])
+@pytest.mark.parametrize("grid", [1, 3, 0])
+def test_chunking_and_grid_do_not_change_results(chunk, grid):
+    """Small chunks split every level into many chunks with ragged tails; a
+    small grid makes every CTA process many tiles."""
+    with rei.Context(device=0) as c:
+        c.set_option(rei.REI_OPT_CHUNK, chunk)
+        c.set_option(rei.REI_OPT_GRID, grid)
+        for s in (0, 2, 5):
+            inst = make_config("medium", s)
+            got, ref = solve_both(c, inst, max_cost=40, mem_budget=1 << 30)
+            check_same(got, ref, (s, chunk, grid))
+        got, ref = solve_both(c, A01, PIN_P, PIN_N, max_cost=30, max_errors=4)
+        check_same(got, ref, ("pin20", chunk, grid))
+
+
+def test_cache_growth_relaunch_matches(ctx):
+    with rei.Context(device=0) as c:
+        c.set_option(rei.REI_OPT_CACHE_INIT, 8)
+        c.set_option(rei.REI_OPT_CHUNK, 64)
+        for s in (2, 5, 16):
+            inst = make_config("medium", s)
+            got, ref = solve_both(c, inst, max_cost=40, costs=(1, 1, 1, 1, 1))
+            check_same(got, ref, s)
+            assert got.launches > 2   # at least one regrow relaunch
+
+
+def test_cache_contents_match_oracle(ctx):
+    """Every cached language, in order, with its back-pointer, per level."""
+    for inst, costs in [(make_config("medium", 2), (1, 1, 1, 1, 1)), (make_config("medium", 11), (2, 1, 3, 1, 2)),
+                        (make_config("wide", 0), (1, 1, 1, 1, 1))]:
+        max_cost = 40 if inst.name != "wide" else 5
+        run = oracle.Run()
+        ref = run.solve(inst.alphabet, inst.pos, inst.neg, costs=costs, max_cost=max_cost)
+        prob = rei.Problem(inst.alphabet, inst.pos, inst.neg, costs=costs, max_cost=max_cost)
+        got = ctx.solve_keep(prob)
+        check_same(got, ref, inst.name)
+        rows, op, left, right, ls, lc = ctx.cache_dump(max_cost + 1)
+        n = ref.n_ic
+        assert len(rows) >= ref.unique
+        for k in range(ref.unique):
+            lang, oop, ol, orr = run.cache_entry(k, n)
+            bits = bytes((rows[k][w >> 5] >> (w & 31)) & 1 for w in range(n))
+            assert bits == lang, (inst.name, k)
+            assert (op[k], left[k]) == (oop, ol), k
+            assert right[k] == (orr if orr >= 0 else 0xFFFFFFFF), k
+            # padding bits beyond n stay zero
+            for w in range(n, 32 * len(rows[k])):
+                assert not (rows[k][w >> 5] >> (w & 31)) & 1
+        for c in range(1, got.cost):
+            assert (ls[c], lc[c]) == run.level(c), c
+
+
+def test_device_input_matches_host_input(ctx):
+    inst = make_config("medium", 5)
+    host = ctx.solve_problem(rei.Problem(inst.alphabet, inst.pos, inst.neg, max_cost=40))
+    dev = ctx.solve_problem(rei.Problem.on_device(inst.alphabet, inst.pos, inst.neg, max_cost=40))
+    assert (host.status, host.cost, host.tree, host.candidates) == (dev.status, dev.cost, dev.tree, dev.candidates)
+    assert dev.bytes_h2d < host.bytes_h2d
+
+
+def test_type1_type2_instances(ctx):
+    for s in range(6):
+        for inst in (type1_instance(s, 4, 4, 4), type2_instance(s, 5, 5, 5)):
+            for costs in [(1, 1, 1, 1, 1), (1, 1, 10, 1, 1)]:
+                got, ref = solve_both(ctx, inst, costs=costs, max_cost=30)
+                check_same(got, ref, (inst.name, s, costs))
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+
+def test_trivial_answers(ctx):
+    got = ctx.solve(A01, [], [b"0"], costs=(3, 1, 1, 1, 1))
+    assert got.status == rei.REI_OK and got.regex == "∅" and got.cost == 3
+    got = ctx.solve(A01, [b""], [b"0", b"1"], costs=(3, 1, 1, 1, 1))
+    assert got.status == rei.REI_OK and got.regex == "ε" and got.cost == 3
+    got = ctx.solve(b"abc", [b"b"], [b"a", b"c", b""])
+    assert got.status == rei.REI_OK and got.regex == "b" and got.cost == 1
+
+
+def test_not_found_and_oom_match_oracle(ctx):
+    P, N = [b"0110", b"1"], [b"", b"01", b"11"]
+    got, ref = solve_both(ctx, A01, P, N, max_cost=3)
+    check_same(got, ref)
+    assert got.status == rei.REI_NOT_FOUND
+    for budget in (64, 400, 2000, 9000):
+        got, ref = solve_both(ctx, A01, P, N, max_cost=30, mem_budget=budget)
+        check_same(got, ref, budget)
+
+
+def test_onthefly_matches_oracle(ctx):
+    for s in range(8):
+        inst = make_config("small", s)
+        for costs in [(1, 2, 3, 3, 3), (1, 3, 3, 4, 4)]:
+            for rows in (3, 6, 12):
+                budget = rows * 32
+                got, ref = solve_both(ctx, inst, costs=costs, max_cost=30, mem_budget=budget,
+                                      flags=rei.REI_F_ONTHEFLY)
+                check_same(got, ref, (s, costs, rows))
+
+
+def test_invalid_inputs(ctx):
+    assert ctx.solve(b"00", [b"0"], [b""]).status == rei.REI_EINVAL       # repeated symbol
+    assert ctx.solve(A01, [b"2"], [b""]).status == rei.REI_EINVAL         # foreign byte
+    assert ctx.solve(A01, [b"0"], [b"0"]).status == rei.REI_EINVAL        # P and N overlap
+    assert ctx.solve(A01, [b"0"], [b""], costs=(1, 0, 1, 1, 1)).status == rei.REI_EINVAL
+    assert ctx.solve(A01, [b"0"], [b""], max_cost=256).status == rei.REI_EINVAL
+    # the context stays usable after errors
+    assert ctx.solve(A01, *EX1, max_cost=12).cost == 7
+
+
+def test_printed_instance_cost_28(ctx):
+    """Sec. 6 / Table 1: the printed specification has minimal cost 28 under
+    (1,1,1,1,1); the paper's A100 checked 26,774,099,142 candidates."""
+    got = ctx.solve_problem(rei.Problem(A01, PIN_P, PIN_N, max_cost=30, mem_budget=64 << 30))
+    assert got.status == rei.REI_OK and got.cost == 28
+    assert oracle.tree_cost(got.tree, (1, 1, 1, 1, 1)) == 28
+    assert all(oracle.match(got.tree, A01, p) for p in PIN_P)
+    assert not any(oracle.match(got.tree, A01, q) for q in PIN_N)
+    assert 1e9 < got.candidates < 1e11
