@@ -48,6 +48,11 @@ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < 
 
 __device__ bool grid_barrier(SolveState *st) {
     __shared__ int s_ok;
+    // every thread publishes its own global writes and reductions (atomicMin
+    // of the answer, atomicOr of survivors, table and cache stores) before the
+    // CTA arrives: a fence by thread 0 alone does not cover other threads'
+    // reductions still in flight
+    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
