@@ -9,6 +9,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -63,7 +64,7 @@ struct rei_ctx {
     uint32_t pair_cap = 1u << 16;
     // search
     DevBuf cs, bp_op, bp_l, bp_r, table, tmp, pending, slotpos, bitmap, blk, lvl_start, lvl_count,
-        state, solve_job, tstack;
+        state, solve_job, tstack, trace;
     // pinned host scratch
     uint8_t *h_pin = nullptr;
     size_t h_pin_bytes = 0;
@@ -454,6 +455,7 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
     if ((s = ensure(c, c->state, sizeof(SolveState) + tree_bytes))) return s;
     if ((s = ensure(c, c->solve_job, sizeof(SolveJob)))) return s;
     if ((s = ensure(c, c->tstack, 16ull * (max_cost + 2)))) return s;
+    if ((s = ensure(c, c->trace, 4ull * grid))) return s;
     if ((s = ensure_pinned(c, sizeof(SolveJob) + sizeof(SolveState) + tree_bytes))) return s;
 
     CK(cudaMemsetAsync(c->table.p, 0xFF, 8ull * tslots, c->stream));
@@ -516,6 +518,7 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
         hj->st = (SolveState *)c->state.p;
         hj->tree = (uint8_t *)c->state.p + sizeof(SolveState);
         hj->tstack = (uint32_t *)c->tstack.p;
+        hj->trace = (uint32_t *)c->trace.p;
         hj->gt_in_smem = gt_smem ? 1 : 0;
     };
     fill_job();
@@ -548,11 +551,23 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
         }
         const uint32_t running = ST_RUNNING;
         CK(cudaMemcpyAsync(&((SolveState *)c->state.p)->status, &running, 4, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemsetAsync(&((SolveState *)c->state.p)->bar_arrive, 0, 8, c->stream));
         CK(cudaStreamSynchronize(c->stream));
         h2d += sizeof(SolveJob) + 4;
         if (relaunch > 64) return REI_ECUDA;
     }
 
+    if (hst->status == ST_TIMEOUT && getenv("REI_DEBUG")) {
+        std::vector<uint32_t> tr(grid);
+        cudaMemcpy(tr.data(), c->trace.p, 4ull * grid, cudaMemcpyDeviceToHost);
+        std::map<uint32_t, uint32_t> hist;
+        for (uint32_t v : tr) hist[v]++;
+        fprintf(stderr, "rei: barrier wait ran out: cta %u epoch %u site %u seen %u (grid %u); "
+                "level %u pos %llu size %u found %llx\n", hst->dbg_cta, hst->dbg_epoch, hst->dbg_site,
+                hst->dbg_seen, grid, hst->level, (unsigned long long)hst->chunk_pos, hst->size,
+                (unsigned long long)hst->found);
+        for (auto &kv : hist) fprintf(stderr, "rei:   %u CTAs last passed epoch %u site %u\n", kv.second, kv.first >> 8, kv.first & 255);
+    }
     c->last_valid = true;
     c->last_W = W;
     c->last_size = hst->size;
@@ -636,7 +651,7 @@ void rei_ctx_destroy(rei_ctx *c) {
                       &c->len_start, &c->gt_off, &c->gt_pair, &c->pos, &c->neg, &c->leaf, &c->cs,
                       &c->bp_op, &c->bp_l, &c->bp_r, &c->table, &c->tmp, &c->pending, &c->slotpos,
                       &c->bitmap, &c->blk, &c->lvl_start, &c->lvl_count, &c->state, &c->solve_job,
-                      &c->tstack};
+                      &c->tstack, &c->trace};
     for (DevBuf *b : bufs) dev_free(c, *b);
     cudaStreamSynchronize(c->stream);
     if (c->h_pin) cudaFreeHost(c->h_pin);

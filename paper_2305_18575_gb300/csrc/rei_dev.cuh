@@ -114,10 +114,10 @@ struct SolveState {
     uint64_t level_total;     // index-space size of the current level
     uint32_t err;             // barrier / bounds error detail
     uint32_t need_rows;       // NEED_MEM: cache rows wanted
-    unsigned int bar_count;
-    unsigned int bar_gen;
+    unsigned long long bar_arrive;  // grid-barrier arrivals of this launch
+    uint32_t dbg_cta, dbg_epoch, dbg_site, dbg_seen;  // where a barrier wait ran out
     uint32_t nseg;
-    uint32_t pad[5];
+    uint32_t pad[3];
 };
 
 struct SolveJob {
@@ -147,6 +147,7 @@ struct SolveJob {
     SolveState *st;
     uint8_t *tree;                   // 2 * (max_cost + 1) bytes
     uint32_t *tstack;                // 4 * (max_cost + 2) words: answer-walk stack
+    uint32_t *trace;                 // per CTA: (barriers passed << 8) | last barrier site
     uint32_t gt_in_smem;             // guide table copied to shared memory
 };
 

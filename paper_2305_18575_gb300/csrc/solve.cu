@@ -27,7 +27,7 @@
 
 namespace rei {
 
-constexpr long long kSpinLimit = 20000000;  // x >= 64 ns sleeps: a wait gives up after >= 1.3 s
+constexpr long long kSpinLimit = 10000000;  // x >= 100 ns sleeps: a wait gives up after >= 1 s
 
 // ---------------------------------------------------------------------------
 // memory helpers: data written during the launch by other CTAs is read through
@@ -41,48 +41,64 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 
 __device__ __forceinline__ uint32_t ldcg(const uint32_t *p) { return __ldcg(p); }
 
+// strong (coherent) loads of control words written by other CTAs
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const void *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 
 // ---------------------------------------------------------------------------
-// bounded grid barrier
+// bounded grid barrier: a monotonic 64-bit arrival counter (never reset during
+// a launch); barrier number e of a launch completes when the counter reaches
+// e * gridDim.x.  A wait that runs out records where it gave up, marks the
+// launch ST_TIMEOUT and returns false so every CTA leaves the kernel.
 
-__device__ bool grid_barrier(SolveState *st) {
+__device__ bool grid_barrier(SolveState *st, uint32_t &epoch, uint32_t site, uint32_t *trace) {
     __shared__ int s_ok;
     // every thread publishes its own global writes and reductions (atomicMin
     // of the answer, atomicOr of survivors, table and cache stores) before the
-    // CTA arrives: a fence by thread 0 alone does not cover other threads'
-    // reductions still in flight
+    // CTA arrives
     __threadfence();
     __syncthreads();
+    epoch++;
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned int *gen = &st->bar_gen;
-        const unsigned int g = *gen;
-        __threadfence();
-        const unsigned int arrived = atomicAdd(&st->bar_count, 1u);
-        if (arrived == gridDim.x - 1) {
-            st->bar_count = 0;
-            __threadfence();
-            atomicAdd(&st->bar_gen, 1u);
-        } else {
-            long long spins = 0;
-            while (*gen == g) {
-                __nanosleep(64);
-                if (++spins > kSpinLimit) {
-                    ok = 0;
-                    break;
-                }
+        const unsigned long long target = (unsigned long long)epoch * gridDim.x;
+        atomicAdd(&st->bar_arrive, 1ull);
+        unsigned long long seen;
+        long long spins = 0;
+        while ((seen = ld_acquire_u64(&st->bar_arrive)) < target) {
+            __nanosleep(100);
+            if (++spins > kSpinLimit) {
+                ok = 0;
+                break;
             }
         }
         __threadfence();
+        if (trace) trace[blockIdx.x] = (epoch << 8) | site;
         if (!ok) {
-            atomicExch(&st->err, 1u);
+            if (atomicCAS(&st->err, 0u, 1u) == 0u) {
+                st->dbg_cta = blockIdx.x;
+                st->dbg_epoch = epoch;
+                st->dbg_site = site;
+                st->dbg_seen = (uint32_t)seen;
+            }
             atomicExch(&st->status, (uint32_t)ST_TIMEOUT);
         }
-        if (*(volatile uint32_t *)&st->err) ok = 0;
+        if (ld_relaxed_u32(&st->err)) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
+    __threadfence();
     return s_ok != 0;
 }
 
@@ -142,8 +158,8 @@ __device__ void plan_level(const SolveJob &J, uint32_t c, Seg *seg, Plan &P) {
     uint32_t ns = 0;
     uint64_t start = 0;
     auto lv = [&](uint32_t cost, uint32_t &base, uint32_t &cnt) {
-        base = (uint32_t)ldcg(reinterpret_cast<const uint32_t *>(&J.lvl_start[cost]));
-        cnt = (uint32_t)ldcg(reinterpret_cast<const uint32_t *>(&J.lvl_count[cost]));
+        base = (uint32_t)ld_relaxed_u64(&J.lvl_start[cost]);
+        cnt = (uint32_t)ld_relaxed_u64(&J.lvl_count[cost]);
     };
     auto push = [&](uint32_t op, uint32_t tri, uint32_t lb, uint32_t lc, uint32_t rb, uint32_t rc, uint64_t size) {
         if (size == 0) return;
@@ -497,6 +513,9 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
     __shared__ Plan s_plan;
     __shared__ uint32_t s_red[32];
     __shared__ uint64_t s_tiles;
+    __shared__ uint32_t s_ctl[8];
+    __shared__ uint64_t s_pos;
+    __shared__ unsigned long long s_found;
 
     const uint32_t W = J.W, n = J.n;
     const uint32_t Ws = (W & 1u) ? W : W + 1;
@@ -542,6 +561,7 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
 
     const uint64_t gwarp = (uint64_t)blockIdx.x * nwarps + wid;
     const uint64_t total_warps = (uint64_t)gridDim.x * nwarps;
+    uint32_t bar_epoch = 0;
     const uint64_t gthread = (uint64_t)blockIdx.x * blockDim.x + tid;
     const uint64_t total_threads = (uint64_t)gridDim.x * blockDim.x;
 
@@ -560,20 +580,32 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
             st->found = kNone;
         }
     }
-    if (!grid_barrier(st)) return;
+    if (!grid_barrier(st, bar_epoch, 1, J.trace)) return;
 
     for (;;) {
-        const uint32_t status = ldcg(&st->status);
+        // one coherent read of the control words per CTA, shared by its threads,
+        // so that every thread of every CTA takes the same branches
+        if (tid == 0) {
+            s_ctl[0] = ld_relaxed_u32(&st->status);
+            s_ctl[1] = ld_relaxed_u32(&st->level);
+            s_ctl[2] = ld_relaxed_u32(&st->size);
+            s_ctl[3] = ld_relaxed_u32(&st->full);
+            s_ctl[4] = ld_relaxed_u32(&st->otf);
+            s_pos = ld_relaxed_u64(&st->chunk_pos);
+        }
+        __syncthreads();
+        const uint32_t status = s_ctl[0];
+        const uint32_t level = s_ctl[1];
+        const uint64_t pos = s_pos;
+        const uint32_t size = s_ctl[2];
+        const uint32_t full = s_ctl[3];
+        const uint32_t otf = s_ctl[4];
+        __syncthreads();
         if (status != ST_RUNNING) break;
-        const uint32_t level = ldcg(&st->level);
-        const uint64_t pos = __ldcg(reinterpret_cast<const unsigned long long *>(&st->chunk_pos));
-        const uint32_t size = ldcg(&st->size);
-        const uint32_t full = ldcg(&st->full);
-        const uint32_t otf = ldcg(&st->otf);
         if (level > J.max_cost) {
             // no level left (also when c_sym > max_cost): Alg. 1 "not_found"
             if (blockIdx.x == 0 && tid == 0) st->status = ST_NOT_FOUND;
-            if (!grid_barrier(st)) return;
+            if (!grid_barrier(st, bar_epoch, 2, J.trace)) return;
             continue;
         }
 
@@ -608,7 +640,8 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
                     } else {
                         J.lvl_start[nl] = size;
                         J.lvl_count[nl] = 0;
-                        if (ldcg(&st->otf) && max_operand_level(J, (int)nl) >= (int)ldcg(&st->partial_level))
+                        if (ld_relaxed_u32(&st->otf) &&
+                            max_operand_level(J, (int)nl) >= (int)ld_relaxed_u32(&st->partial_level))
                             next_status = ST_OOM;
                     }
                 }
@@ -617,7 +650,7 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
                 st->full = 0;
                 st->status = next_status;
             }
-            if (!grid_barrier(st)) return;
+            if (!grid_barrier(st, bar_epoch, 3, J.trace)) return;
             continue;
         }
 
@@ -635,7 +668,7 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
                         st->need_rows = (uint32_t)umin64(J.cap, (uint64_t)size + C);
                         st->status = ST_NEED_MEM;
                     }
-                    if (!grid_barrier(st)) return;
+                    if (!grid_barrier(st, bar_epoch, 4, J.trace)) return;
                     continue;
                 }
             }
@@ -679,24 +712,28 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
                 __syncwarp();
             }
         }
-        if (!grid_barrier(st)) return;
-        if (__ldcg(reinterpret_cast<const unsigned long long *>(&st->found)) != kNone) break;
+        if (!grid_barrier(st, bar_epoch, 5, J.trace)) return;
+        if (tid == 0) s_found = ld_relaxed_u64(&st->found);
+        __syncthreads();
+        if (s_found != kNone) break;
 
         if (!dedup) {
             if (blockIdx.x == 0 && tid == 0) st->chunk_pos = ce0;
-            if (!grid_barrier(st)) return;
+            if (!grid_barrier(st, bar_epoch, 6, J.trace)) return;
             continue;
         }
 
         // ---- phase B: survivors are the slot holders of new languages
-        const uint32_t npend = ldcg(&st->pending_count);
+        if (tid == 0) s_ctl[5] = ld_relaxed_u32(&st->pending_count);
+        __syncthreads();
+        const uint32_t npend = s_ctl[5];
         for (uint64_t i = gthread; i < npend; i += total_threads) {
             const uint32_t q = ldcg(J.pending + i);
             const uint32_t j = (uint32_t)__ldcg(reinterpret_cast<const unsigned long long *>(J.table + q)) & ~kPending;
             atomicOr(&J.bitmap[j >> 5], 1u << (j & 31));
             J.slotpos[j] = q;
         }
-        if (!grid_barrier(st)) return;
+        if (!grid_barrier(st, bar_epoch, 7, J.trace)) return;
 
         // ---- phase C: survivors per CTA (contiguous word ranges of the bitmap)
         const uint64_t nwords = (C + 31) / 32;
@@ -721,7 +758,7 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
             __syncthreads();
         }
         if (blockIdx.x == 0 && tid == 0) st->pending_count = 0;
-        if (!grid_barrier(st)) return;
+        if (!grid_barrier(st, bar_epoch, 8, J.trace)) return;
 
         // ---- phase D: append survivors in candidate order
         {
@@ -801,7 +838,7 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
                 st->chunk_pos = ce0;
             }
         }
-        if (!grid_barrier(st)) return;
+        if (!grid_barrier(st, bar_epoch, 9, J.trace)) return;
     }
 
     // ---- answer: back-pointers of the first precise candidate, then its tree
