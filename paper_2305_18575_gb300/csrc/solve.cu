@@ -682,8 +682,11 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
             for (uint32_t s = 0; s < nseg; s++) {
                 const Seg &g = S.seg[s];
                 S.tile_first[s] = t;
-                const uint64_t a = cs0 > g.start ? cs0 - g.start : 0;
-                const uint64_t e = ce0 < g.start + g.size ? ce0 - g.start : g.size;
+                // chunk [cs0, ce0) intersected with the segment, in segment-local
+                // indices (empty when the segment lies wholly before or after it)
+                const uint64_t g_end = g.start + g.size;
+                const uint64_t a = cs0 <= g.start ? 0 : (cs0 >= g_end ? g.size : cs0 - g.start);
+                const uint64_t e = ce0 <= g.start ? 0 : (ce0 >= g_end ? g.size : ce0 - g.start);
                 S.seg_lo[s] = a;
                 S.seg_hi[s] = e;
                 if (a >= e) continue;
