@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""Benchmark of the REI search on GB300: candidate languages built+deduped/s.
+
+Workload (one step): the medium single-instance configuration -- alphabet
+{0,1}, |P| = |N| = 10, lengths 0-7, each labelled by a seeded random target of
+cost 10-14, |ic| <= 128 -- seeds 0..19, each solved under the cost vectors
+(1,1,1,1,1) and (1,1,5,1,1) with max_cost 40: 40 complete solves per step.
+Inputs are synthetic (the paper's benchmark files are not available).
+
+Prints ONE JSON line (rank 0).  `value` is candidates/s measured with CUDA
+events on the library's stream over exactly --steps steps (inputs already in
+device memory); `e2e` is the same metric through rei_solve with host string
+arrays (host<->device copies inside the timed region).  The L2 cache is
+flushed (a 256 MiB write) between timed steps.
+
+--impl reference times the CPU oracle (the slow reference arm) on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "candidate languages built+deduped/sec"
+UNIT = "candidates/s"
+WORKLOAD = ("medium single instance: alphabet {0,1}, |P|=|N|=10, lengths 0-7, target cost 10-14, "
+            "|ic|<=128 (2-4 x 32-bit words); seeds 0-19 x costs (1,1,1,1,1),(1,1,5,1,1); max_cost 40")
+COSTS = [(1, 1, 1, 1, 1), (1, 1, 5, 1, 1)]
+SEEDS = list(range(20))
+
+
+def problems():
+    from workloads import make_config
+    out = []
+    for costs in COSTS:
+        for s in SEEDS:
+            out.append((make_config("medium", s), costs))
+    return out
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+
+class ClockSampler:
+    def __init__(self, device: int):
+        self.p = None
+        self.device = device
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.p is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle timing (the cpu_baseline leg and the reference arm)
+
+def oracle_sample(max_candidates_each: int, seeds=SEEDS):
+    import oracle
+    from workloads import make_config
+    cands, secs = 0, 0.0
+    for costs in COSTS:
+        for s in seeds:
+            i = make_config("medium", s)
+            r = oracle.solve(i.alphabet, i.pos, i.neg, costs=costs, max_cost=40,
+                             mem_budget=i.mem_budget, max_candidates=max_candidates_each)
+            cands += r.candidates
+            secs += r.seconds
+    return cands, secs
+
+
+def cpu_baseline():
+    cap = 80000
+    cands, secs = oracle_sample(cap)
+    return {"value": cands / secs if secs else None, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"the 40 problems of the workload, each stopped after {cap} candidates "
+                      f"({cands} candidates, {secs:.1f} s, one host thread)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cap = 4000
+    for _ in range(args.warmup):
+        oracle_sample(cap, seeds=SEEDS[:5])
+    t0 = time.perf_counter()
+    tot_c, tot_s = 0, 0.0
+    for _ in range(args.steps):
+        c, s = oracle_sample(cap, seeds=SEEDS[:5])
+        tot_c += c
+        tot_s += s
+    wall = time.perf_counter() - t0
+    value = tot_c / tot_s if tot_s else None
+    sample = (f"per step: seeds 0-4 x both cost vectors, each stopped after {cap} candidates "
+              f"(oracle timing, one host thread)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "none (CPU oracle)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+
+def alu_peak(device: int):
+    from paper_2305_18575_gb300 import build as b
+    L = C.CDLL(b.build_peak())
+    L.rei_peak_lop3.restype = C.c_double
+    L.rei_peak_lop3.argtypes = [C.c_int, C.POINTER(C.c_double)]
+    ms = C.c_double()
+    return L.rei_peak_lop3(device, C.byref(ms))
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import paper_2305_18575_gb300 as rei
+
+    torch.cuda.set_device(local_rank)
+    dev = local_rank
+    stream = torch.cuda.Stream(device=dev)
+    ctx = rei.Context(device=dev, stream=stream.cuda_stream)
+    probs = problems()
+    dprobs = [rei.Problem.on_device(i.alphabet, i.pos, i.neg, device=dev, costs=c, max_cost=40,
+                                    mem_budget=i.mem_budget) for i, c in probs]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
+
+    def step(collect):
+        for p in dprobs:
+            r = ctx.solve_problem(p)
+            if r.status != rei.REI_OK:
+                raise RuntimeError(f"solve failed: {r.status_name}")
+            collect.append(r)
+
+    for _ in range(args.warmup):
+        step([])
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    results = []
+    step_ms = []
+    launches0 = ctx.launches
+    with ClockSampler(dev) as clocks:
+        barrier()
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)  # evict the L2 between steps (outside the events)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            step(results)
+            ev1.record(stream)
+            ev1.synchronize()
+            step_ms.append(ev0.elapsed_time(ev1))
+        barrier()
+    launches = ctx.launches - launches0
+    total_ms = sum(step_ms)
+    cands = sum(r.candidates for r in results)
+
+    # end-to-end through rei_solve with host string arrays
+    e2e_res, e2e_ms = [], []
+    for i, c in probs[:1]:
+        ctx.solve(i.alphabet, i.pos, i.neg, costs=c, max_cost=40, mem_budget=i.mem_budget)
+    for _ in range(max(1, args.steps)):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i, c in probs:
+            r = ctx.solve(i.alphabet, i.pos, i.neg, costs=c, max_cost=40, mem_budget=i.mem_budget)
+            e2e_res.append(r)
+        torch.cuda.synchronize()
+        e2e_ms.append(1000 * (time.perf_counter() - t0))
+    e2e_c = sum(r.candidates for r in e2e_res)
+    nstep_e2e = max(1, args.steps)
+
+    # roofline of the search kernel: its own device time (CUDA events on the
+    # launching stream, accumulated by the library) against algorithmic work
+    k_ms = sum(r.ms_search_kernel for r in results)
+    k_launches = sum(r.search_launches for r in results)
+    pair_ops = sum(r.cand_op[3] * r.guide_pairs + r.cand_op[2] * r.star_pairs +
+                   (r.cand_op[0] + r.cand_op[1] + r.cand_op[4]) * 32 * r.words for r in results)
+    alg_bytes = sum(32 * r.candidates + (12 * 4 * r.words + 17) * r.unique for r in results)
+    peaks, peak_kind = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    lop3 = alu_peak(dev)
+    alu_peak_pairs = lop3 * 32 if lop3 > 0 else None  # one LOP3 = 32 bit-sliced AND-ORs
+    hbm_ach = alg_bytes / (k_ms * 1e-3) / 1e9
+    alu_ach = pair_ops / (k_ms * 1e-3)
+    hbm_frac = hbm_ach / hbm_peak
+    alu_frac = alu_ach / alu_peak_pairs if alu_peak_pairs else 0.0
+    if alu_frac >= hbm_frac:
+        roof = {"bound": "alu", "achieved": alu_ach / 1e12, "peak": alu_peak_pairs / 1e12,
+                "unit": "T bit-pair-ops/s", "frac": alu_frac, "traffic": None,
+                "peak_source": f"LOP3 throughput probe {lop3 / 1e12:.2f} T lane-ops/s x 32 bits"}
+    else:
+        roof = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": hbm_frac, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs"}
+    roof.update({"kernel": "k_solve", "launches": k_launches, "avg_launch_ms": k_ms / max(k_launches, 1),
+                 "alu_frac": alu_frac, "hbm_frac": hbm_frac})
+
+    # whole-job aggregation over ranks (replicas: no data-path collective)
+    t_max = total_ms
+    c_sum = cands
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=f"cuda:{dev}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+        cc = torch.tensor([float(cands)], dtype=torch.float64, device=f"cuda:{dev}")
+        torch.distributed.all_reduce(cc)
+        c_sum = float(cc.item())
+    if rank != 0:
+        return
+    ttm = sorted(r.ms_total for r in results)
+    pct = lambda q: ttm[min(len(ttm) - 1, int(q * len(ttm)))]
+    line = {
+        "metric": METRIC, "value": c_sum / (t_max * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (seeded target-labelled instances; the paper's files are unavailable)",
+        "config": {"workload": WORKLOAD, "problems_per_step": len(dprobs), "l2": "flushed between steps",
+                   "parallelism": f"replicas x{world}", "grid": results[0].grid if results else None},
+        "time_to_min_re_ms": {"p50": pct(0.5), "p99": pct(0.99), "mean": statistics.mean(ttm)},
+        "candidates_per_step": cands / args.steps,
+        "roofline": roof,
+        "e2e": {"value": e2e_c / (sum(e2e_ms) * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": sum(r.bytes_h2d for r in e2e_res) // nstep_e2e,
+                "d2h_bytes_per_step": sum(r.bytes_d2h for r in e2e_res) // nstep_e2e},
+        "clocks": clocks.summary(),
+        "gpu_launches": launches,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -101,6 +101,15 @@ typedef struct rei_stats {
     uint64_t launches;     /* kernels this call launched */
     uint64_t bytes_h2d;    /* host-to-device bytes this call copied */
     uint64_t bytes_d2h;    /* device-to-host bytes this call copied */
+    uint64_t cand_op[5];   /* `candidates` split by outermost operator:
+                              symbol, ?, *, concatenation, union */
+    uint64_t star_pairs;   /* sum over ic words w != eps of |w| (the splits
+                              a star evaluates per candidate) */
+    double ms_search_kernel; /* device time of the search launches (CUDA events) */
+    double ms_stage_kernel;  /* device time of the staging launch (CUDA events) */
+    uint32_t search_launches; /* search-kernel launches (more than 1 when the
+                                 cache grew) */
+    uint32_t grid;           /* CTAs of the search launch */
 } rei_stats;
 
 /* Result of one solve; caller-owned.  `regex` receives the pretty string

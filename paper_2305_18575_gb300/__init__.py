@@ -47,7 +47,10 @@ class rei_stats(C.Structure):
     _fields_ = [("candidates", C.c_uint64), ("unique", C.c_uint64), ("levels", C.c_uint32),
                 ("n_ic", C.c_uint32), ("words", C.c_uint32), ("max_len", C.c_uint32),
                 ("guide_pairs", C.c_uint64), ("ms_stage", C.c_double), ("ms_total", C.c_double),
-                ("launches", C.c_uint64), ("bytes_h2d", C.c_uint64), ("bytes_d2h", C.c_uint64)]
+                ("launches", C.c_uint64), ("bytes_h2d", C.c_uint64), ("bytes_d2h", C.c_uint64),
+                ("cand_op", C.c_uint64 * 5), ("star_pairs", C.c_uint64),
+                ("ms_search_kernel", C.c_double), ("ms_stage_kernel", C.c_double),
+                ("search_launches", C.c_uint32), ("grid", C.c_uint32)]
 
 
 class rei_result(C.Structure):
@@ -220,6 +223,12 @@ class Result:
     launches: int
     bytes_h2d: int
     bytes_d2h: int
+    cand_op: tuple = ()
+    star_pairs: int = 0
+    ms_search_kernel: float = 0.0
+    ms_stage_kernel: float = 0.0
+    search_launches: int = 0
+    grid: int = 0
 
     @property
     def status_name(self) -> str:
@@ -250,7 +259,8 @@ class _OutBuf:
                       self.rbuf.raw[: r.regex_len].decode("utf-8") if ok else None,
                       self.tbuf.raw[: r.tree_len] if ok else None, st.candidates, st.unique,
                       st.levels, st.n_ic, st.words, st.guide_pairs, st.ms_stage, st.ms_total,
-                      st.launches, st.bytes_h2d, st.bytes_d2h)
+                      st.launches, st.bytes_h2d, st.bytes_d2h, tuple(st.cand_op), st.star_pairs,
+                      st.ms_search_kernel, st.ms_stage_kernel, st.search_launches, st.grid)
 
 
 def pack(pos: Sequence[bytes], neg: Sequence[bytes]):

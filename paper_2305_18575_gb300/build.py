@@ -16,6 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 OBJDIR = os.path.join(LIBDIR, "obj")
 LIB = os.path.join(LIBDIR, "librei.so")
+PEAK_LIB = os.path.join(LIBDIR, "librei_peak.so")
 SOURCES = ["stage.cu", "solve.cu", "host.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
@@ -44,6 +45,7 @@ def _stale() -> bool:
 
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
     if not force and not _stale():
+        build_peak()
         return LIB
     os.makedirs(OBJDIR, exist_ok=True)
     cc = nvcc()
@@ -68,7 +70,22 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    build_peak(cc)
     return LIB
+
+
+def build_peak(cc=None) -> str:
+    """The integer-throughput probe the benchmark uses for its ALU roofline."""
+    cc = cc or nvcc()
+    src = os.path.join(CSRC, "peak.cu")
+    os.makedirs(LIBDIR, exist_ok=True)
+    if os.path.exists(PEAK_LIB) and os.path.getmtime(PEAK_LIB) > os.path.getmtime(src):
+        return PEAK_LIB
+    r = subprocess.run([cc, "-shared", "-o", PEAK_LIB, src, *ARCH, "-O3", "-Xcompiler", "-fPIC"],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on peak.cu:\n{r.stderr}")
+    return PEAK_LIB
 
 
 if __name__ == "__main__":

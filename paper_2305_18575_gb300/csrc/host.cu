@@ -73,6 +73,7 @@ struct rei_ctx {
     bool last_valid = false;
     uint32_t last_W = 0, last_size = 0, last_max_cost = 0;
 
+    cudaEvent_t ev[2] = {nullptr, nullptr};
     std::mutex mu;
 };
 
@@ -248,6 +249,7 @@ rei_status check_problem(const rei_problem *p) {
 struct Staged {
     StageInfo info;
     uint64_t h2d = 0, d2h = 0;
+    double ms_kernel = 0;
 };
 
 // stage problem p on the device; inputs end up in ctx buffers
@@ -328,13 +330,18 @@ rei_status stage_problem(rei_ctx *c, const rei_problem *p, Staged &out) {
         CK(cudaMemcpyAsync(dj, hj, sizeof(StageJob), cudaMemcpyHostToDevice, c->stream));
         CK(cudaMemsetAsync(hj->info, 0, sizeof(StageInfo), c->stream));
         out.h2d += sizeof(StageJob);
+        CK(cudaEventRecord(c->ev[0], c->stream));
         CK(launch_stage(dj, 1, c->stream));
+        CK(cudaEventRecord(c->ev[1], c->stream));
         c->launches++;
         StageInfo *hi = (StageInfo *)(c->h_pin + sizeof(StageJob));
         CK(cudaMemcpyAsync(hi, hj->info, sizeof(StageInfo), cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
         out.d2h += sizeof(StageInfo);
         out.info = *hi;
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+        out.ms_kernel = ms;
         if (out.info.status == SE_PAIRS) {
             c->pair_cap = (uint32_t)pow2_at_least(out.info.G);
             continue;
@@ -525,11 +532,21 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
     CK(cudaMemcpyAsync(c->solve_job.p, hj, sizeof(SolveJob), cudaMemcpyHostToDevice, c->stream));
     uint64_t h2d = sg.h2d + sizeof(SolveJob) + sizeof(SolveState), d2h = sg.d2h;
 
+    double ms_search = 0;
+    uint32_t search_launches = 0;
     for (int relaunch = 0;; relaunch++) {
+        CK(cudaEventRecord(c->ev[0], c->stream));
         CK(launch_solve((const SolveJob *)c->solve_job.p, grid, threads, smem, c->stream));
+        CK(cudaEventRecord(c->ev[1], c->stream));
         c->launches++;
+        search_launches++;
         CK(cudaMemcpyAsync(hst, c->state.p, sizeof(SolveState) + tree_bytes, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
+        {
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+            ms_search += ms;
+        }
         d2h += sizeof(SolveState) + tree_bytes;
         if (hst->status != ST_NEED_MEM) break;
         // grow the cache (keeping its rows) and rebuild the table
@@ -597,6 +614,12 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
     out->stats.launches = c->launches - l0;
     out->stats.bytes_h2d = h2d;
     out->stats.bytes_d2h = d2h;
+    for (int k = 0; k < 5; k++) out->stats.cand_op[k] = hst->cand_op[k];
+    out->stats.star_pairs = (uint64_t)G - n;  // sum of |w| over all words: G - n
+    out->stats.ms_search_kernel = ms_search;
+    out->stats.ms_stage_kernel = sg.ms_kernel;
+    out->stats.search_launches = search_launches;
+    out->stats.grid = grid;
     if (ws != REI_OK) return ws;
     return result;
 }
@@ -630,6 +653,10 @@ rei_status rei_ctx_create(rei_ctx **out, int device, const rei_alloc *alloc, voi
         c->alloc = *alloc;
         c->has_alloc = true;
     }
+    if (cudaEventCreate(&c->ev[0]) != cudaSuccess || cudaEventCreate(&c->ev[1]) != cudaSuccess) {
+        delete c;
+        return REI_ECUDA;
+    }
     if (stream) {
         c->stream = (cudaStream_t)stream;
     } else {
@@ -655,6 +682,8 @@ void rei_ctx_destroy(rei_ctx *c) {
     for (DevBuf *b : bufs) dev_free(c, *b);
     cudaStreamSynchronize(c->stream);
     if (c->h_pin) cudaFreeHost(c->h_pin);
+    for (cudaEvent_t e : c->ev)
+        if (e) cudaEventDestroy(e);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }

@@ -1,0 +1,55 @@
+// peak.cu -- integer-pipe throughput probe for the benchmark's ALU roofline
+// (not part of the REI ABI; built into librei_peak.so).
+//
+// Every thread runs 8 independent chains of 3-input logic operations
+// (lop3.b32, the instruction a bit-sliced AND-OR compiles to); the result is
+// stored so nothing is optimised away.  Returns lane-operations per second.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+__global__ void k_lop3(uint32_t *out, uint32_t iters, uint32_t seed) {
+    uint32_t x[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) x[i] = seed * (threadIdx.x + 7u * i + 1u) ^ blockIdx.x;
+    const uint32_t y = seed ^ 0x5A5A5A5Au, z = seed + 0x01234567u;
+    for (uint32_t k = 0; k < iters; k++) {
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            // x = (x & y) | z   (truth table 0xEA), one instruction per chain step
+            asm volatile("lop3.b32 %0, %0, %1, %2, 0xEA;" : "+r"(x[i]) : "r"(y), "r"(z));
+            asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(x[i]) : "r"(z), "r"(y));
+        }
+    }
+    uint32_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) acc ^= x[i];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+extern "C" double rei_peak_lop3(int device, double *ms_out) {
+    if (cudaSetDevice(device) != cudaSuccess) return -1;
+    cudaDeviceProp p;
+    cudaGetDeviceProperties(&p, device);
+    const int threads = 512, blocks = p.multiProcessorCount * 4;
+    const uint32_t iters = 20000;
+    uint32_t *out = nullptr;
+    if (cudaMalloc(&out, sizeof(uint32_t) * threads * blocks) != cudaSuccess) return -1;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    k_lop3<<<blocks, threads>>>(out, iters / 10, 3);  // warm-up
+    cudaEventRecord(a);
+    k_lop3<<<blocks, threads>>>(out, iters, 3);
+    cudaEventRecord(b);
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(out);
+    if (cudaGetLastError() != cudaSuccess || ms <= 0) return -1;
+    if (ms_out) *ms_out = ms;
+    const double ops = (double)threads * blocks * iters * 8 * 2;
+    return ops / (ms * 1e-3);
+}

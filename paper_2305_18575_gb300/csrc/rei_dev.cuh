@@ -114,6 +114,7 @@ struct SolveState {
     uint64_t level_total;     // index-space size of the current level
     uint32_t err;             // barrier / bounds error detail
     uint32_t need_rows;       // NEED_MEM: cache rows wanted
+    uint64_t cand_op[5];      // candidates by operator (completed levels + answer prefix)
     unsigned long long bar_arrive;  // grid-barrier arrivals of this launch
     uint32_t dbg_cta, dbg_epoch, dbg_site, dbg_seen;  // where a barrier wait ran out
     uint32_t nseg;

@@ -618,7 +618,11 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
             // end of level: count it, check the cache cap, enter the next one
             if (blockIdx.x == 0 && tid == 0) {
                 uint64_t vc = 0;
-                for (uint32_t s = 0; s < nseg; s++) vc += valid_count(S.seg[s]);
+                for (uint32_t s = 0; s < nseg; s++) {
+                    const uint64_t v = valid_count(S.seg[s]);
+                    vc += v;
+                    st->cand_op[S.seg[s].op] += v;
+                }
                 st->candidates += vc;
                 uint32_t next_status = ST_RUNNING;
                 if (!otf) {
@@ -857,8 +861,11 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
             uint64_t cnt = 0;
             for (uint32_t s = 0; s < s_plan.nseg; s++) {
                 const Seg &g = S.seg[s];
-                if (g.start + g.size <= f) cnt += valid_count(g);
-                else if (g.start <= f) cnt += valid_upto(g, f - g.start);
+                uint64_t v = 0;
+                if (g.start + g.size <= f) v = valid_count(g);
+                else if (g.start <= f) v = valid_upto(g, f - g.start);
+                cnt += v;
+                st->cand_op[g.op] += v;
             }
             st->candidates += cnt;
             st->tree_len = emit_tree(J, op, l, r);
