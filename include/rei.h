@@ -71,7 +71,9 @@ typedef enum rei_status {
     REI_EBUFSZ = 4,      /* an output buffer is too small; sizes written back */
     REI_ECUDA = 5,       /* a CUDA call failed */
     REI_ETIMEOUT = 6,    /* a bounded device wait or a server wait ran out */
-    REI_EBUSY = 7        /* server full / ticket not finished */
+    REI_EBUSY = 7,       /* server full / ticket not finished */
+    REI_ESCRATCH = 8     /* the problem, or the cache its memory budget asks
+                            for, is larger than rei_solve_noalloc's scratch */
 } rei_status;
 
 /* Cost homomorphism (c_sym, c_?, c_*, c_., c_+), Def. "cost function" (Sec. 3).
@@ -267,6 +269,41 @@ rei_status rei_server_poll(rei_server *srv, uint64_t ticket, rei_result *out, in
 
 /* Stop the server's worker (finishing live problems) and free it. */
 void rei_server_destroy(rei_server *srv);
+
+/* ---- solving without allocating ---- */
+
+/* Size of the device array rei_solve_noalloc works in.  The array is a
+ * file-scope device variable of the library: every GPU that loads the
+ * library holds these bytes until the process exits. */
+#define REI_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/* Solve one problem exactly as rei_solve_problem would (same statuses, cost,
+ * expression, candidate and unique counts), without allocating any memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory while they solve -- code working inside
+ * another framework's fixed memory arena, or a host thread that must not
+ * enter the CUDA allocator (it can block on device-wide synchronisation) --
+ * and it calls no cudaMalloc, cudaFree, pinned-host or other allocating
+ * routine.  It needs no context: it runs on the current device and on
+ * `stream` (a cudaStream_t; NULL for the default stream), and returns after
+ * the stream has finished its work.
+ *
+ * Every piece of device scratch comes from one shared array of
+ * REI_NOALLOC_SCRATCH_BYTES.  The first call on each device looks up the
+ * array's device address (once per device; make that first call before any
+ * stream capture).  The array keeps the previous call's contents; each call
+ * clears on its stream what must start cleared.  Calls that overlap on the
+ * GPU (other streams or host threads) race on the array: issue one at a time.
+ *
+ * The whole language cache of the budget is resident: with W the 32-bit
+ * words of a CS (see the memory rule above), cap = floor(mem_budget /
+ * (4*W + 28)) languages must fit, with their uniqueness table and a chunk
+ * workspace, in what the staged problem leaves of the array (about 61 MiB;
+ * e.g. cap up to about 1.2 million languages at W = 2).  Example bytes are
+ * limited to 1 MiB, examples to 65535 and guide-table pairs to 262144.  A
+ * problem beyond these limits returns REI_ESCRATCH (nothing is truncated);
+ * other errors as rei_solve_problem. */
+rei_status rei_solve_noalloc(const rei_problem *prob, void *stream, rei_result *out);
 
 #ifdef __cplusplus
 }

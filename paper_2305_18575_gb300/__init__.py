@@ -20,9 +20,12 @@ from . import build as _build
 
 LIB_PATH = _build.LIB
 
-REI_OK, REI_NOT_FOUND, REI_OOM, REI_EINVAL, REI_EBUFSZ, REI_ECUDA, REI_ETIMEOUT, REI_EBUSY = range(8)
+(REI_OK, REI_NOT_FOUND, REI_OOM, REI_EINVAL, REI_EBUFSZ, REI_ECUDA, REI_ETIMEOUT, REI_EBUSY,
+ REI_ESCRATCH) = range(9)
 STATUS_NAMES = {REI_OK: "ok", REI_NOT_FOUND: "not_found", REI_OOM: "oom", REI_EINVAL: "einval",
-                REI_EBUFSZ: "ebufsz", REI_ECUDA: "ecuda", REI_ETIMEOUT: "etimeout", REI_EBUSY: "ebusy"}
+                REI_EBUFSZ: "ebufsz", REI_ECUDA: "ecuda", REI_ETIMEOUT: "etimeout", REI_EBUSY: "ebusy",
+                REI_ESCRATCH: "escratch"}
+REI_NOALLOC_SCRATCH_BYTES = 64 << 20
 REI_F_DEVICE_INPUT = 1
 REI_F_ONTHEFLY = 2
 REI_OPT_CHUNK, REI_OPT_GRID, REI_OPT_KEEP_CACHE, REI_OPT_CACHE_INIT = 1, 2, 3, 4
@@ -31,7 +34,8 @@ REI_MAX_IC, REI_MAX_STRLEN, REI_MAX_COST = 4096, 4095, 255
 # every entry point include/rei.h declares
 EXPORTS = ["rei_ctx_create", "rei_ctx_destroy", "rei_ctx_set_option", "rei_ctx_launches",
            "rei_solve", "rei_solve_problem", "rei_stage", "rei_cache_dump", "rei_solve_batch",
-           "rei_server_create", "rei_server_submit", "rei_server_poll", "rei_server_destroy"]
+           "rei_server_create", "rei_server_submit", "rei_server_poll", "rei_server_destroy",
+           "rei_solve_noalloc"]
 
 
 class rei_costs(C.Structure):
@@ -117,6 +121,7 @@ def load(build_if_missing: bool = True):
         "rei_server_submit": (C.c_int, [vp, C.POINTER(rei_problem), u64p]),
         "rei_server_poll": (C.c_int, [vp, C.c_uint64, C.POINTER(rei_result), C.c_int]),
         "rei_server_destroy": (None, [vp]),
+        "rei_solve_noalloc": (C.c_int, [C.POINTER(rei_problem), vp, C.POINTER(rei_result)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -201,6 +206,11 @@ def rei_server_poll(srv, ticket: int, out: rei_result, block_ms: int) -> int:
 
 def rei_server_destroy(srv) -> None:
     load().rei_server_destroy(srv)
+
+
+def rei_solve_noalloc(prob: rei_problem, stream: Optional[int], out: rei_result) -> int:
+    """Solve without allocating (see include/rei.h); `stream` is a cudaStream_t or None."""
+    return load().rei_solve_noalloc(C.byref(prob), C.c_void_p(stream) if stream else None, C.byref(out))
 
 
 # ----------------------------------------------------------------------------

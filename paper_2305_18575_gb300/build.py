@@ -17,7 +17,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 OBJDIR = os.path.join(LIBDIR, "obj")
 LIB = os.path.join(LIBDIR, "librei.so")
 PEAK_LIB = os.path.join(LIBDIR, "librei_peak.so")
-SOURCES = ["stage.cu", "solve.cu", "host.cu"]
+SOURCES = ["stage.cu", "solve.cu", "host.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
