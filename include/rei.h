@@ -178,11 +178,15 @@ void rei_ctx_destroy(rei_ctx *ctx);
  *                      values only change how a level is split into chunks)
  *   REI_OPT_GRID       CTAs of the search kernel (0 = all that fit)
  *   REI_OPT_KEEP_CACHE 1 = keep the cache after a solve for rei_cache_dump
- *   REI_OPT_CACHE_INIT initial cache capacity in languages (0 = automatic) */
+ *   REI_OPT_CACHE_INIT initial cache capacity in languages (0 = automatic)
+ *   REI_OPT_SOLO_TILES chunks of at most this many 32-candidate tiles run on
+ *                      one CTA without grid-wide synchronisation (-1 =
+ *                      automatic, 0 = never) */
 #define REI_OPT_CHUNK 1
 #define REI_OPT_GRID 2
 #define REI_OPT_KEEP_CACHE 3
 #define REI_OPT_CACHE_INIT 4
+#define REI_OPT_SOLO_TILES 5
 rei_status rei_ctx_set_option(rei_ctx *ctx, int option, int64_t value);
 
 /* Number of kernels this context launched since it was created. */

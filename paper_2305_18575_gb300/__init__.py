@@ -28,7 +28,7 @@ STATUS_NAMES = {REI_OK: "ok", REI_NOT_FOUND: "not_found", REI_OOM: "oom", REI_EI
 REI_NOALLOC_SCRATCH_BYTES = 64 << 20
 REI_F_DEVICE_INPUT = 1
 REI_F_ONTHEFLY = 2
-REI_OPT_CHUNK, REI_OPT_GRID, REI_OPT_KEEP_CACHE, REI_OPT_CACHE_INIT = 1, 2, 3, 4
+REI_OPT_CHUNK, REI_OPT_GRID, REI_OPT_KEEP_CACHE, REI_OPT_CACHE_INIT, REI_OPT_SOLO_TILES = 1, 2, 3, 4, 5
 REI_MAX_IC, REI_MAX_STRLEN, REI_MAX_COST = 4096, 4095, 255
 
 # every entry point include/rei.h declares

@@ -56,7 +56,7 @@ struct rei_ctx {
     size_t smem_optin = 0;
     uint64_t launches = 0;
 
-    int64_t opt_chunk = 0, opt_grid = 0, opt_keep = 0, opt_cache_init = 0;
+    int64_t opt_chunk = 0, opt_grid = 0, opt_keep = 0, opt_cache_init = 0, opt_solo_tiles = -1;
 
     // staging
     DevBuf in_bytes, in_offs, stage_job, stage_info, word_start, word_len, len_start, gt_off, gt_pair,
@@ -439,6 +439,13 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
                                           : std::min<uint64_t>(1ull << 22, std::max<uint64_t>(1ull << 16, (1ull << 28) / (4ull * W)));
     chunk_max = std::min<uint64_t>(chunk_max, 1ull << 24);
     uint64_t cache_alloc = c->opt_cache_init > 0 ? (uint64_t)c->opt_cache_init : (1ull << 16);
+    if (c->opt_cache_init <= 0 && c->cs.p && c->bp_l.p && c->bp_r.p && c->bp_op.p) {
+        // rows a previous solve already allocated (up to 1 Mi, so that the
+        // table this solve clears stays small)
+        const uint64_t have = std::min<uint64_t>({(uint64_t)(c->cs.bytes / (4ull * W)), (uint64_t)(c->bp_l.bytes / 4),
+                                                  (uint64_t)(c->bp_r.bytes / 4), (uint64_t)c->bp_op.bytes});
+        cache_alloc = std::max<uint64_t>(cache_alloc, std::min<uint64_t>(have, 1ull << 20));
+    }
     cache_alloc = std::max<uint64_t>(1, std::min<uint64_t>(cache_alloc, cap));
 
     auto table_slots = [&](uint64_t alloc_rows) {
@@ -527,6 +534,7 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
         hj->tstack = (uint32_t *)c->tstack.p;
         hj->trace = (uint32_t *)c->trace.p;
         hj->gt_in_smem = gt_smem ? 1 : 0;
+        hj->solo_tiles = c->opt_solo_tiles >= 0 ? (uint32_t)c->opt_solo_tiles : 8 * warps;
     };
     fill_job();
     CK(cudaMemcpyAsync(c->solve_job.p, hj, sizeof(SolveJob), cudaMemcpyHostToDevice, c->stream));
@@ -566,9 +574,11 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
             CK(launch_rehash((const SolveJob *)c->solve_job.p, (uint32_t)rows, (uint32_t)(c->sm_count * 8), c->stream));
             c->launches++;
         }
-        const uint32_t running = ST_RUNNING;
-        CK(cudaMemcpyAsync(&((SolveState *)c->state.p)->status, &running, 4, cudaMemcpyHostToDevice, c->stream));
-        CK(cudaMemsetAsync(&((SolveState *)c->state.p)->bar_arrive, 0, 8, c->stream));
+        hst->status = ST_RUNNING;
+        hst->bar_arrive = 0;
+        hst->cmd = 0;
+        hst->cmd_seq = 0;
+        CK(cudaMemcpyAsync(c->state.p, hst, sizeof(SolveState), cudaMemcpyHostToDevice, c->stream));
         CK(cudaStreamSynchronize(c->stream));
         h2d += sizeof(SolveJob) + 4;
         if (relaunch > 64) return REI_ECUDA;
@@ -689,12 +699,13 @@ void rei_ctx_destroy(rei_ctx *c) {
 }
 
 rei_status rei_ctx_set_option(rei_ctx *c, int option, int64_t value) {
-    if (!c || value < 0) return REI_EINVAL;
+    if (!c || (value < 0 && option != REI_OPT_SOLO_TILES)) return REI_EINVAL;
     switch (option) {
     case REI_OPT_CHUNK: c->opt_chunk = value; return REI_OK;
     case REI_OPT_GRID: c->opt_grid = value; return REI_OK;
     case REI_OPT_KEEP_CACHE: c->opt_keep = value; return REI_OK;
     case REI_OPT_CACHE_INIT: c->opt_cache_init = value; return REI_OK;
+    case REI_OPT_SOLO_TILES: c->opt_solo_tiles = value; return REI_OK;
     default: return REI_EINVAL;
     }
 }

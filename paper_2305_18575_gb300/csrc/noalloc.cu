@@ -388,6 +388,7 @@ extern "C" rei_status rei_solve_noalloc(const rei_problem *p, void *stream_v, re
     j.tstack = d_tstack;
     j.trace = d_trace;
     j.gt_in_smem = gt_smem ? 1 : 0;
+    j.solo_tiles = 8 * warps;
     NA_CK(cudaMemcpyAsync(d_job, &j, sizeof j, cudaMemcpyHostToDevice, stream));
     NA_CK(launch_solve(d_job, grid, 32 * warps, smem, stream));
     struct {

@@ -95,6 +95,8 @@ struct Seg {
     uint32_t op;
     uint32_t tri;       // union with cl == cr: only l < r is a candidate
     uint32_t lbase, lcnt, rbase, rcnt;
+    uint32_t swap;      // concatenation tiled over 32 left operands (few right ones)
+    uint32_t pad;
 };
 
 struct SolveState {
@@ -118,7 +120,11 @@ struct SolveState {
     unsigned long long bar_arrive;  // grid-barrier arrivals of this launch
     uint32_t dbg_cta, dbg_epoch, dbg_site, dbg_seen;  // where a barrier wait ran out
     uint32_t nseg;
-    uint32_t pad[3];
+    // command from CTA 0 to the other CTAs, and the chunk it describes
+    uint32_t cmd, cmd_seq;
+    uint32_t c_level, c_size, c_dedup;
+    uint64_t c_cs0, c_ce0;
+    uint32_t pad[2];
 };
 
 struct SolveJob {
@@ -150,6 +156,7 @@ struct SolveJob {
     uint32_t *tstack;                // 4 * (max_cost + 2) words: answer-walk stack
     uint32_t *trace;                 // per CTA: (barriers passed << 8) | last barrier site
     uint32_t gt_in_smem;             // guide table copied to shared memory
+    uint32_t solo_tiles;             // chunks of at most this many tiles run on CTA 0 alone
 };
 
 }  // namespace rei

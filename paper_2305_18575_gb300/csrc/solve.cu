@@ -136,13 +136,20 @@ __device__ __forceinline__ uint64_t cs_hash(const uint32_t *c, uint32_t W, uint3
 // ---------------------------------------------------------------------------
 // per-CTA shared-memory view
 
+// tiling of one segment inside the current chunk (segment-local indices)
+struct SegTile {
+    uint64_t lo, hi;  // chunk intersected with the segment
+    uint64_t r0;      // first row (binary ops)
+    uint64_t nb;      // column blocks per row, or row blocks per column (swapped)
+};
+
 struct Shared {
     Seg *seg;                // level plan
     uint64_t *tile_first;    // first tile of each segment in the current chunk (nseg + 1)
-    uint64_t *seg_lo;        // chunk ∩ segment, local index range
-    uint64_t *seg_hi;
+    SegTile *tiles;          // per segment
     uint32_t *pos, *neg;     // precision masks (W words)
     const uint32_t *gt_off, *gt_pair, *len_start;
+    unsigned long long *sortbuf;  // kSortMax keys for the ordered append of few survivors
     uint32_t *warp_mem;      // per warp: lw[W], A[32*Ws], B[32*Ws]
     uint32_t warp_words;
 };
@@ -172,6 +179,7 @@ __device__ void plan_level(const SolveJob &J, uint32_t c, Seg *seg, Plan &P) {
         s.lcnt = lc;
         s.rbase = rb;
         s.rcnt = rc;
+        s.swap = 0;
         start += size;
     };
     if (c == c1) {
@@ -192,6 +200,8 @@ __device__ void plan_level(const SolveJob &J, uint32_t c, Seg *seg, Plan &P) {
                 lv(cl, b, n);
                 lv(rem - cl, b2, n2);
                 push(OP_CAT, 0, b, n, b2, n2, (uint64_t)n * n2);
+                // fewer than 32 right operands: bit-slice over 32 left ones instead
+                if (n * n2 > 0) seg[ns - 1].swap = (n2 < 32 && n > n2) ? 1u : 0u;
             }
         }
         if (c >= 2 * c1 + J.c[4]) {
@@ -295,8 +305,7 @@ __device__ void dedup_insert(const TileCtx &T, const uint32_t *c, uint32_t xl) {
 
 // build the CSs of one tile into A (candidate-major, row stride Ws), then test
 // precision and insert; lanes with !valid only help with the warp collectives
-__device__ void run_tile(const TileCtx &T, const Seg &sg, uint64_t lo, uint64_t hi, uint64_t tile,
-                         uint32_t *wm) {
+__device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uint64_t tile, uint32_t *wm) {
     const SolveJob &J = *T.J;
     const Shared &S = *T.S;
     const uint32_t lane = threadIdx.x & 31;
@@ -305,38 +314,48 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, uint64_t lo, uint64_t 
     uint32_t *A = wm + ((W + 3) & ~3u);
     uint32_t *B = A + 32 * Ws;
     const uint32_t *cs = J.cs;
+    const uint64_t lo = tl.lo, hi = tl.hi;
 
-    // which candidate this lane holds
-    uint64_t x;         // segment-local index
-    uint32_t row = 0, col0 = 0;
+    // which candidate this lane holds; `first` is the first of the tile's 32
+    // consecutive operands (the right ones, the left ones when swapped, or
+    // the only ones)
+    uint64_t x;  // segment-local index
+    uint32_t row = 0, col = 0, first = 0, nrow;
     bool valid;
     const bool binary = sg.op == OP_CAT || sg.op == OP_ALT;
+    const bool swapped = sg.op == OP_CAT && sg.swap;
     if (!binary) {
-        col0 = (uint32_t)(lo + tile * 32);  // first operand of the tile
-        x = (uint64_t)col0 + lane;
+        first = (uint32_t)(lo + tile * 32);
+        x = (uint64_t)first + lane;
         valid = x < hi;
+        nrow = (uint32_t)umin64(32, hi - first);
+    } else if (swapped) {
+        col = (uint32_t)(tile / tl.nb);
+        first = (uint32_t)(tl.r0 + (tile % tl.nb) * 32);
+        row = first + lane;
+        x = (uint64_t)row * sg.rcnt + col;
+        valid = row < sg.lcnt && x >= lo && x < hi;
+        nrow = min(32u, sg.lcnt - first);
     } else {
-        const uint32_t ncb = (sg.rcnt + 31) / 32;
-        const uint64_t row_lo = lo / sg.rcnt;
-        row = (uint32_t)(row_lo + tile / ncb);
-        col0 = (uint32_t)(tile % ncb) * 32;
-        const uint32_t col = col0 + lane;
+        row = (uint32_t)(tl.r0 + tile / tl.nb);
+        first = (uint32_t)(tile % tl.nb) * 32;
+        col = first + lane;
         x = (uint64_t)row * sg.rcnt + col;
         valid = col < sg.rcnt && x >= lo && x < hi && (!sg.tri || col > row);
+        nrow = min(32u, sg.rcnt - first);
     }
     const uint32_t vmask = __ballot_sync(0xFFFFFFFFu, valid);
     if (vmask == 0) return;
-    const uint32_t nrow = binary ? min(32u, sg.rcnt - col0) : (uint32_t)umin64(32, hi - col0);
 
     // ---- build
     if (sg.op == OP_LEAF) {
         for (uint32_t i = lane; i < 32 * W; i += 32) {
             const uint32_t j = i / W, b = i % W;
-            A[j * Ws + b] = j < nrow ? __ldg(J.leaf + (uint64_t)(col0 + j) * J.leaf_stride + b) : 0u;
+            A[j * Ws + b] = j < nrow ? __ldg(J.leaf + (uint64_t)(first + j) * J.leaf_stride + b) : 0u;
         }
         __syncwarp();
     } else if (sg.op == OP_OPT) {
-        const uint32_t *src = cs + (uint64_t)(sg.lbase + col0) * W;
+        const uint32_t *src = cs + (uint64_t)(sg.lbase + first) * W;
         for (uint32_t i = lane; i < 32 * W; i += 32) {
             const uint32_t j = i / W, b = i % W;
             A[j * Ws + b] = j < nrow ? ldcg(src + i) : 0u;
@@ -346,7 +365,7 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, uint64_t lo, uint64_t 
         __syncwarp();
     } else if (sg.op == OP_ALT) {
         const uint32_t *l = cs + (uint64_t)(sg.lbase + row) * W;
-        const uint32_t *src = cs + (uint64_t)(sg.rbase + col0) * W;
+        const uint32_t *src = cs + (uint64_t)(sg.rbase + first) * W;
         for (uint32_t b = lane; b < W; b += 32) lw[b] = ldcg(l + b);
         __syncwarp();
         for (uint32_t i = lane; i < 32 * W; i += 32) {
@@ -355,16 +374,18 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, uint64_t lo, uint64_t 
         }
         __syncwarp();
     } else {
-        // CAT / STAR: bit-sliced over the 32 right (CAT) or only (STAR) operands
-        const uint32_t rb = sg.op == OP_CAT ? sg.rbase : sg.lbase;
-        const uint32_t *src = cs + (uint64_t)(rb + col0) * W;
+        // CAT / STAR: bit-sliced over 32 operands (the right ones of a
+        // concatenation, its left ones when swapped, or a star's only ones)
+        const uint32_t base = sg.op == OP_STAR ? sg.lbase : swapped ? sg.lbase : sg.rbase;
+        const uint32_t *src = cs + (uint64_t)(base + first) * W;
         for (uint32_t i = lane; i < 32 * W; i += 32) {
             const uint32_t j = i / W, b = i % W;
             A[j * Ws + b] = j < nrow ? ldcg(src + i) : 0u;
         }
         if (sg.op == OP_CAT) {
-            const uint32_t *l = cs + (uint64_t)(sg.lbase + row) * W;
-            for (uint32_t b = lane; b < W; b += 32) lw[b] = ldcg(l + b);
+            // the one operand shared by the tile
+            const uint32_t *o = cs + (uint64_t)(swapped ? sg.rbase + col : sg.lbase + row) * W;
+            for (uint32_t b = lane; b < W; b += 32) lw[b] = ldcg(o + b);
         }
         __syncwarp();
         // slices: B[v] bit j = operand j contains word v
@@ -372,17 +393,24 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, uint64_t lo, uint64_t 
         __syncwarp();
         const uint32_t *go = S.gt_off, *gp = S.gt_pair;
         if (sg.op == OP_CAT) {
-            // out[w] = OR over splits w = u v of l[u] and r_j[v]  (Alg. 2)
+            // out[w] = OR over splits w = u v of l[u] and r[v]  (Alg. 2)
             for (uint32_t b = 0; b < W; b++) {
                 const uint32_t w = 32 * b + lane;
                 uint32_t acc = 0;
                 if (w < n) {
                     const uint32_t p1 = go[w + 1];
-                    for (uint32_t p = go[w]; p < p1; p++) {
-                        const uint32_t pr = gp[p];
-                        const uint32_t u = pr & 0xFFFFu, v = pr >> 16;
-                        const uint32_t lb = (lw[u >> 5] >> (u & 31)) & 1u;
-                        acc |= B[v] & (0u - lb);
+                    if (!swapped) {
+                        for (uint32_t p = go[w]; p < p1; p++) {
+                            const uint32_t pr = gp[p];
+                            const uint32_t u = pr & 0xFFFFu, v = pr >> 16;
+                            acc |= B[v] & (0u - ((lw[u >> 5] >> (u & 31)) & 1u));
+                        }
+                    } else {
+                        for (uint32_t p = go[w]; p < p1; p++) {
+                            const uint32_t pr = gp[p];
+                            const uint32_t u = pr & 0xFFFFu, v = pr >> 16;
+                            acc |= B[u] & (0u - ((lw[v >> 5] >> (v & 31)) & 1u));
+                        }
                     }
                 }
                 A[lane * Ws + b] = transpose32(acc, lane);
@@ -505,6 +533,310 @@ __device__ uint32_t emit_tree(const SolveJob &J, uint32_t op, uint32_t l, uint32
 
 // ---------------------------------------------------------------------------
 // the persistent search kernel
+//
+// CTA 0 leads: it plans levels, moves from level to level and decides, chunk by
+// chunk, whether to process the chunk alone (small chunks: its own warps,
+// __syncthreads between phases, no grid-wide wait) or with every CTA.  The
+// other CTAs wait for a command (a sequence number and parameters in the
+// state, published with release / read with acquire), join the chunk's
+// phases with grid barriers, and go back to waiting.
+
+constexpr uint32_t kSortMax = 2048;  // new languages appended by CTA 0 alone, after a sort
+
+enum Cmd : uint32_t { CMD_NONE = 0, CMD_CHUNK = 1, CMD_EXIT = 2 };
+
+struct ChunkArgs {
+    uint32_t level, size, dedup, nseg;
+    uint64_t cs0, ce0;
+};
+
+__device__ void tile_setup(Shared &S, uint32_t nseg, uint64_t cs0, uint64_t ce0, uint64_t *s_tiles) {
+    uint64_t t = 0;
+    for (uint32_t s = 0; s < nseg; s++) {
+        const Seg &g = S.seg[s];
+        S.tile_first[s] = t;
+        // chunk [cs0, ce0) intersected with the segment, in segment-local
+        // indices (empty when the segment lies wholly before or after it)
+        const uint64_t g_end = g.start + g.size;
+        const uint64_t a = cs0 <= g.start ? 0 : (cs0 >= g_end ? g.size : cs0 - g.start);
+        const uint64_t e = ce0 <= g.start ? 0 : (ce0 >= g_end ? g.size : ce0 - g.start);
+        SegTile &tl = S.tiles[s];
+        tl.lo = a;
+        tl.hi = e;
+        tl.r0 = 0;
+        tl.nb = 0;
+        if (a >= e) continue;
+        if (g.op == OP_CAT || g.op == OP_ALT) {
+            const uint64_t r0 = a / g.rcnt, r1 = (e - 1) / g.rcnt;
+            tl.r0 = r0;
+            if (g.op == OP_CAT && g.swap) {
+                tl.nb = (r1 - r0 + 1 + 31) / 32;
+                t += (uint64_t)g.rcnt * tl.nb;
+            } else {
+                tl.nb = (g.rcnt + 31) / 32;
+                t += (r1 - r0 + 1) * tl.nb;
+            }
+        } else {
+            t += (e - a + 31) / 32;
+        }
+    }
+    S.tile_first[nseg] = t;
+    *s_tiles = t;
+}
+
+// the team's barrier: the grid barrier when every CTA works on the chunk,
+// __syncthreads when CTA 0 works alone (global writes of a CTA are visible
+// to its own threads after __syncthreads)
+__device__ __forceinline__ bool team_barrier(bool full, SolveState *st, uint32_t &epoch, uint32_t site,
+                                             uint32_t *trace) {
+    if (full) return grid_barrier(st, epoch, site, trace);
+    __syncthreads();
+    return true;
+}
+
+// survivors of a chunk with few new languages, appended in candidate order by
+// CTA 0 alone: the pending slots' holders are sorted by index, then copied
+__device__ void append_sorted(const SolveJob &J, SolveState *st, Shared &S, const ChunkArgs &a,
+                              uint32_t npend, uint32_t W) {
+    const uint32_t tid = threadIdx.x;
+    uint32_t m = 1;
+    while (m < npend) m <<= 1;
+    unsigned long long *key = S.sortbuf;
+    for (uint32_t i = tid; i < m; i += blockDim.x) {
+        unsigned long long k = ~0ull;
+        if (i < npend) {
+            const uint32_t q = ldcg(J.pending + i);
+            const uint32_t j = (uint32_t)ld_relaxed_u64(J.table + q) & ~kPending;
+            k = ((unsigned long long)j << 32) | q;
+        }
+        key[i] = k;
+    }
+    __syncthreads();
+    for (uint32_t k = 2; k <= m; k <<= 1) {
+        for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
+            for (uint32_t i = tid; i < m; i += blockDim.x) {
+                const uint32_t ix = i ^ jj;
+                if (ix > i) {
+                    const unsigned long long x = key[i], y = key[ix];
+                    const bool up = (i & k) == 0;
+                    if ((x > y) == up) {
+                        key[i] = y;
+                        key[ix] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const uint64_t limit = J.cache_alloc < J.cap ? J.cache_alloc : J.cap;
+    const uint64_t room = limit > a.size ? limit - a.size : 0;
+    for (uint32_t i = tid; i < npend && i < room; i += blockDim.x) {
+        const unsigned long long kk = key[i];
+        const uint32_t j = (uint32_t)(kk >> 32), q = (uint32_t)kk;
+        const uint64_t k = (uint64_t)a.size + i;
+        const uint32_t *srcp = J.tmp + (uint64_t)j * W;
+        uint32_t *dst = J.cs + k * W;
+        for (uint32_t b = 0; b < W; b++) dst[b] = ldcg(srcp + b);
+        uint32_t op, l, r;
+        decode(S.seg, a.nseg, a.cs0 + j, op, l, r);
+        J.bp_op[k] = (uint8_t)op;
+        J.bp_l[k] = l;
+        J.bp_r[k] = r;
+        const unsigned long long old = ld_relaxed_u64(J.table + q);
+        J.table[q] = (old & 0xFFFFFFFF00000000ull) | (uint32_t)k;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const uint64_t added = npend < room ? npend : room;
+        if (npend > room) st->full = 1;
+        st->size = a.size + (uint32_t)added;
+        J.lvl_count[a.level] = (int64_t)(a.size + added) - J.lvl_start[a.level];
+        st->pending_count = 0;
+    }
+}
+
+// one chunk of candidates; returns 1 when a precise candidate was found in it,
+// 0 when done, -1 when a grid barrier gave up
+__device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const ChunkArgs &a, bool full,
+                             uint32_t &bar_epoch, uint64_t *s_tiles, uint32_t *s_red, unsigned long long *s_found,
+                             uint32_t *s_npend, uint32_t *wm) {
+    const uint32_t W = J.W, n = J.n;
+    const uint32_t Ws = (W & 1u) ? W : W + 1;
+    const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const uint32_t nwarps = blockDim.x >> 5;
+    const uint32_t team_n = full ? gridDim.x : 1, team_r = full ? blockIdx.x : 0;
+    const bool dedup = a.dedup != 0;
+
+    if (tid == 0) tile_setup(S, a.nseg, a.cs0, a.ce0, s_tiles);
+    __syncthreads();
+
+    // ---- phase A: build, precision, uniqueness insert
+    {
+        TileCtx TC{&J, st, &S, a.cs0, W, Ws, n, dedup};
+        const uint64_t ntiles = *s_tiles;
+        const uint64_t gw = (uint64_t)team_r * nwarps + wid, nw = (uint64_t)team_n * nwarps;
+        uint32_t s = 0;
+        for (uint64_t t = gw; t < ntiles; t += nw) {
+            while (s + 1 < a.nseg && S.tile_first[s + 1] <= t) s++;
+            const SegTile &tl = S.tiles[s];
+            if (tl.lo >= tl.hi) continue;
+            run_tile(TC, S.seg[s], tl, t - S.tile_first[s], wm);
+            __syncwarp();
+        }
+    }
+    if (!team_barrier(full, st, bar_epoch, 5, J.trace)) return -1;
+    if (tid == 0) {
+        *s_found = ld_relaxed_u64(&st->found);
+        *s_npend = ld_relaxed_u32(&st->pending_count);
+    }
+    __syncthreads();
+    if (*s_found != kNone) return 1;
+    if (!dedup) return 0;
+    const uint32_t npend = *s_npend;
+    __syncthreads();
+
+    // few new languages: CTA 0 appends them alone, in order, after a sort
+    if (npend <= kSortMax) {
+        if (blockIdx.x == 0) append_sorted(J, st, S, a, npend, W);
+        return 0;
+    }
+
+    // ---- phase B: survivors are the slot holders of new languages
+    const uint64_t C = a.ce0 - a.cs0;
+    {
+        const uint64_t gt = (uint64_t)team_r * blockDim.x + tid, nt = (uint64_t)team_n * blockDim.x;
+        for (uint64_t i = gt; i < npend; i += nt) {
+            const uint32_t q = ldcg(J.pending + i);
+            const uint32_t j = (uint32_t)ld_relaxed_u64(J.table + q) & ~kPending;
+            atomicOr(&J.bitmap[j >> 5], 1u << (j & 31));
+            J.slotpos[j] = q;
+        }
+    }
+    if (!team_barrier(full, st, bar_epoch, 7, J.trace)) return -1;
+
+    // ---- phase C: survivors per CTA (contiguous word ranges of the bitmap)
+    const uint64_t nwords = (C + 31) / 32;
+    const uint64_t per_cta = (nwords + team_n - 1) / team_n;
+    const uint64_t w0 = umin64(nwords, team_r * per_cta);
+    const uint64_t w1 = umin64(nwords, w0 + per_cta);
+    const uint64_t per_thr = (w1 - w0 + blockDim.x - 1) / blockDim.x;
+    const uint64_t t0 = umin64(w1, w0 + tid * per_thr);
+    const uint64_t t1 = umin64(w1, t0 + per_thr);
+    uint32_t mycnt = 0;
+    for (uint64_t w = t0; w < t1; w++) mycnt += __popc(ldcg(J.bitmap + w));
+    {
+        uint32_t v = mycnt;
+        for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, d);
+        if (lane == 0) s_red[wid] = v;
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t sum = 0;
+            for (uint32_t k = 0; k < nwarps; k++) sum += s_red[k];
+            J.blk[team_r] = sum;
+        }
+        __syncthreads();
+    }
+    if (blockIdx.x == 0 && tid == 0) st->pending_count = 0;
+    if (!team_barrier(full, st, bar_epoch, 8, J.trace)) return -1;
+
+    // ---- phase D: append survivors in candidate order
+    {
+        uint64_t cta_prefix = 0, total_new = 0;
+        for (uint32_t b = tid; b < team_n; b += blockDim.x) {
+            const uint32_t v = ldcg(J.blk + b);
+            total_new += v;
+            if (b < team_r) cta_prefix += v;
+        }
+        for (int d = 16; d > 0; d >>= 1) {
+            cta_prefix += __shfl_down_sync(0xFFFFFFFFu, cta_prefix, d);
+            total_new += __shfl_down_sync(0xFFFFFFFFu, total_new, d);
+        }
+        __shared__ uint64_t s_a[32], s_b[32], s_pref, s_tot;
+        if (lane == 0) {
+            s_a[wid] = cta_prefix;
+            s_b[wid] = total_new;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            uint64_t x = 0, y = 0;
+            for (uint32_t k = 0; k < nwarps; k++) {
+                x += s_a[k];
+                y += s_b[k];
+            }
+            s_pref = x;
+            s_tot = y;
+        }
+        uint32_t x = mycnt;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+            if (lane >= (uint32_t)d) x += y;
+        }
+        if (lane == 31) s_red[wid] = x;
+        __syncthreads();
+        uint32_t wbefore = 0;
+        for (uint32_t k = 0; k < wid; k++) wbefore += s_red[k];
+        uint64_t rank = s_pref + wbefore + x - mycnt;
+        const uint64_t limit = J.cache_alloc < J.cap ? J.cache_alloc : J.cap;
+        bool dropped = false;
+        for (uint64_t w = t0; w < t1; w++) {
+            uint32_t bits = ldcg(J.bitmap + w);
+            J.bitmap[w] = 0;
+            while (bits) {
+                const uint32_t bit = __ffs(bits) - 1;
+                bits &= bits - 1;
+                const uint32_t j = (uint32_t)(w * 32 + bit);
+                const uint64_t k = (uint64_t)a.size + rank;
+                rank++;
+                if (k >= limit) {
+                    dropped = true;
+                    continue;
+                }
+                const uint32_t *srcp = J.tmp + (uint64_t)j * W;
+                uint32_t *dst = J.cs + k * W;
+                for (uint32_t b = 0; b < W; b++) dst[b] = ldcg(srcp + b);
+                uint32_t op, l, r;
+                decode(S.seg, a.nseg, a.cs0 + j, op, l, r);
+                J.bp_op[k] = (uint8_t)op;
+                J.bp_l[k] = l;
+                J.bp_r[k] = r;
+                const uint32_t q = ldcg(J.slotpos + j);
+                const unsigned long long old = ld_relaxed_u64(J.table + q);
+                J.table[q] = (old & 0xFFFFFFFF00000000ull) | (uint32_t)k;
+            }
+        }
+        if (dropped) atomicExch(&st->full, 1u);
+        __syncthreads();
+        if (blockIdx.x == 0 && tid == 0) {
+            const uint64_t room = limit > a.size ? limit - a.size : 0;
+            const uint64_t added = s_tot < room ? s_tot : room;
+            if (s_tot > room) st->full = 1;
+            st->size = a.size + (uint32_t)added;
+            J.lvl_count[a.level] = (int64_t)(a.size + added) - J.lvl_start[a.level];
+        }
+    }
+    if (!team_barrier(full, st, bar_epoch, 9, J.trace)) return -1;
+    return 0;
+}
+
+// CTA 0 publishes a command (release); the workers pick it up (acquire)
+__device__ void publish(SolveState *st, uint32_t cmd) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->cmd = cmd;
+        __threadfence();
+        atomicAdd(&st->cmd_seq, 1u);
+    }
+    __syncthreads();
+}
+
+constexpr unsigned long long kWorkerWaitNs = 20000000000ull;  // a worker waits at most 20 s for work
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
 
 __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
     const SolveJob &J = *jobp;
@@ -514,13 +846,13 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
     __shared__ uint32_t s_red[32];
     __shared__ uint64_t s_tiles;
     __shared__ uint32_t s_ctl[8];
-    __shared__ uint64_t s_pos;
+    __shared__ uint64_t s_pos[2];
     __shared__ unsigned long long s_found;
+    __shared__ uint32_t s_npend;
 
     const uint32_t W = J.W, n = J.n;
     const uint32_t Ws = (W & 1u) ? W : W + 1;
-    const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const uint32_t nwarps = blockDim.x >> 5;
+    const uint32_t tid = threadIdx.x, wid = tid >> 5;
 
     // carve shared memory
     Shared S;
@@ -529,10 +861,10 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
     p += sizeof(Seg) * J.seg_cap;
     S.tile_first = reinterpret_cast<uint64_t *>(p);
     p += sizeof(uint64_t) * (J.seg_cap + 1);
-    S.seg_lo = reinterpret_cast<uint64_t *>(p);
-    p += sizeof(uint64_t) * J.seg_cap;
-    S.seg_hi = reinterpret_cast<uint64_t *>(p);
-    p += sizeof(uint64_t) * J.seg_cap;
+    S.tiles = reinterpret_cast<SegTile *>(p);
+    p += sizeof(SegTile) * J.seg_cap;
+    S.sortbuf = reinterpret_cast<unsigned long long *>(p);
+    p += sizeof(unsigned long long) * kSortMax;
     S.pos = reinterpret_cast<uint32_t *>(p);
     p += sizeof(uint32_t) * W;
     S.neg = reinterpret_cast<uint32_t *>(p);
@@ -558,16 +890,52 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
         S.neg[b] = J.neg_mask[b];
     }
     uint32_t *wm = S.warp_mem + wid * S.warp_words;
-
-    const uint64_t gwarp = (uint64_t)blockIdx.x * nwarps + wid;
-    const uint64_t total_warps = (uint64_t)gridDim.x * nwarps;
     uint32_t bar_epoch = 0;
-    const uint64_t gthread = (uint64_t)blockIdx.x * blockDim.x + tid;
-    const uint64_t total_threads = (uint64_t)gridDim.x * blockDim.x;
+    __syncthreads();
 
+    if (blockIdx.x != 0) {
+        // ---- worker: run the chunks CTA 0 hands out, until told to stop
+        uint32_t seen = 0;
+        for (;;) {
+            if (tid == 0) {
+                // back off up to 1 us between polls: hundreds of idle CTAs
+                // must not crowd the L2 while CTA 0 works alone
+                const unsigned long long t0 = globaltimer_ns();
+                uint32_t seq, nap = 64;
+                while ((seq = ld_relaxed_u32(&st->cmd_seq)) == seen) {
+                    __nanosleep(nap);
+                    if (nap < 1024) nap <<= 1;
+                    if (globaltimer_ns() - t0 > kWorkerWaitNs) break;
+                }
+                __threadfence();
+                if (seq == seen) {
+                    atomicCAS(&st->err, 0u, 3u);
+                    atomicExch(&st->status, (uint32_t)ST_TIMEOUT);
+                    s_ctl[0] = CMD_EXIT;
+                } else {
+                    s_ctl[0] = ld_relaxed_u32(&st->cmd);
+                    s_ctl[1] = ld_relaxed_u32(&st->c_level);
+                    s_ctl[2] = ld_relaxed_u32(&st->c_size);
+                    s_ctl[3] = ld_relaxed_u32(&st->c_dedup);
+                    s_pos[0] = ld_relaxed_u64(&st->c_cs0);
+                    s_pos[1] = ld_relaxed_u64(&st->c_ce0);
+                }
+            }
+            __syncthreads();
+            __threadfence();
+            seen++;
+            if (s_ctl[0] != CMD_CHUNK) return;
+            ChunkArgs a{s_ctl[1], s_ctl[2], s_ctl[3], 0, s_pos[0], s_pos[1]};
+            if (tid == 0) plan_level(J, a.level, S.seg, s_plan);
+            __syncthreads();
+            a.nseg = s_plan.nseg;
+            if (process_chunk(J, st, S, a, true, bar_epoch, &s_tiles, s_red, &s_found, &s_npend, wm) < 0) return;
+        }
+    }
+
+    // ---- CTA 0 leads
     // trivial specifications (Alg. 1): the empty set, then eps
-    if (blockIdx.x == 0 && tid == 0 && st->status == ST_RUNNING && st->level == J.c[0] &&
-        st->chunk_pos == 0 && st->size == 0) {
+    if (tid == 0 && st->status == ST_RUNNING && st->level == J.c[0] && st->chunk_pos == 0 && st->size == 0) {
         const uint32_t e_empty = J.n_pos_set;
         const uint32_t e_eps = J.n_pos_set - J.pos_eps + J.neg_eps;
         if (e_empty <= J.max_errors || e_eps <= J.max_errors) {
@@ -580,35 +948,29 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
             st->found = kNone;
         }
     }
-    if (!grid_barrier(st, bar_epoch, 1, J.trace)) return;
+    __syncthreads();
 
+    bool found = false;
     for (;;) {
-        // one coherent read of the control words per CTA, shared by its threads,
-        // so that every thread of every CTA takes the same branches
         if (tid == 0) {
             s_ctl[0] = ld_relaxed_u32(&st->status);
             s_ctl[1] = ld_relaxed_u32(&st->level);
             s_ctl[2] = ld_relaxed_u32(&st->size);
             s_ctl[3] = ld_relaxed_u32(&st->full);
             s_ctl[4] = ld_relaxed_u32(&st->otf);
-            s_pos = ld_relaxed_u64(&st->chunk_pos);
+            s_pos[0] = ld_relaxed_u64(&st->chunk_pos);
         }
         __syncthreads();
-        const uint32_t status = s_ctl[0];
-        const uint32_t level = s_ctl[1];
-        const uint64_t pos = s_pos;
-        const uint32_t size = s_ctl[2];
-        const uint32_t full = s_ctl[3];
-        const uint32_t otf = s_ctl[4];
+        const uint32_t status = s_ctl[0], level = s_ctl[1], size = s_ctl[2], full = s_ctl[3], otf = s_ctl[4];
+        const uint64_t pos = s_pos[0];
         __syncthreads();
         if (status != ST_RUNNING) break;
         if (level > J.max_cost) {
             // no level left (also when c_sym > max_cost): Alg. 1 "not_found"
-            if (blockIdx.x == 0 && tid == 0) st->status = ST_NOT_FOUND;
-            if (!grid_barrier(st, bar_epoch, 2, J.trace)) return;
+            if (tid == 0) st->status = ST_NOT_FOUND;
+            __syncthreads();
             continue;
         }
-
         if (tid == 0) plan_level(J, level, S.seg, s_plan);
         __syncthreads();
         const uint32_t nseg = s_plan.nseg;
@@ -616,7 +978,7 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
 
         if (pos >= T) {
             // end of level: count it, check the cache cap, enter the next one
-            if (blockIdx.x == 0 && tid == 0) {
+            if (tid == 0) {
                 uint64_t vc = 0;
                 for (uint32_t s = 0; s < nseg; s++) {
                     const uint64_t v = valid_count(S.seg[s]);
@@ -644,9 +1006,7 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
                     } else {
                         J.lvl_start[nl] = size;
                         J.lvl_count[nl] = 0;
-                        if (ld_relaxed_u32(&st->otf) &&
-                            max_operand_level(J, (int)nl) >= (int)ld_relaxed_u32(&st->partial_level))
-                            next_status = ST_OOM;
+                        if (st->otf && max_operand_level(J, (int)nl) >= (int)st->partial_level) next_status = ST_OOM;
                     }
                 }
                 st->level = next_status == ST_RUNNING ? nl : level;
@@ -654,7 +1014,7 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
                 st->full = 0;
                 st->status = next_status;
             }
-            if (!grid_barrier(st, bar_epoch, 3, J.trace)) return;
+            __syncthreads();
             continue;
         }
 
@@ -668,188 +1028,43 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
                 if (room * 4 >= J.chunk_max || room >= T - pos) {
                     C = room;
                 } else {
-                    if (blockIdx.x == 0 && tid == 0) {
+                    if (tid == 0) {
                         st->need_rows = (uint32_t)umin64(J.cap, (uint64_t)size + C);
                         st->status = ST_NEED_MEM;
                     }
-                    if (!grid_barrier(st, bar_epoch, 4, J.trace)) return;
+                    __syncthreads();
                     continue;
                 }
             }
         }
         if (C == 0) C = 1;  // unreachable with room >= 1; guards the loop
-        const uint64_t cs0 = pos, ce0 = pos + C;
-
-        // tiles of this chunk, per segment
-        if (tid == 0) {
-            uint64_t t = 0;
-            for (uint32_t s = 0; s < nseg; s++) {
-                const Seg &g = S.seg[s];
-                S.tile_first[s] = t;
-                // chunk [cs0, ce0) intersected with the segment, in segment-local
-                // indices (empty when the segment lies wholly before or after it)
-                const uint64_t g_end = g.start + g.size;
-                const uint64_t a = cs0 <= g.start ? 0 : (cs0 >= g_end ? g.size : cs0 - g.start);
-                const uint64_t e = ce0 <= g.start ? 0 : (ce0 >= g_end ? g.size : ce0 - g.start);
-                S.seg_lo[s] = a;
-                S.seg_hi[s] = e;
-                if (a >= e) continue;
-                if (g.op == OP_CAT || g.op == OP_ALT) {
-                    const uint64_t ncb = (g.rcnt + 31) / 32;
-                    t += ((e - 1) / g.rcnt - a / g.rcnt + 1) * ncb;
-                } else {
-                    t += (e - a + 31) / 32;
-                }
-            }
-            S.tile_first[nseg] = t;
-            s_tiles = t;
-        }
+        ChunkArgs a{level, size, dedup ? 1u : 0u, nseg, pos, pos + C};
+        // alone when the chunk is a few tiles per warp of this CTA
+        if (tid == 0) tile_setup(S, nseg, a.cs0, a.ce0, &s_tiles);
         __syncthreads();
-
-        // ---- phase A
-        {
-            TileCtx TC{&J, st, &S, cs0, W, Ws, n, dedup};
-            const uint64_t ntiles = s_tiles;
-            uint32_t s = 0;
-            for (uint64_t t = gwarp; t < ntiles; t += total_warps) {
-                while (s + 1 < nseg && S.tile_first[s + 1] <= t) s++;
-                const Seg &g = S.seg[s];
-                if (S.seg_lo[s] >= S.seg_hi[s]) continue;
-                run_tile(TC, g, S.seg_lo[s], S.seg_hi[s], t - S.tile_first[s], wm);
-                __syncwarp();
-            }
-        }
-        if (!grid_barrier(st, bar_epoch, 5, J.trace)) return;
-        if (tid == 0) s_found = ld_relaxed_u64(&st->found);
-        __syncthreads();
-        if (s_found != kNone) break;
-
-        if (!dedup) {
-            if (blockIdx.x == 0 && tid == 0) st->chunk_pos = ce0;
-            if (!grid_barrier(st, bar_epoch, 6, J.trace)) return;
-            continue;
-        }
-
-        // ---- phase B: survivors are the slot holders of new languages
-        if (tid == 0) s_ctl[5] = ld_relaxed_u32(&st->pending_count);
-        __syncthreads();
-        const uint32_t npend = s_ctl[5];
-        for (uint64_t i = gthread; i < npend; i += total_threads) {
-            const uint32_t q = ldcg(J.pending + i);
-            const uint32_t j = (uint32_t)__ldcg(reinterpret_cast<const unsigned long long *>(J.table + q)) & ~kPending;
-            atomicOr(&J.bitmap[j >> 5], 1u << (j & 31));
-            J.slotpos[j] = q;
-        }
-        if (!grid_barrier(st, bar_epoch, 7, J.trace)) return;
-
-        // ---- phase C: survivors per CTA (contiguous word ranges of the bitmap)
-        const uint64_t nwords = (C + 31) / 32;
-        const uint64_t per_cta = (nwords + gridDim.x - 1) / gridDim.x;
-        const uint64_t w0 = umin64(nwords, blockIdx.x * per_cta);
-        const uint64_t w1 = umin64(nwords, w0 + per_cta);
-        const uint64_t per_thr = (w1 - w0 + blockDim.x - 1) / blockDim.x;
-        const uint64_t t0 = umin64(w1, w0 + tid * per_thr);
-        const uint64_t t1 = umin64(w1, t0 + per_thr);
-        uint32_t mycnt = 0;
-        for (uint64_t w = t0; w < t1; w++) mycnt += __popc(ldcg(J.bitmap + w));
-        {
-            uint32_t v = mycnt;
-            for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, d);
-            if (lane == 0) s_red[wid] = v;
-            __syncthreads();
+        const bool team = s_tiles > (uint64_t)J.solo_tiles;
+        if (team) {
             if (tid == 0) {
-                uint32_t sum = 0;
-                for (uint32_t k = 0; k < nwarps; k++) sum += s_red[k];
-                J.blk[blockIdx.x] = sum;
+                st->c_level = a.level;
+                st->c_size = a.size;
+                st->c_dedup = a.dedup;
+                st->c_cs0 = a.cs0;
+                st->c_ce0 = a.ce0;
             }
-            __syncthreads();
+            publish(st, CMD_CHUNK);
         }
-        if (blockIdx.x == 0 && tid == 0) st->pending_count = 0;
-        if (!grid_barrier(st, bar_epoch, 8, J.trace)) return;
-
-        // ---- phase D: append survivors in candidate order
-        {
-            uint64_t cta_prefix = 0, total_new = 0;
-            for (uint32_t b = tid; b < gridDim.x; b += blockDim.x) {
-                const uint32_t v = ldcg(J.blk + b);
-                total_new += v;
-                if (b < blockIdx.x) cta_prefix += v;
-            }
-            // block reductions of the two sums
-            for (int d = 16; d > 0; d >>= 1) {
-                cta_prefix += __shfl_down_sync(0xFFFFFFFFu, cta_prefix, d);
-                total_new += __shfl_down_sync(0xFFFFFFFFu, total_new, d);
-            }
-            __shared__ uint64_t s_a[32], s_b[32], s_pref, s_tot;
-            if (lane == 0) {
-                s_a[wid] = cta_prefix;
-                s_b[wid] = total_new;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                uint64_t a = 0, b = 0;
-                for (uint32_t k = 0; k < nwarps; k++) {
-                    a += s_a[k];
-                    b += s_b[k];
-                }
-                s_pref = a;
-                s_tot = b;
-            }
-            // thread offset inside the CTA (exclusive scan of mycnt)
-            uint32_t x = mycnt;
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
-                if (lane >= (uint32_t)d) x += y;
-            }
-            if (lane == 31) s_red[wid] = x;
-            __syncthreads();
-            uint32_t wbefore = 0;
-            for (uint32_t k = 0; k < wid; k++) wbefore += s_red[k];
-            uint64_t rank = s_pref + wbefore + x - mycnt;
-            const uint64_t limit = J.cache_alloc < J.cap ? J.cache_alloc : J.cap;
-            bool dropped = false;
-            for (uint64_t w = t0; w < t1; w++) {
-                uint32_t bits = ldcg(J.bitmap + w);
-                J.bitmap[w] = 0;
-                while (bits) {
-                    const uint32_t bit = __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    const uint32_t j = (uint32_t)(w * 32 + bit);
-                    const uint64_t k = (uint64_t)size + rank;
-                    rank++;
-                    if (k >= limit) {
-                        dropped = true;
-                        continue;
-                    }
-                    const uint32_t *srcp = J.tmp + (uint64_t)j * W;
-                    uint32_t *dst = J.cs + k * W;
-                    for (uint32_t b = 0; b < W; b++) dst[b] = ldcg(srcp + b);
-                    uint32_t op, l, r;
-                    decode(S.seg, nseg, cs0 + j, op, l, r);
-                    J.bp_op[k] = (uint8_t)op;
-                    J.bp_l[k] = l;
-                    J.bp_r[k] = r;
-                    const uint32_t q = ldcg(J.slotpos + j);
-                    const unsigned long long old = __ldcg(reinterpret_cast<const unsigned long long *>(J.table + q));
-                    J.table[q] = (old & 0xFFFFFFFF00000000ull) | (uint32_t)k;
-                }
-            }
-            if (dropped) atomicExch(&st->full, 1u);
-            __syncthreads();
-            if (blockIdx.x == 0 && tid == 0) {
-                const uint64_t room = limit > size ? limit - size : 0;
-                const uint64_t added = s_tot < room ? s_tot : room;
-                if (s_tot > room) st->full = 1;
-                st->size = size + (uint32_t)added;
-                J.lvl_count[level] = (int64_t)(size + added) - J.lvl_start[level];
-                st->chunk_pos = ce0;
-            }
+        const int r = process_chunk(J, st, S, a, team, bar_epoch, &s_tiles, s_red, &s_found, &s_npend, wm);
+        if (r < 0) return;
+        if (r == 1) {
+            found = true;
+            break;
         }
-        if (!grid_barrier(st, bar_epoch, 9, J.trace)) return;
+        if (tid == 0) st->chunk_pos = a.ce0;
+        __syncthreads();
     }
 
     // ---- answer: back-pointers of the first precise candidate, then its tree
-    if (blockIdx.x == 0 && tid == 0) {
+    if (found && tid == 0) {
         const unsigned long long f = st->found;
         if (st->status == ST_RUNNING && f != kNone) {
             uint32_t op, l, r;
@@ -872,6 +1087,7 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
             st->status = ST_FOUND;
         }
     }
+    publish(st, CMD_EXIT);
 }
 
 // rebuild the uniqueness table after the cache grew (all entries are distinct)
@@ -894,7 +1110,8 @@ __global__ void k_rehash(const SolveJob *jobp, uint32_t count) {
 size_t solve_smem_bytes(uint32_t W, uint32_t n, uint32_t G, uint32_t max_len, uint32_t seg_cap,
                         bool gt_in_smem, uint32_t warps) {
     const uint32_t Ws = (W & 1u) ? W : W + 1;
-    size_t b = sizeof(Seg) * seg_cap + sizeof(uint64_t) * (seg_cap + 1) + 2 * sizeof(uint64_t) * seg_cap;
+    size_t b = sizeof(Seg) * seg_cap + sizeof(uint64_t) * (seg_cap + 1) + sizeof(SegTile) * seg_cap;
+    b += sizeof(unsigned long long) * kSortMax;
     b += 2 * sizeof(uint32_t) * W;
     if (gt_in_smem) b += sizeof(uint32_t) * (((n + 1 + G + max_len + 2) + 3) & ~3u);
     b += sizeof(uint32_t) * (size_t)warps * (((W + 3) & ~3u) + 2 * 32 * Ws);

@@ -152,12 +152,15 @@ def test_medium_config_matches_oracle(ctx, seed, costs):
 
 @pytest.mark.parametrize("chunk", [1, 7, 100, 4099])
 @pytest.mark.parametrize("grid", [1, 3, 0])
-def test_chunking_and_grid_do_not_change_results(chunk, grid):
+@pytest.mark.parametrize("solo", [-1, 0, 1 << 30])
+def test_chunking_and_grid_do_not_change_results(chunk, grid, solo):
     """Small chunks split every level into many chunks with ragged tails; a
-    small grid makes every CTA process many tiles."""
+    small grid makes every CTA process many tiles; `solo` forces every chunk
+    onto the whole grid (0) or onto CTA 0 alone (2^30)."""
     with rei.Context(device=0) as c:
         c.set_option(rei.REI_OPT_CHUNK, chunk)
         c.set_option(rei.REI_OPT_GRID, grid)
+        c.set_option(rei.REI_OPT_SOLO_TILES, solo)
         for s in (0, 2, 5):
             inst = make_config("medium", s)
             got, ref = solve_both(c, inst, max_cost=40, mem_budget=1 << 30)
