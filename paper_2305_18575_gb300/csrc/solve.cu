@@ -150,8 +150,17 @@ struct Shared {
     uint32_t *pos, *neg;     // precision masks (W words)
     const uint32_t *gt_off, *gt_pair, *len_start;
     unsigned long long *sortbuf;  // kSortMax keys for the ordered append of few survivors
+    uint32_t *lvs, *lvc;     // level table (start, count per cost), mirrored in shared memory
     uint32_t *warp_mem;      // per warp: lw[W], A[32*Ws], B[32*Ws]
     uint32_t warp_words;
+};
+
+// the search state CTA 0 keeps in shared memory while it leads; written back
+// to the global SolveState when the launch ends
+struct Lead {
+    uint32_t status, level, size, full, otf, partial_level;
+    uint64_t chunk_pos, candidates, unique_done;
+    uint64_t cand_op[5];
 };
 
 struct Plan {
@@ -160,13 +169,14 @@ struct Plan {
 };
 
 // Alg. 1 order for level c; only segments with candidates are kept
-__device__ void plan_level(const SolveJob &J, uint32_t c, Seg *seg, Plan &P) {
+__device__ void plan_level(const SolveJob &J, uint32_t c, const uint32_t *lvs, const uint32_t *lvc, Seg *seg,
+                           Plan &P) {
     const uint32_t c1 = J.c[0];
     uint32_t ns = 0;
     uint64_t start = 0;
     auto lv = [&](uint32_t cost, uint32_t &base, uint32_t &cnt) {
-        base = (uint32_t)ld_relaxed_u64(&J.lvl_start[cost]);
-        cnt = (uint32_t)ld_relaxed_u64(&J.lvl_count[cost]);
+        base = lvs[cost];
+        cnt = lvc[cost];
     };
     auto push = [&](uint32_t op, uint32_t tri, uint32_t lb, uint32_t lc, uint32_t rb, uint32_t rc, uint64_t size) {
         if (size == 0) return;
@@ -597,7 +607,7 @@ __device__ __forceinline__ bool team_barrier(bool full, SolveState *st, uint32_t
 // survivors of a chunk with few new languages, appended in candidate order by
 // CTA 0 alone: the pending slots' holders are sorted by index, then copied
 __device__ void append_sorted(const SolveJob &J, SolveState *st, Shared &S, const ChunkArgs &a,
-                              uint32_t npend, uint32_t W) {
+                              uint32_t npend, uint32_t W, Lead *L) {
     const uint32_t tid = threadIdx.x;
     uint32_t m = 1;
     while (m < npend) m <<= 1;
@@ -648,9 +658,10 @@ __device__ void append_sorted(const SolveJob &J, SolveState *st, Shared &S, cons
     __syncthreads();
     if (tid == 0) {
         const uint64_t added = npend < room ? npend : room;
-        if (npend > room) st->full = 1;
-        st->size = a.size + (uint32_t)added;
-        J.lvl_count[a.level] = (int64_t)(a.size + added) - J.lvl_start[a.level];
+        if (npend > room) L->full = 1;
+        L->size = a.size + (uint32_t)added;
+        S.lvc[a.level] = L->size - S.lvs[a.level];
+        J.lvl_count[a.level] = S.lvc[a.level];
         st->pending_count = 0;
     }
 }
@@ -658,8 +669,8 @@ __device__ void append_sorted(const SolveJob &J, SolveState *st, Shared &S, cons
 // one chunk of candidates; returns 1 when a precise candidate was found in it,
 // 0 when done, -1 when a grid barrier gave up
 __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const ChunkArgs &a, bool full,
-                             uint32_t &bar_epoch, uint64_t *s_tiles, uint32_t *s_red, unsigned long long *s_found,
-                             uint32_t *s_npend, uint32_t *wm) {
+                             bool tiles_ready, uint32_t &bar_epoch, uint64_t *s_tiles, uint32_t *s_red,
+                             unsigned long long *s_found, uint32_t *s_npend, uint32_t *wm, Lead *L) {
     const uint32_t W = J.W, n = J.n;
     const uint32_t Ws = (W & 1u) ? W : W + 1;
     const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -667,8 +678,10 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
     const uint32_t team_n = full ? gridDim.x : 1, team_r = full ? blockIdx.x : 0;
     const bool dedup = a.dedup != 0;
 
-    if (tid == 0) tile_setup(S, a.nseg, a.cs0, a.ce0, s_tiles);
-    __syncthreads();
+    if (!tiles_ready) {
+        if (tid == 0) tile_setup(S, a.nseg, a.cs0, a.ce0, s_tiles);
+        __syncthreads();
+    }
 
     // ---- phase A: build, precision, uniqueness insert
     {
@@ -697,7 +710,7 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
 
     // few new languages: CTA 0 appends them alone, in order, after a sort
     if (npend <= kSortMax) {
-        if (blockIdx.x == 0) append_sorted(J, st, S, a, npend, W);
+        if (blockIdx.x == 0) append_sorted(J, st, S, a, npend, W, L);
         return 0;
     }
 
@@ -804,14 +817,15 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
                 J.table[q] = (old & 0xFFFFFFFF00000000ull) | (uint32_t)k;
             }
         }
-        if (dropped) atomicExch(&st->full, 1u);
+        (void)dropped;
         __syncthreads();
         if (blockIdx.x == 0 && tid == 0) {
             const uint64_t room = limit > a.size ? limit - a.size : 0;
             const uint64_t added = s_tot < room ? s_tot : room;
-            if (s_tot > room) st->full = 1;
-            st->size = a.size + (uint32_t)added;
-            J.lvl_count[a.level] = (int64_t)(a.size + added) - J.lvl_start[a.level];
+            if (s_tot > room) L->full = 1;  // every drop shows as s_tot > room
+            L->size = a.size + (uint32_t)added;
+            S.lvc[a.level] = L->size - S.lvs[a.level];
+            J.lvl_count[a.level] = S.lvc[a.level];
         }
     }
     if (!team_barrier(full, st, bar_epoch, 9, J.trace)) return -1;
@@ -849,6 +863,7 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
     __shared__ uint64_t s_pos[2];
     __shared__ unsigned long long s_found;
     __shared__ uint32_t s_npend;
+    __shared__ Lead L;
 
     const uint32_t W = J.W, n = J.n;
     const uint32_t Ws = (W & 1u) ? W : W + 1;
@@ -865,6 +880,10 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
     p += sizeof(SegTile) * J.seg_cap;
     S.sortbuf = reinterpret_cast<unsigned long long *>(p);
     p += sizeof(unsigned long long) * kSortMax;
+    S.lvs = reinterpret_cast<uint32_t *>(p);
+    p += sizeof(uint32_t) * J.seg_cap;
+    S.lvc = reinterpret_cast<uint32_t *>(p);
+    p += sizeof(uint32_t) * J.seg_cap;
     S.pos = reinterpret_cast<uint32_t *>(p);
     p += sizeof(uint32_t) * W;
     S.neg = reinterpret_cast<uint32_t *>(p);
@@ -891,6 +910,11 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
     }
     uint32_t *wm = S.warp_mem + wid * S.warp_words;
     uint32_t bar_epoch = 0;
+    // the level table as left by earlier launches of this search (parallel loads)
+    for (uint32_t c = tid; c <= J.max_cost + 1 && c < J.seg_cap; c += blockDim.x) {
+        S.lvs[c] = (uint32_t)ld_relaxed_u64(&J.lvl_start[c]);
+        S.lvc[c] = (uint32_t)ld_relaxed_u64(&J.lvl_count[c]);
+    }
     __syncthreads();
 
     if (blockIdx.x != 0) {
@@ -926,52 +950,63 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
             seen++;
             if (s_ctl[0] != CMD_CHUNK) return;
             ChunkArgs a{s_ctl[1], s_ctl[2], s_ctl[3], 0, s_pos[0], s_pos[1]};
-            if (tid == 0) plan_level(J, a.level, S.seg, s_plan);
+            // the level table up to this level, as CTA 0 published it
+            for (uint32_t c = tid; c <= a.level; c += blockDim.x) {
+                S.lvs[c] = (uint32_t)ld_relaxed_u64(&J.lvl_start[c]);
+                S.lvc[c] = (uint32_t)ld_relaxed_u64(&J.lvl_count[c]);
+            }
+            __syncthreads();
+            if (tid == 0) plan_level(J, a.level, S.lvs, S.lvc, S.seg, s_plan);
             __syncthreads();
             a.nseg = s_plan.nseg;
-            if (process_chunk(J, st, S, a, true, bar_epoch, &s_tiles, s_red, &s_found, &s_npend, wm) < 0) return;
+            if (process_chunk(J, st, S, a, true, false, bar_epoch, &s_tiles, s_red, &s_found, &s_npend, wm,
+                              nullptr) < 0)
+                return;
         }
     }
 
-    // ---- CTA 0 leads
-    // trivial specifications (Alg. 1): the empty set, then eps
-    if (tid == 0 && st->status == ST_RUNNING && st->level == J.c[0] && st->chunk_pos == 0 && st->size == 0) {
-        const uint32_t e_empty = J.n_pos_set;
-        const uint32_t e_eps = J.n_pos_set - J.pos_eps + J.neg_eps;
-        if (e_empty <= J.max_errors || e_eps <= J.max_errors) {
-            J.tree[0] = e_empty <= J.max_errors ? '0' : 'e';
-            J.tree[1] = 0;
-            st->tree_len = 1;
-            st->ans_cost = J.c[0];
-            st->candidates = 0;
-            st->status = ST_FOUND;
-            st->found = kNone;
+    // ---- CTA 0 leads, with the search state in shared memory
+    if (tid == 0) {
+        L.status = st->status;
+        L.level = st->level;
+        L.size = st->size;
+        L.full = st->full;
+        L.otf = st->otf;
+        L.partial_level = st->partial_level;
+        L.chunk_pos = st->chunk_pos;
+        L.candidates = st->candidates;
+        L.unique_done = st->unique_done;
+        for (int k = 0; k < 5; k++) L.cand_op[k] = st->cand_op[k];
+        // trivial specifications (Alg. 1): the empty set, then eps
+        if (L.status == ST_RUNNING && L.level == J.c[0] && L.chunk_pos == 0 && L.size == 0) {
+            const uint32_t e_empty = J.n_pos_set;
+            const uint32_t e_eps = J.n_pos_set - J.pos_eps + J.neg_eps;
+            if (e_empty <= J.max_errors || e_eps <= J.max_errors) {
+                J.tree[0] = e_empty <= J.max_errors ? '0' : 'e';
+                J.tree[1] = 0;
+                st->tree_len = 1;
+                st->ans_cost = J.c[0];
+                L.candidates = 0;
+                L.status = ST_FOUND;
+                st->found = kNone;
+            }
         }
     }
     __syncthreads();
 
     bool found = false;
     for (;;) {
-        if (tid == 0) {
-            s_ctl[0] = ld_relaxed_u32(&st->status);
-            s_ctl[1] = ld_relaxed_u32(&st->level);
-            s_ctl[2] = ld_relaxed_u32(&st->size);
-            s_ctl[3] = ld_relaxed_u32(&st->full);
-            s_ctl[4] = ld_relaxed_u32(&st->otf);
-            s_pos[0] = ld_relaxed_u64(&st->chunk_pos);
-        }
-        __syncthreads();
-        const uint32_t status = s_ctl[0], level = s_ctl[1], size = s_ctl[2], full = s_ctl[3], otf = s_ctl[4];
-        const uint64_t pos = s_pos[0];
+        const uint32_t status = L.status, level = L.level, size = L.size, full = L.full, otf = L.otf;
+        const uint64_t pos = L.chunk_pos;
         __syncthreads();
         if (status != ST_RUNNING) break;
         if (level > J.max_cost) {
             // no level left (also when c_sym > max_cost): Alg. 1 "not_found"
-            if (tid == 0) st->status = ST_NOT_FOUND;
+            if (tid == 0) L.status = ST_NOT_FOUND;
             __syncthreads();
             continue;
         }
-        if (tid == 0) plan_level(J, level, S.seg, s_plan);
+        if (tid == 0) plan_level(J, level, S.lvs, S.lvc, S.seg, s_plan);
         __syncthreads();
         const uint32_t nseg = s_plan.nseg;
         const uint64_t T = s_plan.total;
@@ -983,20 +1018,20 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
                 for (uint32_t s = 0; s < nseg; s++) {
                     const uint64_t v = valid_count(S.seg[s]);
                     vc += v;
-                    st->cand_op[S.seg[s].op] += v;
+                    L.cand_op[S.seg[s].op] += v;
                 }
-                st->candidates += vc;
+                L.candidates += vc;
                 uint32_t next_status = ST_RUNNING;
                 if (!otf) {
                     if (full) {
                         if (J.flags & REI_F_ONTHEFLY) {
-                            st->otf = 1;
-                            st->partial_level = level;
+                            L.otf = 1;
+                            L.partial_level = level;
                         } else {
                             next_status = ST_OOM;
                         }
                     } else {
-                        st->unique_done = size;
+                        L.unique_done = size;
                     }
                 }
                 const uint32_t nl = level + 1;
@@ -1004,15 +1039,17 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
                     if (nl > J.max_cost) {
                         next_status = ST_NOT_FOUND;
                     } else {
+                        S.lvs[nl] = size;
+                        S.lvc[nl] = 0;
                         J.lvl_start[nl] = size;
                         J.lvl_count[nl] = 0;
-                        if (st->otf && max_operand_level(J, (int)nl) >= (int)st->partial_level) next_status = ST_OOM;
+                        if (L.otf && max_operand_level(J, (int)nl) >= (int)L.partial_level) next_status = ST_OOM;
                     }
                 }
-                st->level = next_status == ST_RUNNING ? nl : level;
-                st->chunk_pos = 0;
-                st->full = 0;
-                st->status = next_status;
+                L.level = next_status == ST_RUNNING ? nl : level;
+                L.chunk_pos = 0;
+                L.full = 0;
+                L.status = next_status;
             }
             __syncthreads();
             continue;
@@ -1030,7 +1067,7 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
                 } else {
                     if (tid == 0) {
                         st->need_rows = (uint32_t)umin64(J.cap, (uint64_t)size + C);
-                        st->status = ST_NEED_MEM;
+                        L.status = ST_NEED_MEM;
                     }
                     __syncthreads();
                     continue;
@@ -1053,26 +1090,26 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
             }
             publish(st, CMD_CHUNK);
         }
-        const int r = process_chunk(J, st, S, a, team, bar_epoch, &s_tiles, s_red, &s_found, &s_npend, wm);
+        const int r = process_chunk(J, st, S, a, team, true, bar_epoch, &s_tiles, s_red, &s_found, &s_npend, wm, &L);
         if (r < 0) return;
         if (r == 1) {
             found = true;
             break;
         }
-        if (tid == 0) st->chunk_pos = a.ce0;
+        if (tid == 0) L.chunk_pos = a.ce0;
         __syncthreads();
     }
 
     // ---- answer: back-pointers of the first precise candidate, then its tree
     if (found && tid == 0) {
-        const unsigned long long f = st->found;
-        if (st->status == ST_RUNNING && f != kNone) {
+        const unsigned long long f = ld_relaxed_u64(&st->found);
+        if (L.status == ST_RUNNING && f != kNone) {
             uint32_t op, l, r;
             decode(S.seg, s_plan.nseg, f, op, l, r);
             st->ans_op = op;
             st->ans_l = l;
             st->ans_r = r;
-            st->ans_cost = st->level;
+            st->ans_cost = L.level;
             uint64_t cnt = 0;
             for (uint32_t s = 0; s < s_plan.nseg; s++) {
                 const Seg &g = S.seg[s];
@@ -1080,12 +1117,25 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
                 if (g.start + g.size <= f) v = valid_count(g);
                 else if (g.start <= f) v = valid_upto(g, f - g.start);
                 cnt += v;
-                st->cand_op[g.op] += v;
+                L.cand_op[g.op] += v;
             }
-            st->candidates += cnt;
+            L.candidates += cnt;
             st->tree_len = emit_tree(J, op, l, r);
-            st->status = ST_FOUND;
+            L.status = ST_FOUND;
         }
+    }
+    // the state the host reads, and a later launch of this search resumes from
+    if (tid == 0) {
+        if (ld_relaxed_u32(&st->status) != ST_TIMEOUT) st->status = L.status;
+        st->level = L.level;
+        st->size = L.size;
+        st->full = L.full;
+        st->otf = L.otf;
+        st->partial_level = L.partial_level;
+        st->chunk_pos = L.chunk_pos;
+        st->candidates = L.candidates;
+        st->unique_done = L.unique_done;
+        for (int k = 0; k < 5; k++) st->cand_op[k] = L.cand_op[k];
     }
     publish(st, CMD_EXIT);
 }
@@ -1112,6 +1162,7 @@ size_t solve_smem_bytes(uint32_t W, uint32_t n, uint32_t G, uint32_t max_len, ui
     const uint32_t Ws = (W & 1u) ? W : W + 1;
     size_t b = sizeof(Seg) * seg_cap + sizeof(uint64_t) * (seg_cap + 1) + sizeof(SegTile) * seg_cap;
     b += sizeof(unsigned long long) * kSortMax;
+    b += 2 * sizeof(uint32_t) * seg_cap;
     b += 2 * sizeof(uint32_t) * W;
     if (gt_in_smem) b += sizeof(uint32_t) * (((n + 1 + G + max_len + 2) + 3) & ~3u);
     b += sizeof(uint32_t) * (size_t)warps * (((W + 3) & ~3u) + 2 * 32 * Ws);
