@@ -26,6 +26,8 @@ def main(argv=None):
     ap.add_argument("--cache-init", type=int, default=0, help="initial cache rows (0 = library default)")
     ap.add_argument("--chunk", type=int, default=0)
     ap.add_argument("--device-input", action="store_true")
+    ap.add_argument("--solo-tiles", type=int, default=None, help="chunks of at most this many tiles run on one CTA")
+    ap.add_argument("--grid", type=int, default=0)
     a = ap.parse_args(argv)
     costs = tuple(int(x) for x in a.costs.split(","))
     inst = make_config(a.config, a.seed)
@@ -34,6 +36,10 @@ def main(argv=None):
             ctx.set_option(rei.REI_OPT_CACHE_INIT, a.cache_init)
         if a.chunk:
             ctx.set_option(rei.REI_OPT_CHUNK, a.chunk)
+        if a.solo_tiles is not None:
+            ctx.set_option(rei.REI_OPT_SOLO_TILES, a.solo_tiles)
+        if a.grid:
+            ctx.set_option(rei.REI_OPT_GRID, a.grid)
         mk = rei.Problem.on_device if a.device_input else rei.Problem
         prob = mk(inst.alphabet, inst.pos, inst.neg, costs=costs, max_cost=a.max_cost,
                   mem_budget=inst.mem_budget)

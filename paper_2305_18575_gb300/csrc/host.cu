@@ -23,10 +23,10 @@
 namespace rei {
 cudaError_t launch_stage(const StageJob *jobs_dev, uint32_t n_jobs, cudaStream_t stream);
 size_t stage_smem_bytes();
-cudaError_t launch_solve(const SolveJob *job_dev, uint32_t grid, uint32_t threads, size_t smem,
+cudaError_t launch_solve(const SolveJob *job, uint32_t grid, uint32_t threads, size_t smem,
                          cudaStream_t stream);
 cudaError_t solve_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm);
-cudaError_t launch_rehash(const SolveJob *job_dev, uint32_t count, uint32_t grid, cudaStream_t stream);
+cudaError_t launch_rehash(const SolveJob *job, uint32_t count, uint32_t grid, cudaStream_t stream);
 size_t solve_smem_bytes(uint32_t W, uint32_t n, uint32_t G, uint32_t max_len, uint32_t seg_cap,
                         bool gt_in_smem, uint32_t warps);
 }  // namespace rei
@@ -537,14 +537,13 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
         hj->solo_tiles = c->opt_solo_tiles >= 0 ? (uint32_t)c->opt_solo_tiles : 8 * warps;
     };
     fill_job();
-    CK(cudaMemcpyAsync(c->solve_job.p, hj, sizeof(SolveJob), cudaMemcpyHostToDevice, c->stream));
-    uint64_t h2d = sg.h2d + sizeof(SolveJob) + sizeof(SolveState), d2h = sg.d2h;
+    uint64_t h2d = sg.h2d + sizeof(SolveState), d2h = sg.d2h;
 
     double ms_search = 0;
     uint32_t search_launches = 0;
     for (int relaunch = 0;; relaunch++) {
         CK(cudaEventRecord(c->ev[0], c->stream));
-        CK(launch_solve((const SolveJob *)c->solve_job.p, grid, threads, smem, c->stream));
+        CK(launch_solve(hj, grid, threads, smem, c->stream));
         CK(cudaEventRecord(c->ev[1], c->stream));
         c->launches++;
         search_launches++;
@@ -569,9 +568,8 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
         if ((s = ensure(c, c->table, 8ull * tslots))) return s;
         CK(cudaMemsetAsync(c->table.p, 0xFF, 8ull * tslots, c->stream));
         fill_job();
-        CK(cudaMemcpyAsync(c->solve_job.p, hj, sizeof(SolveJob), cudaMemcpyHostToDevice, c->stream));
         if (rows) {
-            CK(launch_rehash((const SolveJob *)c->solve_job.p, (uint32_t)rows, (uint32_t)(c->sm_count * 8), c->stream));
+            CK(launch_rehash(hj, (uint32_t)rows, (uint32_t)(c->sm_count * 8), c->stream));
             c->launches++;
         }
         hst->status = ST_RUNNING;
@@ -580,10 +578,17 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
         hst->cmd_seq = 0;
         CK(cudaMemcpyAsync(c->state.p, hst, sizeof(SolveState), cudaMemcpyHostToDevice, c->stream));
         CK(cudaStreamSynchronize(c->stream));
-        h2d += sizeof(SolveJob) + 4;
+        h2d += sizeof(SolveState);
         if (relaunch > 64) return REI_ECUDA;
     }
 
+    if (getenv("REI_PHASES")) {
+        fprintf(stderr, "rei phases: plan %.1f us, solo %.1f us (%llu chunks), team %.1f us (%llu chunks), "
+                "level-end %.1f us (%llu levels); search kernel %.1f us\n", hst->t_phase[0] / 1e3,
+                hst->t_phase[1] / 1e3, (unsigned long long)hst->n_phase[0], hst->t_phase[2] / 1e3,
+                (unsigned long long)hst->n_phase[1], hst->t_phase[3] / 1e3, (unsigned long long)hst->n_phase[2],
+                ms_search * 1e3);
+    }
     if (hst->status == ST_TIMEOUT && getenv("REI_DEBUG")) {
         std::vector<uint32_t> tr(grid);
         cudaMemcpy(tr.data(), c->trace.p, 4ull * grid, cudaMemcpyDeviceToHost);

@@ -30,7 +30,7 @@
 
 namespace rei {
 cudaError_t launch_stage(const StageJob *jobs_dev, uint32_t n_jobs, cudaStream_t stream);
-cudaError_t launch_solve(const SolveJob *job_dev, uint32_t grid, uint32_t threads, size_t smem,
+cudaError_t launch_solve(const SolveJob *job, uint32_t grid, uint32_t threads, size_t smem,
                          cudaStream_t stream);
 cudaError_t solve_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm);
 size_t solve_smem_bytes(uint32_t W, uint32_t n, uint32_t G, uint32_t max_len, uint32_t seg_cap,
@@ -225,7 +225,6 @@ extern "C" rei_status rei_solve_noalloc(const rei_problem *p, void *stream_v, re
     uint32_t *d_pos = (uint32_t *)cv.take(4ull * kMaxWords);
     uint32_t *d_neg = (uint32_t *)cv.take(4ull * kMaxWords);
     uint32_t *d_leaf = (uint32_t *)cv.take(4ull * kMaxWords * 256);
-    SolveJob *d_job = (SolveJob *)cv.take(sizeof(SolveJob));
     const size_t tree_bytes = 2ull * (REI_MAX_COST + 1);
     SolveState *d_st = (SolveState *)cv.take(sizeof(SolveState) + tree_bytes);
     int64_t *d_lvs = (int64_t *)cv.take(8ull * (REI_MAX_COST + 2));
@@ -389,8 +388,7 @@ extern "C" rei_status rei_solve_noalloc(const rei_problem *p, void *stream_v, re
     j.trace = d_trace;
     j.gt_in_smem = gt_smem ? 1 : 0;
     j.solo_tiles = 8 * warps;
-    NA_CK(cudaMemcpyAsync(d_job, &j, sizeof j, cudaMemcpyHostToDevice, stream));
-    NA_CK(launch_solve(d_job, grid, 32 * warps, smem, stream));
+    NA_CK(launch_solve(&j, grid, 32 * warps, smem, stream));
     struct {
         SolveState s;
         uint8_t tree[2 * (REI_MAX_COST + 1)];

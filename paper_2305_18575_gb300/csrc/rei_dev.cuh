@@ -124,6 +124,10 @@ struct SolveState {
     uint32_t cmd, cmd_seq;
     uint32_t c_level, c_size, c_dedup;
     uint64_t c_cs0, c_ce0;
+    // CTA 0's wall time (ns) in: planning, chunks alone, chunks with the grid,
+    // level ends; and how many solo chunks, team chunks, levels
+    uint64_t t_phase[4];
+    uint64_t n_phase[3];
     uint32_t pad[2];
 };
 

@@ -168,65 +168,101 @@ struct Plan {
     uint64_t total;          // index-space size of the level
 };
 
-// Alg. 1 order for level c; only segments with candidates are kept
+// inclusive warp scan of 64-bit values
+__device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, uint32_t lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xFFFFFFFFu, v, d);
+        if (lane >= (uint32_t)d) v += y;
+    }
+    return v;
+}
+
+// Alg. 1 order for level c; only segments with candidates are kept.  Run by
+// one whole warp: lane k describes candidate segment k of each round of 32,
+// the non-empty ones are compacted with a ballot and their starts are a warp
+// scan of the sizes.
 __device__ void plan_level(const SolveJob &J, uint32_t c, const uint32_t *lvs, const uint32_t *lvc, Seg *seg,
                            Plan &P) {
+    const uint32_t lane = threadIdx.x & 31;
     const uint32_t c1 = J.c[0];
     uint32_t ns = 0;
     uint64_t start = 0;
-    auto lv = [&](uint32_t cost, uint32_t &base, uint32_t &cnt) {
-        base = lvs[cost];
-        cnt = lvc[cost];
-    };
-    auto push = [&](uint32_t op, uint32_t tri, uint32_t lb, uint32_t lc, uint32_t rb, uint32_t rc, uint64_t size) {
-        if (size == 0) return;
-        Seg &s = seg[ns++];
-        s.start = start;
-        s.size = size;
-        s.op = op;
-        s.tri = tri;
-        s.lbase = lb;
-        s.lcnt = lc;
-        s.rbase = rb;
-        s.rcnt = rc;
-        s.swap = 0;
-        start += size;
-    };
     if (c == c1) {
-        push(OP_LEAF, 0, 0, J.n_sym, 0, 0, J.n_sym);
-    } else {
-        uint32_t b, n, b2, n2;
-        if (c >= c1 + J.c[1]) {
-            lv(c - J.c[1], b, n);
-            push(OP_OPT, 0, b, n, 0, 0, n);
+        if (lane == 0 && J.n_sym) {
+            Seg &s = seg[0];
+            s.start = 0;
+            s.size = J.n_sym;
+            s.op = OP_LEAF;
+            s.tri = 0;
+            s.lbase = 0;
+            s.lcnt = J.n_sym;
+            s.rbase = 0;
+            s.rcnt = 0;
+            s.swap = 0;
         }
-        if (c >= c1 + J.c[2]) {
-            lv(c - J.c[2], b, n);
-            push(OP_STAR, 0, b, n, 0, 0, n);
+        if (lane == 0) {
+            P.nseg = J.n_sym ? 1 : 0;
+            P.total = J.n_sym;
         }
-        if (c >= 2 * c1 + J.c[3]) {
-            const uint32_t rem = c - J.c[3];
-            for (uint32_t cl = c1; cl + c1 <= rem; cl++) {
-                lv(cl, b, n);
-                lv(rem - cl, b2, n2);
-                push(OP_CAT, 0, b, n, b2, n2, (uint64_t)n * n2);
-                // fewer than 32 right operands: bit-slice over 32 left ones instead
-                if (n * n2 > 0) seg[ns - 1].swap = (n2 < 32 && n > n2) ? 1u : 0u;
-            }
-        }
-        if (c >= 2 * c1 + J.c[4]) {
-            const uint32_t rem = c - J.c[4];
-            for (uint32_t cl = c1; cl + c1 <= rem && cl <= rem - cl; cl++) {
-                lv(cl, b, n);
-                lv(rem - cl, b2, n2);
-                const uint32_t tri = cl == rem - cl;
-                if (tri && n < 2) continue;
-                push(OP_ALT, tri, b, n, b2, n2, (uint64_t)n * n2);
-            }
-        }
+        __syncwarp();
+        return;
     }
-    P.nseg = ns;
-    P.total = start;
+    // candidate segments: [0] ?, [1] *, then concatenation splits, then union splits
+    const int rem_c = (int)c - (int)J.c[3], rem_u = (int)c - (int)J.c[4];
+    const int ncat = rem_c >= 2 * (int)c1 ? rem_c - 2 * (int)c1 + 1 : 0;
+    const int nalt = rem_u >= 2 * (int)c1 ? rem_u / 2 - (int)c1 + 1 : 0;
+    const int total = 2 + ncat + nalt;
+    for (int r0 = 0; r0 < total; r0 += 32) {
+        const int k = r0 + (int)lane;
+        Seg s{};
+        uint64_t size = 0;
+        if (k < total) {
+            if (k < 2) {
+                const uint32_t d = J.c[1 + k];
+                if (c >= c1 + d) {
+                    s.op = k == 0 ? OP_OPT : OP_STAR;
+                    s.lbase = lvs[c - d];
+                    s.lcnt = lvc[c - d];
+                    size = s.lcnt;
+                }
+            } else if (k < 2 + ncat) {
+                const uint32_t cl = c1 + (uint32_t)(k - 2), cr = (uint32_t)rem_c - cl;
+                s.op = OP_CAT;
+                s.lbase = lvs[cl];
+                s.lcnt = lvc[cl];
+                s.rbase = lvs[cr];
+                s.rcnt = lvc[cr];
+                size = (uint64_t)s.lcnt * s.rcnt;
+                // fewer than 32 right operands: bit-slice over 32 left ones instead
+                s.swap = (s.rcnt < 32 && s.lcnt > s.rcnt) ? 1u : 0u;
+            } else {
+                const uint32_t cl = c1 + (uint32_t)(k - 2 - ncat), cr = (uint32_t)rem_u - cl;
+                s.op = OP_ALT;
+                s.tri = cl == cr;
+                s.lbase = lvs[cl];
+                s.lcnt = lvc[cl];
+                s.rbase = lvs[cr];
+                s.rcnt = lvc[cr];
+                size = (s.tri && s.lcnt < 2) ? 0 : (uint64_t)s.lcnt * s.rcnt;
+            }
+        }
+        const bool keep = size > 0;
+        const uint32_t mask = __ballot_sync(0xFFFFFFFFu, keep);
+        const uint64_t incl = warp_incl_scan(size, lane);
+        if (keep) {
+            s.size = size;
+            s.start = start + incl - size;
+            seg[ns + __popc(mask & ((1u << lane) - 1))] = s;
+        }
+        ns += __popc(mask);
+        start += __shfl_sync(0xFFFFFFFFu, incl, 31);
+    }
+    if (lane == 0) {
+        P.nseg = ns;
+        P.total = start;
+    }
+    __syncwarp();
 }
 
 // candidates that are real (the triangle of a cl == cr union) among local
@@ -263,6 +299,7 @@ struct TileCtx {
     uint64_t chunk_start;
     uint32_t W, Ws, n;
     bool dedup;
+    bool grid;  // every CTA works on the chunk (else CTA 0 alone)
 };
 
 // uniqueness insert of candidate xl (chunk-local) whose CS is c[b * 1] (smem)
@@ -278,7 +315,10 @@ __device__ void dedup_insert(const TileCtx &T, const uint32_t *c, uint32_t xl) {
         if (wrote) return;
         uint32_t *dst = J.tmp + (uint64_t)xl * W;
         for (uint32_t b = 0; b < W; b++) dst[b] = c[b];
-        __threadfence();
+        // the row must be visible before the slot that points at it: to every
+        // CTA when the grid works on the chunk, to this CTA when it works alone
+        if (T.grid) __threadfence();
+        else __threadfence_block();
         wrote = true;
     };
     for (uint64_t probe = 0; probe <= J.table_mask; probe++) {
@@ -560,38 +600,50 @@ struct ChunkArgs {
     uint64_t cs0, ce0;
 };
 
+// tiles of the chunk [cs0, ce0) in every segment; run by one whole warp
 __device__ void tile_setup(Shared &S, uint32_t nseg, uint64_t cs0, uint64_t ce0, uint64_t *s_tiles) {
+    const uint32_t lane = threadIdx.x & 31;
     uint64_t t = 0;
-    for (uint32_t s = 0; s < nseg; s++) {
-        const Seg &g = S.seg[s];
-        S.tile_first[s] = t;
-        // chunk [cs0, ce0) intersected with the segment, in segment-local
-        // indices (empty when the segment lies wholly before or after it)
-        const uint64_t g_end = g.start + g.size;
-        const uint64_t a = cs0 <= g.start ? 0 : (cs0 >= g_end ? g.size : cs0 - g.start);
-        const uint64_t e = ce0 <= g.start ? 0 : (ce0 >= g_end ? g.size : ce0 - g.start);
-        SegTile &tl = S.tiles[s];
-        tl.lo = a;
-        tl.hi = e;
-        tl.r0 = 0;
-        tl.nb = 0;
-        if (a >= e) continue;
-        if (g.op == OP_CAT || g.op == OP_ALT) {
-            const uint64_t r0 = a / g.rcnt, r1 = (e - 1) / g.rcnt;
-            tl.r0 = r0;
-            if (g.op == OP_CAT && g.swap) {
-                tl.nb = (r1 - r0 + 1 + 31) / 32;
-                t += (uint64_t)g.rcnt * tl.nb;
-            } else {
-                tl.nb = (g.rcnt + 31) / 32;
-                t += (r1 - r0 + 1) * tl.nb;
+    for (uint32_t r0 = 0; r0 < nseg; r0 += 32) {
+        const uint32_t s = r0 + lane;
+        uint64_t tiles = 0;
+        if (s < nseg) {
+            const Seg &g = S.seg[s];
+            // chunk [cs0, ce0) intersected with the segment, in segment-local
+            // indices (empty when the segment lies wholly before or after it)
+            const uint64_t g_end = g.start + g.size;
+            const uint64_t a = cs0 <= g.start ? 0 : (cs0 >= g_end ? g.size : cs0 - g.start);
+            const uint64_t e = ce0 <= g.start ? 0 : (ce0 >= g_end ? g.size : ce0 - g.start);
+            SegTile &tl = S.tiles[s];
+            tl.lo = a;
+            tl.hi = e;
+            tl.r0 = 0;
+            tl.nb = 0;
+            if (a < e) {
+                if (g.op == OP_CAT || g.op == OP_ALT) {
+                    const uint64_t r0w = a / g.rcnt, r1 = (e - 1) / g.rcnt;
+                    tl.r0 = r0w;
+                    if (g.op == OP_CAT && g.swap) {
+                        tl.nb = (r1 - r0w + 1 + 31) / 32;
+                        tiles = (uint64_t)g.rcnt * tl.nb;
+                    } else {
+                        tl.nb = (g.rcnt + 31) / 32;
+                        tiles = (r1 - r0w + 1) * tl.nb;
+                    }
+                } else {
+                    tiles = (e - a + 31) / 32;
+                }
             }
-        } else {
-            t += (e - a + 31) / 32;
         }
+        const uint64_t incl = warp_incl_scan(tiles, lane);
+        if (s < nseg) S.tile_first[s] = t + incl - tiles;
+        t += __shfl_sync(0xFFFFFFFFu, incl, 31);
     }
-    S.tile_first[nseg] = t;
-    *s_tiles = t;
+    if (lane == 0) {
+        S.tile_first[nseg] = t;
+        *s_tiles = t;
+    }
+    __syncwarp();
 }
 
 // the team's barrier: the grid barrier when every CTA works on the chunk,
@@ -679,13 +731,13 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
     const bool dedup = a.dedup != 0;
 
     if (!tiles_ready) {
-        if (tid == 0) tile_setup(S, a.nseg, a.cs0, a.ce0, s_tiles);
+        if (wid == 0) tile_setup(S, a.nseg, a.cs0, a.ce0, s_tiles);
         __syncthreads();
     }
 
     // ---- phase A: build, precision, uniqueness insert
     {
-        TileCtx TC{&J, st, &S, a.cs0, W, Ws, n, dedup};
+        TileCtx TC{&J, st, &S, a.cs0, W, Ws, n, dedup, full};
         const uint64_t ntiles = *s_tiles;
         const uint64_t gw = (uint64_t)team_r * nwarps + wid, nw = (uint64_t)team_n * nwarps;
         uint32_t s = 0;
@@ -852,8 +904,7 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
-__global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
-    const SolveJob &J = *jobp;
+__global__ void __launch_bounds__(256, 2) k_solve(const __grid_constant__ SolveJob J) {
     SolveState *st = J.st;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     __shared__ Plan s_plan;
@@ -956,7 +1007,7 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
                 S.lvc[c] = (uint32_t)ld_relaxed_u64(&J.lvl_count[c]);
             }
             __syncthreads();
-            if (tid == 0) plan_level(J, a.level, S.lvs, S.lvc, S.seg, s_plan);
+            if (wid == 0) plan_level(J, a.level, S.lvs, S.lvc, S.seg, s_plan);
             __syncthreads();
             a.nseg = s_plan.nseg;
             if (process_chunk(J, st, S, a, true, false, bar_epoch, &s_tiles, s_red, &s_found, &s_npend, wm,
@@ -995,7 +1046,10 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
     __syncthreads();
 
     bool found = false;
+    // per-phase wall time of CTA 0 (ns): plan, solo chunk, team chunk, level end
+    unsigned long long tm[4] = {0, 0, 0, 0}, tcnt[3] = {0, 0, 0};
     for (;;) {
+        const unsigned long long t_it = globaltimer_ns();
         const uint32_t status = L.status, level = L.level, size = L.size, full = L.full, otf = L.otf;
         const uint64_t pos = L.chunk_pos;
         __syncthreads();
@@ -1006,7 +1060,7 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
             __syncthreads();
             continue;
         }
-        if (tid == 0) plan_level(J, level, S.lvs, S.lvc, S.seg, s_plan);
+        if (wid == 0) plan_level(J, level, S.lvs, S.lvc, S.seg, s_plan);
         __syncthreads();
         const uint32_t nseg = s_plan.nseg;
         const uint64_t T = s_plan.total;
@@ -1050,6 +1104,8 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
                 L.chunk_pos = 0;
                 L.full = 0;
                 L.status = next_status;
+                tm[3] += globaltimer_ns() - t_it;
+                tcnt[2]++;
             }
             __syncthreads();
             continue;
@@ -1077,9 +1133,11 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
         if (C == 0) C = 1;  // unreachable with room >= 1; guards the loop
         ChunkArgs a{level, size, dedup ? 1u : 0u, nseg, pos, pos + C};
         // alone when the chunk is a few tiles per warp of this CTA
-        if (tid == 0) tile_setup(S, nseg, a.cs0, a.ce0, &s_tiles);
+        if (wid == 0) tile_setup(S, nseg, a.cs0, a.ce0, &s_tiles);
         __syncthreads();
         const bool team = s_tiles > (uint64_t)J.solo_tiles;
+        const unsigned long long t_chunk = globaltimer_ns();
+        if (tid == 0) tm[0] += t_chunk - t_it;
         if (team) {
             if (tid == 0) {
                 st->c_level = a.level;
@@ -1092,6 +1150,10 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
         }
         const int r = process_chunk(J, st, S, a, team, true, bar_epoch, &s_tiles, s_red, &s_found, &s_npend, wm, &L);
         if (r < 0) return;
+        if (tid == 0) {
+            tm[team ? 2 : 1] += globaltimer_ns() - t_chunk;
+            tcnt[team ? 1 : 0]++;
+        }
         if (r == 1) {
             found = true;
             break;
@@ -1136,13 +1198,14 @@ __global__ void __launch_bounds__(256, 2) k_solve(const SolveJob *jobp) {
         st->candidates = L.candidates;
         st->unique_done = L.unique_done;
         for (int k = 0; k < 5; k++) st->cand_op[k] = L.cand_op[k];
+        for (int k = 0; k < 4; k++) st->t_phase[k] += tm[k];
+        for (int k = 0; k < 3; k++) st->n_phase[k] += tcnt[k];
     }
     publish(st, CMD_EXIT);
 }
 
 // rebuild the uniqueness table after the cache grew (all entries are distinct)
-__global__ void k_rehash(const SolveJob *jobp, uint32_t count) {
-    const SolveJob &J = *jobp;
+__global__ void k_rehash(const __grid_constant__ SolveJob J, uint32_t count) {
     const uint32_t W = J.W;
     for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count;
          k += (uint64_t)gridDim.x * blockDim.x) {
@@ -1169,11 +1232,11 @@ size_t solve_smem_bytes(uint32_t W, uint32_t n, uint32_t G, uint32_t max_len, ui
     return b;
 }
 
-cudaError_t launch_solve(const SolveJob *job_dev, uint32_t grid, uint32_t threads, size_t smem,
+cudaError_t launch_solve(const SolveJob *job, uint32_t grid, uint32_t threads, size_t smem,
                          cudaStream_t stream) {
     cudaError_t e = cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    void *args[] = {(void *)&job_dev};
+    void *args[] = {(void *)job};
     return cudaLaunchCooperativeKernel((const void *)k_solve, dim3(grid), dim3(threads), args, smem, stream);
 }
 
@@ -1183,8 +1246,8 @@ cudaError_t solve_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_solve, (int)threads, smem);
 }
 
-cudaError_t launch_rehash(const SolveJob *job_dev, uint32_t count, uint32_t grid, cudaStream_t stream) {
-    k_rehash<<<grid, 256, 0, stream>>>(job_dev, count);
+cudaError_t launch_rehash(const SolveJob *job, uint32_t count, uint32_t grid, cudaStream_t stream) {
+    k_rehash<<<grid, 256, 0, stream>>>(*job, count);
     return cudaGetLastError();
 }
 
