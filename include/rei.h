@@ -303,7 +303,7 @@ void rei_server_destroy(rei_server *srv);
  * words of a CS (see the memory rule above), cap = floor(mem_budget /
  * (4*W + 28)) languages must fit, with their uniqueness table and a chunk
  * workspace, in what the staged problem leaves of the array (about 61 MiB;
- * e.g. cap up to about 1.2 million languages at W = 2).  Example bytes are
+ * e.g. cap up to about 1.3 million languages at W = 2).  Example bytes are
  * limited to 1 MiB, examples to 65535 and guide-table pairs to 262144.  A
  * problem beyond these limits returns REI_ESCRATCH (nothing is truncated);
  * other errors as rei_solve_problem. */

@@ -438,6 +438,23 @@ class Context:
         rows = [list(cs[i * W:(i + 1) * W]) for i in range(k)]
         return rows, list(op[:k]), list(lf[:k]), list(rt[:k]), list(ls), list(lc)
 
+    def solve_batch(self, probs: Sequence[Problem], warps_per_cta: int = 0) -> List[Result]:
+        """rei_solve_batch over `probs` (one staging and one search launch);
+        warps_per_cta 0 lets the library autotune the CTA shape."""
+        n = len(probs)
+        arr = (rei_problem * max(n, 1))(*[p.p for p in probs])
+        bufs = [_OutBuf() for _ in range(n)]
+        outs = (rei_result * max(n, 1))(*[b.res for b in bufs])
+        tune = rei_tune(1, warps_per_cta, 0) if warps_per_cta else None
+        s = rei_solve_batch(self.h, arr, n, outs, tune)
+        if s != REI_OK:
+            raise RuntimeError(f"rei_solve_batch: {STATUS_NAMES.get(s, s)}")
+        res = []
+        for b, o in zip(bufs, outs):
+            b.res = o
+            res.append(b.result(o.status))
+        return res
+
     def solve_keep(self, prob: Problem) -> Result:
         """solve_problem with the cache kept for cache_dump()."""
         self.set_option(REI_OPT_KEEP_CACHE, 1)

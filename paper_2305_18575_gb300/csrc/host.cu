@@ -21,6 +21,9 @@
 #include "rei_dev.cuh"
 
 namespace rei {
+cudaError_t launch_solve_batch(const BatchJob *jobs_dev, const BatchArgs *args, uint32_t grid, uint32_t threads,
+                               size_t smem, cudaStream_t stream);
+cudaError_t solve_batch_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm);
 cudaError_t launch_stage(const StageJob *jobs_dev, uint32_t n_jobs, cudaStream_t stream);
 size_t stage_smem_bytes();
 cudaError_t launch_solve(const SolveJob *job, uint32_t grid, uint32_t threads, size_t smem,
@@ -64,7 +67,16 @@ struct rei_ctx {
     uint32_t pair_cap = 1u << 16;
     // search
     DevBuf cs, bp_op, bp_l, bp_r, table, tmp, pending, slotpos, bitmap, blk, lvl_start, lvl_count,
-        state, solve_job, tstack, trace;
+        state, solve_job, tstack, trace, used;
+    bool table_clean = false;  // the search kernel leaves the table empty after a normal end
+    // batched form
+    DevBuf b_in, b_sjobs, b_sinfo, b_stage, b_jobs, b_out, b_tree, b_queue;
+    DevBuf s_cs, s_bp_op, s_bp_l, s_bp_r, s_used, s_table, s_tmp, s_pend, s_slotpos, s_bitmap, s_blk, s_lvl,
+        s_state, s_tstack;
+    uint64_t slot_rows = 0, slot_cs_words = 0, slot_table = 0, slot_tmp_words = 0, slot_chunk = 0;
+    uint32_t slot_count = 0;
+    bool slots_clean = false;
+    int batch_warps = 0;  // autotuned warps per CTA of the batched launch (0 = not yet)
     // pinned host scratch
     uint8_t *h_pin = nullptr;
     size_t h_pin_bytes = 0;
@@ -443,7 +455,8 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
         // rows a previous solve already allocated (up to 1 Mi, so that the
         // table this solve clears stays small)
         const uint64_t have = std::min<uint64_t>({(uint64_t)(c->cs.bytes / (4ull * W)), (uint64_t)(c->bp_l.bytes / 4),
-                                                  (uint64_t)(c->bp_r.bytes / 4), (uint64_t)c->bp_op.bytes});
+                                                  (uint64_t)(c->bp_r.bytes / 4), (uint64_t)c->bp_op.bytes,
+                                                  (uint64_t)(c->used.bytes / 4)});
         cache_alloc = std::max<uint64_t>(cache_alloc, std::min<uint64_t>(have, 1ull << 20));
     }
     cache_alloc = std::max<uint64_t>(1, std::min<uint64_t>(cache_alloc, cap));
@@ -457,7 +470,12 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
     if ((s = ensure(c, c->bp_op, cache_alloc))) return s;
     if ((s = ensure(c, c->bp_l, 4ull * cache_alloc))) return s;
     if ((s = ensure(c, c->bp_r, 4ull * cache_alloc))) return s;
-    if ((s = ensure(c, c->table, 8ull * tslots))) return s;
+    if ((s = ensure(c, c->used, 4ull * cache_alloc))) return s;
+    {
+        void *before = c->table.p;
+        if ((s = ensure(c, c->table, 8ull * tslots))) return s;
+        if (c->table.p != before) c->table_clean = false;
+    }
     if ((s = ensure(c, c->tmp, 4ull * W * chunk_max))) return s;
     if ((s = ensure(c, c->pending, 4ull * chunk_max))) return s;
     if ((s = ensure(c, c->slotpos, 4ull * chunk_max))) return s;
@@ -472,11 +490,14 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
     if ((s = ensure(c, c->trace, 4ull * grid))) return s;
     if ((s = ensure_pinned(c, sizeof(SolveJob) + sizeof(SolveState) + tree_bytes))) return s;
 
-    CK(cudaMemsetAsync(c->table.p, 0xFF, 8ull * tslots, c->stream));
-    CK(cudaMemsetAsync(c->bitmap.p, 0, 4ull * ((chunk_max + 31) / 32), c->stream));
+    if (!c->table_clean) {
+        // a new table, or the last search ended abnormally: clear it all once
+        CK(cudaMemsetAsync(c->table.p, 0xFF, c->table.bytes, c->stream));
+        CK(cudaMemsetAsync(c->bitmap.p, 0, c->bitmap.bytes, c->stream));
+    }
+    c->table_clean = false;
     CK(cudaMemsetAsync(c->lvl_start.p, 0, 8ull * (max_cost + 2), c->stream));
     CK(cudaMemsetAsync(c->lvl_count.p, 0, 8ull * (max_cost + 2), c->stream));
-    CK(cudaStreamSynchronize(c->stream));
 
     SolveState *hst = (SolveState *)(c->h_pin + sizeof(SolveJob));
     memset(hst, 0, sizeof(SolveState));
@@ -517,6 +538,7 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
         hj->bp_op = (uint8_t *)c->bp_op.p;
         hj->bp_l = (uint32_t *)c->bp_l.p;
         hj->bp_r = (uint32_t *)c->bp_r.p;
+        hj->used = (uint32_t *)c->used.p;
         hj->cache_alloc = cache_alloc;
         hj->table = (unsigned long long *)c->table.p;
         hj->table_mask = tslots - 1;
@@ -563,10 +585,11 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
         if ((s = grow_keep(c, c->bp_op, want, rows))) return s;
         if ((s = grow_keep(c, c->bp_l, 4ull * want, 4ull * rows))) return s;
         if ((s = grow_keep(c, c->bp_r, 4ull * want, 4ull * rows))) return s;
+        if ((s = grow_keep(c, c->used, 4ull * want, 0))) return s;
         cache_alloc = want;
         tslots = table_slots(cache_alloc);
         if ((s = ensure(c, c->table, 8ull * tslots))) return s;
-        CK(cudaMemsetAsync(c->table.p, 0xFF, 8ull * tslots, c->stream));
+        CK(cudaMemsetAsync(c->table.p, 0xFF, c->table.bytes, c->stream));
         fill_job();
         if (rows) {
             CK(launch_rehash(hj, (uint32_t)rows, (uint32_t)(c->sm_count * 8), c->stream));
@@ -600,6 +623,7 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
                 (unsigned long long)hst->found);
         for (auto &kv : hist) fprintf(stderr, "rei:   %u CTAs last passed epoch %u site %u\n", kv.second, kv.first >> 8, kv.first & 255);
     }
+    c->table_clean = hst->status == ST_FOUND || hst->status == ST_NOT_FOUND || hst->status == ST_OOM;
     c->last_valid = true;
     c->last_W = W;
     c->last_size = hst->size;
@@ -693,7 +717,10 @@ void rei_ctx_destroy(rei_ctx *c) {
                       &c->len_start, &c->gt_off, &c->gt_pair, &c->pos, &c->neg, &c->leaf, &c->cs,
                       &c->bp_op, &c->bp_l, &c->bp_r, &c->table, &c->tmp, &c->pending, &c->slotpos,
                       &c->bitmap, &c->blk, &c->lvl_start, &c->lvl_count, &c->state, &c->solve_job,
-                      &c->tstack, &c->trace};
+                      &c->tstack, &c->trace, &c->used, &c->b_in, &c->b_sjobs, &c->b_sinfo, &c->b_stage,
+                      &c->b_jobs, &c->b_out, &c->b_tree, &c->b_queue, &c->s_cs, &c->s_bp_op, &c->s_bp_l,
+                      &c->s_bp_r, &c->s_used, &c->s_table, &c->s_tmp, &c->s_pend, &c->s_slotpos, &c->s_bitmap,
+                      &c->s_blk, &c->s_lvl, &c->s_state, &c->s_tstack};
     for (DevBuf *b : bufs) dev_free(c, *b);
     cudaStreamSynchronize(c->stream);
     if (c->h_pin) cudaFreeHost(c->h_pin);
@@ -804,20 +831,352 @@ rei_status rei_cache_dump(rei_ctx *c, uint32_t *cs, uint8_t *op, uint32_t *left,
     return REI_OK;
 }
 
-// ---- batched form (first version: problems in sequence on the context) ----
+// ---- batched form: one staging launch and one persistent search launch ----
+
+}  // extern "C"
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct BatchPlan {
+    std::vector<uint32_t> idx;          // outs index of every problem in the launch
+    std::vector<size_t> off_in, off_offs, off_stage;
+    std::vector<uint32_t> n_bound, g_bound, l_bound;
+    size_t in_bytes = 0, stage_bytes = 0;
+};
+
+// Run problems `sel` of `probs` in one batched launch with `warps` warps per
+// CTA.  Problems that outgrow their slot are re-solved alone afterwards.
+rei_status run_batch(rei_ctx *c, const rei_problem *probs, const std::vector<uint32_t> &sel, rei_result *outs,
+                     uint32_t warps, double *kernel_ms) {
+    const uint32_t nb = (uint32_t)sel.size();
+    if (kernel_ms) *kernel_ms = 0;
+    if (nb == 0) return REI_OK;
+    BatchPlan P;
+    // host-side bounds of every problem's staged sizes (exact upper bounds)
+    for (uint32_t t = 0; t < nb; t++) {
+        const rei_problem &p = probs[sel[t]];
+        const uint32_t n_str = p.n_pos + p.n_neg;
+        uint64_t occ = 1, pairs = 1;
+        uint32_t maxl = 0;
+        for (uint32_t k = 0; k < n_str; k++) {
+            const uint64_t L = p.offsets[k + 1] - p.offsets[k];
+            occ += L * (L + 1) / 2;
+            for (uint64_t len = 1; len <= L; len++) pairs += (L - len + 1) * (len + 1);
+            maxl = std::max<uint32_t>(maxl, (uint32_t)L);
+        }
+        const uint32_t nbd = (uint32_t)std::min<uint64_t>(occ, kMaxIC);
+        P.n_bound.push_back(nbd);
+        P.g_bound.push_back((uint32_t)std::min<uint64_t>(pairs, (uint64_t)nbd * (maxl + 1)));
+        P.l_bound.push_back(maxl);
+        P.off_offs.push_back(P.in_bytes);
+        P.in_bytes = align256(P.in_bytes + 4ull * (n_str + 1));
+        P.off_in.push_back(P.in_bytes);
+        P.in_bytes = align256(P.in_bytes + (n_str ? p.offsets[n_str] : 0) + 1);
+        P.off_stage.push_back(P.stage_bytes);
+        P.stage_bytes += align256(8ull * nbd) + align256(4ull * (maxl + 2)) + align256(4ull * (nbd + 1)) +
+                         align256(4ull * P.g_bound.back()) + 2 * align256(4ull * kMaxWords) +
+                         align256(4ull * kMaxWords * p.n_sym);
+    }
+    rei_status s;
+    const size_t tree_bytes = 2ull * (REI_MAX_COST + 1);
+    if ((s = ensure(c, c->b_in, P.in_bytes))) return s;
+    if ((s = ensure(c, c->b_stage, P.stage_bytes))) return s;
+    if ((s = ensure(c, c->b_sjobs, sizeof(StageJob) * nb))) return s;
+    if ((s = ensure(c, c->b_sinfo, sizeof(StageInfo) * nb))) return s;
+    if ((s = ensure(c, c->b_jobs, sizeof(BatchJob) * nb))) return s;
+    if ((s = ensure(c, c->b_out, sizeof(BatchOut) * nb))) return s;
+    if ((s = ensure(c, c->b_tree, tree_bytes * nb))) return s;
+    if ((s = ensure(c, c->b_queue, 16))) return s;
+    const size_t host_bytes = std::max(P.in_bytes, std::max(sizeof(StageJob), sizeof(BatchJob)) * nb) +
+                              (sizeof(StageInfo) + sizeof(BatchOut) + tree_bytes) * nb + 4096;
+    if ((s = ensure_pinned(c, host_bytes))) return s;
+    CK(cudaStreamSynchronize(c->stream));
+    uint8_t *hp = c->h_pin;
+    // inputs: one upload
+    for (uint32_t t = 0; t < nb; t++) {
+        const rei_problem &p = probs[sel[t]];
+        const uint32_t n_str = p.n_pos + p.n_neg;
+        if (n_str) memcpy(hp + P.off_offs[t], p.offsets, 4ull * (n_str + 1));
+        else memset(hp + P.off_offs[t], 0, 4);
+        if (n_str && p.offsets[n_str]) memcpy(hp + P.off_in[t], p.bytes, p.offsets[n_str]);
+    }
+    CK(cudaMemcpyAsync(c->b_in.p, hp, P.in_bytes, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    // staging jobs
+    StageJob *sj = (StageJob *)hp;
+    uint8_t *din = (uint8_t *)c->b_in.p, *dst = (uint8_t *)c->b_stage.p;
+    std::vector<uint32_t *> ws(nb), wl(nb), ls(nb), go(nb), gp(nb), pm(nb), nm(nb), lf(nb);
+    for (uint32_t t = 0; t < nb; t++) {
+        const rei_problem &p = probs[sel[t]];
+        StageJob &j = sj[t];
+        memset(&j, 0, sizeof j);
+        j.bytes = din + P.off_in[t];
+        j.offs = (const uint32_t *)(din + P.off_offs[t]);
+        j.n_pos = p.n_pos;
+        j.n_neg = p.n_neg;
+        memcpy(j.alphabet, p.alphabet, p.n_sym);
+        j.n_sym = p.n_sym;
+        j.info = (StageInfo *)c->b_sinfo.p + t;
+        uint8_t *q = dst + P.off_stage[t];
+        ws[t] = (uint32_t *)q;
+        wl[t] = ws[t] + P.n_bound[t];
+        q += align256(8ull * P.n_bound[t]);
+        ls[t] = (uint32_t *)q;
+        q += align256(4ull * (P.l_bound[t] + 2));
+        go[t] = (uint32_t *)q;
+        q += align256(4ull * (P.n_bound[t] + 1));
+        gp[t] = (uint32_t *)q;
+        q += align256(4ull * P.g_bound[t]);
+        pm[t] = (uint32_t *)q;
+        q += align256(4ull * kMaxWords);
+        nm[t] = (uint32_t *)q;
+        q += align256(4ull * kMaxWords);
+        lf[t] = (uint32_t *)q;
+        j.word_start = ws[t];
+        j.word_len = wl[t];
+        j.len_start = ls[t];
+        j.gt_off = go[t];
+        j.gt_pair = gp[t];
+        j.pair_cap = P.g_bound[t];
+        j.pos_mask = pm[t];
+        j.neg_mask = nm[t];
+        j.leaf = lf[t];
+    }
+    CK(cudaMemcpyAsync(c->b_sjobs.p, sj, sizeof(StageJob) * nb, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->b_sinfo.p, 0, sizeof(StageInfo) * nb, c->stream));
+    CK(launch_stage((const StageJob *)c->b_sjobs.p, nb, c->stream));
+    c->launches++;
+    StageInfo *si = (StageInfo *)(hp + std::max(sizeof(StageJob), sizeof(BatchJob)) * nb);
+    CK(cudaMemcpyAsync(si, c->b_sinfo.p, sizeof(StageInfo) * nb, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+
+    // search jobs; the launch's shared memory fits the largest problem
+    std::vector<uint32_t> live;
+    uint32_t wmax = 1;
+    size_t smem = 0;
+    BatchJob *bj = (BatchJob *)hp;  // reuses the staging-job area (already uploaded)
+    for (uint32_t t = 0; t < nb; t++) {
+        const rei_problem &p = probs[sel[t]];
+        const StageInfo &I = si[t];
+        rei_result &o = outs[sel[t]];
+        o.stats.n_ic = I.n;
+        o.stats.words = I.W;
+        o.stats.max_len = I.max_len;
+        o.stats.guide_pairs = I.G;
+        if (I.status != SE_OK) {
+            o.status = REI_EINVAL;
+            continue;
+        }
+        BatchJob &b = bj[live.size()];
+        memset(&b, 0, sizeof b);
+        SolveJob &J = b.job;
+        J.n = I.n;
+        J.W = I.W;
+        J.G = I.G;
+        J.n_sym = p.n_sym;
+        J.max_len = I.max_len;
+        J.gt_off = go[t];
+        J.gt_pair = gp[t];
+        J.len_start = ls[t];
+        J.pos_mask = pm[t];
+        J.neg_mask = nm[t];
+        J.leaf = lf[t];
+        J.leaf_stride = kMaxWords;
+        J.n_pos_set = I.n_pos_set;
+        J.pos_eps = I.pos_eps;
+        J.neg_eps = I.neg_eps;
+        J.c[0] = p.costs.c_sym;
+        J.c[1] = p.costs.c_opt;
+        J.c[2] = p.costs.c_star;
+        J.c[3] = p.costs.c_cat;
+        J.c[4] = p.costs.c_alt;
+        J.max_cost = p.max_cost;
+        J.max_errors = p.max_errors;
+        J.flags = p.flags & ~REI_F_DEVICE_INPUT;
+        J.cap = budget_cap(p.mem_budget, I.n);
+        J.seg_cap = 2 * p.max_cost + 4;
+        J.gt_in_smem = 4ull * (I.n + 1 + I.G + I.max_len + 2) <= 48 * 1024;
+        b.tree = (uint8_t *)c->b_tree.p + tree_bytes * live.size();
+        b.out = (BatchOut *)c->b_out.p + live.size();
+        smem = std::max(smem, solve_smem_bytes(I.W, I.n, I.G, I.max_len, J.seg_cap, J.gt_in_smem, warps));
+        wmax = std::max(wmax, I.W);
+        live.push_back(t);
+    }
+    const uint32_t nl = (uint32_t)live.size();
+    if (nl == 0) return REI_OK;
+    if (smem > c->smem_optin) return REI_EINVAL;
+    int bps = 0;
+    CK(solve_batch_occupancy(32 * warps, smem, &bps));
+    if (bps < 1) return REI_ECUDA;
+    const uint32_t slots = std::min<uint32_t>(nl, (uint32_t)(c->sm_count * bps));
+
+    // per-slot memory (grow-only; tables and bitmaps kept empty between uses)
+    const uint64_t rows = 1ull << 18, chunk = 1ull << 14;
+    const uint64_t cs_words = rows * wmax, tmp_words = chunk * wmax;
+    const uint64_t tslots = pow2_at_least(2 * (rows + chunk));
+    bool fresh = !c->slots_clean || c->slot_count < slots || c->slot_rows != rows || c->slot_cs_words < cs_words ||
+                 c->slot_table != tslots || c->slot_tmp_words < tmp_words || c->slot_chunk != chunk;
+    if (fresh) {
+        const uint64_t sl = std::max<uint32_t>(slots, c->slot_count);
+        const uint64_t csw = std::max(cs_words, c->slot_cs_words), tw = std::max(tmp_words, c->slot_tmp_words);
+        if ((s = ensure(c, c->s_cs, 4 * sl * csw))) return s;
+        if ((s = ensure(c, c->s_bp_op, sl * rows))) return s;
+        if ((s = ensure(c, c->s_bp_l, 4 * sl * rows))) return s;
+        if ((s = ensure(c, c->s_bp_r, 4 * sl * rows))) return s;
+        if ((s = ensure(c, c->s_used, 4 * sl * rows))) return s;
+        if ((s = ensure(c, c->s_table, 8 * sl * tslots))) return s;
+        if ((s = ensure(c, c->s_tmp, 4 * sl * tw))) return s;
+        if ((s = ensure(c, c->s_pend, 4 * sl * chunk))) return s;
+        if ((s = ensure(c, c->s_slotpos, 4 * sl * chunk))) return s;
+        if ((s = ensure(c, c->s_bitmap, 4 * sl * ((chunk + 31) / 32)))) return s;
+        if ((s = ensure(c, c->s_blk, 4 * sl))) return s;
+        if ((s = ensure(c, c->s_lvl, 8 * sl * 2 * (kMaxCost + 2)))) return s;
+        if ((s = ensure(c, c->s_state, sizeof(SolveState) * sl))) return s;
+        if ((s = ensure(c, c->s_tstack, 16 * sl * (kMaxCost + 2)))) return s;
+        CK(cudaMemsetAsync(c->s_table.p, 0xFF, 8 * sl * tslots, c->stream));
+        CK(cudaMemsetAsync(c->s_bitmap.p, 0, 4 * sl * ((chunk + 31) / 32), c->stream));
+        c->slot_count = (uint32_t)sl;
+        c->slot_rows = rows;
+        c->slot_cs_words = csw;
+        c->slot_table = tslots;
+        c->slot_tmp_words = tw;
+        c->slot_chunk = chunk;
+    }
+    BatchArgs A{};
+    A.slot.cs = (uint32_t *)c->s_cs.p;
+    A.slot.bp_op = (uint8_t *)c->s_bp_op.p;
+    A.slot.bp_l = (uint32_t *)c->s_bp_l.p;
+    A.slot.bp_r = (uint32_t *)c->s_bp_r.p;
+    A.slot.used = (uint32_t *)c->s_used.p;
+    A.slot.table = (unsigned long long *)c->s_table.p;
+    A.slot.tmp = (uint32_t *)c->s_tmp.p;
+    A.slot.pending = (uint32_t *)c->s_pend.p;
+    A.slot.slotpos = (uint32_t *)c->s_slotpos.p;
+    A.slot.bitmap = (uint32_t *)c->s_bitmap.p;
+    A.slot.blk = (uint32_t *)c->s_blk.p;
+    A.slot.lvl = (int64_t *)c->s_lvl.p;
+    A.slot.state = (SolveState *)c->s_state.p;
+    A.slot.tstack = (uint32_t *)c->s_tstack.p;
+    A.slot.rows = rows;
+    A.slot.cs_words = c->slot_cs_words;
+    A.slot.table_slots = tslots;
+    A.slot.tmp_words = c->slot_tmp_words;
+    A.slot.chunk = chunk;
+    A.n = nl;
+    A.queue = (uint32_t *)c->b_queue.p;
+    CK(cudaMemcpyAsync(c->b_jobs.p, bj, sizeof(BatchJob) * nl, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->b_queue.p, 0, 16, c->stream));
+    c->slots_clean = false;
+    CK(cudaEventRecord(c->ev[0], c->stream));
+    CK(launch_solve_batch((const BatchJob *)c->b_jobs.p, &A, slots, 32 * warps, smem, c->stream));
+    CK(cudaEventRecord(c->ev[1], c->stream));
+    c->launches++;
+    BatchOut *bo = (BatchOut *)(hp + std::max(sizeof(StageJob), sizeof(BatchJob)) * nb + sizeof(StageInfo) * nb);
+    uint8_t *tr = (uint8_t *)(bo + nb);
+    CK(cudaMemcpyAsync(bo, c->b_out.p, sizeof(BatchOut) * nl, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(tr, c->b_tree.p, tree_bytes * nl, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->slots_clean = true;
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+    if (kernel_ms) *kernel_ms = ms;
+
+    std::vector<uint32_t> redo;
+    for (uint32_t k = 0; k < nl; k++) {
+        const uint32_t t = live[k];
+        const rei_problem &p = probs[sel[t]];
+        rei_result &o = outs[sel[t]];
+        const BatchOut &b = bo[k];
+        if (b.status == ST_NEED_MEM) {
+            redo.push_back(sel[t]);
+            continue;
+        }
+        o.stats.candidates = b.candidates;
+        o.stats.unique = b.unique;
+        o.stats.levels = b.levels;
+        for (int q = 0; q < 5; q++) o.stats.cand_op[q] = b.cand_op[q];
+        o.stats.star_pairs = o.stats.guide_pairs - o.stats.n_ic;
+        o.stats.ms_search_kernel = b.ns / 1e6;
+        o.stats.ms_total = b.ns / 1e6;
+        o.stats.launches = 2;
+        o.stats.search_launches = 1;
+        o.stats.grid = slots;
+        switch (b.status) {
+        case ST_FOUND: o.status = REI_OK; break;
+        case ST_NOT_FOUND: o.status = REI_NOT_FOUND; break;
+        case ST_OOM: o.status = REI_OOM; break;
+        default: o.status = REI_ECUDA; break;
+        }
+        o.regex_len = o.tree_len = 0;
+        if (o.status == REI_OK) {
+            o.cost = b.cost;
+            if (write_outputs(&o, tr + tree_bytes * k, b.tree_len, p.alphabet) != REI_OK) o.status = REI_EBUFSZ;
+        }
+    }
+    for (uint32_t i : redo) {
+        const rei_status r = solve_one(c, &probs[i], &outs[i]);
+        if (r != REI_OK && r != REI_NOT_FOUND && r != REI_OOM) outs[i].status = r;
+    }
+    return REI_OK;
+}
+
+}  // namespace
+
+extern "C" {
 
 rei_status rei_solve_batch(rei_ctx *c, const rei_problem *probs, uint32_t n, rei_result *outs,
                            const rei_tune *tune) {
     if (!c || (n && (!probs || !outs))) return REI_EINVAL;
-    (void)tune;
+    std::lock_guard<std::mutex> g(c->mu);
+    if (cudaSetDevice(c->device) != cudaSuccess) return REI_ECUDA;
+    const double t0 = now_ms();
+    std::vector<uint32_t> sel;
     for (uint32_t i = 0; i < n; i++) {
-        rei_status s = rei_solve_problem(c, &probs[i], &outs[i]);
-        if (s != REI_OK && s != REI_NOT_FOUND && s != REI_OOM) {
-            if (s == REI_EINVAL || s == REI_EBUFSZ) continue;
-            return s;
+        memset(&outs[i].stats, 0, sizeof(outs[i].stats));
+        outs[i].status = REI_EINVAL;
+        outs[i].cost = 0;
+        outs[i].regex_len = outs[i].tree_len = 0;
+        if (check_problem(&probs[i]) != REI_OK) continue;
+        if (probs[i].flags & REI_F_DEVICE_INPUT) {
+            // device-resident inputs: solved alone (the batch packs host inputs)
+            const rei_status r = solve_one(c, &probs[i], &outs[i]);
+            if (r != REI_OK && r != REI_NOT_FOUND && r != REI_OOM) outs[i].status = r;
+            continue;
+        }
+        sel.push_back(i);
+    }
+    uint32_t warps = tune && tune->warps_per_cta ? tune->warps_per_cta : (uint32_t)c->batch_warps;
+    size_t done = 0;
+    if (warps == 0) {
+        // autotune the CTA shape on two samples of the batch (4 or 8 warps),
+        // each large enough to fill the GPU; results are exact either way
+        warps = 8;
+        const size_t sample = (size_t)std::max(1, c->sm_count);
+        if (sel.size() >= 3 * sample) {
+            double rate[2] = {0, 0};
+            const uint32_t cand[2] = {8, 4};
+            for (int k = 0; k < 2; k++) {
+                std::vector<uint32_t> part(sel.begin() + done, sel.begin() + done + sample);
+                double ms = 0;
+                const rei_status r = run_batch(c, probs, part, outs, cand[k], &ms);
+                if (r != REI_OK) return r;
+                uint64_t cands = 0;
+                for (uint32_t i : part) cands += outs[i].stats.candidates;
+                rate[k] = ms > 0 ? cands / ms : 0;
+                done += sample;
+            }
+            warps = rate[1] > rate[0] ? 4 : 8;
+            c->batch_warps = (int)warps;
         }
     }
-    return REI_OK;
+    std::vector<uint32_t> rest(sel.begin() + done, sel.end());
+    const rei_status r = run_batch(c, probs, rest, outs, warps, nullptr);
+    const double t1 = now_ms();
+    (void)t0;
+    (void)t1;
+    return r;
 }
 
 }  // extern "C"

@@ -302,7 +302,8 @@ extern "C" rei_status rei_solve_noalloc(const rei_problem *p, void *stream_v, re
     uint8_t *d_op = (uint8_t *)cv.take(std::max<uint64_t>(cap, 1));
     uint32_t *d_l = (uint32_t *)cv.take(4ull * std::max<uint64_t>(cap, 1));
     uint32_t *d_r = (uint32_t *)cv.take(4ull * std::max<uint64_t>(cap, 1));
-    if (!d_r) {  // the budget's cache does not fit the array
+    uint32_t *d_used = (uint32_t *)cv.take(4ull * std::max<uint64_t>(cap, 1));
+    if (!d_used) {  // the budget's cache does not fit the array
         out->status = REI_ESCRATCH;
         return REI_ESCRATCH;
     }
@@ -370,6 +371,7 @@ extern "C" rei_status rei_solve_noalloc(const rei_problem *p, void *stream_v, re
     j.bp_op = d_op;
     j.bp_l = d_l;
     j.bp_r = d_r;
+    j.used = d_used;
     j.cache_alloc = cap;  // the whole budget is resident: the search never asks to grow
     j.table = d_table;
     j.table_mask = tslots - 1;

@@ -145,6 +145,7 @@ struct SolveJob {
     uint32_t *cs;
     uint8_t *bp_op;
     uint32_t *bp_l, *bp_r;
+    uint32_t *used;  // table slot of every cached row (to clear the table after the search)
     uint64_t cache_alloc;
     unsigned long long *table;
     uint64_t table_mask;
@@ -161,6 +162,47 @@ struct SolveJob {
     uint32_t *trace;                 // per CTA: (barriers passed << 8) | last barrier site
     uint32_t gt_in_smem;             // guide table copied to shared memory
     uint32_t solo_tiles;             // chunks of at most this many tiles run on CTA 0 alone
+};
+
+// ---- batched search
+
+// memory of the batch launch's slots (one per CTA), each `rows` cache rows
+struct SlotMem {
+    uint32_t *cs;            // slots * cs_words
+    uint8_t *bp_op;          // slots * rows
+    uint32_t *bp_l, *bp_r;   // slots * rows
+    uint32_t *used;          // slots * rows
+    unsigned long long *table;  // slots * table_slots
+    uint32_t *tmp;           // slots * tmp_words
+    uint32_t *pending, *slotpos;  // slots * chunk
+    uint32_t *bitmap;        // slots * ceil(chunk / 32)
+    uint32_t *blk;           // slots
+    int64_t *lvl;            // slots * 2 * (kMaxCost + 2)
+    SolveState *state;       // slots
+    uint32_t *tstack;        // slots * 4 * (kMaxCost + 2)
+    uint64_t rows, cs_words, table_slots, tmp_words, chunk;
+};
+
+// what one batched solve reports (device side)
+struct BatchOut {
+    uint32_t status, cost, tree_len, levels;
+    uint64_t candidates, unique;
+    uint64_t cand_op[5];
+    uint64_t ns;
+};
+
+// one problem of a batch: its job (staged data, costs; memory fields are
+// filled in by the CTA that takes it), where its tree and report go
+struct BatchJob {
+    SolveJob job;
+    uint8_t *tree;
+    BatchOut *out;
+};
+
+struct BatchArgs {
+    SlotMem slot;
+    uint32_t n;        // problems
+    uint32_t *queue;   // next problem to take
 };
 
 }  // namespace rei

@@ -593,7 +593,7 @@ __device__ uint32_t emit_tree(const SolveJob &J, uint32_t op, uint32_t l, uint32
 
 constexpr uint32_t kSortMax = 2048;  // new languages appended by CTA 0 alone, after a sort
 
-enum Cmd : uint32_t { CMD_NONE = 0, CMD_CHUNK = 1, CMD_EXIT = 2 };
+enum Cmd : uint32_t { CMD_NONE = 0, CMD_CHUNK = 1, CMD_EXIT = 2, CMD_CLEAN = 3 };
 
 struct ChunkArgs {
     uint32_t level, size, dedup, nseg;
@@ -657,7 +657,8 @@ __device__ __forceinline__ bool team_barrier(bool full, SolveState *st, uint32_t
 }
 
 // survivors of a chunk with few new languages, appended in candidate order by
-// CTA 0 alone: the pending slots' holders are sorted by index, then copied
+// the chunk's leading CTA alone: the pending slots' holders are sorted by
+// index, then copied
 __device__ void append_sorted(const SolveJob &J, SolveState *st, Shared &S, const ChunkArgs &a,
                               uint32_t npend, uint32_t W, Lead *L) {
     const uint32_t tid = threadIdx.x;
@@ -706,7 +707,12 @@ __device__ void append_sorted(const SolveJob &J, SolveState *st, Shared &S, cons
         J.bp_r[k] = r;
         const unsigned long long old = ld_relaxed_u64(J.table + q);
         J.table[q] = (old & 0xFFFFFFFF00000000ull) | (uint32_t)k;
+        J.used[k] = q;
     }
+    // survivors beyond the cap are not cached: free their slots (uniqueness
+    // stops for the rest of the level, so nothing reads them again)
+    for (uint32_t i = (uint32_t)umin64(room, npend) + tid; i < npend; i += blockDim.x)
+        J.table[(uint32_t)key[i]] = kEmpty;
     __syncthreads();
     if (tid == 0) {
         const uint64_t added = npend < room ? npend : room;
@@ -760,9 +766,9 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
     const uint32_t npend = *s_npend;
     __syncthreads();
 
-    // few new languages: CTA 0 appends them alone, in order, after a sort
+    // few new languages: the leading CTA appends them alone, in order, after a sort
     if (npend <= kSortMax) {
-        if (blockIdx.x == 0) append_sorted(J, st, S, a, npend, W, L);
+        if (team_r == 0) append_sorted(J, st, S, a, npend, W, L);
         return 0;
     }
 
@@ -801,7 +807,7 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
         }
         __syncthreads();
     }
-    if (blockIdx.x == 0 && tid == 0) st->pending_count = 0;
+    if (team_r == 0 && tid == 0) st->pending_count = 0;
     if (!team_barrier(full, st, bar_epoch, 8, J.trace)) return -1;
 
     // ---- phase D: append survivors in candidate order
@@ -842,7 +848,6 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
         for (uint32_t k = 0; k < wid; k++) wbefore += s_red[k];
         uint64_t rank = s_pref + wbefore + x - mycnt;
         const uint64_t limit = J.cache_alloc < J.cap ? J.cache_alloc : J.cap;
-        bool dropped = false;
         for (uint64_t w = t0; w < t1; w++) {
             uint32_t bits = ldcg(J.bitmap + w);
             J.bitmap[w] = 0;
@@ -853,7 +858,7 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
                 const uint64_t k = (uint64_t)a.size + rank;
                 rank++;
                 if (k >= limit) {
-                    dropped = true;
+                    J.table[ldcg(J.slotpos + j)] = kEmpty;  // not cached: free the slot
                     continue;
                 }
                 const uint32_t *srcp = J.tmp + (uint64_t)j * W;
@@ -867,11 +872,11 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
                 const uint32_t q = ldcg(J.slotpos + j);
                 const unsigned long long old = ld_relaxed_u64(J.table + q);
                 J.table[q] = (old & 0xFFFFFFFF00000000ull) | (uint32_t)k;
+                J.used[k] = q;
             }
         }
-        (void)dropped;
         __syncthreads();
-        if (blockIdx.x == 0 && tid == 0) {
+        if (team_r == 0 && tid == 0) {
             const uint64_t room = limit > a.size ? limit - a.size : 0;
             const uint64_t added = s_tot < room ? s_tot : room;
             if (s_tot > room) L->full = 1;  // every drop shows as s_tot > room
@@ -904,24 +909,11 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
-__global__ void __launch_bounds__(256, 2) k_solve(const __grid_constant__ SolveJob J) {
-    SolveState *st = J.st;
-    extern __shared__ __align__(16) uint8_t smem_raw[];
-    __shared__ Plan s_plan;
-    __shared__ uint32_t s_red[32];
-    __shared__ uint64_t s_tiles;
-    __shared__ uint32_t s_ctl[8];
-    __shared__ uint64_t s_pos[2];
-    __shared__ unsigned long long s_found;
-    __shared__ uint32_t s_npend;
-    __shared__ Lead L;
-
+// the shared memory of a search CTA, carved for one staged problem
+__device__ void carve_shared(const SolveJob &J, Shared &S, uint8_t *smem_raw, uint32_t **wm_out) {
     const uint32_t W = J.W, n = J.n;
     const uint32_t Ws = (W & 1u) ? W : W + 1;
     const uint32_t tid = threadIdx.x, wid = tid >> 5;
-
-    // carve shared memory
-    Shared S;
     uint8_t *p = smem_raw;
     S.seg = reinterpret_cast<Seg *>(p);
     p += sizeof(Seg) * J.seg_cap;
@@ -959,64 +951,46 @@ __global__ void __launch_bounds__(256, 2) k_solve(const __grid_constant__ SolveJ
         S.pos[b] = J.pos_mask[b];
         S.neg[b] = J.neg_mask[b];
     }
-    uint32_t *wm = S.warp_mem + wid * S.warp_words;
-    uint32_t bar_epoch = 0;
     // the level table as left by earlier launches of this search (parallel loads)
     for (uint32_t c = tid; c <= J.max_cost + 1 && c < J.seg_cap; c += blockDim.x) {
         S.lvs[c] = (uint32_t)ld_relaxed_u64(&J.lvl_start[c]);
         S.lvc[c] = (uint32_t)ld_relaxed_u64(&J.lvl_count[c]);
     }
+    *wm_out = S.warp_mem + wid * S.warp_words;
     __syncthreads();
+}
 
-    if (blockIdx.x != 0) {
-        // ---- worker: run the chunks CTA 0 hands out, until told to stop
-        uint32_t seen = 0;
-        for (;;) {
-            if (tid == 0) {
-                // back off up to 1 us between polls: hundreds of idle CTAs
-                // must not crowd the L2 while CTA 0 works alone
-                const unsigned long long t0 = globaltimer_ns();
-                uint32_t seq, nap = 64;
-                while ((seq = ld_relaxed_u32(&st->cmd_seq)) == seen) {
-                    __nanosleep(nap);
-                    if (nap < 1024) nap <<= 1;
-                    if (globaltimer_ns() - t0 > kWorkerWaitNs) break;
-                }
-                __threadfence();
-                if (seq == seen) {
-                    atomicCAS(&st->err, 0u, 3u);
-                    atomicExch(&st->status, (uint32_t)ST_TIMEOUT);
-                    s_ctl[0] = CMD_EXIT;
-                } else {
-                    s_ctl[0] = ld_relaxed_u32(&st->cmd);
-                    s_ctl[1] = ld_relaxed_u32(&st->c_level);
-                    s_ctl[2] = ld_relaxed_u32(&st->c_size);
-                    s_ctl[3] = ld_relaxed_u32(&st->c_dedup);
-                    s_pos[0] = ld_relaxed_u64(&st->c_cs0);
-                    s_pos[1] = ld_relaxed_u64(&st->c_ce0);
-                }
-            }
-            __syncthreads();
-            __threadfence();
-            seen++;
-            if (s_ctl[0] != CMD_CHUNK) return;
-            ChunkArgs a{s_ctl[1], s_ctl[2], s_ctl[3], 0, s_pos[0], s_pos[1]};
-            // the level table up to this level, as CTA 0 published it
-            for (uint32_t c = tid; c <= a.level; c += blockDim.x) {
-                S.lvs[c] = (uint32_t)ld_relaxed_u64(&J.lvl_start[c]);
-                S.lvc[c] = (uint32_t)ld_relaxed_u64(&J.lvl_count[c]);
-            }
-            __syncthreads();
-            if (wid == 0) plan_level(J, a.level, S.lvs, S.lvc, S.seg, s_plan);
-            __syncthreads();
-            a.nseg = s_plan.nseg;
-            if (process_chunk(J, st, S, a, true, false, bar_epoch, &s_tiles, s_red, &s_found, &s_npend, wm,
-                              nullptr) < 0)
-                return;
-        }
-    }
+// per-CTA static scratch the search functions share
+struct Cta {
+    Plan *plan;
+    uint32_t *red;
+    uint64_t *tiles;
+    unsigned long long *found;
+    uint32_t *npend;
+    Lead *L;
+    uint32_t *wm;
+};
 
-    // ---- CTA 0 leads, with the search state in shared memory
+// Empty every table slot this search filled, so that the table can be reused
+// without clearing it: the slot of every cached row, and the pending slots of
+// a chunk that ended with the answer before its survivors were appended.
+__device__ void clean_table(const SolveJob &J, uint32_t rows, uint32_t npending, uint32_t team_n,
+                            uint32_t team_r) {
+    const uint64_t t = (uint64_t)team_r * blockDim.x + threadIdx.x, nt = (uint64_t)team_n * blockDim.x;
+    for (uint64_t k = t; k < rows; k += nt) J.table[ldcg(J.used + k)] = kEmpty;
+    for (uint64_t i = t; i < npending; i += nt) J.table[ldcg(J.pending + i)] = kEmpty;
+}
+
+// The leader's search loop (Alg. 1): level after level, chunk after chunk,
+// until the answer, not_found, out-of-memory, or a request for more memory.
+// With allow_team, large chunks are handed to every CTA of the launch.
+// Returns -1 when a grid barrier gave up, else 0; the final state is written
+// back to `st`.
+__device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const Cta &K, bool allow_team,
+                           uint32_t &bar_epoch) {
+    const uint32_t tid = threadIdx.x, wid = tid >> 5;
+    Lead &L = *K.L;
+    Plan &s_plan = *K.plan;
     if (tid == 0) {
         L.status = st->status;
         L.level = st->level;
@@ -1046,7 +1020,7 @@ __global__ void __launch_bounds__(256, 2) k_solve(const __grid_constant__ SolveJ
     __syncthreads();
 
     bool found = false;
-    // per-phase wall time of CTA 0 (ns): plan, solo chunk, team chunk, level end
+    // per-phase wall time of the leader (ns): plan, solo chunk, team chunk, level end
     unsigned long long tm[4] = {0, 0, 0, 0}, tcnt[3] = {0, 0, 0};
     for (;;) {
         const unsigned long long t_it = globaltimer_ns();
@@ -1133,9 +1107,9 @@ __global__ void __launch_bounds__(256, 2) k_solve(const __grid_constant__ SolveJ
         if (C == 0) C = 1;  // unreachable with room >= 1; guards the loop
         ChunkArgs a{level, size, dedup ? 1u : 0u, nseg, pos, pos + C};
         // alone when the chunk is a few tiles per warp of this CTA
-        if (wid == 0) tile_setup(S, nseg, a.cs0, a.ce0, &s_tiles);
+        if (wid == 0) tile_setup(S, nseg, a.cs0, a.ce0, K.tiles);
         __syncthreads();
-        const bool team = s_tiles > (uint64_t)J.solo_tiles;
+        const bool team = allow_team && *K.tiles > (uint64_t)J.solo_tiles;
         const unsigned long long t_chunk = globaltimer_ns();
         if (tid == 0) tm[0] += t_chunk - t_it;
         if (team) {
@@ -1148,8 +1122,8 @@ __global__ void __launch_bounds__(256, 2) k_solve(const __grid_constant__ SolveJ
             }
             publish(st, CMD_CHUNK);
         }
-        const int r = process_chunk(J, st, S, a, team, true, bar_epoch, &s_tiles, s_red, &s_found, &s_npend, wm, &L);
-        if (r < 0) return;
+        const int r = process_chunk(J, st, S, a, team, true, bar_epoch, K.tiles, K.red, K.found, K.npend, K.wm, &L);
+        if (r < 0) return -1;
         if (tid == 0) {
             tm[team ? 2 : 1] += globaltimer_ns() - t_chunk;
             tcnt[team ? 1 : 0]++;
@@ -1201,7 +1175,195 @@ __global__ void __launch_bounds__(256, 2) k_solve(const __grid_constant__ SolveJ
         for (int k = 0; k < 4; k++) st->t_phase[k] += tm[k];
         for (int k = 0; k < 3; k++) st->n_phase[k] += tcnt[k];
     }
-    publish(st, CMD_EXIT);
+    __syncthreads();
+    return 0;
+}
+
+__global__ void __launch_bounds__(256, 2) k_solve(const __grid_constant__ SolveJob J) {
+    SolveState *st = J.st;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    __shared__ Plan s_plan;
+    __shared__ uint32_t s_red[32];
+    __shared__ uint64_t s_tiles;
+    __shared__ uint32_t s_ctl[8];
+    __shared__ uint64_t s_pos[2];
+    __shared__ unsigned long long s_found;
+    __shared__ uint32_t s_npend;
+    __shared__ Lead L;
+
+    const uint32_t tid = threadIdx.x;
+    Shared S;
+    uint32_t *wm;
+    carve_shared(J, S, smem_raw, &wm);
+    const Cta K{&s_plan, s_red, &s_tiles, &s_found, &s_npend, &L, wm};
+    uint32_t bar_epoch = 0;
+
+    if (blockIdx.x != 0) {
+        // ---- worker: run the chunks CTA 0 hands out, until told to stop
+        uint32_t seen = 0;
+        for (;;) {
+            if (tid == 0) {
+                // back off up to 1 us between polls: hundreds of idle CTAs
+                // must not crowd the L2 while CTA 0 works alone
+                const unsigned long long t0 = globaltimer_ns();
+                uint32_t seq, nap = 64;
+                while ((seq = ld_relaxed_u32(&st->cmd_seq)) == seen) {
+                    __nanosleep(nap);
+                    if (nap < 1024) nap <<= 1;
+                    if (globaltimer_ns() - t0 > kWorkerWaitNs) break;
+                }
+                __threadfence();
+                if (seq == seen) {
+                    atomicCAS(&st->err, 0u, 3u);
+                    atomicExch(&st->status, (uint32_t)ST_TIMEOUT);
+                    s_ctl[0] = CMD_EXIT;
+                } else {
+                    s_ctl[0] = ld_relaxed_u32(&st->cmd);
+                    s_ctl[1] = ld_relaxed_u32(&st->c_level);
+                    s_ctl[2] = ld_relaxed_u32(&st->c_size);
+                    s_ctl[3] = ld_relaxed_u32(&st->c_dedup);
+                    s_pos[0] = ld_relaxed_u64(&st->c_cs0);
+                    s_pos[1] = ld_relaxed_u64(&st->c_ce0);
+                }
+            }
+            __syncthreads();
+            __threadfence();
+            seen++;
+            if (s_ctl[0] == CMD_CLEAN) {
+                clean_table(J, s_ctl[1], s_ctl[2], gridDim.x, blockIdx.x);
+                return;
+            }
+            if (s_ctl[0] != CMD_CHUNK) return;
+            ChunkArgs a{s_ctl[1], s_ctl[2], s_ctl[3], 0, s_pos[0], s_pos[1]};
+            // the level table up to this level, as CTA 0 published it
+            for (uint32_t c = tid; c <= a.level; c += blockDim.x) {
+                S.lvs[c] = (uint32_t)ld_relaxed_u64(&J.lvl_start[c]);
+                S.lvc[c] = (uint32_t)ld_relaxed_u64(&J.lvl_count[c]);
+            }
+            __syncthreads();
+            if ((tid >> 5) == 0) plan_level(J, a.level, S.lvs, S.lvc, S.seg, s_plan);
+            __syncthreads();
+            a.nseg = s_plan.nseg;
+            if (process_chunk(J, st, S, a, true, false, bar_epoch, &s_tiles, s_red, &s_found, &s_npend, wm,
+                              nullptr) < 0)
+                return;
+        }
+    }
+
+    // ---- CTA 0 leads
+    if (lead_search(J, st, S, K, true, bar_epoch) < 0) return;
+    const uint32_t status = ld_relaxed_u32(&st->status);
+    if (status == ST_FOUND || status == ST_NOT_FOUND || status == ST_OOM) {
+        // every CTA empties its share of the slots this search filled
+        if (tid == 0) {
+            st->c_level = L.size;
+            st->c_size = ld_relaxed_u32(&st->pending_count);
+        }
+        const uint32_t rows = L.size, npending = ld_relaxed_u32(&st->pending_count);
+        publish(st, CMD_CLEAN);
+        clean_table(J, rows, npending, gridDim.x, 0);
+        __syncthreads();
+        if (tid == 0) st->pending_count = 0;
+    } else {
+        publish(st, CMD_EXIT);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the batched search: one launch for many staged problems; every CTA takes
+// problems from a queue and solves each one on its own (its own memory slot,
+// no grid-wide synchronisation), with the same leader code as k_solve.
+
+__global__ void __launch_bounds__(256, 2) k_solve_batch(const BatchJob *jobs, const __grid_constant__ BatchArgs B) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    __shared__ Plan s_plan;
+    __shared__ uint32_t s_red[32];
+    __shared__ uint64_t s_tiles;
+    __shared__ unsigned long long s_found;
+    __shared__ uint32_t s_npend;
+    __shared__ Lead L;
+    __shared__ SolveJob J;
+    __shared__ uint32_t s_prob;
+    const uint32_t tid = threadIdx.x;
+    const uint32_t slot = blockIdx.x;
+    for (;;) {
+        if (tid == 0) s_prob = atomicAdd(B.queue, 1u);
+        __syncthreads();
+        const uint32_t pi = s_prob;
+        __syncthreads();
+        if (pi >= B.n) return;
+        const BatchJob &bj = jobs[pi];
+        const unsigned long long t_start = globaltimer_ns();
+        // this problem's job: its staged data, this slot's memory
+        if (tid == 0) {
+            J = bj.job;
+            const SlotMem &m = B.slot;
+            const uint64_t so = slot;
+            J.cs = m.cs + so * m.cs_words;
+            J.bp_op = m.bp_op + so * m.rows;
+            J.bp_l = m.bp_l + so * m.rows;
+            J.bp_r = m.bp_r + so * m.rows;
+            J.used = m.used + so * m.rows;
+            J.cache_alloc = umin64(J.cap, m.cs_words / J.W < m.rows ? m.cs_words / J.W : m.rows);
+            J.table = m.table + so * m.table_slots;
+            J.table_mask = m.table_slots - 1;
+            J.tmp = m.tmp + so * m.tmp_words;
+            J.chunk_max = umin64(m.chunk, m.tmp_words / J.W);
+            J.pending = m.pending + so * m.chunk;
+            J.slotpos = m.slotpos + so * m.chunk;
+            J.bitmap = m.bitmap + so * ((m.chunk + 31) / 32);
+            J.blk = m.blk + so;
+            J.lvl_start = m.lvl + so * 2 * (kMaxCost + 2);
+            J.lvl_count = J.lvl_start + (kMaxCost + 2);
+            J.st = m.state + so;
+            J.tree = bj.tree;
+            J.tstack = m.tstack + so * 4 * (kMaxCost + 2);
+            J.trace = nullptr;
+            J.solo_tiles = 0xFFFFFFFFu;
+        }
+        __syncthreads();
+        SolveState *st = J.st;
+        // fresh search state and level table for this problem
+        for (uint32_t c = tid; c < 2 * (kMaxCost + 2); c += blockDim.x) J.lvl_start[c] = 0;
+        if (tid == 0) {
+            SolveState z{};
+            z.status = ST_RUNNING;
+            z.level = J.c[0];
+            z.found = kNone;
+            z.partial_level = J.max_cost + 1;
+            *st = z;
+        }
+        __threadfence();
+        __syncthreads();
+        Shared S;
+        uint32_t *wm;
+        carve_shared(J, S, smem_raw, &wm);
+        const Cta K{&s_plan, s_red, &s_tiles, &s_found, &s_npend, &L, wm};
+        uint32_t epoch = 0;
+        lead_search(J, st, S, K, false, epoch);
+        const uint32_t status = st->status;
+        if (status == ST_FOUND || status == ST_NOT_FOUND || status == ST_OOM) {
+            clean_table(J, L.size, st->pending_count, 1, 0);
+        } else {
+            // ran out of this slot's memory: the host solves it again alone;
+            // this slot's table is rebuilt from scratch
+            for (uint64_t i = tid; i <= J.table_mask; i += blockDim.x) J.table[i] = kEmpty;
+            for (uint64_t i = tid; i < (J.chunk_max + 31) / 32; i += blockDim.x) J.bitmap[i] = 0;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            BatchOut &o = *bj.out;
+            o.status = status;
+            o.cost = st->ans_cost;
+            o.tree_len = st->tree_len;
+            o.candidates = st->candidates;
+            o.unique = st->unique_done;
+            o.levels = st->level;
+            for (int k = 0; k < 5; k++) o.cand_op[k] = st->cand_op[k];
+            o.ns = globaltimer_ns() - t_start;
+        }
+        __syncthreads();
+    }
 }
 
 // rebuild the uniqueness table after the cache grew (all entries are distinct)
@@ -1214,7 +1376,10 @@ __global__ void k_rehash(const __grid_constant__ SolveJob J, uint32_t count) {
         const unsigned long long v = ((uint64_t)(uint32_t)(h >> 32) << 32) | (uint32_t)k;
         uint64_t p = h & J.table_mask;
         for (uint64_t probe = 0; probe <= J.table_mask; probe++) {
-            if (atomicCAS(&J.table[p], kEmpty, v) == kEmpty) break;
+            if (atomicCAS(&J.table[p], kEmpty, v) == kEmpty) {
+                J.used[k] = (uint32_t)p;
+                break;
+            }
             p = (p + 1) & J.table_mask;
         }
     }
@@ -1249,6 +1414,20 @@ cudaError_t solve_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm) {
 cudaError_t launch_rehash(const SolveJob *job, uint32_t count, uint32_t grid, cudaStream_t stream) {
     k_rehash<<<grid, 256, 0, stream>>>(*job, count);
     return cudaGetLastError();
+}
+
+cudaError_t launch_solve_batch(const BatchJob *jobs_dev, const BatchArgs *args, uint32_t grid, uint32_t threads,
+                               size_t smem, cudaStream_t stream) {
+    cudaError_t e = cudaFuncSetAttribute(k_solve_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_solve_batch<<<grid, threads, smem, stream>>>(jobs_dev, *args);
+    return cudaGetLastError();
+}
+
+cudaError_t solve_batch_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_solve_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_solve_batch, (int)threads, smem);
 }
 
 }  // namespace rei

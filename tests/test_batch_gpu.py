@@ -1,0 +1,78 @@
+"""The batched form (rei_solve_batch): one staging launch and one persistent
+search launch for many problems, each result exactly the one the plain entry
+point (and, where it is fast enough, the oracle) gives."""
+import pytest
+
+import oracle
+import paper_2305_18575_gb300 as rei
+from workloads import make_config, type1_instance, type2_instance
+from workloads.gen import batched_instance
+
+pytestmark = pytest.mark.gpu
+
+
+def key(r):
+    return (r.status, r.cost, r.tree, r.regex, r.candidates, r.unique)
+
+
+def mixed_problems():
+    probs = []
+    for s in range(12):
+        i = make_config("small", s)
+        probs.append(rei.Problem(i.alphabet, i.pos, i.neg, costs=(1, 1, 1, 1, 1), max_cost=20))
+    for s in range(10):
+        i = make_config("medium", s)
+        probs.append(rei.Problem(i.alphabet, i.pos, i.neg, costs=(1, 1, 5, 1, 1), max_cost=40,
+                                 mem_budget=i.mem_budget))
+    # the largest medium search caches ~844 K languages: more than a batch slot holds
+    i = make_config("medium", 16)
+    probs.append(rei.Problem(i.alphabet, i.pos, i.neg, costs=(1, 1, 5, 1, 1), max_cost=40, mem_budget=8 << 30))
+    for s in range(6):
+        i = batched_instance(s)
+        probs.append(rei.Problem(i.alphabet, i.pos, i.neg, costs=(1, 1, 1, 1, 1), max_cost=40, mem_budget=1 << 30))
+    for s in range(4):
+        i = type2_instance(s, 4, 4, 5)
+        probs.append(rei.Problem(i.alphabet, i.pos, i.neg, costs=(2, 1, 3, 1, 2), max_cost=30))
+    # invalid ones in the middle: a foreign byte, P and N overlapping
+    probs.insert(5, rei.Problem(b"01", [b"2"], [b""]))
+    probs.insert(9, rei.Problem(b"01", [b"0"], [b"0"]))
+    return probs
+
+
+@pytest.mark.parametrize("warps", [8, 4])
+def test_batch_matches_plain_solves(warps):
+    probs = mixed_problems()
+    with rei.Context(device=0) as ctx:
+        plain = [ctx.solve_problem(p) for p in probs]
+        batch = ctx.solve_batch(probs, warps_per_cta=warps)
+        again = ctx.solve_batch(probs, warps_per_cta=warps)  # slots reused after a batch
+    for k, (a, b, c) in enumerate(zip(plain, batch, again)):
+        assert key(a) == key(b) == key(c), (k, a, b)
+    assert batch[5].status == rei.REI_EINVAL and batch[9].status == rei.REI_EINVAL
+
+
+def test_batch_matches_oracle_on_small_problems():
+    insts = [make_config("small", s) for s in range(30)] + [type1_instance(s, 3, 3, 3) for s in range(6)]
+    probs = [rei.Problem(i.alphabet, i.pos, i.neg, costs=(1, 2, 1, 2, 1), max_cost=20) for i in insts]
+    with rei.Context(device=0) as ctx:
+        got = ctx.solve_batch(probs)
+    for i, g in zip(insts, got):
+        ref = oracle.solve(i.alphabet, i.pos, i.neg, costs=(1, 2, 1, 2, 1), max_cost=20)
+        assert (g.status, g.cost, g.tree, g.candidates, g.unique) == \
+            (rei.REI_OK, ref.cost, ref.tree, ref.candidates, ref.unique)
+
+
+def test_batch_config_with_autotuning():
+    """512 instances of the batched workload: autotuned launch shape, exact results."""
+    insts = [batched_instance(s) for s in range(512)]
+    probs = [rei.Problem(i.alphabet, i.pos, i.neg, costs=(1, 1, 1, 1, 1), max_cost=40, mem_budget=1 << 30)
+             for i in insts]
+    with rei.Context(device=0) as ctx:
+        batch = ctx.solve_batch(probs)
+        for k in range(0, 512, 17):  # a sample against the plain path
+            assert key(ctx.solve_problem(probs[k])) == key(batch[k]), k
+    assert all(r.status == rei.REI_OK for r in batch)
+    for i, r in zip(insts[:64], batch[:64]):
+        assert r.cost <= i.target_cost
+        assert all(oracle.match(r.tree, i.alphabet, p) for p in i.pos)
+        assert not any(oracle.match(r.tree, i.alphabet, q) for q in i.neg)

@@ -18,7 +18,7 @@ from workloads import make_config
 
 pytestmark = pytest.mark.gpu
 
-BUDGET = 40 << 20  # its whole cache (about 1.16 M languages at W = 2) fits the scratch
+BUDGET = 32 << 20  # its whole cache (about 0.93 M languages at W = 2) fits the scratch
 CASES = [("small", 3, (1, 1, 1, 1, 1)), ("medium", 2, (1, 1, 1, 1, 1)),
          ("medium", 5, (1, 1, 5, 1, 1)), ("medium", 16, (1, 1, 5, 1, 1)),
          ("medium", 12, (2, 1, 3, 1, 2)), ("wide", 0, (1, 1, 10, 1, 1))]
