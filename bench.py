@@ -291,9 +291,51 @@ def run_gpu(args, rank, world, local_rank):
         "clocks": clocks.summary(),
         "gpu_launches": launches,
     }
+    if not args.no_batch:
+        line["batched"] = batched_leg(ctx, dev)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
+
+
+BATCH_WORKLOAD = ("batched: 512 instances, |alphabet| 2-4, |P|,|N| uniform 2-20, lengths 0-10, |ic| 16-1024, "
+                  "target cost 4-14, costs (1,1,1,1,1), max_cost 40; one rei_solve_batch call vs 512 rei_solve_problem calls")
+
+
+def batched_leg(ctx, dev):
+    """The batched form against one-at-a-time solves of the same instances on
+    the same GPU (whole calls, host clock around synchronous calls)."""
+    import time as _t
+    import torch
+    import paper_2305_18575_gb300 as rei
+    from workloads.gen import batched_instance
+    insts = [batched_instance(s) for s in range(512)]
+    probs = [rei.Problem(i.alphabet, i.pos, i.neg, costs=(1, 1, 1, 1, 1), max_cost=40, mem_budget=1 << 30)
+             for i in insts]
+    ctx.solve_batch(probs)  # warm-up (also autotunes the launch shape)
+    reps = 3
+    torch.cuda.synchronize()
+    t0 = _t.perf_counter()
+    for _ in range(reps):
+        res = ctx.solve_batch(probs)
+    torch.cuda.synchronize()
+    t_batch = (_t.perf_counter() - t0) / reps
+    for p in probs[:16]:
+        ctx.solve_problem(p)
+    torch.cuda.synchronize()
+    t0 = _t.perf_counter()
+    seq = [ctx.solve_problem(p) for p in probs]
+    torch.cuda.synchronize()
+    t_seq = _t.perf_counter() - t0
+    if any((a.status, a.cost, a.tree) != (b.status, b.cost, b.tree) for a, b in zip(res, seq)):
+        raise RuntimeError("batched and one-at-a-time results differ")
+    lat = sorted(r.ms_total for r in res)
+    cands = sum(r.candidates for r in res)
+    return {"workload": BATCH_WORKLOAD, "instances": len(probs),
+            "instances_per_s": len(probs) / t_batch, "sequential_instances_per_s": len(probs) / t_seq,
+            "speedup_vs_sequential": t_seq / t_batch, "batch_ms": 1000 * t_batch, "sequential_ms": 1000 * t_seq,
+            "candidates_per_s": cands / t_batch,
+            "solve_ms_p50": lat[len(lat) // 2], "solve_ms_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
 
 
 def main():
@@ -303,6 +345,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-form leg")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -169,12 +169,30 @@ class _Nfa:
                 if r not in seen:
                     seen.add(r)
                     stack.append(r)
-        return seen
+        return frozenset(seen)
+
+    def _compile(self):
+        # epsilon-closure of every state, then the closed successor set of
+        # every closed state set per byte, memoised (a lazy subset construction)
+        self._cl = [self._closure([q]) for q in range(len(self.sym))]
+        self._start = self._cl[self.start]
+        self._step = {}
 
     def fullmatch(self, s: bytes) -> bool:
-        cur = self._closure([self.start])
+        if not hasattr(self, "_cl"):
+            self._compile()
+        cur = self._start
         for ch in s:
-            cur = self._closure([self.nxt[q] for q in cur if self.sym[q] == ch])
+            key = (cur, ch)
+            nxt = self._step.get(key)
+            if nxt is None:
+                acc = set()
+                for q in cur:
+                    if self.sym[q] == ch:
+                        acc |= self._cl[self.nxt[q]]
+                nxt = frozenset(acc)
+                self._step[key] = nxt
+            cur = nxt
             if not cur:
                 return False
         return self.accept in cur
@@ -202,7 +220,7 @@ def _n_distinct_substrings(strings) -> int:
 
 def _rand_string(rng, alphabet: bytes, lo: int, hi: int) -> bytes:
     n = rng.randint(lo, hi)
-    return bytes(rng.choice(alphabet) for _ in range(n))
+    return bytes(rng.choices(alphabet, k=n))
 
 
 def make_instance(name: str, seed: int, alphabet: bytes, n_pos: int, n_neg: int,
@@ -223,6 +241,10 @@ def make_instance(name: str, seed: int, alphabet: bytes, n_pos: int, n_neg: int,
         pos, neg, seen = [], [], set()
         for _draw in range(10_000):
             if len(pos) >= n_pos and len(neg) >= n_neg:
+                break
+            # a target that has labelled almost nothing on one side after
+            # 2000 draws cannot fill it: give it up early
+            if _draw == 2000 and (2 * len(pos) < n_pos or 2 * len(neg) < n_neg):
                 break
             s = _rand_string(rng, alphabet, len_lo, len_hi)
             if s in seen:
