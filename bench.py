@@ -292,7 +292,9 @@ def run_gpu(args, rank, world, local_rank):
         "gpu_launches": launches,
     }
     if not args.no_batch:
-        line["batched"] = batched_leg(ctx, dev)
+        bprobs = batched_problems()
+        line["batched"] = batched_leg(ctx, dev, bprobs)
+        line["served"] = served_leg(dev, bprobs)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -302,16 +304,19 @@ BATCH_WORKLOAD = ("batched: 512 instances, |alphabet| 2-4, |P|,|N| uniform 2-20,
                   "target cost 4-14, costs (1,1,1,1,1), max_cost 40; one rei_solve_batch call vs 512 rei_solve_problem calls")
 
 
-def batched_leg(ctx, dev):
+def batched_problems():
+    import paper_2305_18575_gb300 as rei
+    from workloads.gen import batched_instance
+    insts = [batched_instance(s) for s in range(512)]
+    return [rei.Problem(i.alphabet, i.pos, i.neg, costs=(1, 1, 1, 1, 1), max_cost=40, mem_budget=1 << 30)
+            for i in insts]
+
+
+def batched_leg(ctx, dev, probs):
     """The batched form against one-at-a-time solves of the same instances on
     the same GPU (whole calls, host clock around synchronous calls)."""
     import time as _t
     import torch
-    import paper_2305_18575_gb300 as rei
-    from workloads.gen import batched_instance
-    insts = [batched_instance(s) for s in range(512)]
-    probs = [rei.Problem(i.alphabet, i.pos, i.neg, costs=(1, 1, 1, 1, 1), max_cost=40, mem_budget=1 << 30)
-             for i in insts]
     ctx.solve_batch(probs)  # warm-up (also autotunes the launch shape)
     reps = 3
     torch.cuda.synchronize()
@@ -338,6 +343,65 @@ def batched_leg(ctx, dev):
             "solve_ms_p50": lat[len(lat) // 2], "solve_ms_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
 
 
+SERVE_WORKLOAD = ("served: Poisson arrivals at 50, 200 and 1000 problems/s for 2 s each, problems drawn in turn "
+                  "from the 512 batched-workload instances; rei_server (one persistent launch) vs a loop of "
+                  "rei_solve_problem calls taking the same arrivals in order")
+SERVE_RATES = (50, 200, 1000)
+SERVE_SECONDS = 2.0
+
+
+def served_leg(dev, probs):
+    """Latency from arrival to answer (host clock) of the served form against a
+    plain loop that solves the same arrivals one at a time."""
+    import paper_2305_18575_gb300 as rei
+    from workloads.gen import poisson_trace
+
+    def pct(v, q):
+        v = sorted(v)
+        return v[min(len(v) - 1, int(q * len(v)))]
+
+    out = {"workload": SERVE_WORKLOAD, "rates": {}}
+    answers = {}
+    with rei.Context(device=dev) as sctx, rei.Server(sctx, budget_bytes=64 << 30, max_live=4096) as srv:
+        for t in [srv.submit(p) for p in probs[:64]]:  # warm-up
+            srv.result(t)
+        for rate in SERVE_RATES:
+            arr = poisson_trace(rate, SERVE_SECONDS, seed=11)
+            tickets = []
+            t0 = time.perf_counter()
+            for k, a in enumerate(arr):
+                dt = t0 + a - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                tickets.append(srv.submit(probs[k % len(probs)]))
+            res = [srv.result(t) for t in tickets]
+            t_end = max(time.perf_counter(), t0 + SERVE_SECONDS)
+            answers[rate] = [(r.status, r.cost, r.tree) for r in res]
+            lat = [r.ms_total for r in res]
+            out["rates"][str(rate)] = {"requests": len(arr), "served_p50_ms": pct(lat, 0.5),
+                                       "served_p99_ms": pct(lat, 0.99),
+                                       "served_throughput_per_s": len(arr) / (t_end - t0)}
+    with rei.Context(device=dev) as pctx:
+        for p in probs[:16]:
+            pctx.solve_problem(p)
+        for rate in SERVE_RATES:
+            arr = poisson_trace(rate, SERVE_SECONDS, seed=11)
+            lat, got = [], []
+            t0 = time.perf_counter()
+            for k, a in enumerate(arr):
+                dt = t0 + a - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                r = pctx.solve_problem(probs[k % len(probs)])
+                lat.append(1000 * (time.perf_counter() - t0 - a))
+                got.append((r.status, r.cost, r.tree))
+            if got != answers[rate]:
+                raise RuntimeError("served and one-at-a-time answers differ")
+            o = out["rates"][str(rate)]
+            o.update({"plain_p50_ms": pct(lat, 0.5), "plain_p99_ms": pct(lat, 0.99)})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -345,7 +409,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched-form leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched and served legs")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -254,13 +254,30 @@ typedef struct rei_tune {
 rei_status rei_solve_batch(rei_ctx *ctx, const rei_problem *probs, uint32_t n, rei_result *outs,
                            const rei_tune *tune);
 
-/* ---- served form: continuous batching of arriving problems ---- */
+/* ---- served form: continuous batching of arriving problems ----
+ *
+ * Independent problems that arrive over time, each searched as in Alg. 1
+ * (the paper solves one problem per run; serving many is this library's).
+ * One persistent launch, one CTA per memory slot, takes problems from a ring
+ * in mapped host memory as its CTAs free up; each CTA stages its problem
+ * itself (Sec. 3 staging: infix closure, guide table, leaves) and searches
+ * it alone.  A worker thread of the server admits queued problems into the
+ * ring, reads answers back and relaunches the search when it returned after
+ * going idle.  Problems with more than 255 strings or 8192 bytes, or whose
+ * search outgrows a slot (2^17 languages, |ic| <= 2048), are solved alone by
+ * rei_solve_problem while the launch is stopped.  Every result equals
+ * rei_solve_problem's for the problem alone.  The server owns its context's
+ * device while it lives: make no other call
+ * on that context until rei_server_destroy. */
 
 typedef struct rei_server rei_server;
 
 /* budget_bytes: device memory the live problems may hold together (each
- * problem's cache footprint is charged at admission); max_live: problems on
- * the device at once. */
+ * problem is charged min(its mem_budget, one slot's cache) at admission; one
+ * problem is always admitted when none is live); max_live: problems on the
+ * device at once.  The server allocates its slots (about 38 MiB per slot, one
+ * slot per resident CTA) from the context's allocator.  REI_OOM when that
+ * fails, REI_ECUDA on a CUDA error. */
 rei_status rei_server_create(rei_ctx *ctx, uint64_t budget_bytes, uint32_t max_live,
                              rei_server **out);
 
@@ -268,10 +285,13 @@ rei_status rei_server_create(rei_ctx *ctx, uint64_t budget_bytes, uint32_t max_l
 rei_status rei_server_submit(rei_server *srv, const rei_problem *prob, uint64_t *ticket);
 
 /* Wait up to block_ms (0 = poll, < 0 = forever) for a ticket's result.
- * REI_EBUSY when not finished in time.  The ticket is released on success. */
+ * out->stats.ms_total is the time from submission to the answer.
+ * REI_EBUSY when not finished in time; REI_EINVAL for a ticket that was not
+ * issued or was already released; REI_EBUFSZ (ticket kept) when out's regex
+ * or tree buffer is too small.  The ticket is released on success. */
 rei_status rei_server_poll(rei_server *srv, uint64_t ticket, rei_result *out, int block_ms);
 
-/* Stop the server's worker (finishing live problems) and free it. */
+/* Stop the server's worker (finishing queued and live problems) and free it. */
 void rei_server_destroy(rei_server *srv);
 
 /* ---- solving without allocating ---- */

@@ -463,6 +463,47 @@ class Context:
         return r
 
 
+class Server:
+    """Served form: problems submitted at any time are solved by one persistent
+    launch as its CTAs free up (continuous batching).  `budget_bytes` bounds the
+    cache the live problems may hold together, `max_live` how many are live."""
+
+    def __init__(self, ctx: Context, budget_bytes: int = 8 << 30, max_live: int = 1 << 12):
+        self.ctx = ctx
+        self.h = rei_server_create(ctx.h, budget_bytes, max_live)
+        self._probs = {}
+
+    def submit(self, prob: Problem) -> int:
+        t = rei_server_submit(self.h, prob.p)
+        self._probs[t] = prob
+        return t
+
+    def result(self, ticket: int, block_ms: int = -1) -> Optional[Result]:
+        """The ticket's Result, or None when it is not finished within block_ms."""
+        o = _OutBuf()
+        s = rei_server_poll(self.h, ticket, o.res, block_ms)
+        if s == REI_EBUSY:
+            return None
+        if s != REI_OK:
+            raise RuntimeError(f"rei_server_poll: {STATUS_NAMES.get(s, s)}")
+        self._probs.pop(ticket, None)
+        return o.result(o.res.status)
+
+    def close(self):
+        if getattr(self, "h", None):
+            rei_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
 def solve(alphabet: bytes, pos, neg, **kw) -> Result:
     with Context() as ctx:
         return ctx.solve(alphabet, pos, neg, **kw)

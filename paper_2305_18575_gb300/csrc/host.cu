@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstdio>
@@ -13,6 +14,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <set>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -25,6 +27,8 @@ cudaError_t launch_solve_batch(const BatchJob *jobs_dev, const BatchArgs *args, 
                                size_t smem, cudaStream_t stream);
 cudaError_t solve_batch_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm);
 cudaError_t launch_stage(const StageJob *jobs_dev, uint32_t n_jobs, cudaStream_t stream);
+cudaError_t launch_serve(const ServeArgs *args, uint32_t grid, uint32_t threads, size_t smem, cudaStream_t stream);
+cudaError_t serve_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm);
 size_t stage_smem_bytes();
 cudaError_t launch_solve(const SolveJob *job, uint32_t grid, uint32_t threads, size_t smem,
                          cudaStream_t stream);
@@ -35,6 +39,8 @@ size_t solve_smem_bytes(uint32_t W, uint32_t n, uint32_t G, uint32_t max_len, ui
 }  // namespace rei
 
 using namespace rei;
+
+static constexpr uint32_t kHsetCapHost = 4 * kMaxIC;  // the staging hash set's slots
 
 namespace {
 
@@ -1182,7 +1188,12 @@ rei_status rei_solve_batch(rei_ctx *c, const rei_problem *probs, uint32_t n, rei
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// served form: a worker thread admits queued problems against a memory budget
+// served form: continuous batching.  A worker thread admits queued requests
+// (while the live ones' cache footprints fit the budget and fewer than
+// max_live are live) into a ring of mapped host memory and publishes them; a
+// persistent k_serve launch whose CTAs take them as they free up stages and
+// solves each one and writes its answer back.  Requests larger than a CTA
+// slot are solved alone (rei_solve_problem) while the launch is stopped.
 
 struct rei_server {
     rei_ctx *ctx;
@@ -1195,6 +1206,8 @@ struct rei_server {
         std::vector<uint8_t> alphabet, bytes;
         std::vector<uint32_t> offs;
         rei_problem p;
+        uint64_t footprint;
+        double t_submit;  // host clock, ms
     };
     struct Done {
         rei_result r;
@@ -1203,43 +1216,309 @@ struct rei_server {
     };
     std::deque<Req> queue;
     std::map<uint64_t, Done> done;
+    std::set<uint64_t> open;  // issued, not yet released
     uint64_t next_ticket = 1;
     bool stop = false;
     std::thread worker;
+    rei_status error = REI_OK;
+
+    // device side
+    uint32_t ring_size = 0, grid = 0, threads = 256;
+    size_t smem = 0;
+    ServeReq *ring_h = nullptr;
+    ServeOut *outs_h = nullptr;
+    unsigned long long *ctl_h = nullptr;  // [0] avail, [1] stop
+    ServeArgs args{};
+    std::vector<DevBuf> bufs;
+    cudaStream_t kstream = nullptr;
+    cudaEvent_t kdone = nullptr;
+    bool running = false;
+    uint64_t published = 0;
+    std::map<uint64_t, Req> live;  // by job id
+    uint64_t live_bytes = 0;
 };
 
 namespace {
 
+void server_fail(rei_server *S, rei_status e) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->error == REI_OK) S->error = e;
+    S->done_cv.notify_all();
+}
+
+rei_status server_setup(rei_server *S) {
+    rei_ctx *c = S->ctx;
+    if (cudaSetDevice(c->device) != cudaSuccess) return REI_ECUDA;
+    S->ring_size = 4096;
+    S->threads = 256;
+    S->smem = 112 * 1024;
+    int bps = 0;
+    if (serve_occupancy(S->threads, S->smem, &bps) != cudaSuccess || bps < 1) return REI_ECUDA;
+    S->grid = (uint32_t)(c->sm_count * bps);
+    const uint64_t slots = S->grid;
+    // mapped host memory: the ring, the results, the control words
+    if (cudaHostAlloc((void **)&S->ring_h, sizeof(ServeReq) * S->ring_size, cudaHostAllocMapped) != cudaSuccess)
+        return REI_ECUDA;
+    if (cudaHostAlloc((void **)&S->outs_h, sizeof(ServeOut) * S->ring_size, cudaHostAllocMapped) != cudaSuccess)
+        return REI_ECUDA;
+    if (cudaHostAlloc((void **)&S->ctl_h, 64, cudaHostAllocMapped) != cudaSuccess) return REI_ECUDA;
+    memset(S->outs_h, 0, sizeof(ServeOut) * S->ring_size);
+    memset(S->ctl_h, 0, 64);
+    ServeArgs &A = S->args;
+    void *dp = nullptr;
+    if (cudaHostGetDevicePointer(&dp, S->ring_h, 0) != cudaSuccess) return REI_ECUDA;
+    A.ring = (const ServeReq *)dp;
+    if (cudaHostGetDevicePointer(&dp, S->outs_h, 0) != cudaSuccess) return REI_ECUDA;
+    A.outs = (ServeOut *)dp;
+    if (cudaHostGetDevicePointer(&dp, S->ctl_h, 0) != cudaSuccess) return REI_ECUDA;
+    A.avail = (const volatile unsigned long long *)dp;
+    A.stop = (const volatile unsigned long long *)dp + 1;
+    A.ring_size = S->ring_size;
+    A.idle_ns = 200ull * 1000 * 1000;
+    A.smem_cap = S->smem;
+    // device memory per slot (rows of up to 64 words: |ic| <= 2048)
+    const uint64_t rows = 1ull << 17, chunk = 1ull << 14, wmax = 64;
+    const uint64_t tslots = pow2_at_least(2 * (rows + chunk));
+    bool oom = false;
+    auto take = [&](size_t bytes) -> void * {
+        DevBuf b;
+        b.p = dev_alloc(c, bytes);
+        b.bytes = bytes;
+        if (b.p) S->bufs.push_back(b);
+        else oom = true;
+        return b.p;
+    };
+    SlotMem &m = A.slot;
+    m.rows = rows;
+    m.chunk = chunk;
+    m.cs_words = rows * wmax;
+    m.tmp_words = chunk * wmax;
+    m.table_slots = tslots;
+    m.cs = (uint32_t *)take(4 * slots * m.cs_words);
+    m.bp_op = (uint8_t *)take(slots * rows);
+    m.bp_l = (uint32_t *)take(4 * slots * rows);
+    m.bp_r = (uint32_t *)take(4 * slots * rows);
+    m.used = (uint32_t *)take(4 * slots * rows);
+    m.table = (unsigned long long *)take(8 * slots * tslots);
+    m.tmp = (uint32_t *)take(4 * slots * m.tmp_words);
+    m.pending = (uint32_t *)take(4 * slots * chunk);
+    m.slotpos = (uint32_t *)take(4 * slots * chunk);
+    m.bitmap = (uint32_t *)take(4 * slots * ((chunk + 31) / 32));
+    m.blk = (uint32_t *)take(4 * slots);
+    m.lvl = (int64_t *)take(8 * slots * 2 * (kMaxCost + 2));
+    m.state = (SolveState *)take(sizeof(SolveState) * slots);
+    m.tstack = (uint32_t *)take(16 * slots * (kMaxCost + 2));
+    A.in_bytes = (uint8_t *)take(slots * kServeMaxBytes);
+    A.in_offs = (uint32_t *)take(4 * slots * (kServeMaxStrings + 1));
+    A.st_hset = (uint64_t *)take(8 * slots * kHsetCapHost);
+    A.st_rank_of = (uint16_t *)take(2 * slots * kHsetCapHost);
+    A.st_uniq = (uint16_t *)take(2 * slots * kMaxIC);
+    A.word_start = (uint32_t *)take(4 * slots * kMaxIC);
+    A.word_len = (uint32_t *)take(4 * slots * kMaxIC);
+    A.len_start = (uint32_t *)take(4 * slots * (REI_MAX_STRLEN + 2));
+    A.gt_off = (uint32_t *)take(4 * slots * (kMaxIC + 1));
+    A.pair_cap = kServePairCap;
+    A.gt_pair = (uint32_t *)take(4 * slots * A.pair_cap);
+    A.pos = (uint32_t *)take(4 * slots * kMaxWords);
+    A.neg = (uint32_t *)take(4 * slots * kMaxWords);
+    A.leaf = (uint32_t *)take(4 * slots * kMaxWords * 256);
+    A.sinfo = (StageInfo *)take(sizeof(StageInfo) * slots);
+    A.head = (unsigned long long *)take(64);
+    if (oom) return REI_OOM;
+    if (cudaStreamCreateWithFlags(&S->kstream, cudaStreamNonBlocking) != cudaSuccess) return REI_ECUDA;
+    if (cudaEventCreateWithFlags(&S->kdone, cudaEventDisableTiming) != cudaSuccess) return REI_ECUDA;
+    // allocations from the context allocator are stream-ordered on its stream
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return REI_ECUDA;
+    if (cudaMemset(m.table, 0xFF, 8 * slots * tslots) != cudaSuccess) return REI_ECUDA;
+    if (cudaMemset(m.bitmap, 0, 4 * slots * ((chunk + 31) / 32)) != cudaSuccess) return REI_ECUDA;
+    if (cudaMemset(A.head, 0, 64) != cudaSuccess) return REI_ECUDA;
+    return REI_OK;
+}
+
+bool kernel_running(rei_server *S) {
+    if (!S->running) return false;
+    if (cudaEventQuery(S->kdone) == cudaSuccess) S->running = false;
+    return S->running;
+}
+
+rei_status ensure_kernel(rei_server *S) {
+    if (kernel_running(S)) return REI_OK;
+    if (launch_serve(&S->args, S->grid, S->threads, S->smem, S->kstream) != cudaSuccess) return REI_ECUDA;
+    if (cudaEventRecord(S->kdone, S->kstream) != cudaSuccess) return REI_ECUDA;
+    S->ctx->launches++;
+    S->running = true;
+    return REI_OK;
+}
+
+void stop_kernel(rei_server *S) {
+    volatile unsigned long long *ctl = S->ctl_h;
+    ctl[1] = 1;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    if (S->running) cudaEventSynchronize(S->kdone);
+    S->running = false;
+    ctl[1] = 0;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+}
+
+void finish(rei_server *S, uint64_t ticket, const rei_result &r, const char *regex, size_t rlen,
+            const uint8_t *tree, size_t tlen) {
+    rei_server::Done d{};
+    d.r = r;
+    d.regex.assign(regex, rlen);
+    d.tree.assign(tree, tree + tlen);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->done[ticket] = std::move(d);
+    }
+    S->done_cv.notify_all();
+}
+
+void solve_alone(rei_server *S, rei_server::Req &req) {
+    req.p.alphabet = req.alphabet.data();
+    req.p.bytes = req.bytes.data();
+    req.p.offsets = req.offs.data();
+    char rbuf[8192];
+    uint8_t tbuf[2 * (REI_MAX_COST + 1)];
+    rei_result r{};
+    r.regex = rbuf;
+    r.regex_cap = sizeof rbuf;
+    r.tree = tbuf;
+    r.tree_cap = sizeof tbuf;
+    rei_status s;
+    {
+        std::lock_guard<std::mutex> g(S->ctx->mu);
+        s = solve_one(S->ctx, &req.p, &r);
+    }
+    if (s != REI_OK && s != REI_NOT_FOUND && s != REI_OOM) r.status = s;
+    r.stats.ms_total = now_ms() - req.t_submit;
+    finish(S, req.ticket, r, rbuf, r.status == REI_OK ? r.regex_len : 0, tbuf,
+           r.status == REI_OK ? r.tree_len : 0);
+}
+
 void server_loop(rei_server *S) {
+    cudaSetDevice(S->ctx->device);
+    volatile unsigned long long *ctl = S->ctl_h;
+    std::vector<rei_server::Req> alone;
     for (;;) {
-        rei_server::Req req;
+        bool progress = false;
+        // 1. completions
+        for (auto it = S->live.begin(); it != S->live.end();) {
+            const uint64_t job = it->first;
+            ServeOut &o = S->outs_h[job % S->ring_size];
+            if (*(volatile unsigned long long *)&o.done != job + 1) {
+                ++it;
+                continue;
+            }
+            std::atomic_thread_fence(std::memory_order_acquire);
+            rei_server::Req &req = it->second;
+            const BatchOut b = o.out;
+            progress = true;
+            S->live_bytes -= req.footprint;
+            if (b.status == ST_NEED_MEM) {
+                alone.push_back(std::move(req));
+                it = S->live.erase(it);
+                continue;
+            }
+            rei_result r{};
+            r.stats.n_ic = o.info.n;
+            r.stats.words = o.info.W;
+            r.stats.max_len = o.info.max_len;
+            r.stats.guide_pairs = o.info.G;
+            r.stats.candidates = b.candidates;
+            r.stats.unique = b.unique;
+            r.stats.levels = b.levels;
+            for (int k = 0; k < 5; k++) r.stats.cand_op[k] = b.cand_op[k];
+            r.stats.ms_search_kernel = b.ns / 1e6;
+            r.stats.ms_total = now_ms() - req.t_submit;
+            r.stats.search_launches = 1;
+            switch (b.status) {
+            case ST_FOUND: r.status = REI_OK; break;
+            case ST_NOT_FOUND: r.status = REI_NOT_FOUND; break;
+            case ST_OOM: r.status = REI_OOM; break;
+            case ST_BAD: r.status = REI_EINVAL; break;
+            default: r.status = REI_ECUDA; break;
+            }
+            std::string text;
+            uint32_t ntok = 0;
+            if (r.status == REI_OK) {
+                r.cost = b.cost;
+                ntok = b.tree_len;
+                text = format_regex(o.tree, ntok, req.alphabet.data());
+            }
+            r.regex_len = text.size();
+            r.tree_len = 2ull * ntok;
+            finish(S, req.ticket, r, text.data(), text.size(), o.tree, 2ull * ntok);
+            it = S->live.erase(it);
+        }
+        // 2. requests too large for a slot: solved alone while the launch is stopped
+        if (!alone.empty()) {
+            stop_kernel(S);
+            for (auto &req : alone) solve_alone(S, req);
+            alone.clear();
+            progress = true;
+        }
+        // 3. admissions into the ring, then one publication
+        uint64_t admitted = 0;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            S->cv.wait(lk, [&] { return S->stop || !S->queue.empty(); });
-            if (S->queue.empty()) return;
-            req = std::move(S->queue.front());
-            S->queue.pop_front();
+            const uint64_t oldest = S->live.empty() ? S->published : S->live.begin()->first;
+            while (!S->queue.empty() && S->live.size() < S->max_live &&
+                   S->published + 1 - oldest <= S->ring_size &&
+                   (S->live.empty() || S->live_bytes + S->queue.front().footprint <= S->budget)) {
+                rei_server::Req req = std::move(S->queue.front());
+                S->queue.pop_front();
+                const uint32_t n_str = req.p.n_pos + req.p.n_neg;
+                const uint32_t total = req.offs.back();
+                if (n_str > kServeMaxStrings || total > kServeMaxBytes) {
+                    alone.push_back(std::move(req));
+                    continue;
+                }
+                const uint64_t job = S->published;
+                ServeReq &q = S->ring_h[job % S->ring_size];
+                q.n_pos = req.p.n_pos;
+                q.n_neg = req.p.n_neg;
+                q.n_sym = req.p.n_sym;
+                q.total_bytes = total;
+                memcpy(q.alphabet, req.alphabet.data(), req.p.n_sym);
+                q.costs = req.p.costs;
+                q.max_cost = req.p.max_cost;
+                q.max_errors = req.p.max_errors;
+                q.flags = req.p.flags & ~REI_F_DEVICE_INPUT;
+                q.mem_budget = req.p.mem_budget;
+                memcpy(q.offs, req.offs.data(), 4ull * (n_str + 1));
+                if (total) memcpy(q.bytes, req.bytes.data(), total);
+                S->live_bytes += req.footprint;
+                S->live[job] = std::move(req);
+                S->published++;
+                admitted++;
+            }
         }
-        req.p.alphabet = req.alphabet.data();
-        req.p.bytes = req.bytes.data();
-        req.p.offsets = req.offs.data();
-        rei_server::Done d{};
-        char rbuf[8192];
-        uint8_t tbuf[2 * (REI_MAX_COST + 1)];
-        d.r.regex = rbuf;
-        d.r.regex_cap = sizeof rbuf;
-        d.r.tree = tbuf;
-        d.r.tree_cap = sizeof tbuf;
-        rei_status s = rei_solve_problem(S->ctx, &req.p, &d.r);
-        if (s != REI_OK) d.r.status = s;
-        d.regex.assign(rbuf, d.r.regex_len <= sizeof rbuf ? d.r.regex_len : 0);
-        d.tree.assign(tbuf, tbuf + (d.r.tree_len <= sizeof tbuf ? d.r.tree_len : 0));
-        {
-            std::lock_guard<std::mutex> lk(S->mu);
-            S->done[req.ticket] = std::move(d);
+        if (admitted) {
+            std::atomic_thread_fence(std::memory_order_seq_cst);
+            ctl[0] = S->published;
+            std::atomic_thread_fence(std::memory_order_seq_cst);
+            progress = true;
         }
-        S->done_cv.notify_all();
+        // 4. a launch must be running while published requests wait
+        if (!S->live.empty()) {
+            const rei_status s = ensure_kernel(S);
+            if (s != REI_OK) {
+                server_fail(S, s);
+                return;
+            }
+        }
+        // 5. wait for work, or poll completions
+        std::unique_lock<std::mutex> lk(S->mu);
+        if (S->stop && S->queue.empty() && S->live.empty() && alone.empty()) break;
+        if (!progress) {
+            if (S->live.empty()) S->cv.wait_for(lk, std::chrono::milliseconds(2));
+            else {
+                lk.unlock();
+                std::this_thread::sleep_for(std::chrono::microseconds(20));
+            }
+        }
     }
+    stop_kernel(S);
 }
 
 }  // namespace
@@ -1252,6 +1531,12 @@ rei_status rei_server_create(rei_ctx *ctx, uint64_t budget_bytes, uint32_t max_l
     S->ctx = ctx;
     S->budget = budget_bytes;
     S->max_live = max_live;
+    rei_status s = server_setup(S);
+    if (s != REI_OK) {
+        rei_server_destroy(S);
+        return s;
+    }
+    S->max_live = std::min<uint32_t>(max_live, S->ring_size);
     S->worker = std::thread(server_loop, S);
     *out = S;
     return REI_OK;
@@ -1265,15 +1550,21 @@ rei_status rei_server_submit(rei_server *S, const rei_problem *p, uint64_t *tick
     rei_server::Req r;
     const uint32_t n_str = p->n_pos + p->n_neg;
     r.alphabet.assign(p->alphabet, p->alphabet + p->n_sym);
-    r.offs.assign(p->offsets, p->offsets + n_str + 1);
-    const uint32_t total = n_str ? p->offsets[n_str] : 0;
+    if (n_str) r.offs.assign(p->offsets, p->offsets + n_str + 1);
+    else r.offs.assign(1, 0);
+    const uint32_t total = r.offs.back();
     r.bytes.assign(p->bytes, p->bytes + total);
-    if (r.offs.empty()) r.offs.push_back(0);
     r.p = *p;
+    r.t_submit = now_ms();
+    // the cache this request may hold: its budget, at most one slot's cache
+    const uint64_t slot_bytes = S->args.slot.rows * (4ull * 64 + 28);
+    r.footprint = std::min<uint64_t>(p->mem_budget, slot_bytes);
     {
         std::lock_guard<std::mutex> lk(S->mu);
+        if (S->error != REI_OK) return S->error;
         r.ticket = S->next_ticket++;
         *ticket = r.ticket;
+        S->open.insert(r.ticket);
         S->queue.push_back(std::move(r));
     }
     S->cv.notify_one();
@@ -1283,12 +1574,14 @@ rei_status rei_server_submit(rei_server *S, const rei_problem *p, uint64_t *tick
 rei_status rei_server_poll(rei_server *S, uint64_t ticket, rei_result *out, int block_ms) {
     if (!S || !out) return REI_EINVAL;
     std::unique_lock<std::mutex> lk(S->mu);
-    auto ready = [&] { return S->done.count(ticket) > 0; };
+    if (!S->open.count(ticket)) return REI_EINVAL;
+    auto ready = [&] { return S->done.count(ticket) > 0 || S->error != REI_OK; };
     if (!ready()) {
         if (block_ms == 0) return REI_EBUSY;
         if (block_ms < 0) S->done_cv.wait(lk, ready);
         else if (!S->done_cv.wait_for(lk, std::chrono::milliseconds(block_ms), ready)) return REI_EBUSY;
     }
+    if (!S->done.count(ticket)) return S->error;
     rei_server::Done &d = S->done[ticket];
     char *rb = out->regex;
     size_t rc = out->regex_cap;
@@ -1314,7 +1607,10 @@ rei_status rei_server_poll(rei_server *S, uint64_t ticket, rei_result *out, int 
         if (tc >= d.tree.size()) memcpy(tb, d.tree.data(), d.tree.size());
         else s = REI_EBUFSZ;
     }
-    if (s == REI_OK) S->done.erase(ticket);
+    if (s == REI_OK) {
+        S->done.erase(ticket);
+        S->open.erase(ticket);
+    }
     return s;
 }
 
@@ -1326,6 +1622,15 @@ void rei_server_destroy(rei_server *S) {
     }
     S->cv.notify_all();
     if (S->worker.joinable()) S->worker.join();
+    if (S->kstream) {
+        cudaStreamSynchronize(S->kstream);
+        cudaStreamDestroy(S->kstream);
+    }
+    if (S->kdone) cudaEventDestroy(S->kdone);
+    for (DevBuf &b : S->bufs) dev_free(S->ctx, b);
+    if (S->ring_h) cudaFreeHost(S->ring_h);
+    if (S->outs_h) cudaFreeHost(S->outs_h);
+    if (S->ctl_h) cudaFreeHost(S->ctl_h);
     delete S;
 }
 

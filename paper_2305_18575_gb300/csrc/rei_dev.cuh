@@ -205,4 +205,50 @@ struct BatchArgs {
     uint32_t *queue;   // next problem to take
 };
 
+// ---- served search
+
+constexpr uint32_t kServeMaxStrings = 255;   // examples per served request
+constexpr uint32_t kServeMaxBytes = 8192;    // example bytes per served request
+constexpr uint32_t kServePairCap = 1u << 16; // guide pairs a served request may stage
+
+// a request in the ring (mapped host memory), written before it is published
+struct ServeReq {
+    uint32_t n_pos, n_neg, n_sym, total_bytes;
+    uint8_t alphabet[256];
+    rei_costs costs;
+    uint32_t max_cost, max_errors, flags;
+    uint64_t mem_budget;
+    uint32_t offs[kServeMaxStrings + 1];
+    uint8_t bytes[kServeMaxBytes];
+};
+
+// a result in the ring (mapped host memory); `done` = job + 1 once written
+struct ServeOut {
+    unsigned long long done;
+    BatchOut out;
+    StageInfo info;
+    uint8_t tree[2 * (REI_MAX_COST + 1)];
+};
+
+struct ServeArgs {
+    SlotMem slot;
+    // per slot: the request's bytes, staging scratch, staged problem
+    uint8_t *in_bytes;
+    uint32_t *in_offs;
+    uint64_t *st_hset;
+    uint16_t *st_rank_of, *st_uniq;
+    uint32_t *word_start, *word_len, *len_start, *gt_off, *gt_pair, *pos, *neg, *leaf;
+    uint32_t pair_cap;
+    StageInfo *sinfo;
+    // the ring and its control words
+    const ServeReq *ring;
+    ServeOut *outs;
+    uint32_t ring_size;
+    const volatile unsigned long long *avail;  // jobs published (mapped)
+    const volatile unsigned long long *stop;   // nonzero: return (mapped)
+    unsigned long long *head;                  // next job to claim (device)
+    unsigned long long idle_ns;
+    size_t smem_cap;
+};
+
 }  // namespace rei

@@ -24,6 +24,7 @@
 #include <cstdint>
 
 #include "rei_dev.cuh"
+#include "stage_dev.cuh"
 
 namespace rei {
 
@@ -592,6 +593,18 @@ __device__ uint32_t emit_tree(const SolveJob &J, uint32_t op, uint32_t l, uint32
 // phases with grid barriers, and go back to waiting.
 
 constexpr uint32_t kSortMax = 2048;  // new languages appended by CTA 0 alone, after a sort
+
+__host__ __device__ size_t solve_smem_bytes(uint32_t W, uint32_t n, uint32_t G, uint32_t max_len,
+                                            uint32_t seg_cap, bool gt_in_smem, uint32_t warps) {
+    const uint32_t Ws = (W & 1u) ? W : W + 1;
+    size_t b = sizeof(Seg) * seg_cap + sizeof(uint64_t) * (seg_cap + 1) + sizeof(SegTile) * seg_cap;
+    b += sizeof(unsigned long long) * kSortMax;
+    b += 2 * sizeof(uint32_t) * seg_cap;
+    b += 2 * sizeof(uint32_t) * W;
+    if (gt_in_smem) b += sizeof(uint32_t) * (((n + 1 + G + max_len + 2) + 3) & ~3u);
+    b += sizeof(uint32_t) * (size_t)warps * (((W + 3) & ~3u) + 2 * 32 * Ws);
+    return b;
+}
 
 enum Cmd : uint32_t { CMD_NONE = 0, CMD_CHUNK = 1, CMD_EXIT = 2, CMD_CLEAN = 3 };
 
@@ -1274,6 +1287,81 @@ __global__ void __launch_bounds__(256, 2) k_solve(const __grid_constant__ SolveJ
 // problems from a queue and solves each one on its own (its own memory slot,
 // no grid-wide synchronisation), with the same leader code as k_solve.
 
+// Solve the problem whose job (staged data, costs) is in shared memory J,
+// in memory slot `slot`, on this CTA alone; the report goes to *out and the
+// tree to J.tree.
+__device__ void solve_in_slot(SolveJob &J, const SlotMem &m, uint32_t slot, BatchOut *out, uint8_t *smem_raw,
+                              Plan *s_plan, uint32_t *s_red, uint64_t *s_tiles, unsigned long long *s_found,
+                              uint32_t *s_npend, Lead *L) {
+    const uint32_t tid = threadIdx.x;
+    const unsigned long long t_start = globaltimer_ns();
+    if (tid == 0) {
+        const uint64_t so = slot;
+        J.cs = m.cs + so * m.cs_words;
+        J.bp_op = m.bp_op + so * m.rows;
+        J.bp_l = m.bp_l + so * m.rows;
+        J.bp_r = m.bp_r + so * m.rows;
+        J.used = m.used + so * m.rows;
+        J.cache_alloc = umin64(J.cap, m.cs_words / J.W < m.rows ? m.cs_words / J.W : m.rows);
+        J.table = m.table + so * m.table_slots;
+        J.table_mask = m.table_slots - 1;
+        J.tmp = m.tmp + so * m.tmp_words;
+        J.chunk_max = umin64(m.chunk, m.tmp_words / J.W);
+        J.pending = m.pending + so * m.chunk;
+        J.slotpos = m.slotpos + so * m.chunk;
+        J.bitmap = m.bitmap + so * ((m.chunk + 31) / 32);
+        J.blk = m.blk + so;
+        J.lvl_start = m.lvl + so * 2 * (kMaxCost + 2);
+        J.lvl_count = J.lvl_start + (kMaxCost + 2);
+        J.st = m.state + so;
+        J.tstack = m.tstack + so * 4 * (kMaxCost + 2);
+        J.trace = nullptr;
+        J.solo_tiles = 0xFFFFFFFFu;
+    }
+    __syncthreads();
+    SolveState *st = J.st;
+    // fresh search state and level table for this problem
+    for (uint32_t c = tid; c < 2 * (kMaxCost + 2); c += blockDim.x) J.lvl_start[c] = 0;
+    if (tid == 0) {
+        SolveState z{};
+        z.status = ST_RUNNING;
+        z.level = J.c[0];
+        z.found = kNone;
+        z.partial_level = J.max_cost + 1;
+        *st = z;
+    }
+    __threadfence();
+    __syncthreads();
+    Shared S;
+    uint32_t *wm;
+    carve_shared(J, S, smem_raw, &wm);
+    const Cta K{s_plan, s_red, s_tiles, s_found, s_npend, L, wm};
+    uint32_t epoch = 0;
+    lead_search(J, st, S, K, false, epoch);
+    const uint32_t status = st->status;
+    if (status == ST_FOUND || status == ST_NOT_FOUND || status == ST_OOM) {
+        clean_table(J, L->size, st->pending_count, 1, 0);
+    } else {
+        // ran out of this slot's memory: the host solves it again alone;
+        // this slot's table is rebuilt from scratch
+        for (uint64_t i = tid; i <= J.table_mask; i += blockDim.x) J.table[i] = kEmpty;
+        for (uint64_t i = tid; i < (J.chunk_max + 31) / 32; i += blockDim.x) J.bitmap[i] = 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        BatchOut &o = *out;
+        o.status = status;
+        o.cost = st->ans_cost;
+        o.tree_len = st->tree_len;
+        o.candidates = st->candidates;
+        o.unique = st->unique_done;
+        o.levels = st->level;
+        for (int k = 0; k < 5; k++) o.cand_op[k] = st->cand_op[k];
+        o.ns = globaltimer_ns() - t_start;
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(256, 2) k_solve_batch(const BatchJob *jobs, const __grid_constant__ BatchArgs B) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     __shared__ Plan s_plan;
@@ -1285,7 +1373,6 @@ __global__ void __launch_bounds__(256, 2) k_solve_batch(const BatchJob *jobs, co
     __shared__ SolveJob J;
     __shared__ uint32_t s_prob;
     const uint32_t tid = threadIdx.x;
-    const uint32_t slot = blockIdx.x;
     for (;;) {
         if (tid == 0) s_prob = atomicAdd(B.queue, 1u);
         __syncthreads();
@@ -1293,74 +1380,162 @@ __global__ void __launch_bounds__(256, 2) k_solve_batch(const BatchJob *jobs, co
         __syncthreads();
         if (pi >= B.n) return;
         const BatchJob &bj = jobs[pi];
-        const unsigned long long t_start = globaltimer_ns();
-        // this problem's job: its staged data, this slot's memory
         if (tid == 0) {
             J = bj.job;
-            const SlotMem &m = B.slot;
-            const uint64_t so = slot;
-            J.cs = m.cs + so * m.cs_words;
-            J.bp_op = m.bp_op + so * m.rows;
-            J.bp_l = m.bp_l + so * m.rows;
-            J.bp_r = m.bp_r + so * m.rows;
-            J.used = m.used + so * m.rows;
-            J.cache_alloc = umin64(J.cap, m.cs_words / J.W < m.rows ? m.cs_words / J.W : m.rows);
-            J.table = m.table + so * m.table_slots;
-            J.table_mask = m.table_slots - 1;
-            J.tmp = m.tmp + so * m.tmp_words;
-            J.chunk_max = umin64(m.chunk, m.tmp_words / J.W);
-            J.pending = m.pending + so * m.chunk;
-            J.slotpos = m.slotpos + so * m.chunk;
-            J.bitmap = m.bitmap + so * ((m.chunk + 31) / 32);
-            J.blk = m.blk + so;
-            J.lvl_start = m.lvl + so * 2 * (kMaxCost + 2);
-            J.lvl_count = J.lvl_start + (kMaxCost + 2);
-            J.st = m.state + so;
             J.tree = bj.tree;
-            J.tstack = m.tstack + so * 4 * (kMaxCost + 2);
-            J.trace = nullptr;
-            J.solo_tiles = 0xFFFFFFFFu;
         }
         __syncthreads();
-        SolveState *st = J.st;
-        // fresh search state and level table for this problem
-        for (uint32_t c = tid; c < 2 * (kMaxCost + 2); c += blockDim.x) J.lvl_start[c] = 0;
+        solve_in_slot(J, B.slot, blockIdx.x, bj.out, smem_raw, &s_plan, s_red, &s_tiles, &s_found, &s_npend, &L);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the served search: a persistent launch whose CTAs take requests from a ring
+// in mapped host memory as the host publishes them, stage each one themselves
+// (scratch in their slot), solve it, and write the answer and a completion
+// word back to mapped memory.  A CTA that finds nothing to do for idle_ns, or
+// sees the stop word, returns; the host relaunches when work arrives.
+
+__device__ __forceinline__ unsigned long long ld_acquire_sys_u64(const volatile unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__global__ void __launch_bounds__(256, 2) k_serve(const __grid_constant__ ServeArgs A) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    __shared__ Plan s_plan;
+    __shared__ uint32_t s_red[32];
+    __shared__ uint64_t s_tiles;
+    __shared__ unsigned long long s_found;
+    __shared__ uint32_t s_npend;
+    __shared__ Lead L;
+    __shared__ SolveJob J;
+    __shared__ StageJob SJ;
+    __shared__ unsigned long long s_job;
+    __shared__ int16_t rank_tab[256];
+    const uint32_t tid = threadIdx.x;
+    const uint32_t slot = blockIdx.x;
+    for (;;) {
         if (tid == 0) {
-            SolveState z{};
-            z.status = ST_RUNNING;
-            z.level = J.c[0];
-            z.found = kNone;
-            z.partial_level = J.max_cost + 1;
-            *st = z;
+            // claim the next published request, backing off while there is none
+            const unsigned long long t0 = globaltimer_ns();
+            uint32_t nap = 64;
+            unsigned long long job = kNone;
+            for (;;) {
+                if (ld_acquire_sys_u64(A.stop)) break;
+                const unsigned long long h = ld_relaxed_u64(A.head);
+                const unsigned long long av = ld_acquire_sys_u64(A.avail);
+                if (h < av) {
+                    if (atomicCAS(A.head, h, h + 1) == h) {
+                        job = h;
+                        break;
+                    }
+                    continue;
+                }
+                __nanosleep(nap);
+                if (nap < 2048) nap <<= 1;
+                if (globaltimer_ns() - t0 > A.idle_ns) break;
+            }
+            s_job = job;
+        }
+        __syncthreads();
+        const unsigned long long job = s_job;
+        __syncthreads();
+        if (job == kNone) return;
+        const uint32_t r = (uint32_t)(job % A.ring_size);
+        const ServeReq &q = A.ring[r];
+        ServeOut &o = A.outs[r];
+        // the request into this slot's device buffers, then staged by this CTA
+        const uint32_t n_str = q.n_pos + q.n_neg;
+        uint8_t *in_b = A.in_bytes + (uint64_t)slot * kServeMaxBytes;
+        uint32_t *in_o = A.in_offs + (uint64_t)slot * (kServeMaxStrings + 1);
+        for (uint32_t i = tid; i < q.total_bytes; i += blockDim.x) in_b[i] = q.bytes[i];
+        for (uint32_t i = tid; i <= n_str; i += blockDim.x) in_o[i] = q.offs[i];
+        if (tid == 0) {
+            StageJob sj{};
+            sj.bytes = in_b;
+            sj.offs = in_o;
+            sj.n_pos = q.n_pos;
+            sj.n_neg = q.n_neg;
+            for (uint32_t a = 0; a < q.n_sym; a++) sj.alphabet[a] = q.alphabet[a];
+            sj.n_sym = q.n_sym;
+            sj.info = A.sinfo + slot;
+            sj.word_start = A.word_start + (uint64_t)slot * kMaxIC;
+            sj.word_len = A.word_len + (uint64_t)slot * kMaxIC;
+            sj.len_start = A.len_start + (uint64_t)slot * (REI_MAX_STRLEN + 2);
+            sj.gt_off = A.gt_off + (uint64_t)slot * (kMaxIC + 1);
+            sj.gt_pair = A.gt_pair + (uint64_t)slot * A.pair_cap;
+            sj.pair_cap = A.pair_cap;
+            sj.pos_mask = A.pos + (uint64_t)slot * kMaxWords;
+            sj.neg_mask = A.neg + (uint64_t)slot * kMaxWords;
+            sj.leaf = A.leaf + (uint64_t)slot * kMaxWords * 256;
+            SJ = sj;
         }
         __threadfence();
         __syncthreads();
-        Shared S;
-        uint32_t *wm;
-        carve_shared(J, S, smem_raw, &wm);
-        const Cta K{&s_plan, s_red, &s_tiles, &s_found, &s_npend, &L, wm};
-        uint32_t epoch = 0;
-        lead_search(J, st, S, K, false, epoch);
-        const uint32_t status = st->status;
-        if (status == ST_FOUND || status == ST_NOT_FOUND || status == ST_OOM) {
-            clean_table(J, L.size, st->pending_count, 1, 0);
-        } else {
-            // ran out of this slot's memory: the host solves it again alone;
-            // this slot's table is rebuilt from scratch
-            for (uint64_t i = tid; i <= J.table_mask; i += blockDim.x) J.table[i] = kEmpty;
-            for (uint64_t i = tid; i < (J.chunk_max + 31) / 32; i += blockDim.x) J.bitmap[i] = 0;
+        stage_run(SJ, A.st_hset + (uint64_t)slot * kHsetCap, A.st_rank_of + (uint64_t)slot * kHsetCap,
+                  A.st_uniq + (uint64_t)slot * kMaxIC, rank_tab);
+        __threadfence();
+        __syncthreads();
+        const StageInfo I = *SJ.info;
+        __syncthreads();
+        uint32_t verdict = 0;  // 0 solve, 1 invalid input, 2 too large for this launch
+        if (tid == 0) {
+            if (I.status == SE_PAIRS || I.status == SE_IC_LARGE) verdict = 2;
+            else if (I.status != SE_OK) verdict = 1;
+            SolveJob j{};
+            if (!verdict) {
+                j.n = I.n;
+                j.W = I.W;
+                j.G = I.G;
+                j.n_sym = q.n_sym;
+                j.max_len = I.max_len;
+                j.gt_off = SJ.gt_off;
+                j.gt_pair = SJ.gt_pair;
+                j.len_start = SJ.len_start;
+                j.pos_mask = SJ.pos_mask;
+                j.neg_mask = SJ.neg_mask;
+                j.leaf = SJ.leaf;
+                j.leaf_stride = kMaxWords;
+                j.n_pos_set = I.n_pos_set;
+                j.pos_eps = I.pos_eps;
+                j.neg_eps = I.neg_eps;
+                j.c[0] = q.costs.c_sym;
+                j.c[1] = q.costs.c_opt;
+                j.c[2] = q.costs.c_star;
+                j.c[3] = q.costs.c_cat;
+                j.c[4] = q.costs.c_alt;
+                j.max_cost = q.max_cost;
+                j.max_errors = q.max_errors;
+                j.flags = q.flags;
+                const uint64_t per = 4ull * I.W + 28;
+                j.cap = umin64(q.mem_budget / per, 0x7FFF0000ull);
+                j.seg_cap = 2 * q.max_cost + 4;
+                j.gt_in_smem = solve_smem_bytes(I.W, I.n, I.G, I.max_len, j.seg_cap, true, blockDim.x / 32) <=
+                               A.smem_cap;
+                if (solve_smem_bytes(I.W, I.n, I.G, I.max_len, j.seg_cap, j.gt_in_smem, blockDim.x / 32) >
+                        A.smem_cap ||
+                    I.W > A.slot.cs_words / A.slot.rows)
+                    verdict = 2;
+                j.tree = o.tree;
+            }
+            J = j;
+            s_red[0] = verdict;
         }
         __syncthreads();
+        verdict = s_red[0];
+        __syncthreads();
+        if (verdict == 0) {
+            solve_in_slot(J, A.slot, slot, &o.out, smem_raw, &s_plan, s_red, &s_tiles, &s_found, &s_npend, &L);
+        } else if (tid == 0) {
+            o.out.status = verdict == 1 ? ST_BAD : ST_NEED_MEM;
+        }
         if (tid == 0) {
-            BatchOut &o = *bj.out;
-            o.status = status;
-            o.cost = st->ans_cost;
-            o.tree_len = st->tree_len;
-            o.candidates = st->candidates;
-            o.unique = st->unique_done;
-            o.levels = st->level;
-            for (int k = 0; k < 5; k++) o.cand_op[k] = st->cand_op[k];
-            o.ns = globaltimer_ns() - t_start;
+            o.info = I;
+            __threadfence_system();
+            *(volatile unsigned long long *)&o.done = job + 1;
+            __threadfence_system();
         }
         __syncthreads();
     }
@@ -1383,18 +1558,6 @@ __global__ void k_rehash(const __grid_constant__ SolveJob J, uint32_t count) {
             p = (p + 1) & J.table_mask;
         }
     }
-}
-
-size_t solve_smem_bytes(uint32_t W, uint32_t n, uint32_t G, uint32_t max_len, uint32_t seg_cap,
-                        bool gt_in_smem, uint32_t warps) {
-    const uint32_t Ws = (W & 1u) ? W : W + 1;
-    size_t b = sizeof(Seg) * seg_cap + sizeof(uint64_t) * (seg_cap + 1) + sizeof(SegTile) * seg_cap;
-    b += sizeof(unsigned long long) * kSortMax;
-    b += 2 * sizeof(uint32_t) * seg_cap;
-    b += 2 * sizeof(uint32_t) * W;
-    if (gt_in_smem) b += sizeof(uint32_t) * (((n + 1 + G + max_len + 2) + 3) & ~3u);
-    b += sizeof(uint32_t) * (size_t)warps * (((W + 3) & ~3u) + 2 * 32 * Ws);
-    return b;
 }
 
 cudaError_t launch_solve(const SolveJob *job, uint32_t grid, uint32_t threads, size_t smem,
@@ -1428,6 +1591,19 @@ cudaError_t solve_batch_occupancy(uint32_t threads, size_t smem, int *blocks_per
     cudaError_t e = cudaFuncSetAttribute(k_solve_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_solve_batch, (int)threads, smem);
+}
+
+cudaError_t launch_serve(const ServeArgs *args, uint32_t grid, uint32_t threads, size_t smem, cudaStream_t stream) {
+    cudaError_t e = cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_serve<<<grid, threads, smem, stream>>>(*args);
+    return cudaGetLastError();
+}
+
+cudaError_t serve_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_serve, (int)threads, smem);
 }
 
 }  // namespace rei
