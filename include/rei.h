@@ -181,12 +181,22 @@ void rei_ctx_destroy(rei_ctx *ctx);
  *   REI_OPT_CACHE_INIT initial cache capacity in languages (0 = automatic)
  *   REI_OPT_SOLO_TILES chunks of at most this many 32-candidate tiles run on
  *                      one CTA without grid-wide synchronisation (-1 =
- *                      automatic, 0 = never) */
+ *                      automatic, 0 = never)
+ *   REI_OPT_SMALL_ROWS languages the search keeps in one CTA's shared memory
+ *                      at its start, with their uniqueness table (-1 =
+ *                      automatic, 0 = never, else a power of two 256..16384;
+ *                      shrunk until the launch keeps two CTAs per SM).
+ *   REI_OPT_FUSED_STAGE 1 = stage a problem inside its search launch when the
+ *                      launch can hold it (|ic| <= 2048, strings <= 8 KiB;
+ *                      the default), 0 = always a separate staging launch.
+ *                      Results never depend on any option. */
 #define REI_OPT_CHUNK 1
 #define REI_OPT_GRID 2
 #define REI_OPT_KEEP_CACHE 3
 #define REI_OPT_CACHE_INIT 4
 #define REI_OPT_SOLO_TILES 5
+#define REI_OPT_SMALL_ROWS 6
+#define REI_OPT_FUSED_STAGE 7
 rei_status rei_ctx_set_option(rei_ctx *ctx, int option, int64_t value);
 
 /* Number of kernels this context launched since it was created. */

@@ -52,7 +52,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 
     def compile_one(src):
         obj = os.path.join(OBJDIR, src.replace(".cu", ".o"))
-        cmd = [cc, "-c", os.path.join(CSRC, src), "-o", obj, *ARCH, *FLAGS]
+        cmd = [cc, "-c", os.path.join(CSRC, src), "-o", obj, *ARCH, *FLAGS, *os.environ.get("REI_NVCC_EXTRA", "").split()]
         if ptxas_info:
             cmd += ["-Xptxas", "-v"]
         r = subprocess.run(cmd, capture_output=True, text=True)

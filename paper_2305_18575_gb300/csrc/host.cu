@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "rei_dev.cuh"
+#include "stage_dev.cuh"
 
 namespace rei {
 cudaError_t launch_solve_batch(const BatchJob *jobs_dev, const BatchArgs *args, uint32_t grid, uint32_t threads,
@@ -28,6 +29,9 @@ cudaError_t launch_solve_batch(const BatchJob *jobs_dev, const BatchArgs *args, 
 cudaError_t solve_batch_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm);
 cudaError_t launch_stage(const StageJob *jobs_dev, uint32_t n_jobs, cudaStream_t stream);
 cudaError_t launch_serve(const ServeArgs *args, uint32_t grid, uint32_t threads, size_t smem, cudaStream_t stream);
+cudaError_t launch_solve_fused(const FuseArgs *args, uint32_t grid, uint32_t threads, size_t smem,
+                               cudaStream_t stream);
+cudaError_t solve_fused_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm);
 cudaError_t serve_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm);
 size_t stage_smem_bytes();
 cudaError_t launch_solve(const SolveJob *job, uint32_t grid, uint32_t threads, size_t smem,
@@ -35,12 +39,11 @@ cudaError_t launch_solve(const SolveJob *job, uint32_t grid, uint32_t threads, s
 cudaError_t solve_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm);
 cudaError_t launch_rehash(const SolveJob *job, uint32_t count, uint32_t grid, cudaStream_t stream);
 size_t solve_smem_bytes(uint32_t W, uint32_t n, uint32_t G, uint32_t max_len, uint32_t seg_cap,
-                        bool gt_in_smem, uint32_t warps);
+                        bool gt_in_smem, uint32_t warps, uint32_t small_rows = 0);
 }  // namespace rei
 
 using namespace rei;
 
-static constexpr uint32_t kHsetCapHost = 4 * kMaxIC;  // the staging hash set's slots
 
 namespace {
 
@@ -65,7 +68,9 @@ struct rei_ctx {
     size_t smem_optin = 0;
     uint64_t launches = 0;
 
-    int64_t opt_chunk = 0, opt_grid = 0, opt_keep = 0, opt_cache_init = 0, opt_solo_tiles = -1;
+    int64_t opt_chunk = 0, opt_grid = 0, opt_keep = 0, opt_cache_init = 0, opt_solo_tiles = -1, opt_small_rows = -1;
+    int64_t opt_fused = 1;
+    size_t smem_sm = 0;  // shared memory per SM
 
     // staging
     DevBuf in_bytes, in_offs, stage_job, stage_info, word_start, word_len, len_start, gt_off, gt_pair,
@@ -399,6 +404,217 @@ rei_status write_outputs(rei_result *out, const uint8_t *tok, uint32_t ntok, con
 }
 
 // ---------------------------------------------------------------------------
+// the plain solve, staged inside its search launch
+
+// Pinned host layout of a plain solve: the job of a relaunch, then the state,
+// the answer's tokens and the staging report (the device state buffer holds
+// the same three, so one copy brings them back), then the inputs.
+size_t state_bytes(uint32_t max_cost) {
+    return (sizeof(SolveState) + 2ull * (max_cost + 1) + 15) & ~size_t(15);
+}
+
+// Stage and search in one cooperative launch (k_solve_fused).  REI_OK: the
+// launch ran; *hst holds its final state (an answer, not found, out of
+// memory, a timeout, or a request for more memory that the caller's relaunch
+// loop serves) and sg.info the staging report.  REI_EBUSY: the problem needs
+// the separate staging launch (|ic| beyond what the launch stages, a guide
+// table beyond the pair buffer, shared memory, or an invalid input, which the
+// staging launch reports).
+rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_search, uint32_t &grid_out,
+                     uint64_t &h2d, uint64_t &d2h) {
+    rei_status s;
+    const uint32_t n_str = p->n_pos + p->n_neg, max_cost = p->max_cost;
+    const bool dev_in = (p->flags & REI_F_DEVICE_INPUT) != 0;
+    const uint64_t total = dev_in ? p->total_bytes : (n_str ? p->offsets[n_str] : 0);
+    if (total > kServeMaxBytes) return REI_EBUSY;
+    const size_t sb = state_bytes(max_cost);
+    const size_t ob = (4ull * (n_str + 1) + 15) & ~size_t(15);
+    const size_t pin_in = sizeof(SolveJob) + sb + sizeof(StageInfo);
+    if ((s = ensure_pinned(c, pin_in + (dev_in ? 0 : ob + total + 16)))) return s;
+    CK(cudaStreamSynchronize(c->stream));  // pinned buffer reuse
+
+    // inputs
+    const uint8_t *dbytes;
+    const uint32_t *doffs;
+    if (dev_in) {
+        dbytes = p->bytes;
+        doffs = p->offsets;
+        if (n_str == 0) {
+            if ((s = ensure(c, c->in_offs, 16))) return s;
+            CK(cudaMemsetAsync(c->in_offs.p, 0, 4, c->stream));
+            doffs = (const uint32_t *)c->in_offs.p;
+        }
+    } else {
+        if ((s = ensure(c, c->in_bytes, ob + total + 16))) return s;
+        uint8_t *hp = c->h_pin + pin_in;
+        uint32_t *ho = (uint32_t *)hp;
+        if (n_str) memcpy(ho, p->offsets, 4ull * (n_str + 1));
+        else ho[0] = 0;
+        if (total) memcpy(hp + ob, p->bytes, total);
+        CK(cudaMemcpyAsync(c->in_bytes.p, hp, ob + total, cudaMemcpyHostToDevice, c->stream));
+        h2d += ob + total;
+        doffs = (const uint32_t *)c->in_bytes.p;
+        dbytes = (const uint8_t *)c->in_bytes.p + ob;
+    }
+
+    // staged-problem buffers
+    if ((s = ensure(c, c->word_start, 4ull * kMaxIC))) return s;
+    if ((s = ensure(c, c->word_len, 4ull * kMaxIC))) return s;
+    if ((s = ensure(c, c->len_start, 4ull * (REI_MAX_STRLEN + 2)))) return s;
+    if ((s = ensure(c, c->gt_off, 4ull * (kMaxIC + 1)))) return s;
+    if ((s = ensure(c, c->gt_pair, 4ull * c->pair_cap))) return s;
+    if ((s = ensure(c, c->pos, 4ull * kMaxWords))) return s;
+    if ((s = ensure(c, c->neg, 4ull * kMaxWords))) return s;
+    if ((s = ensure(c, c->leaf, 4ull * kMaxWords * p->n_sym))) return s;
+
+    // search buffers, sized before the staged sizes are known: the rows a
+    // previous solve allocated (at least 64 Ki), languages of up to the
+    // previous solve's width; the launch derives its cache and chunk sizes
+    // from what is there
+    uint64_t rows = c->opt_cache_init > 0 ? (uint64_t)c->opt_cache_init : (1ull << 16);
+    if (c->opt_cache_init <= 0 && c->bp_l.p && c->bp_r.p && c->bp_op.p && c->used.p) {
+        const uint64_t have = std::min<uint64_t>({(uint64_t)(c->bp_l.bytes / 4), (uint64_t)(c->bp_r.bytes / 4),
+                                                  (uint64_t)c->bp_op.bytes, (uint64_t)(c->used.bytes / 4)});
+        rows = std::max<uint64_t>(rows, std::min<uint64_t>(have, 1ull << 20));
+    }
+    const uint64_t wguess = std::max<uint32_t>(2u, c->last_W);
+    if ((s = ensure(c, c->cs, 4ull * wguess * rows))) return s;
+    if ((s = ensure(c, c->bp_op, rows))) return s;
+    if ((s = ensure(c, c->bp_l, 4ull * rows))) return s;
+    if ((s = ensure(c, c->bp_r, 4ull * rows))) return s;
+    if ((s = ensure(c, c->used, 4ull * rows))) return s;
+    const uint64_t tslots = pow2_at_least(std::max<uint64_t>(4 * rows, 1024));
+    {
+        // a reallocated table (even at the same address) holds garbage
+        const void *before = c->table.p;
+        const size_t before_bytes = c->table.bytes;
+        if ((s = ensure(c, c->table, 8ull * tslots))) return s;
+        if (c->table.p != before || c->table.bytes != before_bytes) c->table_clean = false;
+    }
+    const uint64_t chunk_words = c->opt_chunk > 0 ? (uint64_t)c->opt_chunk : (1ull << 22);
+    if ((s = ensure(c, c->tmp, std::max<uint64_t>(4ull * 2 * chunk_words, 4ull * 64 * 4096)))) return s;
+    if ((s = ensure(c, c->pending, 4ull * chunk_words))) return s;
+    if ((s = ensure(c, c->slotpos, 4ull * chunk_words))) return s;
+    {
+        const void *before = c->bitmap.p;
+        const size_t before_bytes = c->bitmap.bytes;
+        if ((s = ensure(c, c->bitmap, 4ull * ((chunk_words + 31) / 32)))) return s;
+        if (c->bitmap.p != before || c->bitmap.bytes != before_bytes) c->table_clean = false;
+    }
+    const uint32_t threads = 256;
+    const size_t half = c->smem_sm / 2 > 4096 ? c->smem_sm / 2 - 4096 : 0;
+    const size_t smem = std::min(half, c->smem_optin);
+    int bps = 0;
+    CK(solve_fused_occupancy(threads, smem, &bps));
+    if (bps < 1) return REI_EBUSY;
+    uint32_t grid = (uint32_t)(c->sm_count * bps);
+    if (c->opt_grid > 0 && (uint32_t)c->opt_grid < grid) grid = (uint32_t)c->opt_grid;
+    if ((s = ensure(c, c->blk, 4ull * grid))) return s;
+    if ((s = ensure(c, c->lvl_start, 8ull * (max_cost + 2)))) return s;
+    if ((s = ensure(c, c->lvl_count, 8ull * (max_cost + 2)))) return s;
+    if ((s = ensure(c, c->state, sb + sizeof(StageInfo)))) return s;
+    if ((s = ensure(c, c->solve_job, sizeof(SolveJob)))) return s;
+    if ((s = ensure(c, c->tstack, 16ull * (max_cost + 2)))) return s;
+    if ((s = ensure(c, c->trace, 4ull * grid))) return s;
+    if (!c->table_clean) {
+        CK(cudaMemsetAsync(c->table.p, 0xFF, c->table.bytes, c->stream));
+        CK(cudaMemsetAsync(c->bitmap.p, 0, c->bitmap.bytes, c->stream));
+    }
+    c->table_clean = false;
+    // state, answer tokens, staging report: zero (the launch fills in the rest)
+    CK(cudaMemsetAsync(c->state.p, 0, sb + sizeof(StageInfo), c->stream));
+
+    FuseArgs F;
+    memset(&F, 0, sizeof F);
+    StageJob &sj = F.sj;
+    sj.bytes = dbytes;
+    sj.offs = doffs;
+    sj.n_pos = p->n_pos;
+    sj.n_neg = p->n_neg;
+    memcpy(sj.alphabet, p->alphabet, p->n_sym);
+    sj.n_sym = p->n_sym;
+    sj.info = (StageInfo *)((uint8_t *)c->state.p + sb);
+    sj.word_start = (uint32_t *)c->word_start.p;
+    sj.word_len = (uint32_t *)c->word_len.p;
+    sj.len_start = (uint32_t *)c->len_start.p;
+    sj.gt_off = (uint32_t *)c->gt_off.p;
+    sj.gt_pair = (uint32_t *)c->gt_pair.p;
+    sj.pair_cap = c->pair_cap;
+    sj.pos_mask = (uint32_t *)c->pos.p;
+    sj.neg_mask = (uint32_t *)c->neg.p;
+    sj.leaf = (uint32_t *)c->leaf.p;
+    SolveJob &j = F.tmpl;
+    j.n_sym = p->n_sym;
+    j.gt_off = (const uint32_t *)c->gt_off.p;
+    j.gt_pair = (const uint32_t *)c->gt_pair.p;
+    j.len_start = (const uint32_t *)c->len_start.p;
+    j.pos_mask = (const uint32_t *)c->pos.p;
+    j.neg_mask = (const uint32_t *)c->neg.p;
+    j.leaf = (const uint32_t *)c->leaf.p;
+    j.leaf_stride = kMaxWords;
+    j.c[0] = p->costs.c_sym;
+    j.c[1] = p->costs.c_opt;
+    j.c[2] = p->costs.c_star;
+    j.c[3] = p->costs.c_cat;
+    j.c[4] = p->costs.c_alt;
+    j.max_cost = max_cost;
+    j.max_errors = p->max_errors;
+    j.flags = p->flags & ~REI_F_DEVICE_INPUT;
+    j.cs = (uint32_t *)c->cs.p;
+    j.bp_op = (uint8_t *)c->bp_op.p;
+    j.bp_l = (uint32_t *)c->bp_l.p;
+    j.bp_r = (uint32_t *)c->bp_r.p;
+    j.used = (uint32_t *)c->used.p;
+    j.table = (unsigned long long *)c->table.p;
+    j.table_mask = tslots - 1;
+    j.tmp = (uint32_t *)c->tmp.p;
+    j.pending = (uint32_t *)c->pending.p;
+    j.slotpos = (uint32_t *)c->slotpos.p;
+    j.bitmap = (uint32_t *)c->bitmap.p;
+    j.blk = (uint32_t *)c->blk.p;
+    j.lvl_start = (int64_t *)c->lvl_start.p;
+    j.lvl_count = (int64_t *)c->lvl_count.p;
+    j.seg_cap = 2 * max_cost + 4;
+    j.st = (SolveState *)c->state.p;
+    j.tree = (uint8_t *)c->state.p + sizeof(SolveState);
+    j.tstack = (uint32_t *)c->tstack.p;
+    j.trace = (uint32_t *)c->trace.p;
+    j.solo_tiles = c->opt_solo_tiles >= 0 ? (uint32_t)c->opt_solo_tiles : 8 * (threads / 32);
+    F.job = (SolveJob *)c->solve_job.p;
+    F.mem_budget = p->mem_budget;
+    F.rows_alloc = rows;
+    F.cs_words = c->cs.bytes / 4;
+    F.tmp_words = c->tmp.bytes / 4;
+    F.pend_cap = std::min<uint64_t>({(uint64_t)(c->pending.bytes / 4), (uint64_t)(c->slotpos.bytes / 4),
+                                     (uint64_t)c->bitmap.bytes * 8});
+    F.table_slots = tslots;
+    F.chunk_opt = c->opt_chunk > 0 ? (uint64_t)c->opt_chunk : 0;
+    F.small_opt = c->opt_small_rows < 0 ? 0xFFFFFFFFu : (uint32_t)c->opt_small_rows;
+    F.smem_cap = (uint32_t)smem;
+
+    CK(cudaEventRecord(c->ev[0], c->stream));
+    CK(launch_solve_fused(&F, grid, threads, smem, c->stream));
+    CK(cudaEventRecord(c->ev[1], c->stream));
+    c->launches++;
+    uint8_t *hs = c->h_pin + sizeof(SolveJob);
+    CK(cudaMemcpyAsync(hs, c->state.p, sb + sizeof(StageInfo), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    d2h += sb + sizeof(StageInfo);
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+    ms_search += ms;
+    grid_out = grid;
+    memcpy(&sg.info, hs + sb, sizeof(StageInfo));
+    const SolveState *hst = (const SolveState *)hs;
+    if (hst->status == ST_RESTAGE) {
+        // nothing entered the table: it is still clean
+        c->table_clean = true;
+        return REI_EBUSY;
+    }
+    return REI_OK;
+}
+
+// ---------------------------------------------------------------------------
 // the plain solve
 
 rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
@@ -415,9 +631,28 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
     if (!p->offsets && p->n_pos + p->n_neg) return REI_EINVAL;
 
     Staged sg;
-    s = stage_problem(c, p, sg);
+    double ms_search = 0;
+    uint32_t search_launches = 0, grid = 0;
+    uint64_t h2d = 0, d2h = 0;
+    // staging inside the search launch when the launch can hold the problem
+    bool fused = false;
+    if (c->opt_fused) {
+        s = run_fused(c, p, sg, ms_search, grid, h2d, d2h);
+        if (s == REI_OK) {
+            fused = true;
+            search_launches = 1;
+        } else if (s != REI_EBUSY) {
+            out->status = s;
+            return s;
+        }
+    }
+    if (!fused) {
+        s = stage_problem(c, p, sg);
+        h2d += sg.h2d;
+        d2h += sg.d2h;
+    }
     fill_stats(out, sg.info);
-    if (s) {
+    if (!fused && s) {
         out->status = s;
         return s;
     }
@@ -426,6 +661,9 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
     const uint32_t n = I.n, W = I.W, G = I.G, max_len = I.max_len;
     const uint64_t cap = budget_cap(p->mem_budget, n);
     const uint32_t max_cost = p->max_cost;
+    const size_t tree_bytes = 2ull * (max_cost + 1);
+    SolveState *hst = (SolveState *)(c->h_pin + sizeof(SolveJob));
+    if (!fused || hst->status == ST_NEED_MEM) {
 
     // launch shape
     const uint32_t seg_cap = 2 * max_cost + 4;
@@ -446,11 +684,25 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
         }
     }
     if (smem > c->smem_optin) return REI_EINVAL;
+    // the search's start in CTA 0's shared memory: as many languages as keep
+    // the launch at two CTAs per SM (one, if it already has only one)
+    uint32_t small_rows = 0;
+    if (c->opt_small_rows != 0 && W <= 8) {
+        const size_t half = c->smem_sm / 2 > 4096 ? c->smem_sm / 2 - 4096 : 0;  // static smem + reserve
+        const size_t limit = smem <= half ? half : c->smem_optin;
+        uint32_t r = c->opt_small_rows > 0 ? (uint32_t)c->opt_small_rows : W <= 2 ? 4096u : W <= 4 ? 2048u : 1024u;
+        for (; r >= 256; r >>= 1)
+            if (solve_smem_bytes(W, n, G, max_len, seg_cap, gt_smem, warps, r) <= limit) break;
+        if (r >= 256) {
+            small_rows = r;
+            smem = solve_smem_bytes(W, n, G, max_len, seg_cap, gt_smem, warps, r);
+        }
+    }
     const uint32_t threads = 32 * warps;
     int bps = 0;
     CK(solve_occupancy(threads, smem, &bps));
     if (bps < 1) return REI_ECUDA;
-    uint32_t grid = (uint32_t)(c->sm_count * bps);
+    grid = (uint32_t)(c->sm_count * bps);
     if (c->opt_grid > 0 && (uint32_t)c->opt_grid < grid) grid = (uint32_t)c->opt_grid;
 
     uint64_t chunk_max = c->opt_chunk > 0 ? (uint64_t)c->opt_chunk
@@ -478,40 +730,51 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
     if ((s = ensure(c, c->bp_r, 4ull * cache_alloc))) return s;
     if ((s = ensure(c, c->used, 4ull * cache_alloc))) return s;
     {
-        void *before = c->table.p;
+        const void *before = c->table.p;
+        const size_t before_bytes = c->table.bytes;
         if ((s = ensure(c, c->table, 8ull * tslots))) return s;
-        if (c->table.p != before) c->table_clean = false;
+        if (c->table.p != before || c->table.bytes != before_bytes) c->table_clean = false;
     }
     if ((s = ensure(c, c->tmp, 4ull * W * chunk_max))) return s;
     if ((s = ensure(c, c->pending, 4ull * chunk_max))) return s;
     if ((s = ensure(c, c->slotpos, 4ull * chunk_max))) return s;
-    if ((s = ensure(c, c->bitmap, 4ull * ((chunk_max + 31) / 32)))) return s;
+    {
+        // a reallocated bitmap holds garbage: the search needs it zero
+        const void *before = c->bitmap.p;
+        const size_t before_bytes = c->bitmap.bytes;
+        if ((s = ensure(c, c->bitmap, 4ull * ((chunk_max + 31) / 32)))) return s;
+        if (c->bitmap.p != before || c->bitmap.bytes != before_bytes) {
+            if (fused) CK(cudaMemsetAsync(c->bitmap.p, 0, c->bitmap.bytes, c->stream));
+            else c->table_clean = false;
+        }
+    }
     if ((s = ensure(c, c->blk, 4ull * grid))) return s;
     if ((s = ensure(c, c->lvl_start, 8ull * (max_cost + 2)))) return s;
     if ((s = ensure(c, c->lvl_count, 8ull * (max_cost + 2)))) return s;
-    const size_t tree_bytes = 2ull * (max_cost + 1);
     if ((s = ensure(c, c->state, sizeof(SolveState) + tree_bytes))) return s;
     if ((s = ensure(c, c->solve_job, sizeof(SolveJob)))) return s;
     if ((s = ensure(c, c->tstack, 16ull * (max_cost + 2)))) return s;
     if ((s = ensure(c, c->trace, 4ull * grid))) return s;
     if ((s = ensure_pinned(c, sizeof(SolveJob) + sizeof(SolveState) + tree_bytes))) return s;
+    hst = (SolveState *)(c->h_pin + sizeof(SolveJob));  // (the pinned buffer may have moved)
 
-    if (!c->table_clean) {
-        // a new table, or the last search ended abnormally: clear it all once
-        CK(cudaMemsetAsync(c->table.p, 0xFF, c->table.bytes, c->stream));
-        CK(cudaMemsetAsync(c->bitmap.p, 0, c->bitmap.bytes, c->stream));
+    if (!fused) {
+        if (!c->table_clean) {
+            // a new table, or the last search ended abnormally: clear it all once
+            CK(cudaMemsetAsync(c->table.p, 0xFF, c->table.bytes, c->stream));
+            CK(cudaMemsetAsync(c->bitmap.p, 0, c->bitmap.bytes, c->stream));
+        }
+        c->table_clean = false;
+        CK(cudaMemsetAsync(c->lvl_start.p, 0, 8ull * (max_cost + 2), c->stream));
+        CK(cudaMemsetAsync(c->lvl_count.p, 0, 8ull * (max_cost + 2), c->stream));
+        memset(hst, 0, sizeof(SolveState));
+        hst->status = ST_RUNNING;
+        hst->level = p->costs.c_sym;
+        hst->found = kNone;
+        hst->partial_level = max_cost + 1;
+        CK(cudaMemcpyAsync(c->state.p, hst, sizeof(SolveState), cudaMemcpyHostToDevice, c->stream));
+        h2d += sizeof(SolveState);
     }
-    c->table_clean = false;
-    CK(cudaMemsetAsync(c->lvl_start.p, 0, 8ull * (max_cost + 2), c->stream));
-    CK(cudaMemsetAsync(c->lvl_count.p, 0, 8ull * (max_cost + 2), c->stream));
-
-    SolveState *hst = (SolveState *)(c->h_pin + sizeof(SolveJob));
-    memset(hst, 0, sizeof(SolveState));
-    hst->status = ST_RUNNING;
-    hst->level = p->costs.c_sym;
-    hst->found = kNone;
-    hst->partial_level = max_cost + 1;
-    CK(cudaMemcpyAsync(c->state.p, hst, sizeof(SolveState), cudaMemcpyHostToDevice, c->stream));
 
     SolveJob *hj = (SolveJob *)c->h_pin;
     auto fill_job = [&]() {
@@ -563,26 +826,28 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
         hj->trace = (uint32_t *)c->trace.p;
         hj->gt_in_smem = gt_smem ? 1 : 0;
         hj->solo_tiles = c->opt_solo_tiles >= 0 ? (uint32_t)c->opt_solo_tiles : 8 * warps;
+        hj->small_rows = small_rows;
     };
     fill_job();
-    uint64_t h2d = sg.h2d + sizeof(SolveState), d2h = sg.d2h;
 
-    double ms_search = 0;
-    uint32_t search_launches = 0;
     for (int relaunch = 0;; relaunch++) {
-        CK(cudaEventRecord(c->ev[0], c->stream));
-        CK(launch_solve(hj, grid, threads, smem, c->stream));
-        CK(cudaEventRecord(c->ev[1], c->stream));
-        c->launches++;
-        search_launches++;
-        CK(cudaMemcpyAsync(hst, c->state.p, sizeof(SolveState) + tree_bytes, cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-        {
-            float ms = 0;
-            CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
-            ms_search += ms;
+        // (a fused launch already ran the first part of this search)
+        if (!fused || relaunch > 0) {
+            CK(cudaEventRecord(c->ev[0], c->stream));
+            CK(launch_solve(hj, grid, threads, smem, c->stream));
+            CK(cudaEventRecord(c->ev[1], c->stream));
+            c->launches++;
+            search_launches++;
+            CK(cudaMemcpyAsync(hst, c->state.p, sizeof(SolveState) + tree_bytes, cudaMemcpyDeviceToHost,
+                               c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            {
+                float ms = 0;
+                CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+                ms_search += ms;
+            }
+            d2h += sizeof(SolveState) + tree_bytes;
         }
-        d2h += sizeof(SolveState) + tree_bytes;
         if (hst->status != ST_NEED_MEM) break;
         // grow the cache (keeping its rows) and rebuild the table
         const uint64_t want = std::min<uint64_t>(cap, std::max<uint64_t>(cache_alloc * 4, hst->need_rows));
@@ -610,6 +875,7 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
         h2d += sizeof(SolveState);
         if (relaunch > 64) return REI_ECUDA;
     }
+    }
 
     if (getenv("REI_PHASES")) {
         fprintf(stderr, "rei phases: plan %.1f us, solo %.1f us (%llu chunks), team %.1f us (%llu chunks), "
@@ -617,6 +883,15 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
                 hst->t_phase[1] / 1e3, (unsigned long long)hst->n_phase[0], hst->t_phase[2] / 1e3,
                 (unsigned long long)hst->n_phase[1], hst->t_phase[3] / 1e3, (unsigned long long)hst->n_phase[2],
                 ms_search * 1e3);
+        fprintf(stderr, "rei staging steps (timing builds): init %.1f us, checks %.1f us, insert %.1f us, keys %.1f us, "
+                "ranks %.1f us, guide table %.1f us, masks %.1f us\n", sg.info.pad[0] / 1e3, sg.info.pad[1] / 1e3,
+                sg.info.pad[2] / 1e3, sg.info.pad[3] / 1e3, sg.info.pad[4] / 1e3, sg.info.pad[5] / 1e3,
+                sg.info.pad[6] / 1e3);
+        fprintf(stderr, "rei chunk steps (timing builds): tiles %.1f us, read %.1f us, append %.1f us; "
+                "in append: keys %.1f us, sort %.1f us, copy %.1f us\n", hst->t_sub[0] / 1e3, hst->t_sub[1] / 1e3,
+                hst->t_sub[2] / 1e3, hst->t_sub[3] / 1e3, hst->t_sub[4] / 1e3, hst->t_sub[5] / 1e3);
+        fprintf(stderr, "rei tile steps of warp 0 (timing builds): load %.1f us, build %.1f us, precision %.1f us, "
+                "dedup %.1f us\n", hst->t_sub[6] / 1e3, hst->t_sub[7] / 1e3, hst->t_sub[8] / 1e3, hst->t_sub[9] / 1e3);
     }
     if (hst->status == ST_TIMEOUT && getenv("REI_DEBUG")) {
         std::vector<uint32_t> tr(grid);
@@ -694,6 +969,7 @@ rei_status rei_ctx_create(rei_ctx **out, int device, const rei_alloc *alloc, voi
     }
     c->sm_count = prop.multiProcessorCount;
     c->smem_optin = prop.sharedMemPerBlockOptin;
+    c->smem_sm = prop.sharedMemPerMultiprocessor;
     if (alloc && alloc->alloc && alloc->free) {
         c->alloc = *alloc;
         c->has_alloc = true;
@@ -737,13 +1013,18 @@ void rei_ctx_destroy(rei_ctx *c) {
 }
 
 rei_status rei_ctx_set_option(rei_ctx *c, int option, int64_t value) {
-    if (!c || (value < 0 && option != REI_OPT_SOLO_TILES)) return REI_EINVAL;
+    if (!c || (value < 0 && option != REI_OPT_SOLO_TILES && option != REI_OPT_SMALL_ROWS)) return REI_EINVAL;
     switch (option) {
     case REI_OPT_CHUNK: c->opt_chunk = value; return REI_OK;
     case REI_OPT_GRID: c->opt_grid = value; return REI_OK;
     case REI_OPT_KEEP_CACHE: c->opt_keep = value; return REI_OK;
     case REI_OPT_CACHE_INIT: c->opt_cache_init = value; return REI_OK;
     case REI_OPT_SOLO_TILES: c->opt_solo_tiles = value; return REI_OK;
+    case REI_OPT_FUSED_STAGE: c->opt_fused = value ? 1 : 0; return REI_OK;
+    case REI_OPT_SMALL_ROWS:
+        if (value > 16384 || (value > 0 && (value < 256 || (value & (value - 1))))) return REI_EINVAL;
+        c->opt_small_rows = value < 0 ? -1 : value;
+        return REI_OK;
     default: return REI_EINVAL;
     }
 }
@@ -1252,6 +1533,7 @@ rei_status server_setup(rei_server *S) {
     S->ring_size = 4096;
     S->threads = 256;
     S->smem = 112 * 1024;
+    if (stage_layout(kServeMaxIC, kServeMaxBytes, nullptr, nullptr) > S->smem) return REI_EINVAL;
     int bps = 0;
     if (serve_occupancy(S->threads, S->smem, &bps) != cudaSuccess || bps < 1) return REI_ECUDA;
     S->grid = (uint32_t)(c->sm_count * bps);
@@ -1308,11 +1590,7 @@ rei_status server_setup(rei_server *S) {
     m.lvl = (int64_t *)take(8 * slots * 2 * (kMaxCost + 2));
     m.state = (SolveState *)take(sizeof(SolveState) * slots);
     m.tstack = (uint32_t *)take(16 * slots * (kMaxCost + 2));
-    A.in_bytes = (uint8_t *)take(slots * kServeMaxBytes);
     A.in_offs = (uint32_t *)take(4 * slots * (kServeMaxStrings + 1));
-    A.st_hset = (uint64_t *)take(8 * slots * kHsetCapHost);
-    A.st_rank_of = (uint16_t *)take(2 * slots * kHsetCapHost);
-    A.st_uniq = (uint16_t *)take(2 * slots * kMaxIC);
     A.word_start = (uint32_t *)take(4 * slots * kMaxIC);
     A.word_len = (uint32_t *)take(4 * slots * kMaxIC);
     A.len_start = (uint32_t *)take(4 * slots * (REI_MAX_STRLEN + 2));

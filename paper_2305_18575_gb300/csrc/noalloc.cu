@@ -34,7 +34,7 @@ cudaError_t launch_solve(const SolveJob *job, uint32_t grid, uint32_t threads, s
                          cudaStream_t stream);
 cudaError_t solve_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm);
 size_t solve_smem_bytes(uint32_t W, uint32_t n, uint32_t G, uint32_t max_len, uint32_t seg_cap,
-                        bool gt_in_smem, uint32_t warps);
+                        bool gt_in_smem, uint32_t warps, uint32_t small_rows = 0);
 }  // namespace rei
 
 using namespace rei;

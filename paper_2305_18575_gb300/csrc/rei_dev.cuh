@@ -38,6 +38,7 @@ enum DevStatus : uint32_t {
     ST_NEED_MEM = 4,
     ST_TIMEOUT = 5,
     ST_BAD = 6,
+    ST_RESTAGE = 7,  // staged in the search launch, but the launch cannot hold the problem
 };
 
 // staging error codes
@@ -128,6 +129,7 @@ struct SolveState {
     // level ends; and how many solo chunks, team chunks, levels
     uint64_t t_phase[4];
     uint64_t n_phase[3];
+    uint64_t t_sub[12];  // steps of CTA 0's chunks alone (timing builds only)
     uint32_t pad[2];
 };
 
@@ -162,7 +164,24 @@ struct SolveJob {
     uint32_t *trace;                 // per CTA: (barriers passed << 8) | last barrier site
     uint32_t gt_in_smem;             // guide table copied to shared memory
     uint32_t solo_tiles;             // chunks of at most this many tiles run on CTA 0 alone
+    uint32_t small_rows;             // languages CTA 0 keeps in shared memory at the start (0 = none)
 };
+
+static_assert(sizeof(SolveJob) % 8 == 0, "the job is copied in 8-byte words");
+
+// the search launch that stages its problem first (CTA 0), then searches it
+struct FuseArgs {
+    StageJob sj;              // inputs, and where the staged problem goes
+    SolveJob tmpl;            // the job without the staged sizes and what depends on them
+    SolveJob *job;            // global: the completed job, for every CTA
+    uint64_t mem_budget;
+    uint64_t rows_alloc;      // rows of the back-pointer arrays
+    uint64_t cs_words, tmp_words, pend_cap, table_slots;
+    uint64_t chunk_opt;       // chunk size asked for (0 = automatic)
+    uint32_t small_opt;       // languages in shared memory at the start: 0xFFFFFFFF automatic, 0 none
+    uint32_t smem_cap;        // dynamic shared memory of the launch
+};
+
 
 // ---- batched search
 
@@ -209,6 +228,7 @@ struct BatchArgs {
 
 constexpr uint32_t kServeMaxStrings = 255;   // examples per served request
 constexpr uint32_t kServeMaxBytes = 8192;    // example bytes per served request
+constexpr uint32_t kServeMaxIC = 2048;       // |ic| of a request a server CTA stages and solves
 constexpr uint32_t kServePairCap = 1u << 16; // guide pairs a served request may stage
 
 // a request in the ring (mapped host memory), written before it is published
@@ -232,11 +252,8 @@ struct ServeOut {
 
 struct ServeArgs {
     SlotMem slot;
-    // per slot: the request's bytes, staging scratch, staged problem
-    uint8_t *in_bytes;
+    // per slot: the request's offsets, staged problem
     uint32_t *in_offs;
-    uint64_t *st_hset;
-    uint16_t *st_rank_of, *st_uniq;
     uint32_t *word_start, *word_len, *len_start, *gt_off, *gt_pair, *pos, *neg, *leaf;
     uint32_t pair_cap;
     StageInfo *sinfo;

@@ -151,6 +151,12 @@ struct Shared {
     uint32_t *pos, *neg;     // precision masks (W words)
     const uint32_t *gt_off, *gt_pair, *len_start;
     unsigned long long *sortbuf;  // kSortMax keys for the ordered append of few survivors
+    uint32_t *solo_bits;     // kSortMax / 32 words: candidates of a small chunk that hold a slot
+    uint32_t *solo_pref;     // kSortMax / 32 + 4 words: survivors before each bitmap word, total
+    // the search's start, while every language fits in CTA 0's shared memory
+    uint32_t *sm_rows;       // small_rows rows of W words: the cached languages
+    uint32_t *sm_table;      // 2 * small_rows slots: fp (15 bits) | pending | row or candidate
+    uint32_t *sm_tmp;        // kSortMax rows: the candidates of the current chunk
     uint32_t *lvs, *lvc;     // level table (start, count per cost), mirrored in shared memory
     uint32_t *warp_mem;      // per warp: lw[W], A[32*Ws], B[32*Ws]
     uint32_t warp_words;
@@ -160,6 +166,7 @@ struct Shared {
 // to the global SolveState when the launch ends
 struct Lead {
     uint32_t status, level, size, full, otf, partial_level;
+    uint32_t smode;  // languages and their uniqueness table live in shared memory
     uint64_t chunk_pos, candidates, unique_done;
     uint64_t cand_op[5];
 };
@@ -293,6 +300,32 @@ __device__ int max_operand_level(const SolveJob &J, int c) {
 // ---------------------------------------------------------------------------
 // phase A: one warp tile of up to 32 candidates
 
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// step timing of CTA 0's chunks alone, compiled in with -DREI_TIMING only
+#ifdef REI_TIMING
+#define REI_TMARK(cond, k)                                          \
+    do {                                                            \
+        if ((cond) && threadIdx.x == 0) {                           \
+            const unsigned long long t_now = globaltimer_ns();      \
+            st->t_sub[k] += t_now - t_mark;                         \
+            t_mark = t_now;                                         \
+        }                                                           \
+    } while (0)
+#define REI_TSTART() const unsigned long long t_mark0 = globaltimer_ns(); unsigned long long t_mark = t_mark0
+#else
+#define REI_TMARK(cond, k) \
+    do {                   \
+    } while (0)
+#define REI_TSTART() \
+    do {             \
+    } while (0)
+#endif
+
 struct TileCtx {
     const SolveJob *J;
     SolveState *st;
@@ -301,7 +334,106 @@ struct TileCtx {
     uint32_t W, Ws, n;
     bool dedup;
     bool grid;  // every CTA works on the chunk (else CTA 0 alone)
+    unsigned long long *found;  // minimum precise candidate: shared (small chunk alone) or global
+    unsigned long long *ent;    // small chunk alone: per candidate, fingerprint << 32 | slot; else null
+    uint32_t *bits;             // small chunk alone: candidates that took or won a slot
+    const uint32_t *ops;        // the cached languages operands are read from (shared or global)
+    bool smem;                  // uniqueness in CTA 0's shared table
 };
+
+// an operand word: generic relaxed load (the rows are in shared memory at
+// the search's start, in global memory, written by other CTAs, later)
+__device__ __forceinline__ uint32_t ldop(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+constexpr uint32_t kSmEmpty = 0xFFFFFFFFu;
+constexpr uint32_t kSmPending = 0x10000u;
+
+// uniqueness insert of candidate xl while the languages live in shared
+// memory: the same protocol as dedup_insert_solo on a 32-bit table whose
+// entries are fp (15 bits) << 17 | pending << 16 | row or candidate
+__device__ void dedup_insert_smem(const TileCtx &T, const uint32_t *c, uint32_t xl) {
+    const Shared &S = *T.S;
+    const uint32_t W = T.W;
+    const uint64_t h = cs_hash(c, W, 1);
+    const uint32_t fp = (uint32_t)(h >> 49);  // 15 bits
+    const uint32_t mine = (fp << 17) | kSmPending | xl;
+    const uint32_t mask = 2 * T.J->small_rows - 1;
+    uint32_t p = (uint32_t)h & mask;
+    uint32_t *dst = S.sm_tmp + xl * W;
+    for (uint32_t b = 0; b < W; b++) dst[b] = c[b];
+    __threadfence_block();
+    for (uint32_t probe = 0; probe <= mask; probe++) {
+        const uint32_t v = atomicCAS(&S.sm_table[p], kSmEmpty, mine);
+        if (v == kSmEmpty) {
+            T.ent[xl] = p;
+            atomicOr(&T.bits[xl >> 5], 1u << (xl & 31));
+            return;
+        }
+        if ((v >> 17) == fp) {
+            __threadfence_block();
+            const uint32_t idx = v & 0xFFFFu;
+            const volatile uint32_t *src = (v & kSmPending) ? S.sm_tmp + idx * W : S.sm_rows + idx * W;
+            bool eq = true;
+            for (uint32_t b = 0; b < W && eq; b++) eq = src[b] == c[b];
+            if (eq) {
+                if ((v & kSmPending) && idx > xl && atomicMin(&S.sm_table[p], mine) > mine) {
+                    T.ent[xl] = p;
+                    atomicOr(&T.bits[xl >> 5], 1u << (xl & 31));
+                }
+                return;
+            }
+        }
+        p = (p + 1) & mask;
+    }
+    atomicExch(&T.st->err, 2u);  // table full: cannot happen with load <= 1/2
+}
+
+// uniqueness insert of candidate xl of a small chunk that CTA 0 runs alone
+// (no other CTA touches the table meanwhile).  The candidate's row goes to
+// tmp first, then the slot is claimed with one CAS whose result doubles as
+// the probe; a candidate that takes an empty slot, or replaces a later
+// pending holder of the same language, is marked in T.bits with its slot in
+// T.ent; the append keeps the marks whose slot still names them.
+__device__ void dedup_insert_solo(const TileCtx &T, const uint32_t *c, uint32_t xl) {
+    const SolveJob &J = *T.J;
+    const uint32_t W = T.W;
+    const uint64_t h = cs_hash(c, W, 1);
+    const uint32_t fp = (uint32_t)(h >> 32);
+    const unsigned long long mine = ((uint64_t)fp << 32) | kPending | xl;
+    uint64_t p = h & J.table_mask;
+    uint32_t *dst = J.tmp + (uint64_t)xl * W;
+    for (uint32_t b = 0; b < W; b++) dst[b] = c[b];
+    __threadfence_block();
+    for (uint64_t probe = 0; probe <= J.table_mask; probe++) {
+        const unsigned long long v = atomicCAS(&J.table[p], kEmpty, mine);
+        if (v == kEmpty) {
+            T.ent[xl] = ((unsigned long long)fp << 32) | (uint32_t)p;
+            atomicOr(&T.bits[xl >> 5], 1u << (xl & 31));
+            return;
+        }
+        if ((uint32_t)(v >> 32) == fp) {
+            __threadfence_block();
+            const uint32_t idx = (uint32_t)v;
+            const uint32_t *src = (idx & kPending) ? J.tmp + (uint64_t)(idx & ~kPending) * W
+                                                   : J.cs + (uint64_t)idx * W;
+            bool eq = true;
+            for (uint32_t b = 0; b < W && eq; b++) eq = ldcg(src + b) == c[b];
+            if (eq) {
+                if ((idx & kPending) && (idx & ~kPending) > xl && atomicMin(&J.table[p], mine) > mine) {
+                    T.ent[xl] = ((unsigned long long)fp << 32) | (uint32_t)p;
+                    atomicOr(&T.bits[xl >> 5], 1u << (xl & 31));
+                }
+                return;
+            }
+        }
+        p = (p + 1) & J.table_mask;
+    }
+    atomicExch(&T.st->err, 2u);  // table full: cannot happen with load <= 1/2
+}
 
 // uniqueness insert of candidate xl (chunk-local) whose CS is c[b * 1] (smem)
 __device__ void dedup_insert(const TileCtx &T, const uint32_t *c, uint32_t xl) {
@@ -364,7 +496,7 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uin
     uint32_t *lw = wm;
     uint32_t *A = wm + ((W + 3) & ~3u);
     uint32_t *B = A + 32 * Ws;
-    const uint32_t *cs = J.cs;
+    const uint32_t *cs = T.ops;
     const uint64_t lo = tl.lo, hi = tl.hi;
 
     // which candidate this lane holds; `first` is the first of the tile's 32
@@ -397,6 +529,11 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uin
     }
     const uint32_t vmask = __ballot_sync(0xFFFFFFFFu, valid);
     if (vmask == 0) return;
+#ifdef REI_TIMING
+    SolveState *st = T.st;
+    REI_TSTART();
+    const bool tmk = !T.grid && threadIdx.x == 0;
+#endif
 
     // ---- build
     if (sg.op == OP_LEAF) {
@@ -409,7 +546,7 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uin
         const uint32_t *src = cs + (uint64_t)(sg.lbase + first) * W;
         for (uint32_t i = lane; i < 32 * W; i += 32) {
             const uint32_t j = i / W, b = i % W;
-            A[j * Ws + b] = j < nrow ? ldcg(src + i) : 0u;
+            A[j * Ws + b] = j < nrow ? ldop(src + i) : 0u;
         }
         __syncwarp();
         A[lane * Ws] |= 1u;  // eps is ic word 0
@@ -417,11 +554,11 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uin
     } else if (sg.op == OP_ALT) {
         const uint32_t *l = cs + (uint64_t)(sg.lbase + row) * W;
         const uint32_t *src = cs + (uint64_t)(sg.rbase + first) * W;
-        for (uint32_t b = lane; b < W; b += 32) lw[b] = ldcg(l + b);
+        for (uint32_t b = lane; b < W; b += 32) lw[b] = ldop(l + b);
         __syncwarp();
         for (uint32_t i = lane; i < 32 * W; i += 32) {
             const uint32_t j = i / W, b = i % W;
-            A[j * Ws + b] = j < nrow ? (lw[b] | ldcg(src + i)) : 0u;
+            A[j * Ws + b] = j < nrow ? (lw[b] | ldop(src + i)) : 0u;
         }
         __syncwarp();
     } else {
@@ -431,14 +568,15 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uin
         const uint32_t *src = cs + (uint64_t)(base + first) * W;
         for (uint32_t i = lane; i < 32 * W; i += 32) {
             const uint32_t j = i / W, b = i % W;
-            A[j * Ws + b] = j < nrow ? ldcg(src + i) : 0u;
+            A[j * Ws + b] = j < nrow ? ldop(src + i) : 0u;
         }
         if (sg.op == OP_CAT) {
             // the one operand shared by the tile
             const uint32_t *o = cs + (uint64_t)(swapped ? sg.rbase + col : sg.lbase + row) * W;
-            for (uint32_t b = lane; b < W; b += 32) lw[b] = ldcg(o + b);
+            for (uint32_t b = lane; b < W; b += 32) lw[b] = ldop(o + b);
         }
         __syncwarp();
+        REI_TMARK(tmk, 6);
         // slices: B[v] bit j = operand j contains word v
         for (uint32_t b = 0; b < W; b++) B[32 * b + lane] = transpose32(A[lane * Ws + b], lane);
         __syncwarp();
@@ -496,14 +634,21 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uin
         }
     }
 
+    REI_TMARK(tmk, 7);
     // ---- precision and uniqueness, one candidate per lane
     if (!valid) return;
     const uint32_t *c = A + lane * Ws;
     uint32_t errs = 0;
     for (uint32_t b = 0; b < W; b++) errs += __popc(S.pos[b] & ~c[b]) + __popc(S.neg[b] & c[b]);
     const uint64_t xlev = sg.start + x;
-    if (errs <= J.max_errors) atomicMin(&T.st->found, (unsigned long long)xlev);
-    if (T.dedup) dedup_insert(T, c, (uint32_t)(xlev - T.chunk_start));
+    if (errs <= J.max_errors) atomicMin(T.found, (unsigned long long)xlev);
+    REI_TMARK(tmk, 8);
+    if (T.dedup) {
+        if (T.smem) dedup_insert_smem(T, c, (uint32_t)(xlev - T.chunk_start));
+        else if (T.bits) dedup_insert_solo(T, c, (uint32_t)(xlev - T.chunk_start));
+        else dedup_insert(T, c, (uint32_t)(xlev - T.chunk_start));
+    }
+    REI_TMARK(tmk, 9);
 }
 
 // ---------------------------------------------------------------------------
@@ -595,10 +740,12 @@ __device__ uint32_t emit_tree(const SolveJob &J, uint32_t op, uint32_t l, uint32
 constexpr uint32_t kSortMax = 2048;  // new languages appended by CTA 0 alone, after a sort
 
 __host__ __device__ size_t solve_smem_bytes(uint32_t W, uint32_t n, uint32_t G, uint32_t max_len,
-                                            uint32_t seg_cap, bool gt_in_smem, uint32_t warps) {
+                                            uint32_t seg_cap, bool gt_in_smem, uint32_t warps, uint32_t small_rows) {
     const uint32_t Ws = (W & 1u) ? W : W + 1;
     size_t b = sizeof(Seg) * seg_cap + sizeof(uint64_t) * (seg_cap + 1) + sizeof(SegTile) * seg_cap;
     b += sizeof(unsigned long long) * kSortMax;
+    b += sizeof(uint32_t) * (2 * (kSortMax / 32) + 4);
+    if (small_rows) b += sizeof(uint32_t) * ((size_t)small_rows * W + 2 * small_rows + (size_t)kSortMax * W);
     b += 2 * sizeof(uint32_t) * seg_cap;
     b += 2 * sizeof(uint32_t) * W;
     if (gt_in_smem) b += sizeof(uint32_t) * (((n + 1 + G + max_len + 2) + 3) & ~3u);
@@ -675,6 +822,7 @@ __device__ __forceinline__ bool team_barrier(bool full, SolveState *st, uint32_t
 __device__ void append_sorted(const SolveJob &J, SolveState *st, Shared &S, const ChunkArgs &a,
                               uint32_t npend, uint32_t W, Lead *L) {
     const uint32_t tid = threadIdx.x;
+    REI_TSTART();
     uint32_t m = 1;
     while (m < npend) m <<= 1;
     unsigned long long *key = S.sortbuf;
@@ -688,6 +836,7 @@ __device__ void append_sorted(const SolveJob &J, SolveState *st, Shared &S, cons
         key[i] = k;
     }
     __syncthreads();
+    REI_TMARK(true, 3);
     for (uint32_t k = 2; k <= m; k <<= 1) {
         for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
             for (uint32_t i = tid; i < m; i += blockDim.x) {
@@ -704,6 +853,7 @@ __device__ void append_sorted(const SolveJob &J, SolveState *st, Shared &S, cons
             __syncthreads();
         }
     }
+    REI_TMARK(true, 4);
     const uint64_t limit = J.cache_alloc < J.cap ? J.cache_alloc : J.cap;
     const uint64_t room = limit > a.size ? limit - a.size : 0;
     for (uint32_t i = tid; i < npend && i < room; i += blockDim.x) {
@@ -735,6 +885,184 @@ __device__ void append_sorted(const SolveJob &J, SolveState *st, Shared &S, cons
         J.lvl_count[a.level] = S.lvc[a.level];
         st->pending_count = 0;
     }
+    REI_TMARK(true, 5);
+}
+
+// survivors of a chunk while the languages live in shared memory: as
+// solo_append, with the holders read from the shared table; each survivor's
+// row goes to the shared rows and to the global cache, its back-pointer to
+// the global table of back-pointers
+__device__ void smem_append(const SolveJob &J, Shared &S, const ChunkArgs &a, uint32_t W, Lead *L) {
+    const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    const uint32_t C = (uint32_t)(a.ce0 - a.cs0), nw = (C + 31) / 32;
+    uint32_t *bits = S.solo_bits, *pref = S.solo_pref;
+    const unsigned long long *ent = S.sortbuf;
+    for (uint32_t xl = tid; xl < C; xl += nt) {
+        if (!((bits[xl >> 5] >> (xl & 31)) & 1u)) continue;
+        const uint32_t v = S.sm_table[(uint32_t)ent[xl]];
+        if ((v & 0x1FFFFu) != (kSmPending | xl)) atomicAnd(&bits[xl >> 5], ~(1u << (xl & 31)));
+    }
+    __syncthreads();
+    if (tid < 32) {
+        const uint32_t c0 = 2 * lane < nw ? __popc(bits[2 * lane]) : 0u;
+        const uint32_t c1 = 2 * lane + 1 < nw ? __popc(bits[2 * lane + 1]) : 0u;
+        uint32_t x = c0 + c1;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+            if (lane >= (uint32_t)d) x += y;
+        }
+        const uint32_t before = x - c0 - c1;
+        if (2 * lane < nw) pref[2 * lane] = before;
+        if (2 * lane + 1 < nw) pref[2 * lane + 1] = before + c0;
+        if (lane == 31) pref[kSortMax / 32] = x;
+    }
+    __syncthreads();
+    const uint32_t total = pref[kSortMax / 32];
+    const uint64_t limit = J.cache_alloc < J.cap ? J.cache_alloc : J.cap;
+    const uint64_t room = limit > a.size ? limit - a.size : 0;
+    for (uint32_t xl = tid; xl < C; xl += nt) {
+        const uint32_t wb = bits[xl >> 5];
+        if (!((wb >> (xl & 31)) & 1u)) continue;
+        const uint32_t rank = pref[xl >> 5] + __popc(wb & ((1u << (xl & 31)) - 1u));
+        const uint32_t q = (uint32_t)ent[xl];
+        if (rank >= room) {
+            S.sm_table[q] = kSmEmpty;
+            continue;
+        }
+        const uint32_t k = a.size + rank;
+        const uint32_t *src = S.sm_tmp + xl * W;
+        uint32_t *ds = S.sm_rows + k * W, *dg = J.cs + (uint64_t)k * W;
+        for (uint32_t b = 0; b < W; b++) {
+            const uint32_t x = src[b];
+            ds[b] = x;
+            dg[b] = x;
+        }
+        uint32_t op, l, r;
+        decode(S.seg, a.nseg, a.cs0 + xl, op, l, r);
+        J.bp_op[k] = (uint8_t)op;
+        J.bp_l[k] = l;
+        J.bp_r[k] = r;
+        S.sm_table[q] = (S.sm_table[q] & 0xFFFE0000u) | k;
+    }
+    __syncthreads();
+    for (uint32_t w = tid; w < nw; w += nt) bits[w] = 0;
+    if (tid == 0) {
+        const uint64_t added = total < room ? total : room;
+        if (total > room) L->full = 1;
+        L->size = a.size + (uint32_t)added;
+        S.lvc[a.level] = L->size - S.lvs[a.level];
+        J.lvl_count[a.level] = S.lvc[a.level];
+    }
+    __syncthreads();
+}
+
+// leave the shared-memory start: every cached language goes into the global
+// uniqueness table (all are distinct), so that other CTAs, later launches
+// and the table cleanup see them
+__device__ void switch_to_global(const SolveJob &J, Shared &S, Lead *L) {
+    const uint32_t W = J.W, rows = L->size;
+    for (uint32_t k = threadIdx.x; k < rows; k += blockDim.x) {
+        const uint64_t h = cs_hash(S.sm_rows + (uint64_t)k * W, W, 1);
+        const unsigned long long v = ((uint64_t)(uint32_t)(h >> 32) << 32) | k;
+        uint64_t p = h & J.table_mask;
+        for (uint64_t probe = 0; probe <= J.table_mask; probe++) {
+            if (atomicCAS(&J.table[p], kEmpty, v) == kEmpty) {
+                J.used[k] = (uint32_t)p;
+                break;
+            }
+            p = (p + 1) & J.table_mask;
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) L->smode = 0;
+    __syncthreads();
+}
+
+// survivors of a small chunk CTA 0 ran alone, appended in candidate order: a
+// marked candidate survives when its slot still names it (no later-marked
+// candidate of the same language took the slot from it)
+__device__ void solo_append(const SolveJob &J, SolveState *st, Shared &S, const ChunkArgs &a, uint32_t W,
+                            Lead *L) {
+    const uint32_t tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    const uint32_t C = (uint32_t)(a.ce0 - a.cs0), nw = (C + 31) / 32;
+    uint32_t *bits = S.solo_bits, *pref = S.solo_pref;
+    const unsigned long long *ent = S.sortbuf;
+    REI_TSTART();
+    // 1. drop the marks that lost their slot (loads issued before any use)
+    for (uint32_t base = 0; base < C; base += 8 * nt) {
+        unsigned long long v[8];
+        bool mk[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const uint32_t xl = base + u * nt + tid;
+            mk[u] = xl < C && ((bits[xl >> 5] >> (xl & 31)) & 1u);
+            v[u] = mk[u] ? ld_relaxed_u64(J.table + (uint32_t)ent[xl]) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const uint32_t xl = base + u * nt + tid;
+            if (mk[u] && (uint32_t)v[u] != (kPending | xl)) atomicAnd(&bits[xl >> 5], ~(1u << (xl & 31)));
+        }
+    }
+    __syncthreads();
+    REI_TMARK(true, 3);
+    // 2. survivors before each bitmap word (nw <= 64: two words per lane of warp 0)
+    if (tid < 32) {
+        const uint32_t c0 = 2 * lane < nw ? __popc(bits[2 * lane]) : 0u;
+        const uint32_t c1 = 2 * lane + 1 < nw ? __popc(bits[2 * lane + 1]) : 0u;
+        uint32_t x = c0 + c1;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+            if (lane >= (uint32_t)d) x += y;
+        }
+        const uint32_t before = x - c0 - c1;
+        if (2 * lane < nw) pref[2 * lane] = before;
+        if (2 * lane + 1 < nw) pref[2 * lane + 1] = before + c0;
+        if (lane == 31) pref[kSortMax / 32] = x;
+    }
+    __syncthreads();
+    REI_TMARK(true, 4);
+    // 3. rows, back-pointers and slots of the survivors; beyond the cache's
+    // room they are not cached and their slots are emptied
+    const uint32_t total = pref[kSortMax / 32];
+    const uint64_t limit = J.cache_alloc < J.cap ? J.cache_alloc : J.cap;
+    const uint64_t room = limit > a.size ? limit - a.size : 0;
+    for (uint32_t xl = tid; xl < C; xl += nt) {
+        const uint32_t wb = bits[xl >> 5];
+        if (!((wb >> (xl & 31)) & 1u)) continue;
+        const uint32_t rank = pref[xl >> 5] + __popc(wb & ((1u << (xl & 31)) - 1u));
+        const unsigned long long e = ent[xl];
+        const uint32_t q = (uint32_t)e;
+        if (rank >= room) {
+            J.table[q] = kEmpty;
+            continue;
+        }
+        const uint64_t k = (uint64_t)a.size + rank;
+        const uint32_t *srcp = J.tmp + (uint64_t)xl * W;
+        uint32_t *dst = J.cs + k * W;
+        for (uint32_t b = 0; b < W; b++) dst[b] = ldcg(srcp + b);
+        uint32_t op, l, r;
+        decode(S.seg, a.nseg, a.cs0 + xl, op, l, r);
+        J.bp_op[k] = (uint8_t)op;
+        J.bp_l[k] = l;
+        J.bp_r[k] = r;
+        J.table[q] = (e & 0xFFFFFFFF00000000ull) | (uint32_t)k;
+        J.used[k] = q;
+    }
+    __syncthreads();
+    for (uint32_t w = tid; w < nw; w += nt) bits[w] = 0;
+    if (tid == 0) {
+        const uint64_t added = total < room ? total : room;
+        if (total > room) L->full = 1;
+        L->size = a.size + (uint32_t)added;
+        S.lvc[a.level] = L->size - S.lvs[a.level];
+        J.lvl_count[a.level] = S.lvc[a.level];
+    }
+    __syncthreads();
+    REI_TMARK(true, 5);
 }
 
 // one chunk of candidates; returns 1 when a precise candidate was found in it,
@@ -748,15 +1076,26 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
     const uint32_t nwarps = blockDim.x >> 5;
     const uint32_t team_n = full ? gridDim.x : 1, team_r = full ? blockIdx.x : 0;
     const bool dedup = a.dedup != 0;
+    REI_TSTART();
 
     if (!tiles_ready) {
         if (wid == 0) tile_setup(S, a.nseg, a.cs0, a.ce0, s_tiles);
         __syncthreads();
     }
 
+    // a small chunk CTA 0 runs alone keeps its bookkeeping in shared memory;
+    // at the search's start the languages and their table live there too
+    const bool small = !full && a.ce0 - a.cs0 <= kSortMax;
+    const bool sm = small && L && L->smode;
+    if (small) {
+        if (tid == 0) *s_found = kNone;
+        __syncthreads();
+    }
+
     // ---- phase A: build, precision, uniqueness insert
     {
-        TileCtx TC{&J, st, &S, a.cs0, W, Ws, n, dedup, full};
+        TileCtx TC{&J, st, &S, a.cs0, W, Ws, n, dedup, full, small ? s_found : &st->found,
+                   small ? S.sortbuf : nullptr, small ? S.solo_bits : nullptr, sm ? S.sm_rows : J.cs, sm};
         const uint64_t ntiles = *s_tiles;
         const uint64_t gw = (uint64_t)team_r * nwarps + wid, nw = (uint64_t)team_n * nwarps;
         uint32_t s = 0;
@@ -769,11 +1108,35 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
         }
     }
     if (!team_barrier(full, st, bar_epoch, 5, J.trace)) return -1;
+    REI_TMARK(!full, 0);
+    if (small) {
+        const unsigned long long f = *s_found;
+        if (f != kNone) {
+            // the answer is in this chunk: its survivors are not cached, so
+            // the slots they took are emptied now
+            const uint32_t C = (uint32_t)(a.ce0 - a.cs0);
+            if (!sm)
+                for (uint32_t xl = tid; xl < C; xl += blockDim.x)
+                    if ((S.solo_bits[xl >> 5] >> (xl & 31)) & 1u) J.table[(uint32_t)S.sortbuf[xl]] = kEmpty;
+            __syncthreads();
+            for (uint32_t w = tid; w < kSortMax / 32; w += blockDim.x) S.solo_bits[w] = 0;
+            if (tid == 0) st->found = f;
+            __syncthreads();
+            return 1;
+        }
+        if (dedup) {
+            if (sm) smem_append(J, S, a, W, L);
+            else solo_append(J, st, S, a, W, L);
+        }
+        REI_TMARK(!full, 2);
+        return 0;
+    }
     if (tid == 0) {
         *s_found = ld_relaxed_u64(&st->found);
         *s_npend = ld_relaxed_u32(&st->pending_count);
     }
     __syncthreads();
+    REI_TMARK(!full, 1);
     if (*s_found != kNone) return 1;
     if (!dedup) return 0;
     const uint32_t npend = *s_npend;
@@ -782,6 +1145,7 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
     // few new languages: the leading CTA appends them alone, in order, after a sort
     if (npend <= kSortMax) {
         if (team_r == 0) append_sorted(J, st, S, a, npend, W, L);
+        REI_TMARK(!full, 2);
         return 0;
     }
 
@@ -916,11 +1280,6 @@ __device__ void publish(SolveState *st, uint32_t cmd) {
 
 constexpr unsigned long long kWorkerWaitNs = 20000000000ull;  // a worker waits at most 20 s for work
 
-__device__ __forceinline__ unsigned long long globaltimer_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
 
 // the shared memory of a search CTA, carved for one staged problem
 __device__ void carve_shared(const SolveJob &J, Shared &S, uint8_t *smem_raw, uint32_t **wm_out) {
@@ -936,6 +1295,20 @@ __device__ void carve_shared(const SolveJob &J, Shared &S, uint8_t *smem_raw, ui
     p += sizeof(SegTile) * J.seg_cap;
     S.sortbuf = reinterpret_cast<unsigned long long *>(p);
     p += sizeof(unsigned long long) * kSortMax;
+    S.solo_bits = reinterpret_cast<uint32_t *>(p);
+    p += sizeof(uint32_t) * (kSortMax / 32);
+    S.solo_pref = reinterpret_cast<uint32_t *>(p);
+    p += sizeof(uint32_t) * (kSortMax / 32 + 4);
+    S.sm_rows = S.sm_table = S.sm_tmp = nullptr;
+    if (J.small_rows) {
+        S.sm_rows = reinterpret_cast<uint32_t *>(p);
+        p += sizeof(uint32_t) * J.small_rows * W;
+        S.sm_table = reinterpret_cast<uint32_t *>(p);
+        p += sizeof(uint32_t) * 2 * J.small_rows;
+        S.sm_tmp = reinterpret_cast<uint32_t *>(p);
+        p += sizeof(uint32_t) * kSortMax * W;
+    }
+    for (uint32_t i = tid; i < kSortMax / 32; i += blockDim.x) S.solo_bits[i] = 0;
     S.lvs = reinterpret_cast<uint32_t *>(p);
     p += sizeof(uint32_t) * J.seg_cap;
     S.lvc = reinterpret_cast<uint32_t *>(p);
@@ -1015,6 +1388,8 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
         L.candidates = st->candidates;
         L.unique_done = st->unique_done;
         for (int k = 0; k < 5; k++) L.cand_op[k] = st->cand_op[k];
+        // a fresh search starts with its languages in shared memory
+        L.smode = J.small_rows && L.status == ST_RUNNING && L.level == J.c[0] && L.chunk_pos == 0 && L.size == 0;
         // trivial specifications (Alg. 1): the empty set, then eps
         if (L.status == ST_RUNNING && L.level == J.c[0] && L.chunk_pos == 0 && L.size == 0) {
             const uint32_t e_empty = J.n_pos_set;
@@ -1030,6 +1405,9 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
             }
         }
     }
+    __syncthreads();
+    if (L.smode)
+        for (uint32_t i = tid; i < 2 * J.small_rows; i += blockDim.x) S.sm_table[i] = kSmEmpty;
     __syncthreads();
 
     bool found = false;
@@ -1108,6 +1486,8 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
                 if (room * 4 >= J.chunk_max || room >= T - pos) {
                     C = room;
                 } else {
+                    // the next launch continues from the global tables
+                    if (L.smode) switch_to_global(J, S, &L);
                     if (tid == 0) {
                         st->need_rows = (uint32_t)umin64(J.cap, (uint64_t)size + C);
                         L.status = ST_NEED_MEM;
@@ -1123,6 +1503,9 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
         if (wid == 0) tile_setup(S, nseg, a.cs0, a.ce0, K.tiles);
         __syncthreads();
         const bool team = allow_team && *K.tiles > (uint64_t)J.solo_tiles;
+        // the shared-memory start ends before a chunk it cannot hold
+        if (L.smode && (team || !dedup || C > kSortMax || (uint64_t)size + C > J.small_rows))
+            switch_to_global(J, S, &L);
         const unsigned long long t_chunk = globaltimer_ns();
         if (tid == 0) tm[0] += t_chunk - t_it;
         if (team) {
@@ -1192,7 +1575,8 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
     return 0;
 }
 
-__global__ void __launch_bounds__(256, 2) k_solve(const __grid_constant__ SolveJob J) {
+// the search of one problem by every CTA of the launch (CTA 0 leads)
+__device__ __forceinline__ void solve_body(const SolveJob &J, uint32_t &bar_epoch) {
     SolveState *st = J.st;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     __shared__ Plan s_plan;
@@ -1209,7 +1593,6 @@ __global__ void __launch_bounds__(256, 2) k_solve(const __grid_constant__ SolveJ
     uint32_t *wm;
     carve_shared(J, S, smem_raw, &wm);
     const Cta K{&s_plan, s_red, &s_tiles, &s_found, &s_npend, &L, wm};
-    uint32_t bar_epoch = 0;
 
     if (blockIdx.x != 0) {
         // ---- worker: run the chunks CTA 0 hands out, until told to stop
@@ -1268,11 +1651,12 @@ __global__ void __launch_bounds__(256, 2) k_solve(const __grid_constant__ SolveJ
     const uint32_t status = ld_relaxed_u32(&st->status);
     if (status == ST_FOUND || status == ST_NOT_FOUND || status == ST_OOM) {
         // every CTA empties its share of the slots this search filled
+        // (languages that never left shared memory are in no global slot)
+        const uint32_t rows = L.smode ? 0u : L.size, npending = ld_relaxed_u32(&st->pending_count);
         if (tid == 0) {
-            st->c_level = L.size;
-            st->c_size = ld_relaxed_u32(&st->pending_count);
+            st->c_level = rows;
+            st->c_size = npending;
         }
-        const uint32_t rows = L.size, npending = ld_relaxed_u32(&st->pending_count);
         publish(st, CMD_CLEAN);
         clean_table(J, rows, npending, gridDim.x, 0);
         __syncthreads();
@@ -1280,6 +1664,96 @@ __global__ void __launch_bounds__(256, 2) k_solve(const __grid_constant__ SolveJ
     } else {
         publish(st, CMD_EXIT);
     }
+}
+
+__global__ void __launch_bounds__(256, 2) k_solve(const __grid_constant__ SolveJob J) {
+    uint32_t bar_epoch = 0;
+    solve_body(J, bar_epoch);
+}
+
+// chunk size for W-word languages (the host's rule for the plain launch)
+__device__ __forceinline__ uint64_t auto_chunk(uint32_t W) {
+    uint64_t c = (1ull << 28) / (4ull * W);
+    if (c < (1ull << 16)) c = 1ull << 16;
+    if (c > (1ull << 22)) c = 1ull << 22;
+    return c;
+}
+
+// Stage (CTA 0, the strings and the staging scratch in its shared memory),
+// size the search from the staged problem, then search, all in one launch.
+// A problem whose staging or search the launch cannot hold (|ic| > 2048, a
+// guide table beyond the pair buffer, shared memory) ends with ST_RESTAGE.
+__global__ void __launch_bounds__(256, 2) k_solve_fused(const __grid_constant__ FuseArgs F) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    __shared__ SolveJob J;
+    SolveState *st = F.tmpl.st;
+    uint32_t bar_epoch = 0;
+    if (blockIdx.x == 0) {
+        // the search state and the level table start empty
+        if (threadIdx.x == 0) {
+            st->level = F.tmpl.c[0];
+            st->found = kNone;
+            st->partial_level = F.tmpl.max_cost + 1;
+        }
+        for (uint32_t c = threadIdx.x; c < F.tmpl.max_cost + 2; c += blockDim.x) {
+            F.tmpl.lvl_start[c] = 0;
+            F.tmpl.lvl_count[c] = 0;
+        }
+        {
+            StageSmem M;
+            stage_layout(kServeMaxIC, kServeMaxBytes, smem_raw, &M);
+            stage_run(F.sj, M);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const StageInfo I = *F.sj.info;
+            SolveJob j = F.tmpl;
+            bool ok = I.status == SE_OK;
+            if (ok) {
+                j.n = I.n;
+                j.W = I.W;
+                j.G = I.G;
+                j.max_len = I.max_len;
+                j.n_pos_set = I.n_pos_set;
+                j.pos_eps = I.pos_eps;
+                j.neg_eps = I.neg_eps;
+                const uint32_t W = I.W;
+                j.cap = umin64(F.mem_budget / (4ull * W + 28), 0x7FFF0000ull);
+                const uint64_t tmax = F.table_slots / 2;
+                j.cache_alloc = umin64(umin64(j.cap, F.rows_alloc), umin64(F.cs_words / W, tmax / 2));
+                uint64_t ch = F.chunk_opt ? F.chunk_opt : auto_chunk(W);
+                ch = umin64(umin64(ch, 1ull << 24), umin64(F.tmp_words / W, F.pend_cap));
+                j.chunk_max = umin64(ch, tmax - j.cache_alloc);
+                // shared memory: guide table there if it fits, then the
+                // largest shared-memory start that fits
+                const uint32_t warps = blockDim.x / 32;
+                j.gt_in_smem = solve_smem_bytes(W, I.n, I.G, I.max_len, j.seg_cap, true, warps, 0) <= F.smem_cap;
+                j.small_rows = 0;
+                if (F.small_opt && W <= 8) {
+                    uint32_t r = F.small_opt != 0xFFFFFFFFu ? F.small_opt : W <= 2 ? 4096u : W <= 4 ? 2048u : 1024u;
+                    for (; r >= 256; r >>= 1)
+                        if (solve_smem_bytes(W, I.n, I.G, I.max_len, j.seg_cap, j.gt_in_smem, warps, r) <= F.smem_cap)
+                            break;
+                    if (r >= 256) j.small_rows = r;
+                }
+                ok = j.cache_alloc >= 1 && j.chunk_max >= 1 &&
+                     solve_smem_bytes(W, I.n, I.G, I.max_len, j.seg_cap, j.gt_in_smem, warps, j.small_rows) <=
+                         F.smem_cap;
+            }
+            *F.job = j;
+            if (!ok) st->status = ST_RESTAGE;
+        }
+    }
+    // every CTA waits for the staging, then takes the job into shared memory
+    if (!grid_barrier(st, bar_epoch, 1, F.tmpl.trace)) return;
+    if (ld_relaxed_u32(&st->status) != ST_RUNNING) return;
+    {
+        const unsigned long long *src = reinterpret_cast<const unsigned long long *>(F.job);
+        unsigned long long *dst = reinterpret_cast<unsigned long long *>(&J);
+        for (uint32_t i = threadIdx.x; i < sizeof(SolveJob) / 8; i += blockDim.x) dst[i] = ld_relaxed_u64(src + i);
+    }
+    __syncthreads();
+    solve_body(J, bar_epoch);
 }
 
 // ---------------------------------------------------------------------------
@@ -1340,7 +1814,7 @@ __device__ void solve_in_slot(SolveJob &J, const SlotMem &m, uint32_t slot, Batc
     lead_search(J, st, S, K, false, epoch);
     const uint32_t status = st->status;
     if (status == ST_FOUND || status == ST_NOT_FOUND || status == ST_OOM) {
-        clean_table(J, L->size, st->pending_count, 1, 0);
+        clean_table(J, L->smode ? 0u : L->size, st->pending_count, 1, 0);
     } else {
         // ran out of this slot's memory: the host solves it again alone;
         // this slot's table is rebuilt from scratch
@@ -1413,7 +1887,6 @@ __global__ void __launch_bounds__(256, 2) k_serve(const __grid_constant__ ServeA
     __shared__ SolveJob J;
     __shared__ StageJob SJ;
     __shared__ unsigned long long s_job;
-    __shared__ int16_t rank_tab[256];
     const uint32_t tid = threadIdx.x;
     const uint32_t slot = blockIdx.x;
     for (;;) {
@@ -1446,15 +1919,13 @@ __global__ void __launch_bounds__(256, 2) k_serve(const __grid_constant__ ServeA
         const uint32_t r = (uint32_t)(job % A.ring_size);
         const ServeReq &q = A.ring[r];
         ServeOut &o = A.outs[r];
-        // the request into this slot's device buffers, then staged by this CTA
+        // the request's offsets into this slot's buffer, then staged by this CTA
         const uint32_t n_str = q.n_pos + q.n_neg;
-        uint8_t *in_b = A.in_bytes + (uint64_t)slot * kServeMaxBytes;
         uint32_t *in_o = A.in_offs + (uint64_t)slot * (kServeMaxStrings + 1);
-        for (uint32_t i = tid; i < q.total_bytes; i += blockDim.x) in_b[i] = q.bytes[i];
         for (uint32_t i = tid; i <= n_str; i += blockDim.x) in_o[i] = q.offs[i];
         if (tid == 0) {
             StageJob sj{};
-            sj.bytes = in_b;
+            sj.bytes = q.bytes;  // copied once into shared memory by the staging
             sj.offs = in_o;
             sj.n_pos = q.n_pos;
             sj.n_neg = q.n_neg;
@@ -1474,8 +1945,12 @@ __global__ void __launch_bounds__(256, 2) k_serve(const __grid_constant__ ServeA
         }
         __threadfence();
         __syncthreads();
-        stage_run(SJ, A.st_hset + (uint64_t)slot * kHsetCap, A.st_rank_of + (uint64_t)slot * kHsetCap,
-                  A.st_uniq + (uint64_t)slot * kMaxIC, rank_tab);
+        {
+            // the staging scratch uses the shared memory the search carves later
+            StageSmem M;
+            stage_layout(kServeMaxIC, kServeMaxBytes, smem_raw, &M);
+            stage_run(SJ, M);
+        }
         __threadfence();
         __syncthreads();
         const StageInfo I = *SJ.info;
@@ -1512,9 +1987,9 @@ __global__ void __launch_bounds__(256, 2) k_serve(const __grid_constant__ ServeA
                 const uint64_t per = 4ull * I.W + 28;
                 j.cap = umin64(q.mem_budget / per, 0x7FFF0000ull);
                 j.seg_cap = 2 * q.max_cost + 4;
-                j.gt_in_smem = solve_smem_bytes(I.W, I.n, I.G, I.max_len, j.seg_cap, true, blockDim.x / 32) <=
+                j.gt_in_smem = solve_smem_bytes(I.W, I.n, I.G, I.max_len, j.seg_cap, true, blockDim.x / 32, 0) <=
                                A.smem_cap;
-                if (solve_smem_bytes(I.W, I.n, I.G, I.max_len, j.seg_cap, j.gt_in_smem, blockDim.x / 32) >
+                if (solve_smem_bytes(I.W, I.n, I.G, I.max_len, j.seg_cap, j.gt_in_smem, blockDim.x / 32, 0) >
                         A.smem_cap ||
                     I.W > A.slot.cs_words / A.slot.rows)
                     verdict = 2;
@@ -1566,6 +2041,20 @@ cudaError_t launch_solve(const SolveJob *job, uint32_t grid, uint32_t threads, s
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)job};
     return cudaLaunchCooperativeKernel((const void *)k_solve, dim3(grid), dim3(threads), args, smem, stream);
+}
+
+cudaError_t launch_solve_fused(const FuseArgs *args, uint32_t grid, uint32_t threads, size_t smem,
+                               cudaStream_t stream) {
+    cudaError_t e = cudaFuncSetAttribute(k_solve_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void *args_[] = {(void *)args};
+    return cudaLaunchCooperativeKernel((const void *)k_solve_fused, dim3(grid), dim3(threads), args_, smem, stream);
+}
+
+cudaError_t solve_fused_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_solve_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_solve_fused, (int)threads, smem);
 }
 
 cudaError_t solve_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm) {

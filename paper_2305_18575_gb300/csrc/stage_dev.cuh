@@ -11,10 +11,11 @@
 //     "specification") and of each alphabet symbol (the leaves of Alg. 1).
 //
 // Distinct infixes are found with a hash set of occurrences (start, len) keyed
-// by content; ranks come from counting the shortlex-smaller words.  The hash
-// set and its side arrays live wherever the caller puts them: in shared
-// memory for the staging kernel, in global scratch for a server CTA that
-// stages the requests it takes.
+// by content.  Shortlex ranks come from a sort of 64-bit keys (length, then
+// the symbols' ranks packed most significant first) when every word packs
+// into 39 bits, else from counting the shortlex-smaller words.  All scratch
+// (hash set, keys, word table, a copy of the strings when they fit) is
+// shared memory the caller carves with stage_layout().
 #pragma once
 #include <cstdint>
 
@@ -23,7 +24,6 @@
 namespace rei {
 
 
-constexpr uint32_t kHsetCap = 4 * kMaxIC;  // slots; at most kMaxIC + in-flight entries
 constexpr uint32_t kStageThreads = 1024;
 constexpr uint64_t kTagMask = 0xFFFFFFFF00000000ull;
 constexpr uint64_t kH0 = 0x9E3779B97F4A7C15ull;
@@ -54,35 +54,90 @@ __device__ __forceinline__ bool same_bytes(const uint8_t *b, uint32_t s1, uint32
     return true;
 }
 
-// rank of the infix bytes[start, start + len) in ic, or 0xFFFFFFFF if absent
-__device__ inline uint32_t stage_lookup(const uint8_t *bytes, const uint64_t *hset, const uint16_t *rank_of,
-                                 const int16_t *rank_tab, uint32_t start, uint32_t len) {
-    if (len == 0) return 0;
+// scratch of one staging CTA (shared memory)
+struct StageSmem {
+    uint64_t *hset;            // hcap slots: fingerprint | len | start of one occurrence
+    uint16_t *rank_of;         // hcap: shortlex rank of the word in each slot
+    unsigned long long *keys;  // ic_cap: sort keys (or slots, when ranks are counted)
+    uint32_t *wstart;          // ic_cap: an occurrence of the word of each rank
+    uint16_t *wlen;            // ic_cap: its length
+    int16_t *rank_tab;         // 256: rank of each byte in the alphabet, -1 if none
+    uint8_t *bytes;            // bytes_cap: the strings, when they fit
+    uint32_t hcap, ic_cap, bytes_cap;
+};
+
+// bytes of shared memory the scratch takes; carves it from `base` when given.
+// ic_cap (a power of two) bounds |ic|; strings longer in total than bytes_cap
+// are read from global memory
+__host__ __device__ inline size_t stage_layout(uint32_t ic_cap, uint32_t bytes_cap, uint8_t *base,
+                                               StageSmem *out) {
+    uint32_t hcap = 1;
+    while (hcap < 2 * ic_cap) hcap <<= 1;
+    size_t o = 0;
+    auto carve = [&](size_t bytes) {
+        const size_t at = o;
+        o += (bytes + 15) & ~size_t(15);
+        return at;
+    };
+    const size_t o_hset = carve(8ull * hcap), o_keys = carve(8ull * ic_cap), o_ws = carve(4ull * ic_cap);
+    const size_t o_rank = carve(2ull * hcap), o_wl = carve(2ull * ic_cap), o_tab = carve(2 * 256);
+    const size_t o_bytes = carve(bytes_cap);
+    if (base && out) {
+        out->hset = reinterpret_cast<uint64_t *>(base + o_hset);
+        out->keys = reinterpret_cast<unsigned long long *>(base + o_keys);
+        out->wstart = reinterpret_cast<uint32_t *>(base + o_ws);
+        out->rank_of = reinterpret_cast<uint16_t *>(base + o_rank);
+        out->wlen = reinterpret_cast<uint16_t *>(base + o_wl);
+        out->rank_tab = reinterpret_cast<int16_t *>(base + o_tab);
+        out->bytes = base + o_bytes;
+        out->hcap = hcap;
+        out->ic_cap = ic_cap;
+        out->bytes_cap = bytes_cap;
+    }
+    return o;
+}
+
+// hash of the infix bytes[start, start + len)
+__device__ __forceinline__ uint64_t stage_hash(const uint8_t *bytes, const int16_t *rank_tab, uint32_t start,
+                                               uint32_t len) {
     uint64_t h = kH0;
     for (uint32_t i = 0; i < len; i++) h = stage_mix(h, (uint32_t)rank_tab[bytes[start + i]]);
-    const uint64_t f = stage_final(h, len);
+    return stage_final(h, len);
+}
+
+// rank of the infix bytes[start, start + len) with hash f, or 0xFFFFFFFF
+__device__ inline uint32_t stage_find(const StageSmem &M, const uint8_t *bytes, uint64_t f, uint32_t start,
+                                      uint32_t len) {
+    if (len == 0) return 0;
     const uint64_t tag = stage_tag(f, len);
-    uint32_t q = (uint32_t)f & (kHsetCap - 1);
-    for (uint32_t probe = 0; probe < kHsetCap; probe++) {
-        const uint64_t v = hset[q];
+    const uint32_t mask = M.hcap - 1;
+    uint32_t q = (uint32_t)f & mask;
+    for (uint32_t probe = 0; probe < M.hcap; probe++) {
+        const uint64_t v = M.hset[q];
         if (v == kEmpty) return 0xFFFFFFFFu;
-        if ((v & kTagMask) == tag && same_bytes(bytes, (uint32_t)v, start, len)) return rank_of[q];
-        q = (q + 1) & (kHsetCap - 1);
+        if ((v & kTagMask) == tag && same_bytes(bytes, (uint32_t)v, start, len)) return M.rank_of[q];
+        q = (q + 1) & mask;
     }
     return 0xFFFFFFFFu;
 }
 
-// rank of the one-symbol word `a`, or 0xFFFFFFFF
-__device__ inline uint32_t stage_lookup_symbol(const uint8_t *bytes, const uint64_t *hset,
-                                        const uint16_t *rank_of, uint32_t rank, uint8_t a) {
+__device__ inline uint32_t stage_lookup(const StageSmem &M, const uint8_t *bytes, uint32_t start, uint32_t len) {
+    if (len == 0) return 0;
+    return stage_find(M, bytes, stage_hash(bytes, M.rank_tab, start, len), start, len);
+}
+
+// rank of the one-symbol word `a` (alphabet rank `rank`), or 0xFFFFFFFF
+__device__ inline uint32_t stage_lookup_symbol(const StageSmem &M, const uint8_t *bytes, uint32_t rank,
+                                               uint8_t a) {
     const uint64_t f = stage_final(stage_mix(kH0, rank), 1);
     const uint64_t tag = stage_tag(f, 1);
-    uint32_t q = (uint32_t)f & (kHsetCap - 1);
-    for (uint32_t probe = 0; probe < kHsetCap; probe++) {
-        const uint64_t v = hset[q];
+    const uint32_t mask = M.hcap - 1;
+    uint32_t q = (uint32_t)f & mask;
+    for (uint32_t probe = 0; probe < M.hcap; probe++) {
+        const uint64_t v = M.hset[q];
         if (v == kEmpty) return 0xFFFFFFFFu;
-        if ((v & kTagMask) == tag && bytes[(uint32_t)v] == a) return rank_of[q];
-        q = (q + 1) & (kHsetCap - 1);
+        if ((v & kTagMask) == tag && bytes[(uint32_t)v] == a) return M.rank_of[q];
+        q = (q + 1) & mask;
     }
     return 0xFFFFFFFFu;
 }
@@ -134,20 +189,40 @@ __device__ __forceinline__ uint64_t ld_strong_u64(const uint64_t *p) {
     return v;
 }
 
-// stage problem J with the calling CTA; hset[kHsetCap], rank_of[kHsetCap],
-// uniq[kMaxIC] and rank_tab[256] are the caller's scratch
-__device__ inline void stage_run(const StageJob &J, uint64_t *hset, uint16_t *rank_of, uint16_t *uniq,
-                                 int16_t *rank_tab) {
+// step timing (ns, in StageInfo::pad), compiled in with -DREI_TIMING only
+#ifdef REI_TIMING
+#define STAGE_MARK(k)                                                              \
+    do {                                                                           \
+        if (threadIdx.x == 0) {                                                    \
+            unsigned long long t_now;                                              \
+            asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t_now));               \
+            J.info->pad[k] = (uint32_t)(t_now - t_prev);                           \
+            t_prev = t_now;                                                        \
+        }                                                                          \
+    } while (0)
+#else
+#define STAGE_MARK(k) \
+    do {              \
+    } while (0)
+#endif
+
+// stage problem J with the calling CTA, in the scratch M
+__device__ inline void stage_run(const StageJob &J, const StageSmem &M) {
+#ifdef REI_TIMING
+    unsigned long long t_prev;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t_prev));
+#endif
     __shared__ uint32_t s_err, s_count, s_maxlen, s_total, s_ov, s_np, s_nn;
     __shared__ uint32_t warp_sums[32];
 
     const uint32_t tid = threadIdx.x, nt = blockDim.x;
     const uint32_t n_str = J.n_pos + J.n_neg;
-    const uint8_t *bytes = J.bytes;
     const uint32_t *offs = J.offs;
     const uint32_t total = offs[n_str];
+    uint64_t *hset = M.hset;
+    int16_t *rank_tab = M.rank_tab;
 
-    for (uint32_t q = tid; q < kHsetCap; q += nt) hset[q] = kEmpty;
+    for (uint32_t q = tid; q < M.hcap; q += nt) hset[q] = kEmpty;
     for (uint32_t i = tid; i < 256; i += nt) rank_tab[i] = -1;
     for (uint32_t i = tid; i < kMaxWords; i += nt) {
         J.pos_mask[i] = 0;
@@ -164,8 +239,8 @@ __device__ inline void stage_run(const StageJob &J, uint64_t *hset, uint16_t *ra
     }
     __syncthreads();
     for (uint32_t a = tid; a < J.n_sym; a += nt) rank_tab[J.alphabet[a]] = (int16_t)a;
-    __syncthreads();
 
+    STAGE_MARK(0);
     // offsets start at 0 and never decrease (device inputs are not checked on
     // the host); every byte must be a symbol; strings must fit the length field
     if (offs[0] != 0) s_err = SE_OFFSETS;
@@ -176,6 +251,13 @@ __device__ inline void stage_run(const StageJob &J, uint64_t *hset, uint16_t *ra
         if (tid == 0) J.info->status = s_err;
         return;
     }
+    // the strings into shared memory when they fit
+    const uint8_t *bytes = J.bytes;
+    if (total <= M.bytes_cap) {
+        for (uint32_t p = tid; p < total; p += nt) M.bytes[p] = J.bytes[p];
+        bytes = M.bytes;
+    }
+    __syncthreads();
     for (uint32_t p = tid; p < total; p += nt)
         if (rank_tab[bytes[p]] < 0) s_err = SE_SYMBOL;
     for (uint32_t k = tid; k < n_str; k += nt) atomicMax(&s_maxlen, offs[k + 1] - offs[k]);
@@ -183,8 +265,10 @@ __device__ inline void stage_run(const StageJob &J, uint64_t *hset, uint16_t *ra
     if (s_err == SE_OK && s_maxlen > REI_MAX_STRLEN) s_err = SE_STRLEN;
     __syncthreads();
 
+    STAGE_MARK(1);
     // every occurrence (start p, length len) of every string goes into the set
     if (s_err == SE_OK) {
+        const uint32_t mask = M.hcap - 1;
         for (uint32_t p = tid; p < total; p += nt) {
             // string k with offs[k] <= p < offs[k+1] (strings may be empty)
             uint32_t lo = 0, hi = n_str;  // invariant: offs[lo] <= p < offs[hi]
@@ -201,20 +285,20 @@ __device__ inline void stage_run(const StageJob &J, uint64_t *hset, uint16_t *ra
                 const uint64_t f = stage_final(h, len);
                 const uint64_t tag = stage_tag(f, len);
                 const uint64_t want = tag | p;
-                uint32_t q = (uint32_t)f & (kHsetCap - 1);
-                for (uint32_t probe = 0; probe < kHsetCap; probe++) {
+                uint32_t q = (uint32_t)f & mask;
+                for (uint32_t probe = 0; probe < M.hcap; probe++) {
                     uint64_t v = ld_strong_u64(&hset[q]);
                     if (v == kEmpty) {
                         const unsigned long long old =
                             atomicCAS((unsigned long long *)&hset[q], kEmpty, want);
                         if (old == kEmpty) {
-                            if (atomicAdd(&s_count, 1u) + 2 > kMaxIC) s_err = SE_IC_LARGE;
+                            if (atomicAdd(&s_count, 1u) + 2 > M.ic_cap) s_err = SE_IC_LARGE;
                             break;
                         }
                         v = old;
                     }
                     if ((v & kTagMask) == tag && same_bytes(bytes, (uint32_t)v, p, len)) break;
-                    q = (q + 1) & (kHsetCap - 1);
+                    q = (q + 1) & mask;
                 }
                 if (*(volatile uint32_t *)&s_err != SE_OK) break;
             }
@@ -227,53 +311,98 @@ __device__ inline void stage_run(const StageJob &J, uint64_t *hset, uint16_t *ra
         return;
     }
 
-    // the distinct words (unordered), then their shortlex ranks (eps = 0)
+    STAGE_MARK(2);
+    // the distinct words: packed shortlex keys when every word packs into
+    // 39 bits (length << 52 | symbol ranks << 13 | slot), else their slots
+    uint32_t bsym = 1;
+    while ((1u << bsym) < J.n_sym) bsym++;
+    const bool packed = s_maxlen * bsym <= 39;
     if (tid == 0) s_count = 0;
     __syncthreads();
-    for (uint32_t q = tid; q < kHsetCap; q += nt)
-        if (hset[q] != kEmpty) uniq[atomicAdd(&s_count, 1u)] = (uint16_t)q;
+    for (uint32_t q = tid; q < M.hcap; q += nt) {
+        const uint64_t v = hset[q];
+        if (v == kEmpty) continue;
+        unsigned long long key = q;
+        if (packed) {
+            const uint32_t st = (uint32_t)v, len = (uint32_t)(v >> 32) & 0xFFFu;
+            uint64_t c = 0;
+            for (uint32_t i = 0; i < len; i++) c = (c << bsym) | (uint32_t)rank_tab[bytes[st + i]];
+            key = ((unsigned long long)len << 52) | (c << 13) | q;
+        }
+        M.keys[atomicAdd(&s_count, 1u)] = key;
+    }
     __syncthreads();
     const uint32_t U = s_count, n = U + 1;
-    for (uint32_t i = tid; i < U; i += nt) {
-        const uint64_t vi = hset[uniq[i]];
-        const uint32_t si = (uint32_t)vi, li = (uint32_t)(vi >> 32) & 0xFFFu;
-        uint32_t r = 1;
-        for (uint32_t j = 0; j < U; j++) {
-            const uint64_t vj = hset[uniq[j]];
-            if (shortlex_less(bytes, rank_tab, (uint32_t)vj, (uint32_t)(vj >> 32) & 0xFFFu, si, li)) r++;
+    STAGE_MARK(3);
+    if (packed) {
+        // bitonic sort of the keys (padded to a power of two with ~0)
+        uint32_t m = 1;
+        while (m < U) m <<= 1;
+        for (uint32_t i = U + tid; i < m; i += nt) M.keys[i] = ~0ull;
+        __syncthreads();
+        for (uint32_t k = 2; k <= m; k <<= 1) {
+            for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
+                for (uint32_t i = tid; i < m; i += nt) {
+                    const uint32_t ix = i ^ jj;
+                    if (ix > i) {
+                        const unsigned long long x = M.keys[i], y = M.keys[ix];
+                        if ((x > y) == ((i & k) == 0)) {
+                            M.keys[i] = y;
+                            M.keys[ix] = x;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
         }
-        J.word_start[r] = si;
-        J.word_len[r] = li;
-        rank_of[uniq[i]] = (uint16_t)r;
+        for (uint32_t i = tid; i < U; i += nt) {
+            const uint32_t q = (uint32_t)(M.keys[i] & 0x1FFFu), r = i + 1;
+            const uint64_t v = hset[q];
+            M.rank_of[q] = (uint16_t)r;
+            M.wstart[r] = (uint32_t)v;
+            M.wlen[r] = (uint16_t)((v >> 32) & 0xFFFu);
+        }
+    } else {
+        for (uint32_t i = tid; i < U; i += nt) {
+            const uint32_t qi = (uint32_t)M.keys[i];
+            const uint64_t vi = hset[qi];
+            const uint32_t si = (uint32_t)vi, li = (uint32_t)(vi >> 32) & 0xFFFu;
+            uint32_t r = 1;
+            for (uint32_t j = 0; j < U; j++) {
+                const uint64_t vj = hset[(uint32_t)M.keys[j]];
+                if (shortlex_less(bytes, rank_tab, (uint32_t)vj, (uint32_t)(vj >> 32) & 0xFFFu, si, li)) r++;
+            }
+            M.rank_of[qi] = (uint16_t)r;
+            M.wstart[r] = si;
+            M.wlen[r] = (uint16_t)li;
+        }
     }
     if (tid == 0) {
-        J.word_start[0] = 0;
-        J.word_len[0] = 0;
+        M.wstart[0] = 0;
+        M.wlen[0] = 0;
     }
     __syncthreads();
-
-    // first rank of every length (all lengths 0..max_len occur: ic is infix-closed)
-    uint32_t max_len = 0;
     for (uint32_t r = tid; r < n; r += nt) {
-        const uint32_t L = J.word_len[r];
-        if (r == 0 || J.word_len[r - 1] != L) J.len_start[L] = r;
+        J.word_start[r] = M.wstart[r];
+        J.word_len[r] = M.wlen[r];
     }
-    max_len = J.word_len[n - 1];
+
+    STAGE_MARK(4);
+    // first rank of every length (all lengths 0..max_len occur: ic is infix-closed)
+    for (uint32_t r = tid; r < n; r += nt) {
+        const uint32_t L = M.wlen[r];
+        if (r == 0 || M.wlen[r - 1] != L) J.len_start[L] = r;
+    }
+    const uint32_t max_len = M.wlen[n - 1];
     if (tid == 0) J.len_start[max_len + 1] = n;
 
     // guide-table offsets: exclusive scan of |w| + 1 over words in rank order
     const uint32_t per = (n + nt - 1) / nt;
     const uint32_t r0 = min(n, tid * per), r1 = min(n, r0 + per);
     uint32_t local = 0;
-    for (uint32_t r = r0; r < r1; r++) local += J.word_len[r] + 1;
+    for (uint32_t r = r0; r < r1; r++) local += M.wlen[r] + 1u;
     uint32_t off = block_exclusive_scan(local, warp_sums, &s_total);
-    for (uint32_t r = r0; r < r1; r++) {
-        J.gt_off[r] = off;
-        off += J.word_len[r] + 1;
-    }
     const uint32_t G = s_total;
-    if (tid == 0) J.gt_off[n] = G;
-    __syncthreads();
     if (G > J.pair_cap) {
         if (tid == 0) {
             J.info->status = SE_PAIRS;
@@ -283,25 +412,26 @@ __device__ inline void stage_run(const StageJob &J, uint64_t *hset, uint16_t *ra
         }
         return;
     }
-
-    // guide-table pairs: split k of word r is (prefix of length k, the rest)
-    for (uint32_t g = tid; g < G; g += nt) {
-        uint32_t lo = 0, hi = n;  // gt_off[lo] <= g < gt_off[hi]
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (J.gt_off[mid] <= g) lo = mid;
-            else hi = mid;
+    // guide-table pairs of each word: split k is (prefix of length k, the rest)
+    for (uint32_t r = r0; r < r1; r++) {
+        J.gt_off[r] = off;
+        const uint32_t len = M.wlen[r], st = M.wstart[r];
+        uint64_t hp = kH0;  // hash state of the prefix
+        for (uint32_t k = 0; k <= len; k++) {
+            if (k) hp = stage_mix(hp, (uint32_t)rank_tab[bytes[st + k - 1]]);
+            const uint32_t u = k == 0 ? 0u : stage_find(M, bytes, stage_final(hp, k), st, k);
+            const uint32_t v = stage_lookup(M, bytes, st + k, len - k);
+            if (u >= n || v >= n) s_err = SE_INTERNAL;  // infixes of ic words are in ic
+            J.gt_pair[off + k] = (u & 0xFFFFu) | (v << 16);
         }
-        const uint32_t k = g - J.gt_off[lo], len = J.word_len[lo], st = J.word_start[lo];
-        const uint32_t u = stage_lookup(bytes, hset, rank_of, rank_tab, st, k);
-        const uint32_t v = stage_lookup(bytes, hset, rank_of, rank_tab, st + k, len - k);
-        if (u >= n || v >= n) s_err = SE_INTERNAL;  // infixes of ic words are in ic
-        J.gt_pair[g] = (u & 0xFFFFu) | (v << 16);
+        off += len + 1;
     }
+    if (tid == 0) J.gt_off[n] = G;
 
+    STAGE_MARK(5);
     // characteristic sequences of P and N, and of every symbol
     for (uint32_t k = tid; k < n_str; k += nt) {
-        const uint32_t r = stage_lookup(bytes, hset, rank_of, rank_tab, offs[k], offs[k + 1] - offs[k]);
+        const uint32_t r = stage_lookup(M, bytes, offs[k], offs[k + 1] - offs[k]);
         if (r >= n) {
             s_err = SE_INTERNAL;
             continue;
@@ -310,7 +440,7 @@ __device__ inline void stage_run(const StageJob &J, uint64_t *hset, uint16_t *ra
         atomicOr(&mask[r >> 5], 1u << (r & 31));
     }
     for (uint32_t a = tid; a < J.n_sym; a += nt) {
-        const uint32_t r = stage_lookup_symbol(bytes, hset, rank_of, a, J.alphabet[a]);
+        const uint32_t r = stage_lookup_symbol(M, bytes, a, J.alphabet[a]);
         if (r < n) J.leaf[a * kMaxWords + (r >> 5)] = 1u << (r & 31);
     }
     __syncthreads();
@@ -322,6 +452,7 @@ __device__ inline void stage_run(const StageJob &J, uint64_t *hset, uint16_t *ra
         atomicAdd(&s_nn, (uint32_t)__popc(q));
     }
     __syncthreads();
+    STAGE_MARK(6);
     if (tid == 0) {
         StageInfo *I = J.info;
         I->status = s_err != SE_OK ? s_err : s_ov ? SE_OVERLAP : SE_OK;

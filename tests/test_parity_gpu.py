@@ -169,8 +169,102 @@ def test_chunking_and_grid_do_not_change_results(chunk, grid, solo):
         check_same(got, ref, ("pin20", chunk, grid))
 
 
-def test_cache_growth_relaunch_matches(ctx):
+_ORACLE = {}
+
+
+def oracle_medium(seed, costs):
+    key = (seed, costs)
+    if key not in _ORACLE:
+        inst = make_config("medium", seed)
+        _ORACLE[key] = (inst, oracle.solve(inst.alphabet, inst.pos, inst.neg, costs=costs, max_cost=40))
+    return _ORACLE[key]
+
+
+@pytest.mark.parametrize("small", [0, 256, 1024, -1])
+@pytest.mark.parametrize("chunk,solo", [(0, -1), (7, -1), (100, 1 << 30)])
+def test_shared_memory_start_does_not_change_results(small, chunk, solo):
+    """The search's start with its languages and uniqueness table in CTA 0's
+    shared memory (`small` rows: 0 = never, 256 = leaves it after a few
+    levels, -1 = as many as fit) gives the oracle's results, through the move
+    to the global table in the middle of a search, with chunks split small
+    and with every chunk on CTA 0 alone."""
     with rei.Context(device=0) as c:
+        c.set_option(rei.REI_OPT_SMALL_ROWS, small)
+        c.set_option(rei.REI_OPT_CHUNK, chunk)
+        c.set_option(rei.REI_OPT_SOLO_TILES, solo)
+        for s in (0, 2, 5, 12):
+            for costs in [(1, 1, 1, 1, 1), (1, 1, 5, 1, 1)]:
+                inst, ref = oracle_medium(s, costs)
+                got = c.solve_problem(rei.Problem(inst.alphabet, inst.pos, inst.neg, costs=costs, max_cost=40,
+                                                  mem_budget=inst.mem_budget))
+                check_same(got, ref, (s, costs, small, chunk))
+        got, ref = solve_both(c, A01, PIN_P, PIN_N, max_cost=30, max_errors=4)
+        check_same(got, ref, ("pin20", small, chunk))
+        # budgets that fill the cache while it is still in shared memory
+        P, N = [b"0110", b"1"], [b"", b"01", b"11"]
+        for budget in (64, 400, 2000, 9000):
+            got, ref = solve_both(c, A01, P, N, max_cost=30, mem_budget=budget)
+            check_same(got, ref, (budget, small))
+        for rows in (3, 6, 12):
+            inst = make_config("small", rows)
+            got, ref = solve_both(c, inst, costs=(1, 2, 3, 3, 3), max_cost=30, mem_budget=rows * 32,
+                                  flags=rei.REI_F_ONTHEFLY)
+            check_same(got, ref, ("otf", rows, small))
+
+
+def test_shared_memory_start_with_cache_growth():
+    """A tiny first cache makes the search ask for more memory while its
+    languages are still in shared memory: they move to the global table
+    before the relaunch."""
+    with rei.Context(device=0) as c:
+        c.set_option(rei.REI_OPT_CACHE_INIT, 8)
+        c.set_option(rei.REI_OPT_SMALL_ROWS, 4096)
+        for s in (2, 5, 16):
+            inst = make_config("medium", s)
+            got, ref = solve_both(c, inst, max_cost=40, costs=(1, 1, 1, 1, 1))
+            check_same(got, ref, s)
+            assert got.launches > 2
+
+
+def test_small_rows_option_checked():
+    with rei.Context(device=0) as c:
+        for bad in (1, 100, 255, 300, 32768):
+            with pytest.raises(ValueError):
+                c.set_option(rei.REI_OPT_SMALL_ROWS, bad)
+
+
+@pytest.mark.parametrize("fused", [0, 1])
+def test_fused_and_separate_staging_agree(fused):
+    """Staging inside the search launch (1) or in its own launch (0): the same
+    results, including a problem too large for the fused launch's staging
+    (|ic| = 3538 > 2048), which goes through the separate staging launch."""
+    with rei.Context(device=0) as c:
+        c.set_option(rei.REI_OPT_FUSED_STAGE, fused)
+        for s in (0, 3, 12):
+            for costs in [(1, 1, 1, 1, 1), (1, 1, 5, 1, 1)]:
+                inst, ref = oracle_medium(s, costs)
+                got = c.solve_problem(rei.Problem(inst.alphabet, inst.pos, inst.neg, costs=costs, max_cost=40,
+                                                  mem_budget=inst.mem_budget))
+                check_same(got, ref, (s, costs, fused))
+        for s in range(6):
+            got, ref = solve_both(c, make_config("small", s), max_cost=20)
+            check_same(got, ref, ("small", s))
+        got, ref = solve_both(c, A01, *EX1, max_cost=12)
+        check_same(got, ref, "ex1")
+        rng = random.Random(0)
+        pos = list({bytes(rng.choice(b"abcd") for _ in range(rng.randint(20, 34))) for _ in range(6)})
+        neg = list({bytes(rng.choice(b"abcd") for _ in range(rng.randint(20, 34))) for _ in range(6)} - set(pos))
+        got, ref = solve_both(c, b"abcd", pos, neg, max_cost=3)
+        assert got.n_ic == 3538
+        check_same(got, ref, "ic3538")
+        assert c.solve(A01, [b"2"], [b""]).status == rei.REI_EINVAL
+        assert c.solve(A01, [b"0"], [b"0"]).status == rei.REI_EINVAL
+
+
+@pytest.mark.parametrize("fused", [0, 1])
+def test_cache_growth_relaunch_matches(ctx, fused):
+    with rei.Context(device=0) as c:
+        c.set_option(rei.REI_OPT_FUSED_STAGE, fused)
         c.set_option(rei.REI_OPT_CACHE_INIT, 8)
         c.set_option(rei.REI_OPT_CHUNK, 64)
         for s in (2, 5, 16):
