@@ -170,6 +170,20 @@ def alu_peak(device: int):
     return L.rei_peak_lop3(device, C.byref(ms))
 
 
+def reduce_over_ranks(total_ms: float, cands: float, world: int, device: str):
+    """Whole-job figures of independent replicas: the slowest rank's time and
+    every rank's candidates (the only collective; nothing on the data path)."""
+    if world <= 1:
+        return total_ms, cands
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    cc = torch.tensor([float(cands)], dtype=torch.float64, device=device)
+    dist.all_reduce(cc)
+    return float(t.item()), float(cc.item())
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import paper_2305_18575_gb300 as rei
@@ -262,15 +276,7 @@ def run_gpu(args, rank, world, local_rank):
                  "alu_frac": alu_frac, "hbm_frac": hbm_frac})
 
     # whole-job aggregation over ranks (replicas: no data-path collective)
-    t_max = total_ms
-    c_sum = cands
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=f"cuda:{dev}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-        cc = torch.tensor([float(cands)], dtype=torch.float64, device=f"cuda:{dev}")
-        torch.distributed.all_reduce(cc)
-        c_sum = float(cc.item())
+    t_max, c_sum = reduce_over_ranks(total_ms, cands, world, f"cuda:{dev}")
     if rank != 0:
         return
     ttm = sorted(r.ms_total for r in results)
