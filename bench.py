@@ -300,7 +300,7 @@ def run_gpu(args, rank, world, local_rank):
     if not args.no_batch:
         bprobs = batched_problems()
         line["batched"] = batched_leg(ctx, dev, bprobs)
-        line["served"] = served_leg(dev, bprobs)
+        line["served"] = served_leg(dev, bprobs, args.serve_seconds)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -349,14 +349,14 @@ def batched_leg(ctx, dev, probs):
             "solve_ms_p50": lat[len(lat) // 2], "solve_ms_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
 
 
-SERVE_WORKLOAD = ("served: Poisson arrivals at 50, 200 and 1000 problems/s for 2 s each, problems drawn in turn "
+SERVE_WORKLOAD = ("served: Poisson arrivals at 50, 200 and 1000 problems/s (trace seed = rate), problems drawn in turn "
                   "from the 512 batched-workload instances; rei_server (one persistent launch) vs a loop of "
                   "rei_solve_problem calls taking the same arrivals in order")
 SERVE_RATES = (50, 200, 1000)
 SERVE_SECONDS = 2.0
 
 
-def served_leg(dev, probs):
+def served_leg(dev, probs, seconds=SERVE_SECONDS):
     """Latency from arrival to answer (host clock) of the served form against a
     plain loop that solves the same arrivals one at a time."""
     import paper_2305_18575_gb300 as rei
@@ -366,13 +366,13 @@ def served_leg(dev, probs):
         v = sorted(v)
         return v[min(len(v) - 1, int(q * len(v)))]
 
-    out = {"workload": SERVE_WORKLOAD, "rates": {}}
+    out = {"workload": SERVE_WORKLOAD, "seconds_per_rate": seconds, "rates": {}}
     answers = {}
     with rei.Context(device=dev) as sctx, rei.Server(sctx, budget_bytes=64 << 30, max_live=4096) as srv:
         for t in [srv.submit(p) for p in probs[:64]]:  # warm-up
             srv.result(t)
         for rate in SERVE_RATES:
-            arr = poisson_trace(rate, SERVE_SECONDS, seed=11)
+            arr = poisson_trace(rate, seconds, seed=rate)
             tickets = []
             t0 = time.perf_counter()
             for k, a in enumerate(arr):
@@ -381,7 +381,7 @@ def served_leg(dev, probs):
                     time.sleep(dt)
                 tickets.append(srv.submit(probs[k % len(probs)]))
             res = [srv.result(t) for t in tickets]
-            t_end = max(time.perf_counter(), t0 + SERVE_SECONDS)
+            t_end = max(time.perf_counter(), t0 + seconds)
             answers[rate] = [(r.status, r.cost, r.tree) for r in res]
             lat = [r.ms_total for r in res]
             out["rates"][str(rate)] = {"requests": len(arr), "served_p50_ms": pct(lat, 0.5),
@@ -391,7 +391,7 @@ def served_leg(dev, probs):
         for p in probs[:16]:
             pctx.solve_problem(p)
         for rate in SERVE_RATES:
-            arr = poisson_trace(rate, SERVE_SECONDS, seed=11)
+            arr = poisson_trace(rate, seconds, seed=rate)
             lat, got = [], []
             t0 = time.perf_counter()
             for k, a in enumerate(arr):
@@ -416,6 +416,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched and served legs")
+    ap.add_argument("--serve-seconds", type=float, default=SERVE_SECONDS,
+                    help="length of each arrival trace of the served leg (the served config uses 60)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
