@@ -31,6 +31,7 @@ REI_F_ONTHEFLY = 2
 REI_OPT_CHUNK, REI_OPT_GRID, REI_OPT_KEEP_CACHE, REI_OPT_CACHE_INIT, REI_OPT_SOLO_TILES = 1, 2, 3, 4, 5
 REI_OPT_SMALL_ROWS = 6
 REI_OPT_FUSED_STAGE = 7
+REI_OPT_EXACT_KEYS = 8
 REI_MAX_IC, REI_MAX_STRLEN, REI_MAX_COST = 4096, 4095, 255
 
 # every entry point include/rei.h declares

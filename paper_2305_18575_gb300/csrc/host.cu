@@ -69,7 +69,7 @@ struct rei_ctx {
     uint64_t launches = 0;
 
     int64_t opt_chunk = 0, opt_grid = 0, opt_keep = 0, opt_cache_init = 0, opt_solo_tiles = -1, opt_small_rows = -1;
-    int64_t opt_fused = 1;
+    int64_t opt_fused = 1, opt_exact = 1;
     size_t smem_sm = 0;  // shared memory per SM
 
     // staging
@@ -77,7 +77,7 @@ struct rei_ctx {
         pos, neg, leaf;
     uint32_t pair_cap = 1u << 16;
     // search
-    DevBuf cs, bp_op, bp_l, bp_r, table, tmp, pending, slotpos, bitmap, blk, lvl_start, lvl_count,
+    DevBuf cs, bp_op, bp_l, bp_r, table, minidx, tmp, pending, slotpos, bitmap, blk, lvl_start, lvl_count,
         state, solve_job, tstack, trace, used;
     bool table_clean = false;  // the search kernel leaves the table empty after a normal end
     // batched form
@@ -486,10 +486,13 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
     const uint64_t tslots = pow2_at_least(std::max<uint64_t>(4 * rows, 1024));
     {
         // a reallocated table (even at the same address) holds garbage
-        const void *before = c->table.p;
-        const size_t before_bytes = c->table.bytes;
+        const void *before = c->table.p, *mbefore = c->minidx.p;
+        const size_t before_bytes = c->table.bytes, mbefore_bytes = c->minidx.bytes;
         if ((s = ensure(c, c->table, 8ull * tslots))) return s;
-        if (c->table.p != before || c->table.bytes != before_bytes) c->table_clean = false;
+        if ((s = ensure(c, c->minidx, 4ull * tslots))) return s;
+        if (c->table.p != before || c->table.bytes != before_bytes || c->minidx.p != mbefore ||
+            c->minidx.bytes != mbefore_bytes)
+            c->table_clean = false;
     }
     const uint64_t chunk_words = c->opt_chunk > 0 ? (uint64_t)c->opt_chunk : (1ull << 22);
     if ((s = ensure(c, c->tmp, std::max<uint64_t>(4ull * 2 * chunk_words, 4ull * 64 * 4096)))) return s;
@@ -518,6 +521,7 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
     if ((s = ensure(c, c->trace, 4ull * grid))) return s;
     if (!c->table_clean) {
         CK(cudaMemsetAsync(c->table.p, 0xFF, c->table.bytes, c->stream));
+        CK(cudaMemsetAsync(c->minidx.p, 0xFF, c->minidx.bytes, c->stream));
         CK(cudaMemsetAsync(c->bitmap.p, 0, c->bitmap.bytes, c->stream));
     }
     c->table_clean = false;
@@ -567,6 +571,8 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
     j.used = (uint32_t *)c->used.p;
     j.table = (unsigned long long *)c->table.p;
     j.table_mask = tslots - 1;
+    j.minidx = (uint32_t *)c->minidx.p;
+    j.exact = c->opt_exact ? 1u : 0u;  // allowed; the launch decides from the staged size
     j.tmp = (uint32_t *)c->tmp.p;
     j.pending = (uint32_t *)c->pending.p;
     j.slotpos = (uint32_t *)c->slotpos.p;
@@ -730,10 +736,13 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
     if ((s = ensure(c, c->bp_r, 4ull * cache_alloc))) return s;
     if ((s = ensure(c, c->used, 4ull * cache_alloc))) return s;
     {
-        const void *before = c->table.p;
-        const size_t before_bytes = c->table.bytes;
+        const void *before = c->table.p, *mbefore = c->minidx.p;
+        const size_t before_bytes = c->table.bytes, mbefore_bytes = c->minidx.bytes;
         if ((s = ensure(c, c->table, 8ull * tslots))) return s;
-        if (c->table.p != before || c->table.bytes != before_bytes) c->table_clean = false;
+        if ((s = ensure(c, c->minidx, 4ull * tslots))) return s;
+        if (c->table.p != before || c->table.bytes != before_bytes || c->minidx.p != mbefore ||
+            c->minidx.bytes != mbefore_bytes)
+            c->table_clean = false;
     }
     if ((s = ensure(c, c->tmp, 4ull * W * chunk_max))) return s;
     if ((s = ensure(c, c->pending, 4ull * chunk_max))) return s;
@@ -762,6 +771,7 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
         if (!c->table_clean) {
             // a new table, or the last search ended abnormally: clear it all once
             CK(cudaMemsetAsync(c->table.p, 0xFF, c->table.bytes, c->stream));
+        CK(cudaMemsetAsync(c->minidx.p, 0xFF, c->minidx.bytes, c->stream));
             CK(cudaMemsetAsync(c->bitmap.p, 0, c->bitmap.bytes, c->stream));
         }
         c->table_clean = false;
@@ -810,6 +820,8 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
         hj->used = (uint32_t *)c->used.p;
         hj->cache_alloc = cache_alloc;
         hj->table = (unsigned long long *)c->table.p;
+        hj->minidx = (uint32_t *)c->minidx.p;
+        hj->exact = (W <= 2 && n <= 62 && c->opt_exact) ? 1u : 0u;
         hj->table_mask = tslots - 1;
         hj->tmp = (uint32_t *)c->tmp.p;
         hj->pending = (uint32_t *)c->pending.p;
@@ -860,7 +872,9 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
         cache_alloc = want;
         tslots = table_slots(cache_alloc);
         if ((s = ensure(c, c->table, 8ull * tslots))) return s;
+        if ((s = ensure(c, c->minidx, 4ull * tslots))) return s;
         CK(cudaMemsetAsync(c->table.p, 0xFF, c->table.bytes, c->stream));
+        CK(cudaMemsetAsync(c->minidx.p, 0xFF, c->minidx.bytes, c->stream));
         fill_job();
         if (rows) {
             CK(launch_rehash(hj, (uint32_t)rows, (uint32_t)(c->sm_count * 8), c->stream));
@@ -892,6 +906,12 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
                 hst->t_sub[2] / 1e3, hst->t_sub[3] / 1e3, hst->t_sub[4] / 1e3, hst->t_sub[5] / 1e3);
         fprintf(stderr, "rei tile steps of warp 0 (timing builds): load %.1f us, build %.1f us, precision %.1f us, "
                 "dedup %.1f us\n", hst->t_sub[6] / 1e3, hst->t_sub[7] / 1e3, hst->t_sub[8] / 1e3, hst->t_sub[9] / 1e3);
+        fprintf(stderr, "rei CTA 0 (timing builds): staging to job %.1f us, whole launch %.1f us\n",
+                hst->t_sub[10] / 1e3, hst->t_sub[11] / 1e3);
+        fprintf(stderr, "rei team chunks on CTA 0 (timing builds): tiles+barrier %.1f us, mark+barrier %.1f us, "
+                "count+barrier %.1f us, append+barrier %.1f us; leader appends: keys %.1f sort %.1f copy %.1f us\n",
+                hst->t_sub[12] / 1e3, hst->t_sub[13] / 1e3, hst->t_sub[14] / 1e3, hst->t_sub[15] / 1e3,
+                hst->t_sub[3] / 1e3, hst->t_sub[4] / 1e3, hst->t_sub[5] / 1e3);
     }
     if (hst->status == ST_TIMEOUT && getenv("REI_DEBUG")) {
         std::vector<uint32_t> tr(grid);
@@ -997,7 +1017,7 @@ void rei_ctx_destroy(rei_ctx *c) {
     cudaStreamSynchronize(c->stream);
     DevBuf *bufs[] = {&c->in_bytes, &c->in_offs, &c->stage_job, &c->stage_info, &c->word_start, &c->word_len,
                       &c->len_start, &c->gt_off, &c->gt_pair, &c->pos, &c->neg, &c->leaf, &c->cs,
-                      &c->bp_op, &c->bp_l, &c->bp_r, &c->table, &c->tmp, &c->pending, &c->slotpos,
+                      &c->bp_op, &c->bp_l, &c->bp_r, &c->table, &c->minidx, &c->tmp, &c->pending, &c->slotpos,
                       &c->bitmap, &c->blk, &c->lvl_start, &c->lvl_count, &c->state, &c->solve_job,
                       &c->tstack, &c->trace, &c->used, &c->b_in, &c->b_sjobs, &c->b_sinfo, &c->b_stage,
                       &c->b_jobs, &c->b_out, &c->b_tree, &c->b_queue, &c->s_cs, &c->s_bp_op, &c->s_bp_l,
@@ -1021,6 +1041,7 @@ rei_status rei_ctx_set_option(rei_ctx *c, int option, int64_t value) {
     case REI_OPT_CACHE_INIT: c->opt_cache_init = value; return REI_OK;
     case REI_OPT_SOLO_TILES: c->opt_solo_tiles = value; return REI_OK;
     case REI_OPT_FUSED_STAGE: c->opt_fused = value ? 1 : 0; return REI_OK;
+    case REI_OPT_EXACT_KEYS: c->opt_exact = value ? 1 : 0; return REI_OK;
     case REI_OPT_SMALL_ROWS:
         if (value > 16384 || (value > 0 && (value < 256 || (value & (value - 1))))) return REI_EINVAL;
         c->opt_small_rows = value < 0 ? -1 : value;

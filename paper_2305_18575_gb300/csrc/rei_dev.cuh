@@ -129,7 +129,7 @@ struct SolveState {
     // level ends; and how many solo chunks, team chunks, levels
     uint64_t t_phase[4];
     uint64_t n_phase[3];
-    uint64_t t_sub[12];  // steps of CTA 0's chunks alone (timing builds only)
+    uint64_t t_sub[16];  // steps of CTA 0's chunks and launch (timing builds only)
     uint32_t pad[2];
 };
 
@@ -165,6 +165,11 @@ struct SolveJob {
     uint32_t gt_in_smem;             // guide table copied to shared memory
     uint32_t solo_tiles;             // chunks of at most this many tiles run on CTA 0 alone
     uint32_t small_rows;             // languages CTA 0 keeps in shared memory at the start (0 = none)
+    // exact keys (|ic| <= 62, W <= 2): a table slot holds the language itself
+    // (bit 63: added in the current chunk), minidx[slot] the first candidate
+    // of the chunk with that language; 0 = fingerprint | row slots
+    uint32_t exact;
+    uint32_t *minidx;
 };
 
 static_assert(sizeof(SolveJob) % 8 == 0, "the job is copied in 8-byte words");

@@ -150,7 +150,7 @@ struct Shared {
     SegTile *tiles;          // per segment
     uint32_t *pos, *neg;     // precision masks (W words)
     const uint32_t *gt_off, *gt_pair, *len_start;
-    unsigned long long *sortbuf;  // kSortMax keys for the ordered append of few survivors
+    unsigned long long *sortbuf;  // kSortMax words: a small chunk's slot entries, or a CTA's survivor list
     uint32_t *solo_bits;     // kSortMax / 32 words: candidates of a small chunk that hold a slot
     uint32_t *solo_pref;     // kSortMax / 32 + 4 words: survivors before each bitmap word, total
     // the search's start, while every language fits in CTA 0's shared memory
@@ -435,6 +435,57 @@ __device__ void dedup_insert_solo(const TileCtx &T, const uint32_t *c, uint32_t 
     atomicExch(&T.st->err, 2u);  // table full: cannot happen with load <= 1/2
 }
 
+constexpr unsigned long long kXPend = 1ull << 63;  // exact keys: the language was added in this chunk
+
+// the exact key of a W <= 2 language (padding bits and bit 63 are zero)
+__device__ __forceinline__ unsigned long long exact_key(const uint32_t *c, uint32_t W) {
+    return W == 1 ? (unsigned long long)c[0] : ((unsigned long long)c[1] << 32) | c[0];
+}
+
+// uniqueness insert with exact keys: the slot's key is the language, so a
+// duplicate costs one probe and no row read; a language new in this chunk is
+// claimed with a CAS and every candidate with it lowers minidx[slot] (a
+// reduction, no round trip); `mark` (a small chunk on one CTA) records the
+// claimants in T.bits / T.ent, else the claimed slot joins the pending list
+__device__ void dedup_insert_exact(const TileCtx &T, const uint32_t *c, uint32_t xl) {
+    const SolveJob &J = *T.J;
+    const unsigned long long key = exact_key(c, T.W), pk = key | kXPend;
+    const uint64_t h = cs_hash(c, T.W, 1);
+    uint64_t p = h & J.table_mask;
+    for (uint64_t probe = 0; probe <= J.table_mask; probe++) {
+        unsigned long long v = ld_relaxed_u64(&J.table[p]);
+        if (v == kEmpty) {
+            v = atomicCAS(&J.table[p], kEmpty, pk);
+            if (v == kEmpty) {
+                atomicMin(&J.minidx[p], xl);
+                if (T.bits) {
+                    T.ent[xl] = p;
+                    atomicOr(&T.bits[xl >> 5], 1u << (xl & 31));
+                } else {
+                    const uint32_t am = __activemask(), lane = threadIdx.x & 31, lead = __ffs(am) - 1;
+                    uint32_t k0 = 0;
+                    if (lane == lead) k0 = atomicAdd(&T.st->pending_count, (uint32_t)__popc(am));
+                    k0 = __shfl_sync(am, k0, lead);
+                    J.pending[k0 + __popc(am & ((1u << lane) - 1u))] = (uint32_t)p;
+                }
+                return;
+            }
+        }
+        if ((v & ~kXPend) == key) {
+            if (v & kXPend) {
+                atomicMin(&J.minidx[p], xl);
+                if (T.bits) {
+                    T.ent[xl] = p;
+                    atomicOr(&T.bits[xl >> 5], 1u << (xl & 31));
+                }
+            }
+            return;
+        }
+        p = (p + 1) & J.table_mask;
+    }
+    atomicExch(&T.st->err, 2u);  // table full: cannot happen with load <= 1/2
+}
+
 // uniqueness insert of candidate xl (chunk-local) whose CS is c[b * 1] (smem)
 __device__ void dedup_insert(const TileCtx &T, const uint32_t *c, uint32_t xl) {
     const SolveJob &J = *T.J;
@@ -460,8 +511,12 @@ __device__ void dedup_insert(const TileCtx &T, const uint32_t *c, uint32_t xl) {
             write_tmp();
             const unsigned long long old = atomicCAS(&J.table[p], kEmpty, mine);
             if (old == kEmpty) {
-                const uint32_t k = atomicAdd(&T.st->pending_count, 1u);
-                J.pending[k] = (uint32_t)p;
+                // one counter update per group of lanes that inserted together
+                const uint32_t am = __activemask(), lane = threadIdx.x & 31, lead = __ffs(am) - 1;
+                uint32_t k0 = 0;
+                if (lane == lead) k0 = atomicAdd(&T.st->pending_count, (uint32_t)__popc(am));
+                k0 = __shfl_sync(am, k0, lead);
+                J.pending[k0 + __popc(am & ((1u << lane) - 1u))] = (uint32_t)p;
                 return;
             }
             v = old;
@@ -589,12 +644,14 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uin
                 if (w < n) {
                     const uint32_t p1 = go[w + 1];
                     if (!swapped) {
+#pragma unroll 4
                         for (uint32_t p = go[w]; p < p1; p++) {
                             const uint32_t pr = gp[p];
                             const uint32_t u = pr & 0xFFFFu, v = pr >> 16;
                             acc |= B[v] & (0u - ((lw[u >> 5] >> (u & 31)) & 1u));
                         }
                     } else {
+#pragma unroll 4
                         for (uint32_t p = go[w]; p < p1; p++) {
                             const uint32_t pr = gp[p];
                             const uint32_t u = pr & 0xFFFFu, v = pr >> 16;
@@ -619,6 +676,7 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uin
                 for (uint32_t w = ls[L] + lane; w < w1; w += 32) {
                     uint32_t acc = 0;
                     const uint32_t p1 = go[w + 1];
+#pragma unroll 4
                     for (uint32_t p = go[w] + 1; p < p1; p++) {
                         const uint32_t pr = gp[p];
                         acc |= B[pr & 0xFFFFu] & Sl[pr >> 16];
@@ -644,9 +702,11 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uin
     if (errs <= J.max_errors) atomicMin(T.found, (unsigned long long)xlev);
     REI_TMARK(tmk, 8);
     if (T.dedup) {
-        if (T.smem) dedup_insert_smem(T, c, (uint32_t)(xlev - T.chunk_start));
-        else if (T.bits) dedup_insert_solo(T, c, (uint32_t)(xlev - T.chunk_start));
-        else dedup_insert(T, c, (uint32_t)(xlev - T.chunk_start));
+        const uint32_t xl = (uint32_t)(xlev - T.chunk_start);
+        if (T.smem) dedup_insert_smem(T, c, xl);
+        else if (J.exact) dedup_insert_exact(T, c, xl);
+        else if (T.bits) dedup_insert_solo(T, c, xl);
+        else dedup_insert(T, c, xl);
     }
     REI_TMARK(tmk, 9);
 }
@@ -737,7 +797,7 @@ __device__ uint32_t emit_tree(const SolveJob &J, uint32_t op, uint32_t l, uint32
 // state, published with release / read with acquire), join the chunk's
 // phases with grid barriers, and go back to waiting.
 
-constexpr uint32_t kSortMax = 2048;  // new languages appended by CTA 0 alone, after a sort
+constexpr uint32_t kSortMax = 2048;  // candidates of a chunk CTA 0 runs with shared-memory bookkeeping
 
 __host__ __device__ size_t solve_smem_bytes(uint32_t W, uint32_t n, uint32_t G, uint32_t max_len,
                                             uint32_t seg_cap, bool gt_in_smem, uint32_t warps, uint32_t small_rows) {
@@ -816,78 +876,6 @@ __device__ __forceinline__ bool team_barrier(bool full, SolveState *st, uint32_t
     return true;
 }
 
-// survivors of a chunk with few new languages, appended in candidate order by
-// the chunk's leading CTA alone: the pending slots' holders are sorted by
-// index, then copied
-__device__ void append_sorted(const SolveJob &J, SolveState *st, Shared &S, const ChunkArgs &a,
-                              uint32_t npend, uint32_t W, Lead *L) {
-    const uint32_t tid = threadIdx.x;
-    REI_TSTART();
-    uint32_t m = 1;
-    while (m < npend) m <<= 1;
-    unsigned long long *key = S.sortbuf;
-    for (uint32_t i = tid; i < m; i += blockDim.x) {
-        unsigned long long k = ~0ull;
-        if (i < npend) {
-            const uint32_t q = ldcg(J.pending + i);
-            const uint32_t j = (uint32_t)ld_relaxed_u64(J.table + q) & ~kPending;
-            k = ((unsigned long long)j << 32) | q;
-        }
-        key[i] = k;
-    }
-    __syncthreads();
-    REI_TMARK(true, 3);
-    for (uint32_t k = 2; k <= m; k <<= 1) {
-        for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
-            for (uint32_t i = tid; i < m; i += blockDim.x) {
-                const uint32_t ix = i ^ jj;
-                if (ix > i) {
-                    const unsigned long long x = key[i], y = key[ix];
-                    const bool up = (i & k) == 0;
-                    if ((x > y) == up) {
-                        key[i] = y;
-                        key[ix] = x;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    REI_TMARK(true, 4);
-    const uint64_t limit = J.cache_alloc < J.cap ? J.cache_alloc : J.cap;
-    const uint64_t room = limit > a.size ? limit - a.size : 0;
-    for (uint32_t i = tid; i < npend && i < room; i += blockDim.x) {
-        const unsigned long long kk = key[i];
-        const uint32_t j = (uint32_t)(kk >> 32), q = (uint32_t)kk;
-        const uint64_t k = (uint64_t)a.size + i;
-        const uint32_t *srcp = J.tmp + (uint64_t)j * W;
-        uint32_t *dst = J.cs + k * W;
-        for (uint32_t b = 0; b < W; b++) dst[b] = ldcg(srcp + b);
-        uint32_t op, l, r;
-        decode(S.seg, a.nseg, a.cs0 + j, op, l, r);
-        J.bp_op[k] = (uint8_t)op;
-        J.bp_l[k] = l;
-        J.bp_r[k] = r;
-        const unsigned long long old = ld_relaxed_u64(J.table + q);
-        J.table[q] = (old & 0xFFFFFFFF00000000ull) | (uint32_t)k;
-        J.used[k] = q;
-    }
-    // survivors beyond the cap are not cached: free their slots (uniqueness
-    // stops for the rest of the level, so nothing reads them again)
-    for (uint32_t i = (uint32_t)umin64(room, npend) + tid; i < npend; i += blockDim.x)
-        J.table[(uint32_t)key[i]] = kEmpty;
-    __syncthreads();
-    if (tid == 0) {
-        const uint64_t added = npend < room ? npend : room;
-        if (npend > room) L->full = 1;
-        L->size = a.size + (uint32_t)added;
-        S.lvc[a.level] = L->size - S.lvs[a.level];
-        J.lvl_count[a.level] = S.lvc[a.level];
-        st->pending_count = 0;
-    }
-    REI_TMARK(true, 5);
-}
-
 // survivors of a chunk while the languages live in shared memory: as
 // solo_append, with the holders read from the shared table; each survivor's
 // row goes to the shared rows and to the global cache, its back-pointer to
@@ -963,8 +951,9 @@ __device__ void smem_append(const SolveJob &J, Shared &S, const ChunkArgs &a, ui
 __device__ void switch_to_global(const SolveJob &J, Shared &S, Lead *L) {
     const uint32_t W = J.W, rows = L->size;
     for (uint32_t k = threadIdx.x; k < rows; k += blockDim.x) {
-        const uint64_t h = cs_hash(S.sm_rows + (uint64_t)k * W, W, 1);
-        const unsigned long long v = ((uint64_t)(uint32_t)(h >> 32) << 32) | k;
+        const uint32_t *row = S.sm_rows + (uint64_t)k * W;
+        const uint64_t h = cs_hash(row, W, 1);
+        const unsigned long long v = J.exact ? exact_key(row, W) : ((uint64_t)(uint32_t)(h >> 32) << 32) | k;
         uint64_t p = h & J.table_mask;
         for (uint64_t probe = 0; probe <= J.table_mask; probe++) {
             if (atomicCAS(&J.table[p], kEmpty, v) == kEmpty) {
@@ -998,12 +987,15 @@ __device__ void solo_append(const SolveJob &J, SolveState *st, Shared &S, const 
         for (int u = 0; u < 8; u++) {
             const uint32_t xl = base + u * nt + tid;
             mk[u] = xl < C && ((bits[xl >> 5] >> (xl & 31)) & 1u);
-            v[u] = mk[u] ? ld_relaxed_u64(J.table + (uint32_t)ent[xl]) : 0ull;
+            v[u] = !mk[u] ? 0ull
+                   : J.exact ? ld_relaxed_u32(J.minidx + (uint32_t)ent[xl])
+                             : ld_relaxed_u64(J.table + (uint32_t)ent[xl]);
         }
 #pragma unroll
         for (int u = 0; u < 8; u++) {
             const uint32_t xl = base + u * nt + tid;
-            if (mk[u] && (uint32_t)v[u] != (kPending | xl)) atomicAnd(&bits[xl >> 5], ~(1u << (xl & 31)));
+            const uint32_t want = J.exact ? xl : (kPending | xl);
+            if (mk[u] && (uint32_t)v[u] != want) atomicAnd(&bits[xl >> 5], ~(1u << (xl & 31)));
         }
     }
     __syncthreads();
@@ -1038,18 +1030,28 @@ __device__ void solo_append(const SolveJob &J, SolveState *st, Shared &S, const 
         const uint32_t q = (uint32_t)e;
         if (rank >= room) {
             J.table[q] = kEmpty;
+            if (J.exact) J.minidx[q] = 0xFFFFFFFFu;
             continue;
         }
         const uint64_t k = (uint64_t)a.size + rank;
-        const uint32_t *srcp = J.tmp + (uint64_t)xl * W;
         uint32_t *dst = J.cs + k * W;
-        for (uint32_t b = 0; b < W; b++) dst[b] = ldcg(srcp + b);
+        if (J.exact) {
+            // the language is the slot's key
+            const unsigned long long key = ld_relaxed_u64(J.table + q) & ~kXPend;
+            dst[0] = (uint32_t)key;
+            if (W == 2) dst[1] = (uint32_t)(key >> 32);
+            J.table[q] = key;
+            J.minidx[q] = 0xFFFFFFFFu;
+        } else {
+            const uint32_t *srcp = J.tmp + (uint64_t)xl * W;
+            for (uint32_t b = 0; b < W; b++) dst[b] = ldcg(srcp + b);
+            J.table[q] = (e & 0xFFFFFFFF00000000ull) | (uint32_t)k;
+        }
         uint32_t op, l, r;
         decode(S.seg, a.nseg, a.cs0 + xl, op, l, r);
         J.bp_op[k] = (uint8_t)op;
         J.bp_l[k] = l;
         J.bp_r[k] = r;
-        J.table[q] = (e & 0xFFFFFFFF00000000ull) | (uint32_t)k;
         J.used[k] = q;
     }
     __syncthreads();
@@ -1087,7 +1089,7 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
     // at the search's start the languages and their table live there too
     const bool small = !full && a.ce0 - a.cs0 <= kSortMax;
     const bool sm = small && L && L->smode;
-    if (small) {
+    if (small && !tiles_ready) {
         if (tid == 0) *s_found = kNone;
         __syncthreads();
     }
@@ -1109,6 +1111,7 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
     }
     if (!team_barrier(full, st, bar_epoch, 5, J.trace)) return -1;
     REI_TMARK(!full, 0);
+    REI_TMARK(full && blockIdx.x == 0, 12);
     if (small) {
         const unsigned long long f = *s_found;
         if (f != kNone) {
@@ -1117,7 +1120,11 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
             const uint32_t C = (uint32_t)(a.ce0 - a.cs0);
             if (!sm)
                 for (uint32_t xl = tid; xl < C; xl += blockDim.x)
-                    if ((S.solo_bits[xl >> 5] >> (xl & 31)) & 1u) J.table[(uint32_t)S.sortbuf[xl]] = kEmpty;
+                    if ((S.solo_bits[xl >> 5] >> (xl & 31)) & 1u) {
+                        const uint32_t q = (uint32_t)S.sortbuf[xl];
+                        J.table[q] = kEmpty;
+                        if (J.exact) J.minidx[q] = 0xFFFFFFFFu;
+                    }
             __syncthreads();
             for (uint32_t w = tid; w < kSortMax / 32; w += blockDim.x) S.solo_bits[w] = 0;
             if (tid == 0) st->found = f;
@@ -1142,12 +1149,8 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
     const uint32_t npend = *s_npend;
     __syncthreads();
 
-    // few new languages: the leading CTA appends them alone, in order, after a sort
-    if (npend <= kSortMax) {
-        if (team_r == 0) append_sorted(J, st, S, a, npend, W, L);
-        REI_TMARK(!full, 2);
-        return 0;
-    }
+    // no new language: nothing to append
+    if (npend == 0) return 0;
 
     // ---- phase B: survivors are the slot holders of new languages
     const uint64_t C = a.ce0 - a.cs0;
@@ -1155,12 +1158,13 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
         const uint64_t gt = (uint64_t)team_r * blockDim.x + tid, nt = (uint64_t)team_n * blockDim.x;
         for (uint64_t i = gt; i < npend; i += nt) {
             const uint32_t q = ldcg(J.pending + i);
-            const uint32_t j = (uint32_t)ld_relaxed_u64(J.table + q) & ~kPending;
+            const uint32_t j = J.exact ? ld_relaxed_u32(J.minidx + q) : (uint32_t)ld_relaxed_u64(J.table + q) & ~kPending;
             atomicOr(&J.bitmap[j >> 5], 1u << (j & 31));
             J.slotpos[j] = q;
         }
     }
     if (!team_barrier(full, st, bar_epoch, 7, J.trace)) return -1;
+    REI_TMARK(full && blockIdx.x == 0, 13);
 
     // ---- phase C: survivors per CTA (contiguous word ranges of the bitmap)
     const uint64_t nwords = (C + 31) / 32;
@@ -1186,6 +1190,7 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
     }
     if (team_r == 0 && tid == 0) st->pending_count = 0;
     if (!team_barrier(full, st, bar_epoch, 8, J.trace)) return -1;
+    REI_TMARK(full && blockIdx.x == 0, 14);
 
     // ---- phase D: append survivors in candidate order
     {
@@ -1221,35 +1226,128 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
         }
         if (lane == 31) s_red[wid] = x;
         __syncthreads();
-        uint32_t wbefore = 0;
-        for (uint32_t k = 0; k < wid; k++) wbefore += s_red[k];
-        uint64_t rank = s_pref + wbefore + x - mycnt;
+        uint32_t wbefore = 0, cta_cnt = 0;
+        for (uint32_t k = 0; k < nwarps; k++) {
+            if (k < wid) wbefore += s_red[k];
+            cta_cnt += s_red[k];
+        }
         const uint64_t limit = J.cache_alloc < J.cap ? J.cache_alloc : J.cap;
-        for (uint64_t w = t0; w < t1; w++) {
-            uint32_t bits = ldcg(J.bitmap + w);
-            J.bitmap[w] = 0;
-            while (bits) {
-                const uint32_t bit = __ffs(bits) - 1;
-                bits &= bits - 1;
-                const uint32_t j = (uint32_t)(w * 32 + bit);
-                const uint64_t k = (uint64_t)a.size + rank;
-                rank++;
-                if (k >= limit) {
-                    J.table[ldcg(J.slotpos + j)] = kEmpty;  // not cached: free the slot
-                    continue;
+        constexpr uint32_t kListMax = 2 * kSortMax;  // this CTA's survivors listed in shared memory
+        if (cta_cnt <= kListMax) {
+            // the CTA's survivors in order into a shared list, then rows and
+            // back-pointers spread over all its threads with loads batched
+            uint32_t *list = reinterpret_cast<uint32_t *>(S.sortbuf);
+            uint32_t pos = wbefore + x - mycnt;
+            for (uint64_t w = t0; w < t1; w++) {
+                uint32_t bits = ldcg(J.bitmap + w);
+                J.bitmap[w] = 0;
+                while (bits) {
+                    list[pos++] = (uint32_t)(w * 32 + (__ffs(bits) - 1));
+                    bits &= bits - 1;
                 }
-                const uint32_t *srcp = J.tmp + (uint64_t)j * W;
-                uint32_t *dst = J.cs + k * W;
-                for (uint32_t b = 0; b < W; b++) dst[b] = ldcg(srcp + b);
-                uint32_t op, l, r;
-                decode(S.seg, a.nseg, a.cs0 + j, op, l, r);
-                J.bp_op[k] = (uint8_t)op;
-                J.bp_l[k] = l;
-                J.bp_r[k] = r;
-                const uint32_t q = ldcg(J.slotpos + j);
-                const unsigned long long old = ld_relaxed_u64(J.table + q);
-                J.table[q] = (old & 0xFFFFFFFF00000000ull) | (uint32_t)k;
-                J.used[k] = q;
+            }
+            __syncthreads();
+            const uint64_t base = (uint64_t)a.size + s_pref;  // cache row of this CTA's first survivor
+            const uint32_t fit = base >= limit ? 0u : (uint32_t)umin64(cta_cnt, limit - base);
+            const uint32_t nt = blockDim.x, nf = J.exact ? 0u : fit * W;  // (exact keys: rows from the keys)
+            for (uint32_t f0 = tid; f0 < nf; f0 += 4 * nt) {
+                uint32_t v[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const uint32_t f = f0 + u * nt;
+                    if (f < nf) {
+                        const uint32_t i = f / W, b = f - i * W;
+                        v[u] = ldcg(J.tmp + (uint64_t)list[i] * W + b);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const uint32_t f = f0 + u * nt;
+                    if (f < nf) {
+                        const uint32_t i = f / W, b = f - i * W;
+                        J.cs[(base + i) * W + b] = v[u];
+                    }
+                }
+            }
+            for (uint32_t i0 = tid; i0 < cta_cnt; i0 += 4 * nt) {
+                uint32_t q[4];
+                unsigned long long old[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const uint32_t i = i0 + u * nt;
+                    if (i < cta_cnt) q[u] = ldcg(J.slotpos + list[i]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const uint32_t i = i0 + u * nt;
+                    if (i < fit) old[u] = ld_relaxed_u64(J.table + q[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const uint32_t i = i0 + u * nt;
+                    if (i >= cta_cnt) continue;
+                    if (i >= fit) {
+                        J.table[q[u]] = kEmpty;  // not cached: free the slot
+                        if (J.exact) J.minidx[q[u]] = 0xFFFFFFFFu;
+                        continue;
+                    }
+                    const uint64_t k = base + i;
+                    uint32_t op, l, r;
+                    decode(S.seg, a.nseg, a.cs0 + list[i], op, l, r);
+                    J.bp_op[k] = (uint8_t)op;
+                    J.bp_l[k] = l;
+                    J.bp_r[k] = r;
+                    if (J.exact) {
+                        const unsigned long long key = old[u] & ~kXPend;
+                        J.cs[k * W] = (uint32_t)key;
+                        if (W == 2) J.cs[k * W + 1] = (uint32_t)(key >> 32);
+                        J.table[q[u]] = key;
+                        J.minidx[q[u]] = 0xFFFFFFFFu;
+                    } else {
+                        J.table[q[u]] = (old[u] & 0xFFFFFFFF00000000ull) | (uint32_t)k;
+                    }
+                    J.used[k] = q[u];
+                }
+            }
+        } else {
+            // many survivors in this CTA's range: each thread appends its own
+            uint64_t rank = s_pref + wbefore + x - mycnt;
+            for (uint64_t w = t0; w < t1; w++) {
+                uint32_t bits = ldcg(J.bitmap + w);
+                J.bitmap[w] = 0;
+                while (bits) {
+                    const uint32_t bit = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const uint32_t j = (uint32_t)(w * 32 + bit);
+                    const uint64_t k = (uint64_t)a.size + rank;
+                    rank++;
+                    if (k >= limit) {
+                        const uint32_t q = ldcg(J.slotpos + j);
+                        J.table[q] = kEmpty;  // not cached: free the slot
+                        if (J.exact) J.minidx[q] = 0xFFFFFFFFu;
+                        continue;
+                    }
+                    uint32_t *dst = J.cs + k * W;
+                    const uint32_t q = ldcg(J.slotpos + j);
+                    const unsigned long long old = ld_relaxed_u64(J.table + q);
+                    if (J.exact) {
+                        const unsigned long long key = old & ~kXPend;
+                        dst[0] = (uint32_t)key;
+                        if (W == 2) dst[1] = (uint32_t)(key >> 32);
+                        J.table[q] = key;
+                        J.minidx[q] = 0xFFFFFFFFu;
+                    } else {
+                        const uint32_t *srcp = J.tmp + (uint64_t)j * W;
+                        for (uint32_t b = 0; b < W; b++) dst[b] = ldcg(srcp + b);
+                        J.table[q] = (old & 0xFFFFFFFF00000000ull) | (uint32_t)k;
+                    }
+                    uint32_t op, l, r;
+                    decode(S.seg, a.nseg, a.cs0 + j, op, l, r);
+                    J.bp_op[k] = (uint8_t)op;
+                    J.bp_l[k] = l;
+                    J.bp_r[k] = r;
+                    J.used[k] = q;
+                }
             }
         }
         __syncthreads();
@@ -1263,6 +1361,7 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
         }
     }
     if (!team_barrier(full, st, bar_epoch, 9, J.trace)) return -1;
+    REI_TMARK(full && blockIdx.x == 0, 15);
     return 0;
 }
 
@@ -1364,7 +1463,11 @@ __device__ void clean_table(const SolveJob &J, uint32_t rows, uint32_t npending,
                             uint32_t team_r) {
     const uint64_t t = (uint64_t)team_r * blockDim.x + threadIdx.x, nt = (uint64_t)team_n * blockDim.x;
     for (uint64_t k = t; k < rows; k += nt) J.table[ldcg(J.used + k)] = kEmpty;
-    for (uint64_t i = t; i < npending; i += nt) J.table[ldcg(J.pending + i)] = kEmpty;
+    for (uint64_t i = t; i < npending; i += nt) {
+        const uint32_t q = ldcg(J.pending + i);
+        J.table[q] = kEmpty;
+        if (J.exact) J.minidx[q] = 0xFFFFFFFFu;
+    }
 }
 
 // The leader's search loop (Alg. 1): level after level, chunk after chunk,
@@ -1411,6 +1514,7 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
     __syncthreads();
 
     bool found = false;
+    uint32_t planned = 0xFFFFFFFFu;  // the level whose plan is in S.seg / s_plan
     // per-phase wall time of the leader (ns): plan, solo chunk, team chunk, level end
     unsigned long long tm[4] = {0, 0, 0, 0}, tcnt[3] = {0, 0, 0};
     for (;;) {
@@ -1425,8 +1529,12 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
             __syncthreads();
             continue;
         }
-        if (wid == 0) plan_level(J, level, S.lvs, S.lvc, S.seg, s_plan);
-        __syncthreads();
+        // a level's plan depends on lower levels only: once per level
+        if (level != planned) {
+            if (wid == 0) plan_level(J, level, S.lvs, S.lvc, S.seg, s_plan);
+            __syncthreads();
+            planned = level;
+        }
         const uint32_t nseg = s_plan.nseg;
         const uint64_t T = s_plan.total;
 
@@ -1501,6 +1609,7 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
         ChunkArgs a{level, size, dedup ? 1u : 0u, nseg, pos, pos + C};
         // alone when the chunk is a few tiles per warp of this CTA
         if (wid == 0) tile_setup(S, nseg, a.cs0, a.ce0, K.tiles);
+        if (tid == 0) *K.found = kNone;  // a small chunk's answer slot
         __syncthreads();
         const bool team = allow_team && *K.tiles > (uint64_t)J.solo_tiles;
         // the shared-memory start ends before a chunk it cannot hold
@@ -1688,6 +1797,9 @@ __global__ void __launch_bounds__(256, 2) k_solve_fused(const __grid_constant__ 
     __shared__ SolveJob J;
     SolveState *st = F.tmpl.st;
     uint32_t bar_epoch = 0;
+#ifdef REI_TIMING
+    const unsigned long long t_begin = globaltimer_ns();
+#endif
     if (blockIdx.x == 0) {
         // the search state and the level table start empty
         if (threadIdx.x == 0) {
@@ -1719,6 +1831,7 @@ __global__ void __launch_bounds__(256, 2) k_solve_fused(const __grid_constant__ 
                 j.neg_eps = I.neg_eps;
                 const uint32_t W = I.W;
                 j.cap = umin64(F.mem_budget / (4ull * W + 28), 0x7FFF0000ull);
+                j.exact = F.tmpl.exact && W <= 2 && I.n <= 62 ? 1u : 0u;
                 const uint64_t tmax = F.table_slots / 2;
                 j.cache_alloc = umin64(umin64(j.cap, F.rows_alloc), umin64(F.cs_words / W, tmax / 2));
                 uint64_t ch = F.chunk_opt ? F.chunk_opt : auto_chunk(W);
@@ -1753,7 +1866,13 @@ __global__ void __launch_bounds__(256, 2) k_solve_fused(const __grid_constant__ 
         for (uint32_t i = threadIdx.x; i < sizeof(SolveJob) / 8; i += blockDim.x) dst[i] = ld_relaxed_u64(src + i);
     }
     __syncthreads();
+#ifdef REI_TIMING
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->t_sub[10] = globaltimer_ns() - t_begin;
+#endif
     solve_body(J, bar_epoch);
+#ifdef REI_TIMING
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->t_sub[11] = globaltimer_ns() - t_begin;
+#endif
 }
 
 // ---------------------------------------------------------------------------
@@ -2023,7 +2142,8 @@ __global__ void k_rehash(const __grid_constant__ SolveJob J, uint32_t count) {
          k += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t *c = J.cs + k * W;
         const uint64_t h = cs_hash(c, W, 1);
-        const unsigned long long v = ((uint64_t)(uint32_t)(h >> 32) << 32) | (uint32_t)k;
+        const unsigned long long v =
+            J.exact ? exact_key(c, W) : ((uint64_t)(uint32_t)(h >> 32) << 32) | (uint32_t)k;
         uint64_t p = h & J.table_mask;
         for (uint64_t probe = 0; probe <= J.table_mask; probe++) {
             if (atomicCAS(&J.table[p], kEmpty, v) == kEmpty) {

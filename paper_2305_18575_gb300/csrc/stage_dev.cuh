@@ -58,12 +58,15 @@ __device__ __forceinline__ bool same_bytes(const uint8_t *b, uint32_t s1, uint32
 struct StageSmem {
     uint64_t *hset;            // hcap slots: fingerprint | len | start of one occurrence
     uint16_t *rank_of;         // hcap: shortlex rank of the word in each slot
-    unsigned long long *keys;  // ic_cap: sort keys (or slots, when ranks are counted)
+    unsigned long long *keys;  // ic_cap: the words' slots, then their sort keys
     uint32_t *wstart;          // ic_cap: an occurrence of the word of each rank
     uint16_t *wlen;            // ic_cap: its length
+    uint16_t *dfirst, *dlast;  // ic_cap: rank of the word without its first / last symbol
+    uint32_t *masks;           // 2 * kMaxWords: P and N characteristic sequences
+    uint32_t *offs;            // offs_cap: the string offsets, when they fit
     int16_t *rank_tab;         // 256: rank of each byte in the alphabet, -1 if none
     uint8_t *bytes;            // bytes_cap: the strings, when they fit
-    uint32_t hcap, ic_cap, bytes_cap;
+    uint32_t hcap, ic_cap, bytes_cap, offs_cap;
 };
 
 // bytes of shared memory the scratch takes; carves it from `base` when given.
@@ -79,20 +82,28 @@ __host__ __device__ inline size_t stage_layout(uint32_t ic_cap, uint32_t bytes_c
         o += (bytes + 15) & ~size_t(15);
         return at;
     };
+    const uint32_t offs_cap = 1024;
     const size_t o_hset = carve(8ull * hcap), o_keys = carve(8ull * ic_cap), o_ws = carve(4ull * ic_cap);
-    const size_t o_rank = carve(2ull * hcap), o_wl = carve(2ull * ic_cap), o_tab = carve(2 * 256);
+    const size_t o_masks = carve(4ull * 2 * kMaxWords), o_offs = carve(4ull * offs_cap);
+    const size_t o_rank = carve(2ull * hcap), o_wl = carve(2ull * ic_cap), o_df = carve(2ull * ic_cap);
+    const size_t o_dl = carve(2ull * ic_cap), o_tab = carve(2 * 256);
     const size_t o_bytes = carve(bytes_cap);
     if (base && out) {
         out->hset = reinterpret_cast<uint64_t *>(base + o_hset);
         out->keys = reinterpret_cast<unsigned long long *>(base + o_keys);
         out->wstart = reinterpret_cast<uint32_t *>(base + o_ws);
+        out->masks = reinterpret_cast<uint32_t *>(base + o_masks);
+        out->offs = reinterpret_cast<uint32_t *>(base + o_offs);
         out->rank_of = reinterpret_cast<uint16_t *>(base + o_rank);
         out->wlen = reinterpret_cast<uint16_t *>(base + o_wl);
+        out->dfirst = reinterpret_cast<uint16_t *>(base + o_df);
+        out->dlast = reinterpret_cast<uint16_t *>(base + o_dl);
         out->rank_tab = reinterpret_cast<int16_t *>(base + o_tab);
         out->bytes = base + o_bytes;
         out->hcap = hcap;
         out->ic_cap = ic_cap;
         out->bytes_cap = bytes_cap;
+        out->offs_cap = offs_cap;
     }
     return o;
 }
@@ -182,6 +193,33 @@ __device__ inline uint32_t block_exclusive_scan(uint32_t v, uint32_t *warp_sums,
     return r;
 }
 
+// ascending sort of m (a power of two) 64-bit keys in shared memory by the
+// calling CTA (blockDim.x a multiple of 32); element i is handled by thread
+// i % blockDim.x, so compare-exchanges closer than 32 stay within a warp and
+// need only a warp barrier before the next one of the same kind
+__device__ inline void block_bitonic_sort(unsigned long long *key, uint32_t m) {
+    const uint32_t tid = threadIdx.x, nt = blockDim.x;
+    for (uint32_t k = 2; k <= m; k <<= 1) {
+        for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
+            for (uint32_t i = tid; i < m; i += nt) {
+                const uint32_t ix = i ^ jj;
+                if (ix > i) {
+                    const unsigned long long x = key[i], y = key[ix];
+                    if ((x > y) == ((i & k) == 0)) {
+                        key[i] = y;
+                        key[ix] = x;
+                    }
+                }
+            }
+            // the next exchange distance: jj / 2, or k at the next k
+            const uint32_t next = jj > 1 ? jj >> 1 : k;
+            if (next >= 32) __syncthreads();
+            else __syncwarp();
+        }
+    }
+    __syncthreads();
+}
+
 // a coherent 64-bit load through a generic address (shared or global)
 __device__ __forceinline__ uint64_t ld_strong_u64(const uint64_t *p) {
     uint64_t v;
@@ -217,17 +255,18 @@ __device__ inline void stage_run(const StageJob &J, const StageSmem &M) {
 
     const uint32_t tid = threadIdx.x, nt = blockDim.x;
     const uint32_t n_str = J.n_pos + J.n_neg;
-    const uint32_t *offs = J.offs;
-    const uint32_t total = offs[n_str];
     uint64_t *hset = M.hset;
     int16_t *rank_tab = M.rank_tab;
 
+    // the offsets into shared memory when they fit
+    const uint32_t *offs = J.offs;
+    if (n_str + 1 <= M.offs_cap) {
+        for (uint32_t k = tid; k <= n_str; k += nt) M.offs[k] = J.offs[k];
+        offs = M.offs;
+    }
     for (uint32_t q = tid; q < M.hcap; q += nt) hset[q] = kEmpty;
     for (uint32_t i = tid; i < 256; i += nt) rank_tab[i] = -1;
-    for (uint32_t i = tid; i < kMaxWords; i += nt) {
-        J.pos_mask[i] = 0;
-        J.neg_mask[i] = 0;
-    }
+    for (uint32_t i = tid; i < 2 * kMaxWords; i += nt) M.masks[i] = 0;
     for (uint32_t i = tid; i < J.n_sym * kMaxWords; i += nt) J.leaf[i] = 0;
     if (tid == 0) {
         s_err = SE_OK;
@@ -239,8 +278,9 @@ __device__ inline void stage_run(const StageJob &J, const StageSmem &M) {
     }
     __syncthreads();
     for (uint32_t a = tid; a < J.n_sym; a += nt) rank_tab[J.alphabet[a]] = (int16_t)a;
-
+    const uint32_t total = offs[n_str];
     STAGE_MARK(0);
+
     // offsets start at 0 and never decrease (device inputs are not checked on
     // the host); every byte must be a symbol; strings must fit the length field
     if (offs[0] != 0) s_err = SE_OFFSETS;
@@ -264,9 +304,10 @@ __device__ inline void stage_run(const StageJob &J, const StageSmem &M) {
     __syncthreads();
     if (s_err == SE_OK && s_maxlen > REI_MAX_STRLEN) s_err = SE_STRLEN;
     __syncthreads();
-
     STAGE_MARK(1);
-    // every occurrence (start p, length len) of every string goes into the set
+
+    // every occurrence (start p, length len) of every string goes into the
+    // set; the first occurrence of each word also records its slot
     if (s_err == SE_OK) {
         const uint32_t mask = M.hcap - 1;
         for (uint32_t p = tid; p < total; p += nt) {
@@ -292,7 +333,9 @@ __device__ inline void stage_run(const StageJob &J, const StageSmem &M) {
                         const unsigned long long old =
                             atomicCAS((unsigned long long *)&hset[q], kEmpty, want);
                         if (old == kEmpty) {
-                            if (atomicAdd(&s_count, 1u) + 2 > M.ic_cap) s_err = SE_IC_LARGE;
+                            const uint32_t u = atomicAdd(&s_count, 1u);
+                            if (u + 2 > M.ic_cap) s_err = SE_IC_LARGE;
+                            else M.keys[u] = q;
                             break;
                         }
                         v = old;
@@ -310,51 +353,34 @@ __device__ inline void stage_run(const StageJob &J, const StageSmem &M) {
         if (tid == 0) J.info->status = s_err;
         return;
     }
-
     STAGE_MARK(2);
-    // the distinct words: packed shortlex keys when every word packs into
-    // 39 bits (length << 52 | symbol ranks << 13 | slot), else their slots
+
+    // shortlex ranks (eps = 0).  Packed keys (length << 52 | symbol ranks
+    // << 13 | slot) when every word packs into 39 bits: counted for a few
+    // words, sorted for many; else counted with byte comparisons
+    const uint32_t U = s_count, n = U + 1;
     uint32_t bsym = 1;
     while ((1u << bsym) < J.n_sym) bsym++;
     const bool packed = s_maxlen * bsym <= 39;
-    if (tid == 0) s_count = 0;
-    __syncthreads();
-    for (uint32_t q = tid; q < M.hcap; q += nt) {
-        const uint64_t v = hset[q];
-        if (v == kEmpty) continue;
-        unsigned long long key = q;
-        if (packed) {
+    if (packed) {
+        for (uint32_t i = tid; i < U; i += nt) {
+            const uint32_t q = (uint32_t)M.keys[i];
+            const uint64_t v = hset[q];
             const uint32_t st = (uint32_t)v, len = (uint32_t)(v >> 32) & 0xFFFu;
             uint64_t c = 0;
-            for (uint32_t i = 0; i < len; i++) c = (c << bsym) | (uint32_t)rank_tab[bytes[st + i]];
-            key = ((unsigned long long)len << 52) | (c << 13) | q;
+            for (uint32_t k = 0; k < len; k++) c = (c << bsym) | (uint32_t)rank_tab[bytes[st + k]];
+            M.keys[i] = ((unsigned long long)len << 52) | (c << 13) | q;
         }
-        M.keys[atomicAdd(&s_count, 1u)] = key;
+        __syncthreads();
     }
-    __syncthreads();
-    const uint32_t U = s_count, n = U + 1;
     STAGE_MARK(3);
-    if (packed) {
+    if (packed && U > 256) {
         // bitonic sort of the keys (padded to a power of two with ~0)
         uint32_t m = 1;
         while (m < U) m <<= 1;
         for (uint32_t i = U + tid; i < m; i += nt) M.keys[i] = ~0ull;
         __syncthreads();
-        for (uint32_t k = 2; k <= m; k <<= 1) {
-            for (uint32_t jj = k >> 1; jj > 0; jj >>= 1) {
-                for (uint32_t i = tid; i < m; i += nt) {
-                    const uint32_t ix = i ^ jj;
-                    if (ix > i) {
-                        const unsigned long long x = M.keys[i], y = M.keys[ix];
-                        if ((x > y) == ((i & k) == 0)) {
-                            M.keys[i] = y;
-                            M.keys[ix] = x;
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-        }
+        block_bitonic_sort(M.keys, m);
         for (uint32_t i = tid; i < U; i += nt) {
             const uint32_t q = (uint32_t)(M.keys[i] & 0x1FFFu), r = i + 1;
             const uint64_t v = hset[q];
@@ -364,13 +390,18 @@ __device__ inline void stage_run(const StageJob &J, const StageSmem &M) {
         }
     } else {
         for (uint32_t i = tid; i < U; i += nt) {
-            const uint32_t qi = (uint32_t)M.keys[i];
+            const unsigned long long ki = M.keys[i];
+            const uint32_t qi = packed ? (uint32_t)(ki & 0x1FFFu) : (uint32_t)ki;
             const uint64_t vi = hset[qi];
             const uint32_t si = (uint32_t)vi, li = (uint32_t)(vi >> 32) & 0xFFFu;
             uint32_t r = 1;
-            for (uint32_t j = 0; j < U; j++) {
-                const uint64_t vj = hset[(uint32_t)M.keys[j]];
-                if (shortlex_less(bytes, rank_tab, (uint32_t)vj, (uint32_t)(vj >> 32) & 0xFFFu, si, li)) r++;
+            if (packed) {
+                for (uint32_t j = 0; j < U; j++) r += M.keys[j] < ki;
+            } else {
+                for (uint32_t j = 0; j < U; j++) {
+                    const uint64_t vj = hset[(uint32_t)M.keys[j]];
+                    if (shortlex_less(bytes, rank_tab, (uint32_t)vj, (uint32_t)(vj >> 32) & 0xFFFu, si, li)) r++;
+                }
             }
             M.rank_of[qi] = (uint16_t)r;
             M.wstart[r] = si;
@@ -380,18 +411,24 @@ __device__ inline void stage_run(const StageJob &J, const StageSmem &M) {
     if (tid == 0) {
         M.wstart[0] = 0;
         M.wlen[0] = 0;
+        M.dfirst[0] = 0;
+        M.dlast[0] = 0;
     }
     __syncthreads();
-    for (uint32_t r = tid; r < n; r += nt) {
-        J.word_start[r] = M.wstart[r];
-        J.word_len[r] = M.wlen[r];
-    }
-
     STAGE_MARK(4);
-    // first rank of every length (all lengths 0..max_len occur: ic is infix-closed)
+    // the word table, and each word without its first / last symbol (infixes:
+    // in ic); first rank of every length (all lengths 0..max_len occur)
     for (uint32_t r = tid; r < n; r += nt) {
-        const uint32_t L = M.wlen[r];
+        const uint32_t st = M.wstart[r], L = M.wlen[r];
+        J.word_start[r] = st;
+        J.word_len[r] = L;
         if (r == 0 || M.wlen[r - 1] != L) J.len_start[L] = r;
+        if (r) {
+            const uint32_t a = stage_lookup(M, bytes, st + 1, L - 1), b = stage_lookup(M, bytes, st, L - 1);
+            if (a >= n || b >= n) s_err = SE_INTERNAL;
+            M.dfirst[r] = (uint16_t)a;
+            M.dlast[r] = (uint16_t)b;
+        }
     }
     const uint32_t max_len = M.wlen[n - 1];
     if (tid == 0) J.len_start[max_len + 1] = n;
@@ -401,7 +438,7 @@ __device__ inline void stage_run(const StageJob &J, const StageSmem &M) {
     const uint32_t r0 = min(n, tid * per), r1 = min(n, r0 + per);
     uint32_t local = 0;
     for (uint32_t r = r0; r < r1; r++) local += M.wlen[r] + 1u;
-    uint32_t off = block_exclusive_scan(local, warp_sums, &s_total);
+    uint32_t off = block_exclusive_scan(local, warp_sums, &s_total);  // (synchronises the CTA)
     const uint32_t G = s_total;
     if (G > J.pair_cap) {
         if (tid == 0) {
@@ -412,32 +449,35 @@ __device__ inline void stage_run(const StageJob &J, const StageSmem &M) {
         }
         return;
     }
-    // guide-table pairs of each word: split k is (prefix of length k, the rest)
+    // pairs of word r: split k is (prefix of length k, the rest); prefixes by
+    // dropping last symbols from r, suffixes by dropping first symbols
     for (uint32_t r = r0; r < r1; r++) {
         J.gt_off[r] = off;
-        const uint32_t len = M.wlen[r], st = M.wstart[r];
-        uint64_t hp = kH0;  // hash state of the prefix
+        const uint32_t len = M.wlen[r];
+        uint32_t *out = J.gt_pair + off;
+        uint32_t v = r;
         for (uint32_t k = 0; k <= len; k++) {
-            if (k) hp = stage_mix(hp, (uint32_t)rank_tab[bytes[st + k - 1]]);
-            const uint32_t u = k == 0 ? 0u : stage_find(M, bytes, stage_final(hp, k), st, k);
-            const uint32_t v = stage_lookup(M, bytes, st + k, len - k);
-            if (u >= n || v >= n) s_err = SE_INTERNAL;  // infixes of ic words are in ic
-            J.gt_pair[off + k] = (u & 0xFFFFu) | (v << 16);
+            out[k] = v << 16;
+            v = M.dfirst[v];
+        }
+        uint32_t u = r;
+        for (uint32_t k = len + 1; k-- > 0;) {
+            out[k] |= u;
+            u = M.dlast[u];
         }
         off += len + 1;
     }
     if (tid == 0) J.gt_off[n] = G;
-
     STAGE_MARK(5);
-    // characteristic sequences of P and N, and of every symbol
+
+    // characteristic sequences of P and N (shared), and of every symbol
     for (uint32_t k = tid; k < n_str; k += nt) {
         const uint32_t r = stage_lookup(M, bytes, offs[k], offs[k + 1] - offs[k]);
         if (r >= n) {
             s_err = SE_INTERNAL;
             continue;
         }
-        uint32_t *mask = k < J.n_pos ? J.pos_mask : J.neg_mask;
-        atomicOr(&mask[r >> 5], 1u << (r & 31));
+        atomicOr(&M.masks[(k < J.n_pos ? 0 : kMaxWords) + (r >> 5)], 1u << (r & 31));
     }
     for (uint32_t a = tid; a < J.n_sym; a += nt) {
         const uint32_t r = stage_lookup_symbol(M, bytes, a, J.alphabet[a]);
@@ -445,11 +485,13 @@ __device__ inline void stage_run(const StageJob &J, const StageSmem &M) {
     }
     __syncthreads();
     const uint32_t W = padded_words(n);
-    for (uint32_t b = tid; b < W; b += nt) {
-        const uint32_t p = J.pos_mask[b], q = J.neg_mask[b];
+    for (uint32_t b = tid; b < kMaxWords; b += nt) {
+        const uint32_t p = M.masks[b], q = M.masks[kMaxWords + b];
+        J.pos_mask[b] = p;
+        J.neg_mask[b] = q;
         if (p & q) s_ov = 1;
-        atomicAdd(&s_np, (uint32_t)__popc(p));
-        atomicAdd(&s_nn, (uint32_t)__popc(q));
+        if (p) atomicAdd(&s_np, (uint32_t)__popc(p));
+        if (q) atomicAdd(&s_nn, (uint32_t)__popc(q));
     }
     __syncthreads();
     STAGE_MARK(6);
@@ -462,8 +504,8 @@ __device__ inline void stage_run(const StageJob &J, const StageSmem &M) {
         I->G = G;
         I->n_pos_set = s_np;
         I->n_neg_set = s_nn;
-        I->pos_eps = J.pos_mask[0] & 1u;
-        I->neg_eps = J.neg_mask[0] & 1u;
+        I->pos_eps = M.masks[0] & 1u;
+        I->neg_eps = M.masks[kMaxWords] & 1u;
     }
 }
 

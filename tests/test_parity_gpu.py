@@ -261,6 +261,39 @@ def test_fused_and_separate_staging_agree(fused):
         assert c.solve(A01, [b"0"], [b"0"]).status == rei.REI_EINVAL
 
 
+@pytest.mark.parametrize("exact", [0, 1])
+@pytest.mark.parametrize("chunk,solo,small", [(0, -1, -1), (7, -1, 0), (0, 0, 0), (0, 1 << 30, 0)])
+def test_exact_keys_do_not_change_results(exact, chunk, solo, small):
+    """Uniqueness keyed by the languages themselves (|ic| <= 62) or by
+    fingerprints and rows: the same results, on chunks split small, on the
+    whole grid (solo 0), on one CTA (solo 2^30), with and without the
+    shared-memory start, through cache growth and out-of-memory ends."""
+    with rei.Context(device=0) as c:
+        c.set_option(rei.REI_OPT_EXACT_KEYS, exact)
+        c.set_option(rei.REI_OPT_CHUNK, chunk)
+        c.set_option(rei.REI_OPT_SOLO_TILES, solo)
+        c.set_option(rei.REI_OPT_SMALL_ROWS, small)
+        for s in (0, 3, 5, 12):
+            for costs in [(1, 1, 1, 1, 1), (1, 1, 5, 1, 1)]:
+                inst, ref = oracle_medium(s, costs)
+                got = c.solve_problem(rei.Problem(inst.alphabet, inst.pos, inst.neg, costs=costs, max_cost=40,
+                                                  mem_budget=inst.mem_budget))
+                check_same(got, ref, (s, costs, exact, chunk, solo))
+        got, ref = solve_both(c, A01, PIN_P, PIN_N, max_cost=30, max_errors=4)
+        check_same(got, ref, ("pin20", exact))
+        P, N = [b"0110", b"1"], [b"", b"01", b"11"]
+        for budget in (64, 400, 2000, 9000):
+            got, ref = solve_both(c, A01, P, N, max_cost=30, mem_budget=budget)
+            check_same(got, ref, (budget, exact))
+    with rei.Context(device=0) as c:
+        c.set_option(rei.REI_OPT_EXACT_KEYS, exact)
+        c.set_option(rei.REI_OPT_CACHE_INIT, 8)
+        for s in (2, 5):
+            inst = make_config("medium", s)
+            got, ref = solve_both(c, inst, max_cost=40, costs=(1, 1, 1, 1, 1))
+            check_same(got, ref, ("growth", s, exact))
+
+
 @pytest.mark.parametrize("fused", [0, 1])
 def test_cache_growth_relaunch_matches(ctx, fused):
     with rei.Context(device=0) as c:
