@@ -47,6 +47,29 @@ def problems():
     return out
 
 
+def recorded_traffic():
+    """DRAM bytes per k_solve_fused launch from the committed ncu summary, while
+    the kernel sources are the ones it was measured on (else nothing)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("solve.cu", "stage_dev.cuh", "rei_dev.cuh"):
+        with open(os.path.join(ROOT, "paper_2305_18575_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    rec = {}
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_k_solve_fused.md")) as fh:
+            for line in fh:
+                k, sep, v = line.partition(":")
+                if sep and k.strip() in ("kernel_sources_sha256_16", "medium_traffic_bytes_per_launch",
+                                         "printed_traffic_bytes_per_launch"):
+                    rec[k.strip()] = v.strip()
+    except OSError:
+        return {}
+    if rec.get("kernel_sources_sha256_16") != h.hexdigest()[:16]:
+        return {}
+    return {k: int(v) for k, v in rec.items() if k.endswith("per_launch")}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -272,8 +295,10 @@ def run_gpu(args, rank, world, local_rank):
     else:
         roof = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
                 "frac": hbm_frac, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs"}
-    roof.update({"kernel": "k_solve", "launches": k_launches, "avg_launch_ms": k_ms / max(k_launches, 1),
-                 "alu_frac": alu_frac, "hbm_frac": hbm_frac})
+    roof["traffic"] = recorded_traffic().get("medium_traffic_bytes_per_launch")
+    roof.update({"kernel": "k_solve_fused", "launches": k_launches, "avg_launch_ms": k_ms / max(k_launches, 1),
+                 "alg_bytes_per_launch": alg_bytes / max(k_launches, 1), "alu_frac": alu_frac,
+                 "hbm_frac": hbm_frac})
 
     # whole-job aggregation over ranks (replicas: no data-path collective)
     t_max, c_sum = reduce_over_ranks(total_ms, cands, world, f"cuda:{dev}")
@@ -297,6 +322,8 @@ def run_gpu(args, rank, world, local_rank):
         "clocks": clocks.summary(),
         "gpu_launches": launches,
     }
+    if not args.no_paper:
+        line["paper_instance"] = paper_instance_leg(ctx, dev)
     if not args.no_batch:
         bprobs = batched_problems()
         line["batched"] = batched_leg(ctx, dev, bprobs)
@@ -347,6 +374,40 @@ def batched_leg(ctx, dev, probs):
             "speedup_vs_sequential": t_seq / t_batch, "batch_ms": 1000 * t_batch, "sequential_ms": 1000 * t_seq,
             "candidates_per_s": cands / t_batch,
             "solve_ms_p50": lat[len(lat) // 2], "solve_ms_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
+
+
+PAPER_WORKLOAD = ("the specification printed in Sec. 6 (Table 1, Type 1 No 50): 10 positive and 12 negative "
+                  "binary strings, |ic| = 25, costs (1,1,1,1,1), max_cost 30, minimal cost 28")
+PAPER_A100_S = 4.9512          # Table 1: the paper's A100 time for this instance (context, other hardware)
+PAPER_A100_REs = 26774099142   # Table 1: its candidate count there
+
+
+def paper_instance_leg(ctx, dev):
+    """Time to the minimal regex on the one instance the paper prints with its
+    GPU time: a search of ~2.6e10 candidates whose uniqueness table (22 M
+    languages) lives in HBM, the regime where the search is throughput-bound."""
+    import paper_2305_18575_gb300 as rei
+    from workloads import printed_instance
+    i = printed_instance()
+    prob = rei.Problem(i.alphabet, i.pos, i.neg, costs=i.costs, max_cost=i.max_cost, mem_budget=i.mem_budget)
+    ctx.solve_problem(prob)  # warm-up (the context sizes its cache and table)
+    runs = [ctx.solve_problem(prob) for _ in range(2)]
+    r = min(runs, key=lambda x: x.ms_total)
+    if r.status != rei.REI_OK or r.cost != 28:
+        raise RuntimeError(f"printed instance: {r.status_name} cost {r.cost}")
+    peaks, kind = measured_peaks()
+    alg_bytes = 32 * r.candidates + (12 * 4 * r.words + 17) * r.unique
+    hbm = alg_bytes / (r.ms_search_kernel * 1e-3) / 1e9
+    return {"workload": PAPER_WORKLOAD, "regex": r.regex, "cost": r.cost, "candidates": r.candidates,
+            "unique": r.unique, "time_to_min_re_s": r.ms_total / 1e3, "kernel_s": r.ms_search_kernel / 1e3,
+            "candidates_per_s": r.candidates / (r.ms_total * 1e-3), "search_launches": r.search_launches,
+            "roofline": {"bound": "hbm", "achieved": hbm, "peak": float(peaks.get("hbm_gbs", 6800.0)),
+                         "unit": "GB/s", "frac": hbm / float(peaks.get("hbm_gbs", 6800.0)),
+                         "peak_source": f"{kind} hbm_gbs", "alg_bytes_per_launch": alg_bytes / r.search_launches,
+                         "traffic": recorded_traffic().get("printed_traffic_bytes_per_launch"),
+                         "alg_bytes": "32 B probe per candidate + (48 W + 17) B per new language"},
+            "paper_a100": {"seconds": PAPER_A100_S, "candidates": PAPER_A100_REs,
+                           "note": "the paper's own run on an A100 (Table 1); context, not a target"}}
 
 
 SERVE_WORKLOAD = ("served: Poisson arrivals at 50, 200 and 1000 problems/s (trace seed = rate), problems drawn in turn "
@@ -416,6 +477,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched and served legs")
+    ap.add_argument("--no-paper", action="store_true", help="skip the printed-instance leg")
     ap.add_argument("--serve-seconds", type=float, default=SERVE_SECONDS,
                     help="length of each arrival trace of the served leg (the served config uses 60)")
     args = ap.parse_args()

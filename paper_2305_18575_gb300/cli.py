@@ -15,13 +15,13 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
 def main(argv=None):
     import paper_2305_18575_gb300 as rei
-    from workloads import make_config
+    from workloads import make_config, printed_instance
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("config", choices=["small", "medium", "wide", "batched", "served"])
+    ap.add_argument("config", choices=["small", "medium", "wide", "batched", "served", "printed"])
     ap.add_argument("seed", type=int)
     ap.add_argument("--costs", default="1,1,1,1,1")
-    ap.add_argument("--max-cost", type=int, default=40)
+    ap.add_argument("--max-cost", type=int, default=None, help="default: 30 for the printed instance, else 40")
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--cache-init", type=int, default=0, help="initial cache rows (0 = library default)")
     ap.add_argument("--chunk", type=int, default=0)
@@ -30,7 +30,7 @@ def main(argv=None):
     ap.add_argument("--grid", type=int, default=0)
     a = ap.parse_args(argv)
     costs = tuple(int(x) for x in a.costs.split(","))
-    inst = make_config(a.config, a.seed)
+    inst = printed_instance() if a.config == "printed" else make_config(a.config, a.seed)
     with rei.Context(device=0) as ctx:
         if a.cache_init:
             ctx.set_option(rei.REI_OPT_CACHE_INIT, a.cache_init)
@@ -41,7 +41,8 @@ def main(argv=None):
         if a.grid:
             ctx.set_option(rei.REI_OPT_GRID, a.grid)
         mk = rei.Problem.on_device if a.device_input else rei.Problem
-        prob = mk(inst.alphabet, inst.pos, inst.neg, costs=costs, max_cost=a.max_cost,
+        max_cost = a.max_cost if a.max_cost is not None else inst.max_cost if a.config == "printed" else 40
+        prob = mk(inst.alphabet, inst.pos, inst.neg, costs=costs, max_cost=max_cost,
                   mem_budget=inst.mem_budget)
         for _ in range(a.repeat):
             r = ctx.solve_problem(prob)

@@ -31,3 +31,20 @@ def test_poisson_trace():
     t = poisson_trace(200.0, 5.0)
     assert t == poisson_trace(200.0, 5.0)
     assert all(x < y for x, y in zip(t, t[1:])) and 700 < len(t) < 1300
+
+
+def test_printed_instance_is_the_papers():
+    """The benchmark's copy of the specification printed in Sec. 6 (Table 1,
+    Type 1 No 50) equals the golden fixture transcribed from the paper."""
+    import os
+    from workloads import printed_instance
+    inst = printed_instance()
+    path = os.path.join(os.path.dirname(__file__), "golden", "allowed_error_table.txt")
+    P = N = None
+    for line in open(path):
+        if line.startswith("P:"):
+            P = [w.encode() for w in line.split()[1:]]
+        if line.startswith("N:"):
+            N = [b"" if w == "_" else w.encode() for w in line.split()[1:]]
+    assert inst.pos == P and inst.neg == N
+    assert inst.alphabet == b"01" and inst.costs == (1, 1, 1, 1, 1) and inst.target_cost == 28

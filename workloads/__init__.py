@@ -8,4 +8,5 @@ from .gen import (  # noqa: F401
     type1_instance,
     type2_instance,
     poisson_trace,
+    printed_instance,
 )
