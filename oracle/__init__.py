@@ -53,6 +53,12 @@ def lib():
         L.oracle_solve.argtypes = [vp, C.c_char_p, C.c_int, C.c_char_p, u32p, C.c_int, C.c_int,
                                    i32p, C.c_int, C.c_uint64, C.c_uint, C.c_uint32, C.c_uint64]
         L.oracle_solve.restype = C.c_int
+        L.oracle_solve_sc.argtypes = [vp, C.c_char_p, C.c_int, C.c_char_p, u32p, C.c_int, C.c_int,
+                                      i32p, i32p, C.c_int, C.c_uint64, C.c_uint, C.c_uint32, C.c_uint64]
+        L.oracle_solve_sc.restype = C.c_int
+        L.oracle_tree_cost_sc.argtypes = [C.c_char_p, C.c_int, i32p, i32p]
+        L.oracle_brute_min_cost_sc.argtypes = [C.c_char_p, C.c_int, C.c_char_p, u32p, C.c_int, C.c_int,
+                                               i32p, i32p, C.c_int, C.c_long, C.c_char_p, C.c_int, i32p]
         L.oracle_stats_of.argtypes = [vp]
         L.oracle_stats_of.restype = C.POINTER(_Stats)
         L.oracle_answer_tree.argtypes = [vp, C.c_char_p, C.c_int]
@@ -93,6 +99,15 @@ def _costs(costs):
     return (C.c_int * 5)(*costs)
 
 
+def _sym(sym_costs, n_sym):
+    """Per-symbol costs (one per alphabet symbol), or None for c_sym each."""
+    if sym_costs is None:
+        return None
+    if len(sym_costs) != n_sym:
+        raise ValueError("one cost per alphabet symbol")
+    return (C.c_int * max(n_sym, 1))(*sym_costs)
+
+
 @dataclass
 class Result:
     status: int
@@ -123,11 +138,12 @@ class Run:
 
     def solve(self, alphabet: bytes, pos: Sequence[bytes], neg: Sequence[bytes],
               costs=(1, 1, 1, 1, 1), max_cost: int = 20, mem_budget: int = 1 << 30,
-              flags: int = 0, max_errors: int = 0, max_candidates: int = 0) -> Result:
+              flags: int = 0, max_errors: int = 0, max_candidates: int = 0, sym_costs=None) -> Result:
         buf, offs = _pack(list(pos) + list(neg))
         L = lib()
-        L.oracle_solve(self._h, alphabet, len(alphabet), buf, offs, len(pos), len(neg),
-                       _costs(costs), max_cost, mem_budget, flags, max_errors, max_candidates)
+        L.oracle_solve_sc(self._h, alphabet, len(alphabet), buf, offs, len(pos), len(neg),
+                          _costs(costs), _sym(sym_costs, len(alphabet)), max_cost, mem_budget, flags,
+                          max_errors, max_candidates)
         st = L.oracle_stats_of(self._h).contents
         tree = text = None
         if st.status == OK:
@@ -182,8 +198,9 @@ def match(tree: bytes, alphabet: bytes, s: bytes) -> bool:
     return bool(r)
 
 
-def tree_cost(tree: bytes, costs) -> int:
-    return lib().oracle_tree_cost(tree, len(tree) // 2, _costs(costs))
+def tree_cost(tree: bytes, costs, sym_costs=None) -> int:
+    sc = None if sym_costs is None else (C.c_int * max(len(sym_costs), 1))(*sym_costs)
+    return lib().oracle_tree_cost_sc(tree, len(tree) // 2, _costs(costs), sc)
 
 
 def tree_text(tree: bytes, alphabet: bytes) -> str:
@@ -230,14 +247,14 @@ def tree_lang(tree: bytes, alphabet: bytes, strings: Sequence[bytes]) -> bytes:
 
 
 def brute_min_cost(alphabet, pos, neg, costs=(1, 1, 1, 1, 1), max_cost=8,
-                   node_limit=30_000_000):
+                   node_limit=30_000_000, sym_costs=None):
     """(minimal cost or 0 if none <= max_cost, postfix tree) by brute force."""
     buf, offs = _pack(list(pos) + list(neg))
     tok = C.create_string_buffer(4096)
     tl = C.c_int()
-    c = lib().oracle_brute_min_cost(alphabet, len(alphabet), buf, offs, len(pos), len(neg),
-                                    _costs(costs), max_cost, node_limit, tok, 4096,
-                                    C.byref(tl))
+    c = lib().oracle_brute_min_cost_sc(alphabet, len(alphabet), buf, offs, len(pos), len(neg),
+                                       _costs(costs), _sym(sym_costs, len(alphabet)), max_cost,
+                                       node_limit, tok, 4096, C.byref(tl))
     return c, tok.raw[: 2 * tl.value]
 
 

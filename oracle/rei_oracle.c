@@ -22,6 +22,8 @@
  *   - trivial answers for P = {} and P = {eps}          Alg. 1 (first two tests)
  *   - OnTheFly mode after the cache is full             Sec. 3, "OnTheFly mode"
  *   - REI with an allowed number of errors              Sec. 6, "Future Work"
+ *   - different costs for different alphabet symbols    Sec. 3, the remark after
+ *                                                       Def. "cost function"
  *
  * Independent cross-checks it also carries:
  *   - a Brzozowski-derivative matcher (Brzozowski 1964) on regex trees, used to
@@ -37,6 +39,9 @@
  *     splits cl = c1 .. in ascending order (left index outer, right inner),
  *     then + likewise, visiting only cl <= cr and, when cl == cr, pairs i < j
  *     (the skipped pairs always repeat an earlier candidate's language);
+ *   - with per-symbol costs c(a) >= 1, level c starts with the symbols of cost
+ *     c in alphabet order, and operand levels start at the cheapest symbol's
+ *     cost (no expression is cheaper); eps and the empty set keep c_sym;
  *   - the first candidate in that order with a given language is the one kept,
  *     and the first precise unique candidate is the answer;
  *   - the cache holds at most cap = floor(budget / (4*W + 28)) languages with W
@@ -311,15 +316,18 @@ bad:
     return root;
 }
 
-static int tree_cost(const tarena *T, int x, const int *c)
+/* cost of a tree under the homomorphism c, with symbol a costing sc[a] when
+ * sc is given (else c_sym) */
+static int tree_cost(const tarena *T, int x, const int *c, const int *sc)
 {
     const tnode *t = &T->v[x];
     switch (t->k) {
-    case TK_SYM: case TK_EPS: case TK_EMPTY: return c[0];
-    case TK_OPT: return tree_cost(T, t->l, c) + c[1];
-    case TK_STAR: return tree_cost(T, t->l, c) + c[2];
-    case TK_CAT: return tree_cost(T, t->l, c) + tree_cost(T, t->r, c) + c[3];
-    case TK_ALT: return tree_cost(T, t->l, c) + tree_cost(T, t->r, c) + c[4];
+    case TK_SYM: return sc ? sc[t->a] : c[0];
+    case TK_EPS: case TK_EMPTY: return c[0];
+    case TK_OPT: return tree_cost(T, t->l, c, sc) + c[1];
+    case TK_STAR: return tree_cost(T, t->l, c, sc) + c[2];
+    case TK_CAT: return tree_cost(T, t->l, c, sc) + tree_cost(T, t->r, c, sc) + c[3];
+    case TK_ALT: return tree_cost(T, t->l, c, sc) + tree_cost(T, t->r, c, sc) + c[4];
     }
     return -1;
 }
@@ -455,6 +463,8 @@ typedef struct {
     ic_t ic;
     int n;
     int c[5];
+    int sc[256]; /* cost of each alphabet symbol (c_sym unless given per symbol) */
+    int cmin;    /* the cheapest symbol: no expression costs less */
     int max_cost;
     uint64_t cap;
     unsigned flags;
@@ -662,30 +672,30 @@ static void level_range(const search_t *S, int c, int64_t *st, int64_t *cnt)
 static int max_operand_level(const search_t *S, int c)
 {
     int m = -1;
-    const int *k = S->c;
-    if (c - k[1] >= k[0] && c - k[1] > m) m = c - k[1];
-    if (c - k[2] >= k[0] && c - k[2] > m) m = c - k[2];
-    if (c - k[3] >= 2 * k[0] && c - k[3] - k[0] > m) m = c - k[3] - k[0];
-    if (c - k[4] >= 2 * k[0] && c - k[4] - k[0] > m) m = c - k[4] - k[0];
+    const int *k = S->c, c1 = S->cmin;
+    if (c - k[1] >= c1 && c - k[1] > m) m = c - k[1];
+    if (c - k[2] >= c1 && c - k[2] > m) m = c - k[2];
+    if (c - k[3] >= 2 * c1 && c - k[3] - c1 > m) m = c - k[3] - c1;
+    if (c - k[4] >= 2 * c1 && c - k[4] - c1 > m) m = c - k[4] - c1;
     return m;
 }
 
-/* Alg. 1 main loop body for one cost level c > c1 */
+/* Alg. 1 main loop body for the composite candidates of cost level c */
 static void build_level(search_t *S, int c)
 {
-    const int *k = S->c;
+    const int *k = S->c, c1 = g_mutation == 9 ? S->c[0] : S->cmin;
     int64_t st, cnt, st2, cnt2;
     /* questions, then stars */
     for (int pass = 0; pass < 2; pass++) {
         int star = (pass == 1) != (g_mutation == 5);
         int d = star ? k[2] : k[1];
         level_range(S, c - d, &st, &cnt);
-        if (c - d >= k[0])
+        if (c - d >= c1)
             for (int64_t i = 0; i < cnt; i++) candidate(S, c, star ? OP_STAR : OP_OPT, st + i, -1);
     }
     /* concatenations: every split cl + cr = c - c4 */
     int rem = c - k[3];
-    for (int cl = k[0]; cl <= rem - k[0]; cl++) {
+    for (int cl = c1; cl <= rem - c1; cl++) {
         level_range(S, cl, &st, &cnt);
         level_range(S, rem - cl, &st2, &cnt2);
         for (int64_t i = 0; i < cnt; i++)
@@ -693,7 +703,7 @@ static void build_level(search_t *S, int c)
     }
     /* unions: splits cl + cr = c - c5 with cl <= cr, and i < j when cl == cr */
     rem = c - k[4];
-    for (int cl = k[0]; cl <= rem - k[0] && cl <= rem - cl; cl++) {
+    for (int cl = c1; cl <= rem - c1 && cl <= rem - cl; cl++) {
         int cr = rem - cl;
         if (g_mutation == 7 && cl == cr) continue;
         level_range(S, cl, &st, &cnt);
@@ -787,10 +797,10 @@ static double now_s(void)
  * string k being bytes[offs[k] .. offs[k+1]).  costs = (c_sym, c_?, c_*, c_., c_+).
  * Returns the status (also in R->st.status).
  */
-int oracle_solve(oracle_run *R, const unsigned char *alphabet, int n_sym,
-                 const unsigned char *bytes, const uint32_t *offs, int n_pos, int n_neg,
-                 const int *costs, int max_cost, uint64_t mem_budget, unsigned flags,
-                 uint32_t max_errors, uint64_t max_candidates)
+int oracle_solve_sc(oracle_run *R, const unsigned char *alphabet, int n_sym,
+                    const unsigned char *bytes, const uint32_t *offs, int n_pos, int n_neg,
+                    const int *costs, const int *sym_costs, int max_cost, uint64_t mem_budget,
+                    unsigned flags, uint32_t max_errors, uint64_t max_candidates)
 {
     double t0 = now_s();
     search_free(&R->S);
@@ -817,6 +827,12 @@ int oracle_solve(oracle_run *R, const unsigned char *alphabet, int n_sym,
         for (uint32_t i = offs[k]; i < offs[k + 1]; i++)
             if (S->A.rank[bytes[i]] < 0) return R->st.status = OR_EINVAL;
     memcpy(S->c, costs, sizeof S->c);
+    S->cmin = costs[0];
+    for (int a = 0; a < n_sym; a++) {
+        S->sc[a] = sym_costs ? sym_costs[a] : costs[0];
+        if (S->sc[a] < 1) return R->st.status = OR_EINVAL;
+        if (a == 0 || S->sc[a] < S->cmin) S->cmin = S->sc[a];
+    }
     S->max_cost = max_cost;
     S->flags = flags;
     S->max_candidates = max_candidates;
@@ -863,17 +879,17 @@ int oracle_solve(oracle_run *R, const unsigned char *alphabet, int n_sym,
     S->s2 = (unsigned char *)malloc((size_t)n);
     S->partial_level = max_cost + 1;
     status = OR_NOT_FOUND;
-    for (int c = costs[0]; c <= max_cost; c++) {
+    for (int c = S->cmin; c <= max_cost; c++) {
         if (S->otf && max_operand_level(S, c) >= S->partial_level) {
             status = OR_OOM;
             break;
         }
         S->lvl_start[c] = (int64_t)S->size;
         uint64_t before = S->size;
-        if (c == costs[0])
-            for (int a = 0; a < n_sym; a++) candidate(S, c, OP_LEAF, a, -1);
-        else
-            build_level(S, c);
+        /* the symbols of cost c, then the composite candidates */
+        for (int a = 0; a < n_sym && !S->found && !S->err; a++)
+            if ((g_mutation == 8 ? S->c[0] : S->sc[a]) == c) candidate(S, c, OP_LEAF, a, -1);
+        if (!S->found && !S->err) build_level(S, c);
         S->lvl_count[c] = (int64_t)(S->size - before);
         S->levels = c;
         if (S->err) {
@@ -1011,14 +1027,19 @@ int oracle_match(const unsigned char *tok, int ntok, const unsigned char *alphab
     return m;
 }
 
-int oracle_tree_cost(const unsigned char *tok, int ntok, const int *costs)
+int oracle_tree_cost_sc(const unsigned char *tok, int ntok, const int *costs, const int *sym_costs)
 {
     tarena T;
     memset(&T, 0, sizeof T);
     int root = tree_from_postfix(&T, tok, ntok);
-    int c = root < 0 ? -1 : tree_cost(&T, root, costs);
+    int c = root < 0 ? -1 : tree_cost(&T, root, costs, sym_costs);
     free(T.v);
     return c;
+}
+
+int oracle_tree_cost(const unsigned char *tok, int ntok, const int *costs)
+{
+    return oracle_tree_cost_sc(tok, ntok, costs, NULL);
 }
 
 int oracle_tree_text(const unsigned char *tok, int ntok, const unsigned char *alphabet,
@@ -1140,10 +1161,10 @@ int oracle_ic(const unsigned char *alphabet, int n_sym, const unsigned char *byt
  * (c == c1), or t?, t* over trees of cost c-c2, c-c3, or t.u, t+u over all
  * pairs with cost(t) + cost(u) = c - c4 (resp. c - c5), both orders.
  */
-int oracle_brute_min_cost(const unsigned char *alphabet, int n_sym, const unsigned char *bytes,
-                          const uint32_t *offs, int n_pos, int n_neg, const int *costs,
-                          int max_cost, long node_limit, unsigned char *tok_out, int tok_cap,
-                          int *tok_len)
+int oracle_brute_min_cost_sc(const unsigned char *alphabet, int n_sym, const unsigned char *bytes,
+                             const uint32_t *offs, int n_pos, int n_neg, const int *costs,
+                             const int *sym_costs, int max_cost, long node_limit,
+                             unsigned char *tok_out, int tok_cap, int *tok_len)
 {
     alphabet_t A;
     if (setup_alpha(&A, alphabet, n_sym)) return -1;
@@ -1186,8 +1207,8 @@ int oracle_brute_min_cost(const unsigned char *alphabet, int n_sym, const unsign
         }                                                                      \
         lst[m++] = (x);                                                        \
     } while (0)
-        if (c == costs[0])
-            for (int a = 0; a < n_sym; a++) PUSH(tnew(&T, TK_SYM, a, -1, -1));
+        for (int a = 0; a < n_sym; a++)
+            if (c == (sym_costs ? sym_costs[a] : costs[0])) PUSH(tnew(&T, TK_SYM, a, -1, -1));
         if (c - costs[1] >= 1)
             for (long i = 0; i < cnt[c - costs[1]]; i++) PUSH(tnew(&T, TK_OPT, 0, by[c - costs[1]][i], -1));
         if (c - costs[2] >= 1)
@@ -1340,3 +1361,20 @@ int oracle_parse(const char *text, const unsigned char *alphabet, int n_sym, uns
 
 /* the budget rule, exported so tests can check both sides state the same one */
 uint64_t oracle_budget_cap(uint64_t budget, int n) { return budget_cap(budget, n); }
+
+/* the same entry points with every symbol at c_sym */
+int oracle_solve(oracle_run *R, const unsigned char *alphabet, int n_sym, const unsigned char *bytes,
+                 const uint32_t *offs, int n_pos, int n_neg, const int *costs, int max_cost,
+                 uint64_t mem_budget, unsigned flags, uint32_t max_errors, uint64_t max_candidates)
+{
+    return oracle_solve_sc(R, alphabet, n_sym, bytes, offs, n_pos, n_neg, costs, NULL, max_cost, mem_budget,
+                           flags, max_errors, max_candidates);
+}
+
+int oracle_brute_min_cost(const unsigned char *alphabet, int n_sym, const unsigned char *bytes,
+                          const uint32_t *offs, int n_pos, int n_neg, const int *costs, int max_cost,
+                          long node_limit, unsigned char *tok_out, int tok_cap, int *tok_len)
+{
+    return oracle_brute_min_cost_sc(alphabet, n_sym, bytes, offs, n_pos, n_neg, costs, NULL, max_cost,
+                                    node_limit, tok_out, tok_cap, tok_len);
+}

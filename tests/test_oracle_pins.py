@@ -235,6 +235,56 @@ def test_search_minimal_cost_equals_brute_force(costs):
         assert not any(oracle.match(r.tree, inst.alphabet, q) for q in inst.neg)
 
 
+SYM_COSTS = [((1, 1, 1, 1, 1), [1, 3]), ((1, 1, 1, 1, 1), [4, 1]), ((2, 1, 3, 1, 2), [2, 5]),
+             ((3, 2, 1, 2, 1), [1, 2]), ((5, 1, 1, 1, 1), [2, 2])]
+
+
+@pytest.mark.parametrize("costs,sym", SYM_COSTS)
+def test_per_symbol_costs_minimal_cost_equals_brute_force(costs, sym):
+    """Different costs for different symbols (the remark after the cost
+    function's definition, Sec. 3): the search's cost is the brute force's."""
+    insts = _tiny_instances() + [type1_instance(s, 3, 3, 3, alphabet=b"abc") for s in range(3)]
+    for inst in insts:
+        sc = (sym + [3])[:len(inst.alphabet)]
+        r = oracle.solve(inst.alphabet, inst.pos, inst.neg, costs=costs, max_cost=40, sym_costs=sc,
+                         flags=oracle.F_SELFCHECK)
+        assert r.status == oracle.OK
+        assert oracle.tree_cost(r.tree, costs, sc) == r.cost
+        assert all(oracle.match(r.tree, inst.alphabet, p) for p in inst.pos)
+        assert not any(oracle.match(r.tree, inst.alphabet, q) for q in inst.neg)
+        if r.cost > 12:
+            continue
+        bc, _ = oracle.brute_min_cost(inst.alphabet, inst.pos, inst.neg, costs=costs, max_cost=r.cost,
+                                      node_limit=4_000_000, sym_costs=sc)
+        if bc < 0:
+            continue
+        assert bc == r.cost, (inst.seed, costs, sc, r.text)
+
+
+def test_uniform_symbol_costs_are_the_plain_homomorphism():
+    for inst in _tiny_instances():
+        for costs in [(1, 1, 1, 1, 1), (2, 1, 3, 1, 2)]:
+            a = oracle.solve(inst.alphabet, inst.pos, inst.neg, costs=costs, max_cost=30)
+            b = oracle.solve(inst.alphabet, inst.pos, inst.neg, costs=costs, max_cost=30,
+                             sym_costs=[costs[0]] * len(inst.alphabet))
+            assert (a.status, a.cost, a.tree, a.candidates, a.unique) == \
+                (b.status, b.cost, b.tree, b.candidates, b.unique)
+
+
+def test_symbol_costs_change_the_answer():
+    # only the symbol 1 separates the sides; it costs 7, so no answer up to 6
+    r = oracle.solve(A01, [b"1"], [b"", b"0"], max_cost=20, sym_costs=[1, 7])
+    assert (r.cost, r.text) == (7, "1")
+    r = oracle.solve(A01, [b"1"], [b"", b"0"], max_cost=6, sym_costs=[1, 7])
+    assert r.status == oracle.NOT_FOUND
+    # eps and the empty set keep c_sym
+    r = oracle.solve(A01, [b""], [b"0"], costs=(5, 1, 1, 1, 1), max_cost=20, sym_costs=[1, 1])
+    assert (r.cost, r.text) == (5, "ε")
+    # an invalid symbol cost
+    r = oracle.solve(A01, [b"1"], [b"0"], max_cost=20, sym_costs=[1, 0])
+    assert r.status == oracle.EINVAL
+
+
 def test_upper_bound_by_target_cost():
     for s in range(6):
         inst = make_config("medium", s)
@@ -345,10 +395,17 @@ def _pins_pass():
     for pct, cost, text in [(20, 12, "(0+11)*(1+00)"), (35, 7, "1+(0+1)0")]:
         r = oracle.solve(A01, g["P"], g["N"], max_cost=30, max_errors=pct * 22 // 100)
         checks.append(r.cost == cost and r.text == text)
+    # per-symbol costs: the only precise symbol costs 7; with symbols at cost 1
+    # and c_sym = 3, the answer must use them as operands (brute force: cost 4)
+    r = oracle.solve(A01, [b"1"], [b"", b"0"], max_cost=20, sym_costs=[1, 7])
+    checks.append(r.cost == 7 and r.text == "1")
+    r = oracle.solve(A01, [b"1", b"11"], [b"", b"0"], costs=(3, 1, 1, 1, 1), max_cost=20, sym_costs=[1, 1])
+    checks.append(r.cost == oracle.brute_min_cost(A01, [b"1", b"11"], [b"", b"0"], costs=(3, 1, 1, 1, 1),
+                                                  max_cost=8, sym_costs=[1, 1])[0] == 4)
     return all(checks)
 
 
-@pytest.mark.parametrize("mutation", range(1, 8))
+@pytest.mark.parametrize("mutation", range(1, 10))
 def test_planted_mistakes_are_caught(mutation):
     assert _pins_pass()
     oracle.set_mutation(mutation)
