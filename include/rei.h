@@ -161,6 +161,12 @@ typedef struct rei_problem {
     uint64_t mem_budget;
     uint32_t max_errors;
     uint32_t flags;
+    /* Per-symbol costs (Sec. 3: a cost homomorphism may give different alphabet
+     * symbols different costs): NULL = every symbol costs costs.c_sym; else
+     * n_sym costs >= 1 in host memory, one per alphabet symbol in alphabet
+     * order.  A level c starts with the symbols of cost c (alphabet order);
+     * eps and the empty set keep costs.c_sym. */
+    const uint32_t *sym_costs;
 } rei_problem;
 
 typedef struct rei_ctx rei_ctx;

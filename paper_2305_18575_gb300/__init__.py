@@ -78,7 +78,8 @@ class rei_problem(C.Structure):
     _fields_ = [("alphabet", C.c_void_p), ("n_sym", C.c_uint32), ("bytes", C.c_void_p),
                 ("offsets", C.c_void_p), ("n_pos", C.c_uint32), ("n_neg", C.c_uint32),
                 ("total_bytes", C.c_uint64), ("costs", rei_costs), ("max_cost", C.c_uint32),
-                ("mem_budget", C.c_uint64), ("max_errors", C.c_uint32), ("flags", C.c_uint32)]
+                ("mem_budget", C.c_uint64), ("max_errors", C.c_uint32), ("flags", C.c_uint32),
+                ("sym_costs", C.c_void_p)]
 
 
 class rei_staged(C.Structure):
@@ -289,7 +290,7 @@ class Problem:
 
     def __init__(self, alphabet: bytes, pos: Sequence[bytes], neg: Sequence[bytes],
                  costs=(1, 1, 1, 1, 1), max_cost: int = 20, mem_budget: int = 1 << 30,
-                 max_errors: int = 0, flags: int = 0, device_tensors=None):
+                 max_errors: int = 0, flags: int = 0, device_tensors=None, sym_costs=None):
         self.alphabet = bytes(alphabet)
         self._abuf = C.create_string_buffer(self.alphabet, max(len(self.alphabet), 1))
         buf, offs = pack(pos, neg)
@@ -304,6 +305,11 @@ class Problem:
         p.mem_budget = mem_budget
         p.max_errors = max_errors
         p.flags = flags
+        if sym_costs is not None:
+            if len(sym_costs) != len(self.alphabet):
+                raise ValueError("sym_costs: one cost per alphabet symbol")
+            self._sbuf = (C.c_uint32 * max(len(sym_costs), 1))(*sym_costs)
+            p.sym_costs = C.cast(self._sbuf, C.c_void_p)
         if device_tensors is not None:
             # (uint8 tensor of bytes, int32 tensor of offsets), already on the device
             tb, to = device_tensors

@@ -22,6 +22,7 @@
 
 #include "rei_dev.cuh"
 #include "stage_dev.cuh"
+#include "leaves.h"
 
 namespace rei {
 cudaError_t launch_solve_batch(const BatchJob *jobs_dev, const BatchArgs *args, uint32_t grid, uint32_t threads,
@@ -251,6 +252,7 @@ rei_status check_problem(const rei_problem *p) {
     for (uint32_t v : c)
         if (v < 1 || v > REI_MAX_COST) return REI_EINVAL;
     if (p->max_cost > REI_MAX_COST) return REI_EINVAL;
+    if (check_sym_costs(p)) return REI_EINVAL;
     bool seen[256] = {};
     for (uint32_t i = 0; i < p->n_sym; i++) {
         if (seen[p->alphabet[i]]) return REI_EINVAL;
@@ -556,6 +558,7 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
     j.neg_mask = (const uint32_t *)c->neg.p;
     j.leaf = (const uint32_t *)c->leaf.p;
     j.leaf_stride = kMaxWords;
+    fill_leaves(p, &j.cmin, j.leaf_cost, j.leaf_sym);
     j.c[0] = p->costs.c_sym;
     j.c[1] = p->costs.c_opt;
     j.c[2] = p->costs.c_star;
@@ -730,11 +733,15 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
         return pow2_at_least(std::max<uint64_t>(2 * need, 1024));
     };
     uint64_t tslots = table_slots(cache_alloc);
-    if ((s = ensure(c, c->cs, 4ull * W * cache_alloc))) return s;
-    if ((s = ensure(c, c->bp_op, cache_alloc))) return s;
-    if ((s = ensure(c, c->bp_l, 4ull * cache_alloc))) return s;
-    if ((s = ensure(c, c->bp_r, 4ull * cache_alloc))) return s;
-    if ((s = ensure(c, c->used, 4ull * cache_alloc))) return s;
+    // after a fused launch the cache holds its rows: grow keeping them
+    auto ensure_rows = [&](DevBuf &b, size_t bytes) {
+        return fused ? grow_keep(c, b, bytes, b.bytes) : ensure(c, b, bytes);
+    };
+    if ((s = ensure_rows(c->cs, 4ull * W * cache_alloc))) return s;
+    if ((s = ensure_rows(c->bp_op, cache_alloc))) return s;
+    if ((s = ensure_rows(c->bp_l, 4ull * cache_alloc))) return s;
+    if ((s = ensure_rows(c->bp_r, 4ull * cache_alloc))) return s;
+    if ((s = ensure(c, c->used, 4ull * cache_alloc))) return s;  // (rebuilt with the table)
     {
         const void *before = c->table.p, *mbefore = c->minidx.p;
         const size_t before_bytes = c->table.bytes, mbefore_bytes = c->minidx.bytes;
@@ -771,15 +778,21 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
         if (!c->table_clean) {
             // a new table, or the last search ended abnormally: clear it all once
             CK(cudaMemsetAsync(c->table.p, 0xFF, c->table.bytes, c->stream));
-        CK(cudaMemsetAsync(c->minidx.p, 0xFF, c->minidx.bytes, c->stream));
+            CK(cudaMemsetAsync(c->minidx.p, 0xFF, c->minidx.bytes, c->stream));
             CK(cudaMemsetAsync(c->bitmap.p, 0, c->bitmap.bytes, c->stream));
         }
         c->table_clean = false;
+        uint32_t hj_cmin;
+        {
+            uint16_t lc[256];
+            uint8_t ls[256];
+            fill_leaves(p, &hj_cmin, lc, ls);
+        }
         CK(cudaMemsetAsync(c->lvl_start.p, 0, 8ull * (max_cost + 2), c->stream));
         CK(cudaMemsetAsync(c->lvl_count.p, 0, 8ull * (max_cost + 2), c->stream));
         memset(hst, 0, sizeof(SolveState));
         hst->status = ST_RUNNING;
-        hst->level = p->costs.c_sym;
+        hst->level = hj_cmin;
         hst->found = kNone;
         hst->partial_level = max_cost + 1;
         CK(cudaMemcpyAsync(c->state.p, hst, sizeof(SolveState), cudaMemcpyHostToDevice, c->stream));
@@ -804,6 +817,7 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
         hj->n_pos_set = I.n_pos_set;
         hj->pos_eps = I.pos_eps;
         hj->neg_eps = I.neg_eps;
+        fill_leaves(p, &hj->cmin, hj->leaf_cost, hj->leaf_sym);
         hj->c[0] = p->costs.c_sym;
         hj->c[1] = p->costs.c_opt;
         hj->c[2] = p->costs.c_star;
@@ -1295,6 +1309,7 @@ rei_status run_batch(rei_ctx *c, const rei_problem *probs, const std::vector<uin
         J.n_pos_set = I.n_pos_set;
         J.pos_eps = I.pos_eps;
         J.neg_eps = I.neg_eps;
+        fill_leaves(&p, &J.cmin, J.leaf_cost, J.leaf_sym);
         J.c[0] = p.costs.c_sym;
         J.c[1] = p.costs.c_opt;
         J.c[2] = p.costs.c_star;
@@ -1506,7 +1521,7 @@ struct rei_server {
     struct Req {
         uint64_t ticket;
         std::vector<uint8_t> alphabet, bytes;
-        std::vector<uint32_t> offs;
+        std::vector<uint32_t> offs, sym_costs;
         rei_problem p;
         uint64_t footprint;
         double t_submit;  // host clock, ms
@@ -1553,7 +1568,8 @@ rei_status server_setup(rei_server *S) {
     if (cudaSetDevice(c->device) != cudaSuccess) return REI_ECUDA;
     S->ring_size = 4096;
     S->threads = 256;
-    S->smem = 112 * 1024;
+    // two CTAs per SM with their static shared memory and reserve
+    S->smem = c->smem_sm / 2 > 8192 ? c->smem_sm / 2 - 4096 : 48 * 1024;
     if (stage_layout(kServeMaxIC, kServeMaxBytes, nullptr, nullptr) > S->smem) return REI_EINVAL;
     int bps = 0;
     if (serve_occupancy(S->threads, S->smem, &bps) != cudaSuccess || bps < 1) return REI_ECUDA;
@@ -1676,6 +1692,7 @@ void solve_alone(rei_server *S, rei_server::Req &req) {
     req.p.alphabet = req.alphabet.data();
     req.p.bytes = req.bytes.data();
     req.p.offsets = req.offs.data();
+    req.p.sym_costs = req.sym_costs.empty() ? nullptr : req.sym_costs.data();
     char rbuf[8192];
     uint8_t tbuf[2 * (REI_MAX_COST + 1)];
     rei_result r{};
@@ -1784,6 +1801,9 @@ void server_loop(rei_server *S) {
                 q.max_errors = req.p.max_errors;
                 q.flags = req.p.flags & ~REI_F_DEVICE_INPUT;
                 q.mem_budget = req.p.mem_budget;
+                req.p.alphabet = req.alphabet.data();
+                req.p.sym_costs = req.sym_costs.empty() ? nullptr : req.sym_costs.data();
+                fill_leaves(&req.p, &q.cmin, q.leaf_cost, q.leaf_sym);
                 memcpy(q.offs, req.offs.data(), 4ull * (n_str + 1));
                 if (total) memcpy(q.bytes, req.bytes.data(), total);
                 S->live_bytes += req.footprint;
@@ -1853,6 +1873,7 @@ rei_status rei_server_submit(rei_server *S, const rei_problem *p, uint64_t *tick
     else r.offs.assign(1, 0);
     const uint32_t total = r.offs.back();
     r.bytes.assign(p->bytes, p->bytes + total);
+    if (p->sym_costs) r.sym_costs.assign(p->sym_costs, p->sym_costs + p->n_sym);
     r.p = *p;
     r.t_submit = now_ms();
     // the cache this request may hold: its budget, at most one slot's cache

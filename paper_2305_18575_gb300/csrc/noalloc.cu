@@ -27,6 +27,7 @@
 #include <mutex>
 
 #include "rei_dev.cuh"
+#include "leaves.h"
 
 namespace rei {
 cudaError_t launch_stage(const StageJob *jobs_dev, uint32_t n_jobs, cudaStream_t stream);
@@ -189,6 +190,7 @@ extern "C" rei_status rei_solve_noalloc(const rei_problem *p, void *stream_v, re
         if (seen[p->alphabet[i]]) return REI_EINVAL;
         seen[p->alphabet[i]] = true;
     }
+    if (check_sym_costs(p)) return REI_EINVAL;
     const uint32_t n_str = p->n_pos + p->n_neg;
     const bool dev_in = (p->flags & REI_F_DEVICE_INPUT) != 0;
     if (n_str && !p->offsets) return REI_EINVAL;
@@ -340,7 +342,11 @@ extern "C" rei_status rei_solve_noalloc(const rei_problem *p, void *stream_v, re
     SolveState hs;
     memset(&hs, 0, sizeof hs);
     hs.status = ST_RUNNING;
-    hs.level = p->costs.c_sym;
+    {
+        uint16_t lc[256];
+        uint8_t ls[256];
+        fill_leaves(p, &hs.level, lc, ls);
+    }
     hs.found = kNone;
     hs.partial_level = max_cost + 1;
     NA_CK(cudaMemcpyAsync(d_st, &hs, sizeof hs, cudaMemcpyHostToDevice, stream));
@@ -363,6 +369,7 @@ extern "C" rei_status rei_solve_noalloc(const rei_problem *p, void *stream_v, re
     j.pos_eps = I.pos_eps;
     j.neg_eps = I.neg_eps;
     for (int k = 0; k < 5; k++) j.c[k] = cc[k];
+    fill_leaves(p, &j.cmin, j.leaf_cost, j.leaf_sym);
     j.max_cost = max_cost;
     j.max_errors = p->max_errors;
     j.flags = p->flags;

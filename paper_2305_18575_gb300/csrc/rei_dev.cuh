@@ -170,6 +170,13 @@ struct SolveJob {
     // of the chunk with that language; 0 = fingerprint | row slots
     uint32_t exact;
     uint32_t *minidx;
+    // leaves: the alphabet symbols ordered by (cost, alphabet order) and
+    // their costs (every symbol costs c[0] unless costs are given per
+    // symbol; a cost above REI_MAX_COST is stored as REI_MAX_COST + 1);
+    // cmin is the cheapest, below which no expression costs
+    uint32_t cmin, leaf_pad;
+    uint16_t leaf_cost[256];
+    uint8_t leaf_sym[256];
 };
 
 static_assert(sizeof(SolveJob) % 8 == 0, "the job is copied in 8-byte words");
@@ -243,6 +250,9 @@ struct ServeReq {
     rei_costs costs;
     uint32_t max_cost, max_errors, flags;
     uint64_t mem_budget;
+    uint32_t cmin;                 // leaves, as in SolveJob
+    uint16_t leaf_cost[256];
+    uint8_t leaf_sym[256];
     uint32_t offs[kServeMaxStrings + 1];
     uint8_t bytes[kServeMaxBytes];
 };

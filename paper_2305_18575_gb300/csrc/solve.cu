@@ -193,49 +193,46 @@ __device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v, uint32_t lane) {
 __device__ void plan_level(const SolveJob &J, uint32_t c, const uint32_t *lvs, const uint32_t *lvc, Seg *seg,
                            Plan &P) {
     const uint32_t lane = threadIdx.x & 31;
-    const uint32_t c1 = J.c[0];
+    const uint32_t c1 = J.cmin;  // no expression is cheaper
     uint32_t ns = 0;
     uint64_t start = 0;
-    if (c == c1) {
-        if (lane == 0 && J.n_sym) {
-            Seg &s = seg[0];
-            s.start = 0;
-            s.size = J.n_sym;
-            s.op = OP_LEAF;
-            s.tri = 0;
-            s.lbase = 0;
-            s.lcnt = J.n_sym;
-            s.rbase = 0;
-            s.rcnt = 0;
-            s.swap = 0;
-        }
-        if (lane == 0) {
-            P.nseg = J.n_sym ? 1 : 0;
-            P.total = J.n_sym;
-        }
-        __syncwarp();
-        return;
+    // the symbols of cost c: entries [lo, hi) of the cost-ordered leaf table
+    uint32_t lo = 0, hi = 0;
+    for (uint32_t a = lane; a < J.n_sym; a += 32) {
+        lo += J.leaf_cost[a] < c;
+        hi += J.leaf_cost[a] <= c;
     }
-    // candidate segments: [0] ?, [1] *, then concatenation splits, then union splits
+    for (int d = 16; d > 0; d >>= 1) {
+        lo += __shfl_xor_sync(0xFFFFFFFFu, lo, d);
+        hi += __shfl_xor_sync(0xFFFFFFFFu, hi, d);
+    }
+    // candidate segments: [0] symbols, [1] ?, [2] *, then concatenation
+    // splits, then union splits
     const int rem_c = (int)c - (int)J.c[3], rem_u = (int)c - (int)J.c[4];
     const int ncat = rem_c >= 2 * (int)c1 ? rem_c - 2 * (int)c1 + 1 : 0;
     const int nalt = rem_u >= 2 * (int)c1 ? rem_u / 2 - (int)c1 + 1 : 0;
-    const int total = 2 + ncat + nalt;
+    const int total = 3 + ncat + nalt;
+
     for (int r0 = 0; r0 < total; r0 += 32) {
         const int k = r0 + (int)lane;
         Seg s{};
         uint64_t size = 0;
         if (k < total) {
-            if (k < 2) {
-                const uint32_t d = J.c[1 + k];
+            if (k == 0) {
+                s.op = OP_LEAF;
+                s.lbase = lo;
+                s.lcnt = hi - lo;
+                size = hi - lo;
+            } else if (k < 3) {
+                const uint32_t d = J.c[k];
                 if (c >= c1 + d) {
-                    s.op = k == 0 ? OP_OPT : OP_STAR;
+                    s.op = k == 1 ? OP_OPT : OP_STAR;
                     s.lbase = lvs[c - d];
                     s.lcnt = lvc[c - d];
                     size = s.lcnt;
                 }
-            } else if (k < 2 + ncat) {
-                const uint32_t cl = c1 + (uint32_t)(k - 2), cr = (uint32_t)rem_c - cl;
+            } else if (k < 3 + ncat) {
+                const uint32_t cl = c1 + (uint32_t)(k - 3), cr = (uint32_t)rem_c - cl;
                 s.op = OP_CAT;
                 s.lbase = lvs[cl];
                 s.lcnt = lvc[cl];
@@ -245,7 +242,7 @@ __device__ void plan_level(const SolveJob &J, uint32_t c, const uint32_t *lvs, c
                 // fewer than 32 right operands: bit-slice over 32 left ones instead
                 s.swap = (s.rcnt < 32 && s.lcnt > s.rcnt) ? 1u : 0u;
             } else {
-                const uint32_t cl = c1 + (uint32_t)(k - 2 - ncat), cr = (uint32_t)rem_u - cl;
+                const uint32_t cl = c1 + (uint32_t)(k - 3 - ncat), cr = (uint32_t)rem_u - cl;
                 s.op = OP_ALT;
                 s.tri = cl == cr;
                 s.lbase = lvs[cl];
@@ -288,7 +285,7 @@ __device__ __forceinline__ uint64_t valid_count(const Seg &s) {
 
 // the highest operand level a level refers to (OnTheFly feasibility)
 __device__ int max_operand_level(const SolveJob &J, int c) {
-    const int c1 = (int)J.c[0];
+    const int c1 = (int)J.cmin;
     int m = -1;
     if (c - (int)J.c[1] >= c1) m = max(m, c - (int)J.c[1]);
     if (c - (int)J.c[2] >= c1) m = max(m, c - (int)J.c[2]);
@@ -594,7 +591,8 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uin
     if (sg.op == OP_LEAF) {
         for (uint32_t i = lane; i < 32 * W; i += 32) {
             const uint32_t j = i / W, b = i % W;
-            A[j * Ws + b] = j < nrow ? __ldg(J.leaf + (uint64_t)(first + j) * J.leaf_stride + b) : 0u;
+            A[j * Ws + b] = j < nrow ? __ldg(J.leaf + (uint64_t)J.leaf_sym[sg.lbase + first + j] * J.leaf_stride + b)
+                                     : 0u;
         }
         __syncwarp();
     } else if (sg.op == OP_OPT) {
@@ -714,14 +712,15 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uin
 // ---------------------------------------------------------------------------
 // decode a level-local index into (segment, op, left, right)
 
-__device__ void decode(const Seg *seg, uint32_t nseg, uint64_t xlev, uint32_t &op, uint32_t &l, uint32_t &r) {
+__device__ void decode(const Seg *seg, uint32_t nseg, const uint8_t *leaf_sym, uint64_t xlev, uint32_t &op,
+                       uint32_t &l, uint32_t &r) {
     uint32_t s = 0;
     while (s + 1 < nseg && seg[s + 1].start <= xlev) s++;
     const Seg &g = seg[s];
     const uint64_t x = xlev - g.start;
     op = g.op;
     if (g.op == OP_LEAF) {
-        l = (uint32_t)x;
+        l = leaf_sym[g.lbase + x];  // the symbol's alphabet index
         r = kNoRight;
     } else if (g.op == OP_OPT || g.op == OP_STAR) {
         l = g.lbase + (uint32_t)x;
@@ -927,7 +926,7 @@ __device__ void smem_append(const SolveJob &J, Shared &S, const ChunkArgs &a, ui
             dg[b] = x;
         }
         uint32_t op, l, r;
-        decode(S.seg, a.nseg, a.cs0 + xl, op, l, r);
+        decode(S.seg, a.nseg, J.leaf_sym, a.cs0 + xl, op, l, r);
         J.bp_op[k] = (uint8_t)op;
         J.bp_l[k] = l;
         J.bp_r[k] = r;
@@ -1048,7 +1047,7 @@ __device__ void solo_append(const SolveJob &J, SolveState *st, Shared &S, const 
             J.table[q] = (e & 0xFFFFFFFF00000000ull) | (uint32_t)k;
         }
         uint32_t op, l, r;
-        decode(S.seg, a.nseg, a.cs0 + xl, op, l, r);
+        decode(S.seg, a.nseg, J.leaf_sym, a.cs0 + xl, op, l, r);
         J.bp_op[k] = (uint8_t)op;
         J.bp_l[k] = l;
         J.bp_r[k] = r;
@@ -1293,7 +1292,7 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
                     }
                     const uint64_t k = base + i;
                     uint32_t op, l, r;
-                    decode(S.seg, a.nseg, a.cs0 + list[i], op, l, r);
+                    decode(S.seg, a.nseg, J.leaf_sym, a.cs0 + list[i], op, l, r);
                     J.bp_op[k] = (uint8_t)op;
                     J.bp_l[k] = l;
                     J.bp_r[k] = r;
@@ -1342,7 +1341,7 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
                         J.table[q] = (old & 0xFFFFFFFF00000000ull) | (uint32_t)k;
                     }
                     uint32_t op, l, r;
-                    decode(S.seg, a.nseg, a.cs0 + j, op, l, r);
+                    decode(S.seg, a.nseg, J.leaf_sym, a.cs0 + j, op, l, r);
                     J.bp_op[k] = (uint8_t)op;
                     J.bp_l[k] = l;
                     J.bp_r[k] = r;
@@ -1492,9 +1491,9 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
         L.unique_done = st->unique_done;
         for (int k = 0; k < 5; k++) L.cand_op[k] = st->cand_op[k];
         // a fresh search starts with its languages in shared memory
-        L.smode = J.small_rows && L.status == ST_RUNNING && L.level == J.c[0] && L.chunk_pos == 0 && L.size == 0;
+        L.smode = J.small_rows && L.status == ST_RUNNING && L.level == J.cmin && L.chunk_pos == 0 && L.size == 0;
         // trivial specifications (Alg. 1): the empty set, then eps
-        if (L.status == ST_RUNNING && L.level == J.c[0] && L.chunk_pos == 0 && L.size == 0) {
+        if (L.status == ST_RUNNING && L.level == J.cmin && L.chunk_pos == 0 && L.size == 0) {
             const uint32_t e_empty = J.n_pos_set;
             const uint32_t e_eps = J.n_pos_set - J.pos_eps + J.neg_eps;
             if (e_empty <= J.max_errors || e_eps <= J.max_errors) {
@@ -1646,7 +1645,7 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
         const unsigned long long f = ld_relaxed_u64(&st->found);
         if (L.status == ST_RUNNING && f != kNone) {
             uint32_t op, l, r;
-            decode(S.seg, s_plan.nseg, f, op, l, r);
+            decode(S.seg, s_plan.nseg, J.leaf_sym, f, op, l, r);
             st->ans_op = op;
             st->ans_l = l;
             st->ans_r = r;
@@ -1803,7 +1802,7 @@ __global__ void __launch_bounds__(256, 2) k_solve_fused(const __grid_constant__ 
     if (blockIdx.x == 0) {
         // the search state and the level table start empty
         if (threadIdx.x == 0) {
-            st->level = F.tmpl.c[0];
+            st->level = F.tmpl.cmin;
             st->found = kNone;
             st->partial_level = F.tmpl.max_cost + 1;
         }
@@ -1918,7 +1917,7 @@ __device__ void solve_in_slot(SolveJob &J, const SlotMem &m, uint32_t slot, Batc
     if (tid == 0) {
         SolveState z{};
         z.status = ST_RUNNING;
-        z.level = J.c[0];
+        z.level = J.cmin;
         z.found = kNone;
         z.partial_level = J.max_cost + 1;
         *st = z;
@@ -2075,11 +2074,24 @@ __global__ void __launch_bounds__(256, 2) k_serve(const __grid_constant__ ServeA
         const StageInfo I = *SJ.info;
         __syncthreads();
         uint32_t verdict = 0;  // 0 solve, 1 invalid input, 2 too large for this launch
+        // the job, built in shared memory (zeroed, the leaf table by every
+        // thread, the rest by thread 0)
         if (tid == 0) {
             if (I.status == SE_PAIRS || I.status == SE_IC_LARGE) verdict = 2;
             else if (I.status != SE_OK) verdict = 1;
-            SolveJob j{};
-            if (!verdict) {
+            s_red[0] = verdict;
+        }
+        for (uint32_t i = tid; i < sizeof(SolveJob) / 8; i += blockDim.x)
+            reinterpret_cast<unsigned long long *>(&J)[i] = 0;
+        __syncthreads();
+        verdict = s_red[0];
+        if (!verdict) {
+            for (uint32_t a = tid; a < 256; a += blockDim.x) {
+                J.leaf_cost[a] = q.leaf_cost[a];
+                J.leaf_sym[a] = q.leaf_sym[a];
+            }
+            if (tid == 0) {
+                SolveJob &j = J;
                 j.n = I.n;
                 j.W = I.W;
                 j.G = I.G;
@@ -2095,6 +2107,7 @@ __global__ void __launch_bounds__(256, 2) k_serve(const __grid_constant__ ServeA
                 j.n_pos_set = I.n_pos_set;
                 j.pos_eps = I.pos_eps;
                 j.neg_eps = I.neg_eps;
+                j.cmin = q.cmin;
                 j.c[0] = q.costs.c_sym;
                 j.c[1] = q.costs.c_opt;
                 j.c[2] = q.costs.c_star;
@@ -2111,11 +2124,9 @@ __global__ void __launch_bounds__(256, 2) k_serve(const __grid_constant__ ServeA
                 if (solve_smem_bytes(I.W, I.n, I.G, I.max_len, j.seg_cap, j.gt_in_smem, blockDim.x / 32, 0) >
                         A.smem_cap ||
                     I.W > A.slot.cs_words / A.slot.rows)
-                    verdict = 2;
+                    s_red[0] = 2;
                 j.tree = o.tree;
             }
-            J = j;
-            s_red[0] = verdict;
         }
         __syncthreads();
         verdict = s_red[0];

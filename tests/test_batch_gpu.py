@@ -76,3 +76,17 @@ def test_batch_config_with_autotuning():
         assert r.cost <= i.target_cost
         assert all(oracle.match(r.tree, i.alphabet, p) for p in i.pos)
         assert not any(oracle.match(r.tree, i.alphabet, q) for q in i.neg)
+
+
+def test_batch_with_per_symbol_costs():
+    insts = [make_config("small", s) for s in range(12)] + [batched_instance(s) for s in range(12)]
+    probs = []
+    for k, i in enumerate(insts):
+        sc = [1 + (a * 3 + k) % 4 for a in range(len(i.alphabet))]
+        probs.append(rei.Problem(i.alphabet, i.pos, i.neg, max_cost=40, mem_budget=1 << 30, sym_costs=sc))
+    with rei.Context(device=0) as ctx:
+        plain = [ctx.solve_problem(p) for p in probs]
+        batch = ctx.solve_batch(probs)
+    for k, (a, b) in enumerate(zip(plain, batch)):
+        assert key(a) == key(b), k
+

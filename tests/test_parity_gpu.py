@@ -294,6 +294,49 @@ def test_exact_keys_do_not_change_results(exact, chunk, solo, small):
             check_same(got, ref, ("growth", s, exact))
 
 
+SYM = [((1, 1, 1, 1, 1), [1, 3]), ((1, 1, 1, 1, 1), [4, 1]), ((2, 1, 3, 1, 2), [2, 5]), ((5, 1, 1, 1, 1), [2, 2])]
+
+
+@pytest.mark.parametrize("costs,sym", SYM)
+def test_per_symbol_costs_match_oracle(ctx, costs, sym):
+    """Different costs for different symbols (Sec. 3): the same answers, counts
+    and trees as the oracle, on both staging paths and on the whole grid."""
+    insts = [make_config("small", s) for s in range(10)] + [make_config("medium", s) for s in (0, 2, 7)]
+    insts += [type1_instance(s, 3, 3, 3, alphabet=b"abc") for s in range(3)]
+    for fused, solo in [(1, -1), (0, -1), (1, 0)]:
+        with rei.Context(device=0) as c:
+            c.set_option(rei.REI_OPT_FUSED_STAGE, fused)
+            c.set_option(rei.REI_OPT_SOLO_TILES, solo)
+            for inst in insts:
+                sc = (sym + [3])[:len(inst.alphabet)]
+                ref = oracle.solve(inst.alphabet, inst.pos, inst.neg, costs=costs, max_cost=40, sym_costs=sc,
+                                   max_candidates=3_000_000)
+                if ref.status == oracle.LIMIT:
+                    continue
+                got = c.solve_problem(rei.Problem(inst.alphabet, inst.pos, inst.neg, costs=costs, max_cost=40,
+                                                  sym_costs=sc, mem_budget=1 << 30))
+                check_same(got, ref, (inst.name, inst.seed, costs, sc, fused, solo))
+    bad = rei.Problem(A01, [b"1"], [b"0"], sym_costs=[1, 0])
+    assert ctx.solve_problem(bad).status == rei.REI_EINVAL
+
+
+def test_fused_launch_growth_keeps_rows_of_wide_languages():
+    """A fused launch sizes its cache from what the context holds (here rows of
+    2 words) and asks for more memory on a 12-word problem; the relaunch must
+    keep the rows it cached."""
+    from workloads.gen import batched_instance
+    i = batched_instance(0)
+    sc = [1, 4, 3, 2][:len(i.alphabet)]
+    ref = oracle.solve(i.alphabet, i.pos, i.neg, max_cost=40, sym_costs=sc)
+    for sym in (sc, None):
+        with rei.Context(device=0) as c:
+            got = c.solve_problem(rei.Problem(i.alphabet, i.pos, i.neg, max_cost=40, mem_budget=1 << 30,
+                                              sym_costs=sym))
+            if sym is not None:
+                check_same(got, ref, "sym")
+                assert got.launches > 1
+
+
 @pytest.mark.parametrize("fused", [0, 1])
 def test_cache_growth_relaunch_matches(ctx, fused):
     with rei.Context(device=0) as c:

@@ -106,3 +106,18 @@ def test_serve_poll_without_blocking_and_not_found():
         assert r is not None and r.status == rei.REI_NOT_FOUND
         with pytest.raises(RuntimeError):
             srv.result(t, block_ms=0)  # released once read
+
+
+def test_serve_with_per_symbol_costs():
+    insts = [make_config("small", s) for s in range(10)] + [batched_instance(s) for s in range(10)]
+    probs = []
+    for k, i in enumerate(insts):
+        sc = [1 + (a * 5 + k) % 3 for a in range(len(i.alphabet))]
+        probs.append(rei.Problem(i.alphabet, i.pos, i.neg, max_cost=40, mem_budget=1 << 30, sym_costs=sc))
+    with rei.Context(device=0) as ctx:
+        plain = [ctx.solve_problem(p) for p in probs]
+        with rei.Server(ctx) as srv:
+            got = [srv.result(t) for t in [srv.submit(p) for p in probs]]
+    for k, (a, b) in enumerate(zip(plain, got)):
+        assert key(a) == key(b), k
+

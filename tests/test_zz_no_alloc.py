@@ -66,3 +66,14 @@ def test_noalloc_refuses_what_does_not_fit():
     # and keeps working afterwards
     prob = rei.Problem(inst.alphabet, inst.pos, inst.neg, max_cost=40, mem_budget=BUDGET)
     assert noalloc(prob).status == rei.REI_OK
+
+
+def test_noalloc_with_per_symbol_costs():
+    with rei.Context(device=0) as ctx:
+        for seed in range(4):
+            inst = make_config("small", seed)
+            prob = rei.Problem(inst.alphabet, inst.pos, inst.neg, max_cost=30, mem_budget=BUDGET,
+                               sym_costs=[1, 3])
+            want = ctx.solve_problem(prob)
+            assert key(noalloc(prob)) == key(want)
+
