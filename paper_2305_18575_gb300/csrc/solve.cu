@@ -550,6 +550,11 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uin
     uint32_t *B = A + 32 * Ws;
     const uint32_t *cs = T.ops;
     const uint64_t lo = tl.lo, hi = tl.hi;
+    // word i of the tile's candidate-major rows is word b of row j (shift for a power-of-two W)
+    const uint32_t wlog = (W & (W - 1)) == 0 ? (uint32_t)(__ffs(W) - 1) : 32u;
+#define TILE_JB(i, j, b)                                     \
+    const uint32_t j = wlog < 32 ? (i) >> wlog : (i) / W; \
+    const uint32_t b = (i) - j * W
 
     // which candidate this lane holds; `first` is the first of the tile's 32
     // consecutive operands (the right ones, the left ones when swapped, or
@@ -565,15 +570,18 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uin
         valid = x < hi;
         nrow = (uint32_t)umin64(32, hi - first);
     } else if (swapped) {
-        col = (uint32_t)(tile / tl.nb);
-        first = (uint32_t)(tl.r0 + (tile % tl.nb) * 32);
+        // (a segment's tiles in a chunk and its blocks per row fit 32 bits)
+        const uint32_t t32 = (uint32_t)tile, nb = (uint32_t)tl.nb, qt = t32 / nb;
+        col = qt;
+        first = (uint32_t)tl.r0 + (t32 - qt * nb) * 32;
         row = first + lane;
         x = (uint64_t)row * sg.rcnt + col;
         valid = row < sg.lcnt && x >= lo && x < hi;
         nrow = min(32u, sg.lcnt - first);
     } else {
-        row = (uint32_t)(tl.r0 + tile / tl.nb);
-        first = (uint32_t)(tile % tl.nb) * 32;
+        const uint32_t t32 = (uint32_t)tile, nb = (uint32_t)tl.nb, qt = t32 / nb;
+        row = (uint32_t)tl.r0 + qt;
+        first = (t32 - qt * nb) * 32;
         col = first + lane;
         x = (uint64_t)row * sg.rcnt + col;
         valid = col < sg.rcnt && x >= lo && x < hi && (!sg.tri || col > row);
@@ -590,7 +598,7 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uin
     // ---- build
     if (sg.op == OP_LEAF) {
         for (uint32_t i = lane; i < 32 * W; i += 32) {
-            const uint32_t j = i / W, b = i % W;
+            TILE_JB(i, j, b);
             A[j * Ws + b] = j < nrow ? __ldg(J.leaf + (uint64_t)J.leaf_sym[sg.lbase + first + j] * J.leaf_stride + b)
                                      : 0u;
         }
@@ -598,7 +606,7 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uin
     } else if (sg.op == OP_OPT) {
         const uint32_t *src = cs + (uint64_t)(sg.lbase + first) * W;
         for (uint32_t i = lane; i < 32 * W; i += 32) {
-            const uint32_t j = i / W, b = i % W;
+            TILE_JB(i, j, b);
             A[j * Ws + b] = j < nrow ? ldop(src + i) : 0u;
         }
         __syncwarp();
@@ -610,7 +618,7 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uin
         for (uint32_t b = lane; b < W; b += 32) lw[b] = ldop(l + b);
         __syncwarp();
         for (uint32_t i = lane; i < 32 * W; i += 32) {
-            const uint32_t j = i / W, b = i % W;
+            TILE_JB(i, j, b);
             A[j * Ws + b] = j < nrow ? (lw[b] | ldop(src + i)) : 0u;
         }
         __syncwarp();
@@ -620,7 +628,7 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uin
         const uint32_t base = sg.op == OP_STAR ? sg.lbase : swapped ? sg.lbase : sg.rbase;
         const uint32_t *src = cs + (uint64_t)(base + first) * W;
         for (uint32_t i = lane; i < 32 * W; i += 32) {
-            const uint32_t j = i / W, b = i % W;
+            TILE_JB(i, j, b);
             A[j * Ws + b] = j < nrow ? ldop(src + i) : 0u;
         }
         if (sg.op == OP_CAT) {
@@ -708,6 +716,8 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uin
     }
     REI_TMARK(tmk, 9);
 }
+
+#undef TILE_JB
 
 // ---------------------------------------------------------------------------
 // decode a level-local index into (segment, op, left, right)
