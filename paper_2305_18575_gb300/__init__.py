@@ -32,6 +32,7 @@ REI_OPT_CHUNK, REI_OPT_GRID, REI_OPT_KEEP_CACHE, REI_OPT_CACHE_INIT, REI_OPT_SOL
 REI_OPT_SMALL_ROWS = 6
 REI_OPT_FUSED_STAGE = 7
 REI_OPT_EXACT_KEYS = 8
+REI_OPT_HANDOVER = 9
 REI_MAX_IC, REI_MAX_STRLEN, REI_MAX_COST = 4096, 4095, 255
 
 # every entry point include/rei.h declares

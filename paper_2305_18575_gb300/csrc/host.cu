@@ -71,6 +71,7 @@ struct rei_ctx {
 
     int64_t opt_chunk = 0, opt_grid = 0, opt_keep = 0, opt_cache_init = 0, opt_solo_tiles = -1, opt_small_rows = -1;
     int64_t opt_fused = 1, opt_exact = 1;
+    uint64_t opt_handover = 1ull << 22;  // levels of more candidates leave the fused launch
     size_t smem_sm = 0;  // shared memory per SM
 
     // staging
@@ -506,7 +507,7 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
         if ((s = ensure(c, c->bitmap, 4ull * ((chunk_words + 31) / 32)))) return s;
         if (c->bitmap.p != before || c->bitmap.bytes != before_bytes) c->table_clean = false;
     }
-    const uint32_t threads = 256;
+    const uint32_t threads = 256;  // (the launch bounds of k_solve_fused)
     const size_t half = c->smem_sm / 2 > 4096 ? c->smem_sm / 2 - 4096 : 0;
     const size_t smem = std::min(half, c->smem_optin);
     int bps = 0;
@@ -588,7 +589,7 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
     j.tree = (uint8_t *)c->state.p + sizeof(SolveState);
     j.tstack = (uint32_t *)c->tstack.p;
     j.trace = (uint32_t *)c->trace.p;
-    j.solo_tiles = c->opt_solo_tiles >= 0 ? (uint32_t)c->opt_solo_tiles : 8 * (threads / 32);
+    j.solo_tiles = c->opt_solo_tiles >= 0 ? (uint32_t)c->opt_solo_tiles : 64;
     F.job = (SolveJob *)c->solve_job.p;
     F.mem_budget = p->mem_budget;
     F.rows_alloc = rows;
@@ -600,6 +601,7 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
     F.chunk_opt = c->opt_chunk > 0 ? (uint64_t)c->opt_chunk : 0;
     F.small_opt = c->opt_small_rows < 0 ? 0xFFFFFFFFu : (uint32_t)c->opt_small_rows;
     F.smem_cap = (uint32_t)smem;
+    F.handover = c->opt_handover;
 
     CK(cudaEventRecord(c->ev[0], c->stream));
     CK(launch_solve_fused(&F, grid, threads, smem, c->stream));
@@ -677,7 +679,7 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
     // launch shape
     const uint32_t seg_cap = 2 * max_cost + 4;
     bool gt_smem = 4ull * (n + 1 + G + max_len + 2) <= 96 * 1024;
-    uint32_t warps = 8;
+    uint32_t warps = 16;  // (the launch bounds of k_solve)
     size_t smem = solve_smem_bytes(W, n, G, max_len, seg_cap, gt_smem, warps);
     while (smem > c->smem_optin && warps > 1) {
         warps /= 2;
@@ -685,7 +687,7 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
     }
     if (smem > c->smem_optin && gt_smem) {
         gt_smem = false;
-        warps = 8;
+        warps = 16;
         smem = solve_smem_bytes(W, n, G, max_len, seg_cap, gt_smem, warps);
         while (smem > c->smem_optin && warps > 1) {
             warps /= 2;
@@ -851,7 +853,7 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
         hj->tstack = (uint32_t *)c->tstack.p;
         hj->trace = (uint32_t *)c->trace.p;
         hj->gt_in_smem = gt_smem ? 1 : 0;
-        hj->solo_tiles = c->opt_solo_tiles >= 0 ? (uint32_t)c->opt_solo_tiles : 8 * warps;
+        hj->solo_tiles = c->opt_solo_tiles >= 0 ? (uint32_t)c->opt_solo_tiles : 64;
         hj->small_rows = small_rows;
     };
     fill_job();
@@ -1056,6 +1058,7 @@ rei_status rei_ctx_set_option(rei_ctx *c, int option, int64_t value) {
     case REI_OPT_SOLO_TILES: c->opt_solo_tiles = value; return REI_OK;
     case REI_OPT_FUSED_STAGE: c->opt_fused = value ? 1 : 0; return REI_OK;
     case REI_OPT_EXACT_KEYS: c->opt_exact = value ? 1 : 0; return REI_OK;
+    case REI_OPT_HANDOVER: c->opt_handover = (uint64_t)value; return REI_OK;
     case REI_OPT_SMALL_ROWS:
         if (value > 16384 || (value > 0 && (value < 256 || (value & (value - 1))))) return REI_EINVAL;
         c->opt_small_rows = value < 0 ? -1 : value;

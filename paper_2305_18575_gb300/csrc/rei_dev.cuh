@@ -175,6 +175,7 @@ struct SolveJob {
     // symbol; a cost above REI_MAX_COST is stored as REI_MAX_COST + 1);
     // cmin is the cheapest, below which no expression costs
     uint32_t cmin, leaf_pad;
+    uint64_t handover;  // levels above this many candidates end the launch (0 = never)
     uint16_t leaf_cost[256];
     uint8_t leaf_sym[256];
 };
@@ -191,6 +192,7 @@ struct FuseArgs {
     uint64_t cs_words, tmp_words, pend_cap, table_slots;
     uint64_t chunk_opt;       // chunk size asked for (0 = automatic)
     uint32_t small_opt;       // languages in shared memory at the start: 0xFFFFFFFF automatic, 0 none
+    uint64_t handover;        // levels above this many candidates go to the relaunch (0 = never)
     uint32_t smem_cap;        // dynamic shared memory of the launch
 };
 

@@ -806,6 +806,11 @@ __device__ uint32_t emit_tree(const SolveJob &J, uint32_t op, uint32_t l, uint32
 // state, published with release / read with acquire), join the chunk's
 // phases with grid barriers, and go back to waiting.
 
+// CTAs of the plain path, two per SM: the fused launch (staging, then the
+// levels of a small or medium search, latency-bound) runs 8 warps; the
+// relaunch that takes over large levels runs 16 for more loads in flight
+constexpr uint32_t kFusedThreads = 256;
+constexpr uint32_t kSolveThreads = 512;
 constexpr uint32_t kSortMax = 2048;  // candidates of a chunk CTA 0 runs with shared-memory bookkeeping
 
 __host__ __device__ size_t solve_smem_bytes(uint32_t W, uint32_t n, uint32_t G, uint32_t max_len,
@@ -1593,6 +1598,17 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
             continue;
         }
 
+        // a level larger than `handover` candidates goes to the relaunch
+        // (a launch shaped for throughput), which continues from here
+        if (J.handover && pos == 0 && T > J.handover && size > 0) {
+            if (L.smode) switch_to_global(J, S, &L);
+            if (tid == 0) {
+                st->need_rows = size;
+                L.status = ST_NEED_MEM;
+            }
+            __syncthreads();
+            continue;
+        }
         // chunk [pos, pos + C) of the level
         const bool dedup = !full && !otf;
         uint64_t C = T - pos;
@@ -1784,7 +1800,7 @@ __device__ __forceinline__ void solve_body(const SolveJob &J, uint32_t &bar_epoc
     }
 }
 
-__global__ void __launch_bounds__(256, 2) k_solve(const __grid_constant__ SolveJob J) {
+__global__ void __launch_bounds__(kSolveThreads, 2) k_solve(const __grid_constant__ SolveJob J) {
     uint32_t bar_epoch = 0;
     solve_body(J, bar_epoch);
 }
@@ -1801,7 +1817,7 @@ __device__ __forceinline__ uint64_t auto_chunk(uint32_t W) {
 // size the search from the staged problem, then search, all in one launch.
 // A problem whose staging or search the launch cannot hold (|ic| > 2048, a
 // guide table beyond the pair buffer, shared memory) ends with ST_RESTAGE.
-__global__ void __launch_bounds__(256, 2) k_solve_fused(const __grid_constant__ FuseArgs F) {
+__global__ void __launch_bounds__(kFusedThreads, 2) k_solve_fused(const __grid_constant__ FuseArgs F) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     __shared__ SolveJob J;
     SolveState *st = F.tmpl.st;
@@ -1841,6 +1857,7 @@ __global__ void __launch_bounds__(256, 2) k_solve_fused(const __grid_constant__ 
                 const uint32_t W = I.W;
                 j.cap = umin64(F.mem_budget / (4ull * W + 28), 0x7FFF0000ull);
                 j.exact = F.tmpl.exact && W <= 2 && I.n <= 62 ? 1u : 0u;
+                j.handover = F.handover;
                 const uint64_t tmax = F.table_slots / 2;
                 j.cache_alloc = umin64(umin64(j.cap, F.rows_alloc), umin64(F.cs_words / W, tmax / 2));
                 uint64_t ch = F.chunk_opt ? F.chunk_opt : auto_chunk(W);

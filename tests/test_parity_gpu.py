@@ -320,6 +320,25 @@ def test_per_symbol_costs_match_oracle(ctx, costs, sym):
     assert ctx.solve_problem(bad).status == rei.REI_EINVAL
 
 
+@pytest.mark.parametrize("handover", [1, 500, 20000])
+def test_handover_to_the_relaunch_does_not_change_results(handover):
+    """Levels above `handover` candidates leave the fused launch for the
+    relaunch; with small thresholds every search crosses over mid-way."""
+    with rei.Context(device=0) as c:
+        c.set_option(rei.REI_OPT_HANDOVER, handover)
+        for s in (0, 3, 5, 12):
+            for costs in [(1, 1, 1, 1, 1), (1, 1, 5, 1, 1)]:
+                inst, ref = oracle_medium(s, costs)
+                got = c.solve_problem(rei.Problem(inst.alphabet, inst.pos, inst.neg, costs=costs, max_cost=40,
+                                                  mem_budget=inst.mem_budget))
+                check_same(got, ref, (s, costs, handover))
+        got, ref = solve_both(c, A01, PIN_P, PIN_N, max_cost=30, max_errors=4)
+        check_same(got, ref, ("pin20", handover))
+        for s in range(4):
+            got, ref = solve_both(c, make_config("small", s), max_cost=20, sym_costs=[1, 2])
+            check_same(got, ref, ("small sym", s, handover))
+
+
 def test_fused_launch_growth_keeps_rows_of_wide_languages():
     """A fused launch sizes its cache from what the context holds (here rows of
     2 words) and asks for more memory on a 12-word problem; the relaunch must
