@@ -93,6 +93,7 @@ struct rei_ctx {
     // pinned host scratch
     uint8_t *h_pin = nullptr;
     size_t h_pin_bytes = 0;
+    bool pin_clean = false;  // no copy from or to h_pin is in flight (the last user synchronised)
 
     // last solve (for rei_cache_dump)
     bool last_valid = false;
@@ -157,6 +158,7 @@ rei_status grow_keep(rei_ctx *c, DevBuf &b, size_t bytes, size_t keep) {
 }
 
 rei_status ensure_pinned(rei_ctx *c, size_t bytes) {
+    c->pin_clean = false;  // the caller is about to use it
     if (c->h_pin_bytes >= bytes) return REI_OK;
     if (c->h_pin) {
         cudaStreamSynchronize(c->stream);
@@ -433,8 +435,9 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
     const size_t sb = state_bytes(max_cost);
     const size_t ob = (4ull * (n_str + 1) + 15) & ~size_t(15);
     const size_t pin_in = sizeof(SolveJob) + sb + sizeof(StageInfo);
+    const bool pin_was_clean = c->pin_clean;
     if ((s = ensure_pinned(c, pin_in + (dev_in ? 0 : ob + total + 16)))) return s;
-    CK(cudaStreamSynchronize(c->stream));  // pinned buffer reuse
+    if (!pin_was_clean) CK(cudaStreamSynchronize(c->stream));  // pinned buffer reuse
 
     // inputs
     const uint8_t *dbytes;
@@ -610,6 +613,7 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
     uint8_t *hs = c->h_pin + sizeof(SolveJob);
     CK(cudaMemcpyAsync(hs, c->state.p, sb + sizeof(StageInfo), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    c->pin_clean = true;
     d2h += sb + sizeof(StageInfo);
     float ms = 0;
     CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));

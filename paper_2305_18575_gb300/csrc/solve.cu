@@ -22,6 +22,9 @@
 //      temporary storage -> language cache copy of Sec. 3, "GPU language
 //      cache implementation"), and make their table slots point at the cache.
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "rei_dev.cuh"
 #include "stage_dev.cuh"
@@ -2193,9 +2196,55 @@ __global__ void k_rehash(const __grid_constant__ SolveJob J, uint32_t count) {
     }
 }
 
+// the dynamic shared memory limit of a kernel, raised once per device to the
+// opt-in maximum (so that launches need no attribute call), and occupancy
+// queries remembered per (device, kernel, threads, shared memory)
+static std::mutex g_attr_mu;
+static std::map<std::pair<int, const void *>, bool> g_attr_set;
+static std::map<std::tuple<int, const void *, uint32_t, size_t>, int> g_occ;
+
+static cudaError_t prepare(const void *fn) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    auto key = std::make_pair(dev, fn);
+    if (g_attr_set.count(key)) return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    if (e != cudaSuccess) return e;
+    g_attr_set[key] = true;
+    return cudaSuccess;
+}
+
+static cudaError_t occupancy(const void *fn, uint32_t threads, size_t smem, int *bps) {
+    cudaError_t e = prepare(fn);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lk(g_attr_mu);
+        auto it = g_occ.find(std::make_tuple(dev, fn, threads, smem));
+        if (it != g_occ.end()) {
+            *bps = it->second;
+            return cudaSuccess;
+        }
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, fn, (int)threads, smem);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    g_occ[std::make_tuple(dev, fn, threads, smem)] = *bps;
+    return cudaSuccess;
+}
+
 cudaError_t launch_solve(const SolveJob *job, uint32_t grid, uint32_t threads, size_t smem,
                          cudaStream_t stream) {
-    cudaError_t e = cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = prepare((const void *)k_solve);
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)job};
     return cudaLaunchCooperativeKernel((const void *)k_solve, dim3(grid), dim3(threads), args, smem, stream);
@@ -2203,22 +2252,18 @@ cudaError_t launch_solve(const SolveJob *job, uint32_t grid, uint32_t threads, s
 
 cudaError_t launch_solve_fused(const FuseArgs *args, uint32_t grid, uint32_t threads, size_t smem,
                                cudaStream_t stream) {
-    cudaError_t e = cudaFuncSetAttribute(k_solve_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = prepare((const void *)k_solve_fused);
     if (e != cudaSuccess) return e;
     void *args_[] = {(void *)args};
     return cudaLaunchCooperativeKernel((const void *)k_solve_fused, dim3(grid), dim3(threads), args_, smem, stream);
 }
 
 cudaError_t solve_fused_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(k_solve_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_solve_fused, (int)threads, smem);
+    return occupancy((const void *)k_solve_fused, threads, smem, blocks_per_sm);
 }
 
 cudaError_t solve_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(k_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_solve, (int)threads, smem);
+    return occupancy((const void *)k_solve, threads, smem, blocks_per_sm);
 }
 
 cudaError_t launch_rehash(const SolveJob *job, uint32_t count, uint32_t grid, cudaStream_t stream) {
@@ -2228,29 +2273,25 @@ cudaError_t launch_rehash(const SolveJob *job, uint32_t count, uint32_t grid, cu
 
 cudaError_t launch_solve_batch(const BatchJob *jobs_dev, const BatchArgs *args, uint32_t grid, uint32_t threads,
                                size_t smem, cudaStream_t stream) {
-    cudaError_t e = cudaFuncSetAttribute(k_solve_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = prepare((const void *)k_solve_batch);
     if (e != cudaSuccess) return e;
     k_solve_batch<<<grid, threads, smem, stream>>>(jobs_dev, *args);
     return cudaGetLastError();
 }
 
 cudaError_t solve_batch_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(k_solve_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_solve_batch, (int)threads, smem);
+    return occupancy((const void *)k_solve_batch, threads, smem, blocks_per_sm);
 }
 
 cudaError_t launch_serve(const ServeArgs *args, uint32_t grid, uint32_t threads, size_t smem, cudaStream_t stream) {
-    cudaError_t e = cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = prepare((const void *)k_serve);
     if (e != cudaSuccess) return e;
     k_serve<<<grid, threads, smem, stream>>>(*args);
     return cudaGetLastError();
 }
 
 cudaError_t serve_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_serve, (int)threads, smem);
+    return occupancy((const void *)k_serve, threads, smem, blocks_per_sm);
 }
 
 }  // namespace rei
