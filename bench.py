@@ -61,13 +61,13 @@ def recorded_traffic():
             for line in fh:
                 k, sep, v = line.partition(":")
                 if sep and k.strip() in ("kernel_sources_sha256_16", "medium_traffic_bytes_per_launch",
-                                         "printed_traffic_bytes_per_launch"):
+                                         "printed_traffic_bytes_per_solve"):
                     rec[k.strip()] = v.strip()
     except OSError:
         return {}
     if rec.get("kernel_sources_sha256_16") != h.hexdigest()[:16]:
         return {}
-    return {k: int(v) for k, v in rec.items() if k.endswith("per_launch")}
+    return {k: int(v) for k, v in rec.items() if k != "kernel_sources_sha256_16"}
 
 
 def measured_peaks():
@@ -403,9 +403,10 @@ def paper_instance_leg(ctx, dev):
             "candidates_per_s": r.candidates / (r.ms_total * 1e-3), "search_launches": r.search_launches,
             "roofline": {"bound": "hbm", "achieved": hbm, "peak": float(peaks.get("hbm_gbs", 6800.0)),
                          "unit": "GB/s", "frac": hbm / float(peaks.get("hbm_gbs", 6800.0)),
-                         "peak_source": f"{kind} hbm_gbs", "alg_bytes_per_launch": alg_bytes / r.search_launches,
-                         "traffic": recorded_traffic().get("printed_traffic_bytes_per_launch"),
-                         "alg_bytes": "32 B probe per candidate + (48 W + 17) B per new language"},
+                         "peak_source": f"{kind} hbm_gbs", "alg_bytes_per_solve": alg_bytes,
+                         "traffic_per_solve": recorded_traffic().get("printed_traffic_bytes_per_solve"),
+                         "alg_bytes": "32 B probe per candidate + (48 W + 17) B per new language",
+                         "kernels": "k_solve_fused, then k_solve for levels above 4 Mi candidates"},
             "paper_a100": {"seconds": PAPER_A100_S, "candidates": PAPER_A100_REs,
                            "note": "the paper's own run on an A100 (Table 1); context, not a target"}}
 
