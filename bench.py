@@ -433,6 +433,14 @@ def served_leg(dev, probs, seconds=SERVE_SECONDS):
     with rei.Context(device=dev) as sctx, rei.Server(sctx, budget_bytes=64 << 30, max_live=4096) as srv:
         for t in [srv.submit(p) for p in probs[:64]]:  # warm-up
             srv.result(t)
+        # saturated: all 512 problems at once, instances/s to the last answer
+        t0 = time.perf_counter()
+        tickets = [srv.submit(p) for p in probs]
+        sat = [srv.result(t) for t in tickets]
+        t_sat = time.perf_counter() - t0
+        lat = [r.ms_total for r in sat]
+        out["saturated"] = {"requests": len(probs), "instances_per_s": len(probs) / t_sat,
+                            "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99)}
         for rate in SERVE_RATES:
             arr = poisson_trace(rate, seconds, seed=rate)
             tickets = []
@@ -452,6 +460,10 @@ def served_leg(dev, probs, seconds=SERVE_SECONDS):
     with rei.Context(device=dev) as pctx:
         for p in probs[:16]:
             pctx.solve_problem(p)
+        t0 = time.perf_counter()
+        for p in probs:
+            pctx.solve_problem(p)
+        out["saturated"]["plain_instances_per_s"] = len(probs) / (time.perf_counter() - t0)
         for rate in SERVE_RATES:
             arr = poisson_trace(rate, seconds, seed=rate)
             lat, got = [], []

@@ -198,6 +198,10 @@ void rei_ctx_destroy(rei_ctx *ctx);
  *   REI_OPT_HANDOVER   a level with more candidates than this leaves the
  *                      first (latency-shaped) launch for a relaunch shaped
  *                      for throughput (default 4 Mi; 0 = never)
+ *   REI_OPT_YIELD_US   a batched or served problem still searching on its one
+ *                      CTA after this many microseconds gives up there and
+ *                      is solved again on the whole GPU, like a problem that
+ *                      outgrows its slot (default 2000; 0 = never)
  *   REI_OPT_FUSED_STAGE 1 = stage a problem inside its search launch when the
  *                      launch can hold it (|ic| <= 2048, strings <= 8 KiB;
  *                      the default), 0 = always a separate staging launch.
@@ -211,6 +215,7 @@ void rei_ctx_destroy(rei_ctx *ctx);
 #define REI_OPT_FUSED_STAGE 7
 #define REI_OPT_EXACT_KEYS 8
 #define REI_OPT_HANDOVER 9
+#define REI_OPT_YIELD_US 10
 rei_status rei_ctx_set_option(rei_ctx *ctx, int option, int64_t value);
 
 /* Number of kernels this context launched since it was created. */

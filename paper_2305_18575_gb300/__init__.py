@@ -33,6 +33,7 @@ REI_OPT_SMALL_ROWS = 6
 REI_OPT_FUSED_STAGE = 7
 REI_OPT_EXACT_KEYS = 8
 REI_OPT_HANDOVER = 9
+REI_OPT_YIELD_US = 10
 REI_MAX_IC, REI_MAX_STRLEN, REI_MAX_COST = 4096, 4095, 255
 
 # every entry point include/rei.h declares

@@ -72,6 +72,7 @@ struct rei_ctx {
     int64_t opt_chunk = 0, opt_grid = 0, opt_keep = 0, opt_cache_init = 0, opt_solo_tiles = -1, opt_small_rows = -1;
     int64_t opt_fused = 1, opt_exact = 1;
     uint64_t opt_handover = 1ull << 22;  // levels of more candidates leave the fused launch
+    uint64_t opt_yield_us = 2000;        // batched / served problems longer than this go to the plain path
     size_t smem_sm = 0;  // shared memory per SM
 
     // staging
@@ -1063,6 +1064,7 @@ rei_status rei_ctx_set_option(rei_ctx *c, int option, int64_t value) {
     case REI_OPT_FUSED_STAGE: c->opt_fused = value ? 1 : 0; return REI_OK;
     case REI_OPT_EXACT_KEYS: c->opt_exact = value ? 1 : 0; return REI_OK;
     case REI_OPT_HANDOVER: c->opt_handover = (uint64_t)value; return REI_OK;
+    case REI_OPT_YIELD_US: c->opt_yield_us = (uint64_t)value; return REI_OK;
     case REI_OPT_SMALL_ROWS:
         if (value > 16384 || (value > 0 && (value < 256 || (value & (value - 1))))) return REI_EINVAL;
         c->opt_small_rows = value < 0 ? -1 : value;
@@ -1182,6 +1184,8 @@ rei_status run_batch(rei_ctx *c, const rei_problem *probs, const std::vector<uin
     const uint32_t nb = (uint32_t)sel.size();
     if (kernel_ms) *kernel_ms = 0;
     if (nb == 0) return REI_OK;
+    const double tb0 = now_ms();
+    double tb_up = 0, tb_stage = 0, tb_launch = 0;
     BatchPlan P;
     // host-side bounds of every problem's staged sizes (exact upper bounds)
     for (uint32_t t = 0; t < nb; t++) {
@@ -1275,6 +1279,7 @@ rei_status run_batch(rei_ctx *c, const rei_problem *probs, const std::vector<uin
     }
     CK(cudaMemcpyAsync(c->b_sjobs.p, sj, sizeof(StageJob) * nb, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemsetAsync(c->b_sinfo.p, 0, sizeof(StageInfo) * nb, c->stream));
+    tb_up = now_ms();
     CK(launch_stage((const StageJob *)c->b_sjobs.p, nb, c->stream));
     c->launches++;
     StageInfo *si = (StageInfo *)(hp + std::max(sizeof(StageJob), sizeof(BatchJob)) * nb);
@@ -1286,7 +1291,15 @@ rei_status run_batch(rei_ctx *c, const rei_problem *probs, const std::vector<uin
     uint32_t wmax = 1;
     size_t smem = 0;
     BatchJob *bj = (BatchJob *)hp;  // reuses the staging-job area (already uploaded)
-    for (uint32_t t = 0; t < nb; t++) {
+    // the CTAs take problems in queue order: the widest first, so that the
+    // longest searches start early and the short ones fill in around them
+    std::vector<uint32_t> order(nb);
+    for (uint32_t t = 0; t < nb; t++) order[t] = t;
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+        if (si[x].W != si[y].W) return si[x].W > si[y].W;
+        return si[x].n > si[y].n;
+    });
+    for (uint32_t t : order) {
         const rei_problem &p = probs[sel[t]];
         const StageInfo &I = si[t];
         rei_result &o = outs[sel[t]];
@@ -1396,10 +1409,12 @@ rei_status run_batch(rei_ctx *c, const rei_problem *probs, const std::vector<uin
     A.slot.chunk = chunk;
     A.n = nl;
     A.queue = (uint32_t *)c->b_queue.p;
+    A.yield_ns = c->opt_yield_us * 1000ull;
     CK(cudaMemcpyAsync(c->b_jobs.p, bj, sizeof(BatchJob) * nl, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemsetAsync(c->b_queue.p, 0, 16, c->stream));
     c->slots_clean = false;
     CK(cudaEventRecord(c->ev[0], c->stream));
+    tb_launch = now_ms();
     CK(launch_solve_batch((const BatchJob *)c->b_jobs.p, &A, slots, 32 * warps, smem, c->stream));
     CK(cudaEventRecord(c->ev[1], c->stream));
     c->launches++;
@@ -1412,6 +1427,10 @@ rei_status run_batch(rei_ctx *c, const rei_problem *probs, const std::vector<uin
     float ms = 0;
     CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
     if (kernel_ms) *kernel_ms = ms;
+    if (getenv("REI_PHASES"))
+        fprintf(stderr, "rei batch of %u: upload %.3f ms, staging+jobs %.3f ms, search launch to answers %.3f ms "
+                "(kernel %.3f ms), total %.3f ms\n", nb, tb_up - tb0, tb_launch - tb_up, now_ms() - tb_launch, ms,
+                now_ms() - tb0);
 
     std::vector<uint32_t> redo;
     for (uint32_t k = 0; k < nl; k++) {
@@ -1601,6 +1620,7 @@ rei_status server_setup(rei_server *S) {
     A.stop = (const volatile unsigned long long *)dp + 1;
     A.ring_size = S->ring_size;
     A.idle_ns = 200ull * 1000 * 1000;
+    A.yield_ns = c->opt_yield_us * 1000ull;
     A.smem_cap = S->smem;
     // device memory per slot (rows of up to 64 words: |ic| <= 2048)
     const uint64_t rows = 1ull << 17, chunk = 1ull << 14, wmax = 64;

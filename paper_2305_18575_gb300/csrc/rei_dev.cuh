@@ -176,6 +176,9 @@ struct SolveJob {
     // cmin is the cheapest, below which no expression costs
     uint32_t cmin, leaf_pad;
     uint64_t handover;  // levels above this many candidates end the launch (0 = never)
+    // a search on one CTA of the batched or served form gives up (and is
+    // solved again on the whole GPU) after yield_ns from t_start (0 = never)
+    uint64_t yield_ns, t_start;
     uint16_t leaf_cost[256];
     uint8_t leaf_sym[256];
 };
@@ -236,6 +239,7 @@ struct BatchArgs {
     SlotMem slot;
     uint32_t n;        // problems
     uint32_t *queue;   // next problem to take
+    uint64_t yield_ns; // a problem still searching after this long goes back to the host (0 = never)
 };
 
 // ---- served search
@@ -280,6 +284,7 @@ struct ServeArgs {
     uint32_t ring_size;
     const volatile unsigned long long *avail;  // jobs published (mapped)
     const volatile unsigned long long *stop;   // nonzero: return (mapped)
+    uint64_t yield_ns;  // as BatchArgs::yield_ns
     unsigned long long *head;                  // next job to claim (device)
     unsigned long long idle_ns;
     size_t smem_cap;

@@ -1612,6 +1612,12 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
             __syncthreads();
             continue;
         }
+        // a search on one CTA past its time allowance goes back to the host
+        if (J.yield_ns) {
+            if (tid == 0 && globaltimer_ns() - J.t_start > J.yield_ns) L.status = ST_NEED_MEM;
+            __syncthreads();
+            if (L.status == ST_NEED_MEM) continue;
+        }
         // chunk [pos, pos + C) of the level
         const bool dedup = !full && !otf;
         uint64_t C = T - pos;
@@ -1914,10 +1920,12 @@ __global__ void __launch_bounds__(kFusedThreads, 2) k_solve_fused(const __grid_c
 // tree to J.tree.
 __device__ void solve_in_slot(SolveJob &J, const SlotMem &m, uint32_t slot, BatchOut *out, uint8_t *smem_raw,
                               Plan *s_plan, uint32_t *s_red, uint64_t *s_tiles, unsigned long long *s_found,
-                              uint32_t *s_npend, Lead *L) {
+                              uint32_t *s_npend, Lead *L, uint64_t yield_ns) {
     const uint32_t tid = threadIdx.x;
     const unsigned long long t_start = globaltimer_ns();
     if (tid == 0) {
+        J.yield_ns = yield_ns;
+        J.t_start = t_start;
         const uint64_t so = slot;
         J.cs = m.cs + so * m.cs_words;
         J.bp_op = m.bp_op + so * m.rows;
@@ -2007,7 +2015,8 @@ __global__ void __launch_bounds__(256, 2) k_solve_batch(const BatchJob *jobs, co
             J.tree = bj.tree;
         }
         __syncthreads();
-        solve_in_slot(J, B.slot, blockIdx.x, bj.out, smem_raw, &s_plan, s_red, &s_tiles, &s_found, &s_npend, &L);
+        solve_in_slot(J, B.slot, blockIdx.x, bj.out, smem_raw, &s_plan, s_red, &s_tiles, &s_found, &s_npend, &L,
+                      B.yield_ns);
     }
 }
 
@@ -2162,7 +2171,8 @@ __global__ void __launch_bounds__(256, 2) k_serve(const __grid_constant__ ServeA
         verdict = s_red[0];
         __syncthreads();
         if (verdict == 0) {
-            solve_in_slot(J, A.slot, slot, &o.out, smem_raw, &s_plan, s_red, &s_tiles, &s_found, &s_npend, &L);
+            solve_in_slot(J, A.slot, slot, &o.out, smem_raw, &s_plan, s_red, &s_tiles, &s_found, &s_npend, &L,
+                          A.yield_ns);
         } else if (tid == 0) {
             o.out.status = verdict == 1 ? ST_BAD : ST_NEED_MEM;
         }

@@ -90,3 +90,16 @@ def test_batch_with_per_symbol_costs():
     for k, (a, b) in enumerate(zip(plain, batch)):
         assert key(a) == key(b), k
 
+
+
+@pytest.mark.parametrize("yield_us", [0, 1, 300])
+def test_batch_time_allowance_does_not_change_results(yield_us):
+    """A problem still searching on its CTA after yield_us gives up there and
+    is solved again on the whole GPU (1 us: nearly all do; 0: none does)."""
+    probs = mixed_problems()
+    with rei.Context(device=0) as ctx:
+        plain = [ctx.solve_problem(p) for p in probs]
+        ctx.set_option(rei.REI_OPT_YIELD_US, yield_us)
+        batch = ctx.solve_batch(probs)
+    for k, (a, b) in enumerate(zip(plain, batch)):
+        assert key(a) == key(b), (k, yield_us)

@@ -121,3 +121,15 @@ def test_serve_with_per_symbol_costs():
     for k, (a, b) in enumerate(zip(plain, got)):
         assert key(a) == key(b), k
 
+
+
+@pytest.mark.parametrize("yield_us", [0, 1, 300])
+def test_serve_time_allowance_does_not_change_results(yield_us):
+    probs = mixed_problems()
+    with rei.Context(device=0) as ctx:
+        plain = [ctx.solve_problem(p) for p in probs]
+        ctx.set_option(rei.REI_OPT_YIELD_US, yield_us)
+        with rei.Server(ctx) as srv:
+            got = [srv.result(t) for t in [srv.submit(p) for p in probs]]
+    for k, (a, b) in enumerate(zip(plain, got)):
+        assert key(a) == key(b), (k, yield_us)
