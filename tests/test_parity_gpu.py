@@ -150,6 +150,33 @@ def test_medium_config_matches_oracle(ctx, seed, costs):
     check_same(got, ref, f"medium{seed} {costs}")
 
 
+def _wide_expected():
+    import os
+    rows = []
+    with open(os.path.join(os.path.dirname(__file__), "golden", "wide_expected.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            sd, st, cost, cand, uniq, n_ic, tree = line.split()
+            rows.append((int(sd), int(st), int(cost), int(cand), int(uniq), int(n_ic), bytes.fromhex(tree)))
+    return rows
+
+
+@pytest.mark.parametrize("fused", [1, 0])
+def test_wide_config_matches_stored_oracle_results(fused):
+    """The wide configuration at full size (|ic| 400-480, 16-word languages):
+    every seed's answer, tree and counts equal the oracle's (stored by
+    tests/golden/make_wide_expected.py, which calls only the oracle)."""
+    with rei.Context(device=0) as c:
+        c.set_option(rei.REI_OPT_FUSED_STAGE, fused)
+        for sd, st, cost, cand, uniq, n_ic, tree in _wide_expected():
+            inst = make_config("wide", sd)
+            got = c.solve_problem(rei.Problem(inst.alphabet, inst.pos, inst.neg, max_cost=40,
+                                              mem_budget=inst.mem_budget))
+            assert got.status == ST[st], sd
+            assert (got.cost, got.tree, got.candidates, got.unique, got.n_ic) == (cost, tree, cand, uniq, n_ic), sd
+
+
 @pytest.mark.parametrize("chunk", [1, 7, 100, 4099])
 @pytest.mark.parametrize("grid", [1, 3, 0])
 @pytest.mark.parametrize("solo", [-1, 0, 1 << 30])
