@@ -12,6 +12,8 @@ is importable, supplies device memory (its caching allocator, through the
 from __future__ import annotations
 
 import ctypes as C
+import itertools
+import struct
 import os
 from dataclasses import dataclass, field
 from typing import List, Optional, Sequence
@@ -163,10 +165,15 @@ def rei_ctx_launches(ctx) -> int:
 
 def rei_solve(ctx, alphabet: bytes, P: Sequence[bytes], N: Sequence[bytes], costs, max_cost: int,
               mem_budget: int, out: rei_result) -> int:
-    keep = [C.create_string_buffer(bytes(s), max(len(s), 1)) for s in list(P) + list(N)]
-    arr = (rei_str * max(len(keep), 1))()
-    for i, (s, b) in enumerate(zip(list(P) + list(N), keep)):
-        arr[i] = rei_str(C.cast(b, C.c_void_p), len(s))
+    strs = list(P) + list(N)
+    n = len(strs)
+    keep = C.create_string_buffer(b"".join(strs))  # every string, back to back
+    base = C.addressof(keep)
+    lens = [len(x) for x in strs]
+    starts = list(itertools.accumulate(lens, initial=base))[:n]
+    # the rei_str array {pointer, length} in one pack
+    flat = [v for pair in zip(starts, lens) for v in pair]
+    arr = (rei_str * max(n, 1)).from_buffer_copy(struct.pack("<" + "QI4x" * n, *flat) or bytes(C.sizeof(rei_str)))
     nP = len(P)
     pP = C.cast(arr, C.POINTER(rei_str))
     pN = C.cast(C.byref(arr, nP * C.sizeof(rei_str)), C.POINTER(rei_str))

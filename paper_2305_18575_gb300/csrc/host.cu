@@ -1185,7 +1185,7 @@ rei_status run_batch(rei_ctx *c, const rei_problem *probs, const std::vector<uin
     if (kernel_ms) *kernel_ms = 0;
     if (nb == 0) return REI_OK;
     const double tb0 = now_ms();
-    double tb_up = 0, tb_stage = 0, tb_launch = 0;
+    double tb_up = 0, tb_launch = 0;
     BatchPlan P;
     // host-side bounds of every problem's staged sizes (exact upper bounds)
     for (uint32_t t = 0; t < nb; t++) {

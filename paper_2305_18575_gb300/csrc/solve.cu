@@ -1532,6 +1532,45 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
 
     bool found = false;
     uint32_t planned = 0xFFFFFFFFu;  // the level whose plan is in S.seg / s_plan
+    // end of a level (thread 0): count it, check the cache cap, enter the next one
+    auto end_level = [&](uint32_t level, uint32_t nseg) {
+        uint64_t vc = 0;
+        for (uint32_t s = 0; s < nseg; s++) {
+            const uint64_t v = valid_count(S.seg[s]);
+            vc += v;
+            L.cand_op[S.seg[s].op] += v;
+        }
+        L.candidates += vc;
+        uint32_t next_status = ST_RUNNING;
+        if (!L.otf) {
+            if (L.full) {
+                if (J.flags & REI_F_ONTHEFLY) {
+                    L.otf = 1;
+                    L.partial_level = level;
+                } else {
+                    next_status = ST_OOM;
+                }
+            } else {
+                L.unique_done = L.size;
+            }
+        }
+        const uint32_t nl = level + 1;
+        if (next_status == ST_RUNNING) {
+            if (nl > J.max_cost) {
+                next_status = ST_NOT_FOUND;
+            } else {
+                S.lvs[nl] = L.size;
+                S.lvc[nl] = 0;
+                J.lvl_start[nl] = L.size;
+                J.lvl_count[nl] = 0;
+                if (L.otf && max_operand_level(J, (int)nl) >= (int)L.partial_level) next_status = ST_OOM;
+            }
+        }
+        L.level = next_status == ST_RUNNING ? nl : level;
+        L.chunk_pos = 0;
+        L.full = 0;
+        L.status = next_status;
+    };
     // per-phase wall time of the leader (ns): plan, solo chunk, team chunk, level end
     unsigned long long tm[4] = {0, 0, 0, 0}, tcnt[3] = {0, 0, 0};
     for (;;) {
@@ -1556,44 +1595,8 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
         const uint64_t T = s_plan.total;
 
         if (pos >= T) {
-            // end of level: count it, check the cache cap, enter the next one
             if (tid == 0) {
-                uint64_t vc = 0;
-                for (uint32_t s = 0; s < nseg; s++) {
-                    const uint64_t v = valid_count(S.seg[s]);
-                    vc += v;
-                    L.cand_op[S.seg[s].op] += v;
-                }
-                L.candidates += vc;
-                uint32_t next_status = ST_RUNNING;
-                if (!otf) {
-                    if (full) {
-                        if (J.flags & REI_F_ONTHEFLY) {
-                            L.otf = 1;
-                            L.partial_level = level;
-                        } else {
-                            next_status = ST_OOM;
-                        }
-                    } else {
-                        L.unique_done = size;
-                    }
-                }
-                const uint32_t nl = level + 1;
-                if (next_status == ST_RUNNING) {
-                    if (nl > J.max_cost) {
-                        next_status = ST_NOT_FOUND;
-                    } else {
-                        S.lvs[nl] = size;
-                        S.lvc[nl] = 0;
-                        J.lvl_start[nl] = size;
-                        J.lvl_count[nl] = 0;
-                        if (L.otf && max_operand_level(J, (int)nl) >= (int)L.partial_level) next_status = ST_OOM;
-                    }
-                }
-                L.level = next_status == ST_RUNNING ? nl : level;
-                L.chunk_pos = 0;
-                L.full = 0;
-                L.status = next_status;
+                end_level(level, nseg);
                 tm[3] += globaltimer_ns() - t_it;
                 tcnt[2]++;
             }
@@ -1671,7 +1674,10 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
             found = true;
             break;
         }
-        if (tid == 0) L.chunk_pos = a.ce0;
+        if (tid == 0) {
+            L.chunk_pos = a.ce0;
+            if (a.ce0 >= T) end_level(level, nseg);  // the level's last chunk
+        }
         __syncthreads();
     }
 
