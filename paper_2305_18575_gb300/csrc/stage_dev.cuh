@@ -220,13 +220,6 @@ __device__ inline void block_bitonic_sort(unsigned long long *key, uint32_t m) {
     __syncthreads();
 }
 
-// a coherent 64-bit load through a generic address (shared or global)
-__device__ __forceinline__ uint64_t ld_strong_u64(const uint64_t *p) {
-    uint64_t v;
-    asm volatile("ld.relaxed.gpu.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
 // step timing (ns, in StageInfo::pad), compiled in with -DREI_TIMING only
 #ifdef REI_TIMING
 #define STAGE_MARK(k)                                                              \
@@ -328,7 +321,7 @@ __device__ inline void stage_run(const StageJob &J, const StageSmem &M) {
                 const uint64_t want = tag | p;
                 uint32_t q = (uint32_t)f & mask;
                 for (uint32_t probe = 0; probe < M.hcap; probe++) {
-                    uint64_t v = ld_strong_u64(&hset[q]);
+                    uint64_t v = *(volatile const uint64_t *)&hset[q];  // (shared memory: CTA-coherent)
                     if (v == kEmpty) {
                         const unsigned long long old =
                             atomicCAS((unsigned long long *)&hset[q], kEmpty, want);
