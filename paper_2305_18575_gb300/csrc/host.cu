@@ -721,9 +721,13 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
     grid = (uint32_t)(c->sm_count * bps);
     if (c->opt_grid > 0 && (uint32_t)c->opt_grid < grid) grid = (uint32_t)c->opt_grid;
 
+    // a chunk costs a fixed ~15 us of barriers and bookkeeping, so the
+    // large levels this launch runs take chunks of up to 32 Mi candidates
+    // (at most 1 GiB of candidate rows in tmp; the chunk that holds the
+    // answer still runs to its end, which bounds the size from above)
     uint64_t chunk_max = c->opt_chunk > 0 ? (uint64_t)c->opt_chunk
-                                          : std::min<uint64_t>(1ull << 22, std::max<uint64_t>(1ull << 16, (1ull << 28) / (4ull * W)));
-    chunk_max = std::min<uint64_t>(chunk_max, 1ull << 24);
+                                          : std::min<uint64_t>(1ull << 25, std::max<uint64_t>(1ull << 16, (1ull << 30) / (4ull * W)));
+    chunk_max = std::min<uint64_t>(chunk_max, 1ull << 26);
     uint64_t cache_alloc = c->opt_cache_init > 0 ? (uint64_t)c->opt_cache_init : (1ull << 16);
     if (c->opt_cache_init <= 0 && c->cs.p && c->bp_l.p && c->bp_r.p && c->bp_op.p) {
         // rows a previous solve already allocated (up to 1 Mi, so that the
