@@ -355,9 +355,10 @@ constexpr uint32_t kSmPending = 0x10000u;
 // uniqueness insert of candidate xl while the languages live in shared
 // memory: the same protocol as dedup_insert_solo on a 32-bit table whose
 // entries are fp (15 bits) << 17 | pending << 16 | row or candidate
+template <uint32_t WT>
 __device__ void dedup_insert_smem(const TileCtx &T, const uint32_t *c, uint32_t xl) {
     const Shared &S = *T.S;
-    const uint32_t W = T.W;
+    const uint32_t W = WT ? WT : T.W;
     const uint64_t h = cs_hash(c, W, 1);
     const uint32_t fp = (uint32_t)(h >> 49);  // 15 bits
     const uint32_t mine = (fp << 17) | kSmPending | xl;
@@ -398,9 +399,10 @@ __device__ void dedup_insert_smem(const TileCtx &T, const uint32_t *c, uint32_t 
 // the probe; a candidate that takes an empty slot, or replaces a later
 // pending holder of the same language, is marked in T.bits with its slot in
 // T.ent; the append keeps the marks whose slot still names them.
+template <uint32_t WT>
 __device__ void dedup_insert_solo(const TileCtx &T, const uint32_t *c, uint32_t xl) {
     const SolveJob &J = *T.J;
-    const uint32_t W = T.W;
+    const uint32_t W = WT ? WT : T.W;
     const uint64_t h = cs_hash(c, W, 1);
     const uint32_t fp = (uint32_t)(h >> 32);
     const unsigned long long mine = ((uint64_t)fp << 32) | kPending | xl;
@@ -447,10 +449,12 @@ __device__ __forceinline__ unsigned long long exact_key(const uint32_t *c, uint3
 // claimed with a CAS and every candidate with it lowers minidx[slot] (a
 // reduction, no round trip); `mark` (a small chunk on one CTA) records the
 // claimants in T.bits / T.ent, else the claimed slot joins the pending list
+template <uint32_t WT>
 __device__ void dedup_insert_exact(const TileCtx &T, const uint32_t *c, uint32_t xl) {
     const SolveJob &J = *T.J;
-    const unsigned long long key = exact_key(c, T.W), pk = key | kXPend;
-    const uint64_t h = cs_hash(c, T.W, 1);
+    const uint32_t W = WT ? WT : T.W;
+    const unsigned long long key = exact_key(c, W), pk = key | kXPend;
+    const uint64_t h = cs_hash(c, W, 1);
     uint64_t p = h & J.table_mask;
     for (uint64_t probe = 0; probe <= J.table_mask; probe++) {
         unsigned long long v = ld_relaxed_u64(&J.table[p]);
@@ -487,9 +491,10 @@ __device__ void dedup_insert_exact(const TileCtx &T, const uint32_t *c, uint32_t
 }
 
 // uniqueness insert of candidate xl (chunk-local) whose CS is c[b * 1] (smem)
+template <uint32_t WT>
 __device__ void dedup_insert(const TileCtx &T, const uint32_t *c, uint32_t xl) {
     const SolveJob &J = *T.J;
-    const uint32_t W = T.W;
+    const uint32_t W = WT ? WT : T.W;
     const uint64_t h = cs_hash(c, W, 1);
     const uint32_t fp = (uint32_t)(h >> 32);
     const uint64_t mine = ((uint64_t)fp << 32) | kPending | xl;
@@ -542,12 +547,14 @@ __device__ void dedup_insert(const TileCtx &T, const uint32_t *c, uint32_t xl) {
 }
 
 // build the CSs of one tile into A (candidate-major, row stride Ws), then test
-// precision and insert; lanes with !valid only help with the warp collectives
+// precision and insert; lanes with !valid only help with the warp collectives.
+// WT > 0 fixes the language width at compile time (W = WT), 0 reads it from T.
+template <uint32_t WT>
 __device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uint64_t tile, uint32_t *wm) {
     const SolveJob &J = *T.J;
     const Shared &S = *T.S;
     const uint32_t lane = threadIdx.x & 31;
-    const uint32_t W = T.W, Ws = T.Ws, n = T.n;
+    const uint32_t W = WT ? WT : T.W, Ws = WT ? ((WT & 1u) ? WT : WT + 1) : T.Ws, n = T.n;
     uint32_t *lw = wm;
     uint32_t *A = wm + ((W + 3) & ~3u);
     uint32_t *B = A + 32 * Ws;
@@ -712,10 +719,10 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uin
     REI_TMARK(tmk, 8);
     if (T.dedup) {
         const uint32_t xl = (uint32_t)(xlev - T.chunk_start);
-        if (T.smem) dedup_insert_smem(T, c, xl);
-        else if (J.exact) dedup_insert_exact(T, c, xl);
-        else if (T.bits) dedup_insert_solo(T, c, xl);
-        else dedup_insert(T, c, xl);
+        if (T.smem) dedup_insert_smem<WT>(T, c, xl);
+        else if (J.exact) dedup_insert_exact<WT>(T, c, xl);
+        else if (T.bits) dedup_insert_solo<WT>(T, c, xl);
+        else dedup_insert<WT>(T, c, xl);
     }
     REI_TMARK(tmk, 9);
 }
@@ -1122,7 +1129,9 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
             while (s + 1 < a.nseg && S.tile_first[s + 1] <= t) s++;
             const SegTile &tl = S.tiles[s];
             if (tl.lo >= tl.hi) continue;
-            run_tile(TC, S.seg[s], tl, t - S.tile_first[s], wm);
+            if (W == 1) run_tile<1>(TC, S.seg[s], tl, t - S.tile_first[s], wm);
+            else if (W == 2) run_tile<2>(TC, S.seg[s], tl, t - S.tile_first[s], wm);
+            else run_tile<0>(TC, S.seg[s], tl, t - S.tile_first[s], wm);
             __syncwarp();
         }
     }
