@@ -657,7 +657,21 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uin
             for (uint32_t b = 0; b < W; b++) {
                 const uint32_t w = 32 * b + lane;
                 uint32_t acc = 0;
-                if (w < n) {
+                if (WT == 1 || WT == 2) {
+                    // the shared operand's words in registers
+                    if (w < n) {
+                        const uint32_t l0 = lw[0], l1 = WT == 2 ? lw[1] : 0u;
+                        const uint32_t p1 = go[w + 1];
+                        const uint32_t sh = swapped ? 16u : 0u;  // which half of a pair indexes the shared operand
+#pragma unroll 4
+                        for (uint32_t p = go[w]; p < p1; p++) {
+                            const uint32_t pr = gp[p];
+                            const uint32_t k = (pr >> sh) & 0xFFFFu, o = (pr >> (16u - sh)) & 0xFFFFu;
+                            const uint32_t lv = (WT == 2 && (k & 32u)) ? l1 : l0;
+                            acc |= B[o] & (0u - ((lv >> (k & 31u)) & 1u));
+                        }
+                    }
+                } else if (w < n) {
                     const uint32_t p1 = go[w + 1];
                     if (!swapped) {
 #pragma unroll 4
