@@ -130,7 +130,8 @@ struct SolveState {
     uint64_t t_phase[4];
     uint64_t n_phase[3];
     uint64_t t_sub[16];  // steps of CTA 0's chunks and launch (timing builds only)
-    uint32_t pad[2];
+    uint32_t tile_next;  // the next tile of a team chunk handed out dynamically
+    uint32_t pad;
 };
 
 struct SolveJob {

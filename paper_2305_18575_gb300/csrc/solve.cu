@@ -1105,6 +1105,11 @@ __device__ void solo_append(const SolveJob &J, SolveState *st, Shared &S, const 
     REI_TMARK(true, 5);
 }
 
+// a chunk with at least this many tiles per warp hands its tiles out
+// dynamically, kGrab at a time
+constexpr uint32_t kDynTilesPerWarp = 32;
+constexpr uint32_t kGrab = 4;
+
 // one chunk of candidates; returns 1 when a precise candidate was found in it,
 // 0 when done, -1 when a grid barrier gave up
 __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const ChunkArgs &a, bool full,
@@ -1136,17 +1141,41 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
     {
         TileCtx TC{&J, st, &S, a.cs0, W, Ws, n, dedup, full, small ? s_found : &st->found,
                    small ? S.sortbuf : nullptr, small ? S.solo_bits : nullptr, sm ? S.sm_rows : J.cs, sm};
-        const uint64_t ntiles = *s_tiles;
-        const uint64_t gw = (uint64_t)team_r * nwarps + wid, nw = (uint64_t)team_n * nwarps;
+        // (a chunk's tiles, at most 2^26 / 32 plus one per segment, fit 32 bits)
+        const uint32_t ntiles = (uint32_t)*s_tiles;
+        const uint32_t gw = team_r * nwarps + wid, nw = team_n * nwarps;
         uint32_t s = 0;
-        for (uint64_t t = gw; t < ntiles; t += nw) {
+        // many tiles per warp: hand them out kGrab at a time from a counter,
+        // so that every warp ends within a few tiles of the others (the
+        // order of tiles does not change any result); the next grab is in
+        // flight while the warp works on the current one.  Else tile t goes
+        // to warp t mod (warps of the team).
+        const bool dyn = full && ntiles >= kDynTilesPerWarp * nw;
+        uint32_t t = gw, end = ntiles, step = nw;
+        uint32_t nxt = 0;
+        if (dyn) {
+            uint32_t cur = 0;
+            if (lane == 0) cur = atomicAdd(&st->tile_next, kGrab);
+            t = __shfl_sync(0xFFFFFFFFu, cur, 0);
+            end = min(t + kGrab, ntiles);
+            step = 1;
+            if (lane == 0 && t < ntiles) nxt = atomicAdd(&st->tile_next, kGrab);
+        }
+        while (t < ntiles) {
             while (s + 1 < a.nseg && S.tile_first[s + 1] <= t) s++;
             const SegTile &tl = S.tiles[s];
-            if (tl.lo >= tl.hi) continue;
-            if (W == 1) run_tile<1>(TC, S.seg[s], tl, t - S.tile_first[s], wm);
-            else if (W == 2) run_tile<2>(TC, S.seg[s], tl, t - S.tile_first[s], wm);
-            else run_tile<0>(TC, S.seg[s], tl, t - S.tile_first[s], wm);
-            __syncwarp();
+            if (tl.lo < tl.hi) {
+                if (W == 1) run_tile<1>(TC, S.seg[s], tl, t - S.tile_first[s], wm);
+                else if (W == 2) run_tile<2>(TC, S.seg[s], tl, t - S.tile_first[s], wm);
+                else run_tile<0>(TC, S.seg[s], tl, t - S.tile_first[s], wm);
+                __syncwarp();
+            }
+            t += step;
+            if (dyn && t >= end) {
+                t = __shfl_sync(0xFFFFFFFFu, nxt, 0);
+                end = min(t + kGrab, ntiles);
+                if (lane == 0 && t < ntiles) nxt = atomicAdd(&st->tile_next, kGrab);
+            }
         }
     }
     if (!team_barrier(full, st, bar_epoch, 5, J.trace)) return -1;
@@ -1679,6 +1708,7 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
         if (tid == 0) tm[0] += t_chunk - t_it;
         if (team) {
             if (tid == 0) {
+                st->tile_next = 0;  // (every CTA left the previous chunk's tiles at its barriers)
                 st->c_level = a.level;
                 st->c_size = a.size;
                 st->c_dedup = a.dedup;
