@@ -433,8 +433,9 @@ class Context:
                        pos=list(pm[:Wn]), neg=list(nm[:Wn]),
                        leaf=[list(lf[a * W: a * W + Wn]) for a in range(prob.p.n_sym)])
 
-    def cache_dump(self, n_levels: int):
-        """(cs words per row, op, left, right, level_start, level_count) of the last solve."""
+    def cache_dump(self, n_levels: int, raw: bool = False):
+        """(cs words per row, op, left, right, level_start, level_count) of the last solve;
+        raw=True gives the four arrays as little-endian bytes instead of lists."""
         cnt = C.c_uint64(0)
         s = rei_cache_dump(self.h, None, None, None, None, cnt, None, None, 0)
         if s not in (REI_OK, REI_EBUFSZ):
@@ -453,6 +454,8 @@ class Context:
                            n_levels)
         if s != REI_OK:
             raise RuntimeError(f"rei_cache_dump: {STATUS_NAMES.get(s, s)}")
+        if raw:
+            return (bytes(cs)[:4 * k * W], bytes(op)[:k], bytes(lf)[:4 * k], bytes(rt)[:4 * k], list(ls), list(lc))
         rows = [list(cs[i * W:(i + 1) * W]) for i in range(k)]
         return rows, list(op[:k]), list(lf[:k]), list(rt[:k]), list(ls), list(lc)
 

@@ -422,6 +422,27 @@ def test_cache_contents_match_oracle(ctx):
             assert (ls[c], lc[c]) == run.level(c), c
 
 
+def test_dynamic_tile_handout_keeps_results_and_cache():
+    """A chunk of at least 32 tiles per warp of the grid hands its tiles out
+    from a counter, in an order that varies from run to run; the order must not
+    change anything.  The printed specification searched to cost 22 (levels of
+    tens of millions of candidates, chunks of up to 32 Mi) gives the same result
+    and the same cache, row for row, as with chunks of 1 Mi candidates (32 Ki
+    tiles, below 32 per warp: the fixed round robin)."""
+    out = []
+    for chunk in (0, 1 << 20):
+        with rei.Context(device=0) as c:
+            if chunk:
+                c.set_option(rei.REI_OPT_CHUNK, chunk)
+            got = c.solve_keep(rei.Problem(A01, PIN_P, PIN_N, max_cost=22, mem_budget=64 << 30))
+            out.append((got, c.cache_dump(23, raw=True)))
+    (a, ca), (b, cb) = out
+    assert a.status == b.status == rei.REI_NOT_FOUND
+    assert (a.candidates, a.unique, a.levels) == (b.candidates, b.unique, b.levels)
+    assert a.candidates > 5e7   # levels large enough for the counter
+    assert ca == cb
+
+
 def test_device_input_matches_host_input(ctx):
     inst = make_config("medium", 5)
     host = ctx.solve_problem(rei.Problem(inst.alphabet, inst.pos, inst.neg, max_cost=40))
