@@ -1301,24 +1301,41 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
             cta_cnt += s_red[k];
         }
         const uint64_t limit = J.cache_alloc < J.cap ? J.cache_alloc : J.cap;
-        constexpr uint32_t kListMax = 2 * kSortMax;  // this CTA's survivors listed in shared memory
-        if (cta_cnt <= kListMax) {
-            // the CTA's survivors in order into a shared list, then rows and
-            // back-pointers spread over all its threads with loads batched
-            uint32_t *list = reinterpret_cast<uint32_t *>(S.sortbuf);
-            uint32_t pos = wbefore + x - mycnt;
-            for (uint64_t w = t0; w < t1; w++) {
-                uint32_t bits = ldcg(J.bitmap + w);
-                J.bitmap[w] = 0;
-                while (bits) {
-                    list[pos++] = (uint32_t)(w * 32 + (__ffs(bits) - 1));
-                    bits &= bits - 1;
+        constexpr uint32_t kListMax = 2 * kSortMax;  // survivors listed in shared memory per round
+        // the CTA's survivors in order, kListMax at a time, into a shared
+        // list; then rows and back-pointers spread over all its threads with
+        // loads batched.  A thread's survivors have the consecutive CTA-local
+        // ranks [pos, my_end); it lists those of each round's window.
+        uint32_t *list = reinterpret_cast<uint32_t *>(S.sortbuf);
+        uint32_t pos = wbefore + x - mycnt;
+        const uint32_t my_end = wbefore + x;
+        uint64_t w = t0;
+        uint32_t bits = 0;
+        if (mycnt) {
+            bits = ldcg(J.bitmap + w);
+            J.bitmap[w] = 0;
+        }
+        const uint64_t base = (uint64_t)a.size + s_pref;  // cache row of this CTA's first survivor
+        const uint32_t fit = base >= limit ? 0u : (uint32_t)umin64(cta_cnt, limit - base);
+        const uint32_t nt = blockDim.x;
+        for (uint32_t lo = 0; lo < cta_cnt; lo += kListMax) {
+            const uint32_t hi = min(cta_cnt, lo + kListMax);
+            const uint32_t stop = min(hi, my_end);
+            while (pos < stop) {
+                while (bits == 0 && w + 1 < t1) {
+                    w++;
+                    bits = ldcg(J.bitmap + w);
+                    J.bitmap[w] = 0;
                 }
+                list[pos - lo] = (uint32_t)(w * 32 + (__ffs(bits) - 1));
+                bits &= bits - 1;
+                pos++;
             }
             __syncthreads();
-            const uint64_t base = (uint64_t)a.size + s_pref;  // cache row of this CTA's first survivor
-            const uint32_t fit = base >= limit ? 0u : (uint32_t)umin64(cta_cnt, limit - base);
-            const uint32_t nt = blockDim.x, nf = J.exact ? 0u : fit * W;  // (exact keys: rows from the keys)
+            const uint32_t cnt = hi - lo;                           // listed this round
+            const uint32_t nfit = fit > lo ? min(fit - lo, cnt) : 0u;  // of them, cached
+            const uint64_t b0 = base + lo;
+            const uint32_t nf = J.exact ? 0u : nfit * W;  // (exact keys: rows from the keys)
             for (uint32_t f0 = tid; f0 < nf; f0 += 4 * nt) {
                 uint32_t v[4];
 #pragma unroll
@@ -1334,33 +1351,33 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
                     const uint32_t f = f0 + u * nt;
                     if (f < nf) {
                         const uint32_t i = f / W, b = f - i * W;
-                        J.cs[(base + i) * W + b] = v[u];
+                        J.cs[(b0 + i) * W + b] = v[u];
                     }
                 }
             }
-            for (uint32_t i0 = tid; i0 < cta_cnt; i0 += 4 * nt) {
+            for (uint32_t i0 = tid; i0 < cnt; i0 += 4 * nt) {
                 uint32_t q[4];
                 unsigned long long old[4];
 #pragma unroll
                 for (int u = 0; u < 4; u++) {
                     const uint32_t i = i0 + u * nt;
-                    if (i < cta_cnt) q[u] = ldcg(J.slotpos + list[i]);
+                    if (i < cnt) q[u] = ldcg(J.slotpos + list[i]);
                 }
 #pragma unroll
                 for (int u = 0; u < 4; u++) {
                     const uint32_t i = i0 + u * nt;
-                    if (i < fit) old[u] = ld_relaxed_u64(J.table + q[u]);
+                    if (i < nfit) old[u] = ld_relaxed_u64(J.table + q[u]);
                 }
 #pragma unroll
                 for (int u = 0; u < 4; u++) {
                     const uint32_t i = i0 + u * nt;
-                    if (i >= cta_cnt) continue;
-                    if (i >= fit) {
+                    if (i >= cnt) continue;
+                    if (i >= nfit) {
                         J.table[q[u]] = kEmpty;  // not cached: free the slot
                         if (J.exact) J.minidx[q[u]] = 0xFFFFFFFFu;
                         continue;
                     }
-                    const uint64_t k = base + i;
+                    const uint64_t k = b0 + i;
                     uint32_t op, l, r;
                     decode(S.seg, a.nseg, J.leaf_sym, a.cs0 + list[i], op, l, r);
                     J.bp_op[k] = (uint8_t)op;
@@ -1378,46 +1395,7 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
                     J.used[k] = q[u];
                 }
             }
-        } else {
-            // many survivors in this CTA's range: each thread appends its own
-            uint64_t rank = s_pref + wbefore + x - mycnt;
-            for (uint64_t w = t0; w < t1; w++) {
-                uint32_t bits = ldcg(J.bitmap + w);
-                J.bitmap[w] = 0;
-                while (bits) {
-                    const uint32_t bit = __ffs(bits) - 1;
-                    bits &= bits - 1;
-                    const uint32_t j = (uint32_t)(w * 32 + bit);
-                    const uint64_t k = (uint64_t)a.size + rank;
-                    rank++;
-                    if (k >= limit) {
-                        const uint32_t q = ldcg(J.slotpos + j);
-                        J.table[q] = kEmpty;  // not cached: free the slot
-                        if (J.exact) J.minidx[q] = 0xFFFFFFFFu;
-                        continue;
-                    }
-                    uint32_t *dst = J.cs + k * W;
-                    const uint32_t q = ldcg(J.slotpos + j);
-                    const unsigned long long old = ld_relaxed_u64(J.table + q);
-                    if (J.exact) {
-                        const unsigned long long key = old & ~kXPend;
-                        dst[0] = (uint32_t)key;
-                        if (W == 2) dst[1] = (uint32_t)(key >> 32);
-                        J.table[q] = key;
-                        J.minidx[q] = 0xFFFFFFFFu;
-                    } else {
-                        const uint32_t *srcp = J.tmp + (uint64_t)j * W;
-                        for (uint32_t b = 0; b < W; b++) dst[b] = ldcg(srcp + b);
-                        J.table[q] = (old & 0xFFFFFFFF00000000ull) | (uint32_t)k;
-                    }
-                    uint32_t op, l, r;
-                    decode(S.seg, a.nseg, J.leaf_sym, a.cs0 + j, op, l, r);
-                    J.bp_op[k] = (uint8_t)op;
-                    J.bp_l[k] = l;
-                    J.bp_r[k] = r;
-                    J.used[k] = q;
-                }
-            }
+            __syncthreads();  // (the list is refilled next round)
         }
         __syncthreads();
         if (team_r == 0 && tid == 0) {
