@@ -327,6 +327,8 @@ def run_gpu(args, rank, world, local_rank):
     if not args.no_batch:
         bprobs = batched_problems()
         line["batched"] = batched_leg(ctx, dev, bprobs)
+        if not args.no_cpu_baseline:
+            line["batched"]["cpu_oracle"] = cpu_batched_baseline(line["batched"]["mean_candidates"])
         line["served"] = served_leg(dev, bprobs, args.serve_seconds)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
@@ -372,8 +374,43 @@ def batched_leg(ctx, dev, probs):
     return {"workload": BATCH_WORKLOAD, "instances": len(probs),
             "instances_per_s": len(probs) / t_batch, "sequential_instances_per_s": len(probs) / t_seq,
             "speedup_vs_sequential": t_seq / t_batch, "batch_ms": 1000 * t_batch, "sequential_ms": 1000 * t_seq,
-            "candidates_per_s": cands / t_batch,
+            "candidates_per_s": cands / t_batch, "mean_candidates": cands / len(res),
             "solve_ms_p50": lat[len(lat) // 2], "solve_ms_p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
+
+
+def _oracle_batched_one(task):
+    seed, cap = task
+    import oracle
+    from workloads.gen import batched_instance
+    i = batched_instance(seed)
+    r = oracle.solve(i.alphabet, i.pos, i.neg, costs=(1, 1, 1, 1, 1), max_cost=40, mem_budget=1 << 30,
+                     max_candidates=cap)
+    return r.candidates
+
+
+def _noop(_):
+    return 0
+
+
+def cpu_batched_baseline(mean_candidates: float):
+    """The oracle on every host core, one batched-workload instance per core at
+    a time (a bounded sample: each instance stopped after `cap` candidates); its
+    candidates/s over the wall time of the sample, and the instances/s that rate
+    gives at the workload's mean candidates per instance (from the GPU results)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    cap = 20000
+    tasks = [(s, cap) for s in range(2 * cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_noop, range(cores))  # workers started before the clock
+        t0 = time.perf_counter()
+        cands = sum(pool.map(_oracle_batched_one, tasks, chunksize=1))
+        wall = time.perf_counter() - t0
+    cps = cands / wall if wall else None
+    return {"candidates_per_s": cps, "cores": cores, "kind": "oracle",
+            "instances_per_s_est": cps / mean_candidates if cps and mean_candidates else None,
+            "sample": f"instances 0-{len(tasks) - 1} of the batched workload, each stopped after {cap} "
+                      f"candidates ({cands} candidates, {wall:.1f} s wall, {cores} processes)"}
 
 
 PAPER_WORKLOAD = ("the specification printed in Sec. 6 (Table 1, Type 1 No 50): 10 positive and 12 negative "
