@@ -517,7 +517,7 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
     int bps = 0;
     CK(solve_fused_occupancy(threads, smem, &bps));
     if (bps < 1) return REI_EBUSY;
-    uint32_t grid = (uint32_t)(c->sm_count * bps);
+    uint32_t grid = std::min<uint32_t>((uint32_t)(c->sm_count * bps), kMaxTeam);
     if (c->opt_grid > 0 && (uint32_t)c->opt_grid < grid) grid = (uint32_t)c->opt_grid;
     if ((s = ensure(c, c->blk, 4ull * grid))) return s;
     if ((s = ensure(c, c->lvl_start, 8ull * (max_cost + 2)))) return s;
@@ -718,7 +718,7 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
     int bps = 0;
     CK(solve_occupancy(threads, smem, &bps));
     if (bps < 1) return REI_ECUDA;
-    grid = (uint32_t)(c->sm_count * bps);
+    grid = std::min<uint32_t>((uint32_t)(c->sm_count * bps), kMaxTeam);
     if (c->opt_grid > 0 && (uint32_t)c->opt_grid < grid) grid = (uint32_t)c->opt_grid;
 
     // a chunk costs a fixed ~15 us of barriers and bookkeeping, so the

@@ -332,7 +332,7 @@ extern "C" rei_status rei_solve_noalloc(const rei_problem *p, void *stream_v, re
     int bps = 0;
     NA_CK(solve_occupancy(32 * warps, smem, &bps));
     if (bps < 1) return REI_ECUDA;
-    const uint32_t grid = std::min<uint32_t>(kMaxGrid, (uint32_t)(prop.multiProcessorCount * bps));
+    const uint32_t grid = std::min<uint32_t>(kMaxTeam, (uint32_t)(prop.multiProcessorCount * bps));
 
     // what must start cleared: table, survivor bitmap, level sizes
     NA_CK(cudaMemsetAsync(d_table, 0xFF, 8ull * tslots, stream));

@@ -23,6 +23,7 @@ constexpr uint32_t kMaxWords = (REI_MAX_IC + 31) / 32;
 constexpr uint32_t kMaxCost = REI_MAX_COST;
 constexpr uint64_t kEmpty = ~0ull;
 constexpr uint32_t kPending = 0x80000000u;
+constexpr uint32_t kMaxTeam = 2047;  // CTAs of a plain search launch at most (the ordered append's prefix table)
 constexpr uint32_t kNoRight = 0xFFFFFFFFu;
 constexpr unsigned long long kNone = ~0ull;
 

@@ -836,6 +836,7 @@ __device__ uint32_t emit_tree(const SolveJob &J, uint32_t op, uint32_t l, uint32
 constexpr uint32_t kFusedThreads = 256;
 constexpr uint32_t kSolveThreads = 512;
 constexpr uint32_t kSortMax = 2048;  // candidates of a chunk CTA 0 runs with shared-memory bookkeeping
+static_assert(kMaxTeam < kSortMax, "the append's prefix table of per-CTA counts lives in sortbuf");
 
 __host__ __device__ size_t solve_smem_bytes(uint32_t W, uint32_t n, uint32_t G, uint32_t max_len,
                                             uint32_t seg_cap, bool gt_in_smem, uint32_t warps, uint32_t small_rows) {
@@ -1235,7 +1236,11 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
     if (!team_barrier(full, st, bar_epoch, 7, J.trace)) return -1;
     REI_TMARK(full && blockIdx.x == 0, 13);
 
-    // ---- phase C: survivors per CTA (contiguous word ranges of the bitmap)
+    // ---- phase C: survivors per CTA (contiguous word ranges of the bitmap),
+    // counted, then listed in order into pending[] over the CTA's own range
+    // of candidates (phase B has read the pending list; the k-th survivor of
+    // a range starting at candidate w0 * 32 is a candidate >= w0 * 32 + k, so
+    // the lists stay inside their ranges); the bitmap is cleared on the way
     const uint64_t nwords = (C + 31) / 32;
     const uint64_t per_cta = (nwords + team_n - 1) / team_n;
     const uint64_t w0 = umin64(nwords, team_r * per_cta);
@@ -1246,48 +1251,6 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
     uint32_t mycnt = 0;
     for (uint64_t w = t0; w < t1; w++) mycnt += __popc(ldcg(J.bitmap + w));
     {
-        uint32_t v = mycnt;
-        for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, d);
-        if (lane == 0) s_red[wid] = v;
-        __syncthreads();
-        if (tid == 0) {
-            uint32_t sum = 0;
-            for (uint32_t k = 0; k < nwarps; k++) sum += s_red[k];
-            J.blk[team_r] = sum;
-        }
-        __syncthreads();
-    }
-    if (team_r == 0 && tid == 0) st->pending_count = 0;
-    if (!team_barrier(full, st, bar_epoch, 8, J.trace)) return -1;
-    REI_TMARK(full && blockIdx.x == 0, 14);
-
-    // ---- phase D: append survivors in candidate order
-    {
-        uint64_t cta_prefix = 0, total_new = 0;
-        for (uint32_t b = tid; b < team_n; b += blockDim.x) {
-            const uint32_t v = ldcg(J.blk + b);
-            total_new += v;
-            if (b < team_r) cta_prefix += v;
-        }
-        for (int d = 16; d > 0; d >>= 1) {
-            cta_prefix += __shfl_down_sync(0xFFFFFFFFu, cta_prefix, d);
-            total_new += __shfl_down_sync(0xFFFFFFFFu, total_new, d);
-        }
-        __shared__ uint64_t s_a[32], s_b[32], s_pref, s_tot;
-        if (lane == 0) {
-            s_a[wid] = cta_prefix;
-            s_b[wid] = total_new;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            uint64_t x = 0, y = 0;
-            for (uint32_t k = 0; k < nwarps; k++) {
-                x += s_a[k];
-                y += s_b[k];
-            }
-            s_pref = x;
-            s_tot = y;
-        }
         uint32_t x = mycnt;
         for (int d = 1; d < 32; d <<= 1) {
             const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
@@ -1300,41 +1263,70 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
             if (k < wid) wbefore += s_red[k];
             cta_cnt += s_red[k];
         }
-        const uint64_t limit = J.cache_alloc < J.cap ? J.cache_alloc : J.cap;
-        constexpr uint32_t kListMax = 2 * kSortMax;  // survivors listed in shared memory per round
-        // the CTA's survivors in order, kListMax at a time, into a shared
-        // list; then rows and back-pointers spread over all its threads with
-        // loads batched.  A thread's survivors have the consecutive CTA-local
-        // ranks [pos, my_end); it lists those of each round's window.
-        uint32_t *list = reinterpret_cast<uint32_t *>(S.sortbuf);
+        uint32_t *out = J.pending + w0 * 32;
         uint32_t pos = wbefore + x - mycnt;
-        const uint32_t my_end = wbefore + x;
-        uint64_t w = t0;
-        uint32_t bits = 0;
-        if (mycnt) {
-            bits = ldcg(J.bitmap + w);
+        for (uint64_t w = t0; w < t1 && mycnt; w++) {
+            uint32_t bits = ldcg(J.bitmap + w);
+            if (!bits) continue;
             J.bitmap[w] = 0;
-        }
-        const uint64_t base = (uint64_t)a.size + s_pref;  // cache row of this CTA's first survivor
-        const uint32_t fit = base >= limit ? 0u : (uint32_t)umin64(cta_cnt, limit - base);
-        const uint32_t nt = blockDim.x;
-        for (uint32_t lo = 0; lo < cta_cnt; lo += kListMax) {
-            const uint32_t hi = min(cta_cnt, lo + kListMax);
-            const uint32_t stop = min(hi, my_end);
-            while (pos < stop) {
-                while (bits == 0 && w + 1 < t1) {
-                    w++;
-                    bits = ldcg(J.bitmap + w);
-                    J.bitmap[w] = 0;
-                }
-                list[pos - lo] = (uint32_t)(w * 32 + (__ffs(bits) - 1));
+            while (bits) {
+                out[pos++] = (uint32_t)(w * 32 + (__ffs(bits) - 1));
                 bits &= bits - 1;
-                pos++;
+            }
+        }
+        if (tid == 0) J.blk[team_r] = cta_cnt;
+        __syncthreads();
+    }
+    if (team_r == 0 && tid == 0) st->pending_count = 0;
+    if (!team_barrier(full, st, bar_epoch, 8, J.trace)) return -1;
+    REI_TMARK(full && blockIdx.x == 0, 14);
+
+    // ---- phase D: append survivors in candidate order.  Survivor g (of all
+    // the chunk's, in order) is the (g - pref[b])-th of CTA range b's list;
+    // every CTA appends an equal share of the ranks, however unevenly the
+    // new languages fall over the ranges.
+    {
+        uint32_t *pref = reinterpret_cast<uint32_t *>(S.sortbuf);  // team_n + 1 entries (team_n < kSortMax)
+        uint32_t *list = pref + kSortMax;                          // kSortMax candidates per round
+        for (uint32_t b = tid; b < team_n; b += blockDim.x) pref[b + 1] = ldcg(J.blk + b);
+        if (tid == 0) pref[0] = 0;
+        __syncthreads();
+        if (wid == 0) {
+            uint32_t carry = 0;
+            for (uint32_t b0 = 1; b0 <= team_n; b0 += 32) {
+                const uint32_t b = b0 + lane;
+                const uint32_t v = b <= team_n ? pref[b] : 0u;
+                uint32_t x = v;
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+                    if (lane >= (uint32_t)d) x += y;
+                }
+                if (b <= team_n) pref[b] = carry + x;
+                carry += __shfl_sync(0xFFFFFFFFu, x, 31);
+            }
+        }
+        __syncthreads();
+        const uint64_t total = pref[team_n];
+        const uint64_t g0 = total * team_r / team_n, g1 = total * (team_r + 1) / team_n;
+        const uint64_t limit = J.cache_alloc < J.cap ? J.cache_alloc : J.cap;
+        const uint32_t nt = blockDim.x;
+        for (uint64_t lo = g0; lo < g1; lo += kSortMax) {
+            const uint32_t cnt = (uint32_t)umin64(kSortMax, g1 - lo);
+            // the round's candidates: rank g -> its range b (the last b with pref[b] <= g)
+            for (uint32_t i = tid; i < cnt; i += nt) {
+                const uint32_t g = (uint32_t)(lo + i);
+                uint32_t b = 0, hi_b = team_n;  // pref[b] <= g < pref[hi_b]
+                while (hi_b - b > 1) {
+                    const uint32_t m = (b + hi_b) >> 1;
+                    if (pref[m] <= g) b = m;
+                    else hi_b = m;
+                }
+                const uint64_t bw0 = umin64(nwords, b * per_cta);
+                list[i] = ldcg(J.pending + bw0 * 32 + (g - pref[b]));
             }
             __syncthreads();
-            const uint32_t cnt = hi - lo;                           // listed this round
-            const uint32_t nfit = fit > lo ? min(fit - lo, cnt) : 0u;  // of them, cached
-            const uint64_t b0 = base + lo;
+            const uint64_t b0 = (uint64_t)a.size + lo;  // cache row of the round's first survivor
+            const uint32_t nfit = b0 >= limit ? 0u : (uint32_t)umin64(cnt, limit - b0);
             const uint32_t nf = J.exact ? 0u : nfit * W;  // (exact keys: rows from the keys)
             for (uint32_t f0 = tid; f0 < nf; f0 += 4 * nt) {
                 uint32_t v[4];
@@ -1397,11 +1389,10 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
             }
             __syncthreads();  // (the list is refilled next round)
         }
-        __syncthreads();
         if (team_r == 0 && tid == 0) {
             const uint64_t room = limit > a.size ? limit - a.size : 0;
-            const uint64_t added = s_tot < room ? s_tot : room;
-            if (s_tot > room) L->full = 1;  // every drop shows as s_tot > room
+            const uint64_t added = total < room ? total : room;
+            if (total > room) L->full = 1;  // every drop shows as total > room
             L->size = a.size + (uint32_t)added;
             S.lvc[a.level] = L->size - S.lvs[a.level];
             J.lvl_count[a.level] = S.lvc[a.level];
