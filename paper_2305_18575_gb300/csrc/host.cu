@@ -1681,14 +1681,22 @@ rei_status server_setup(rei_server *S) {
     return REI_OK;
 }
 
-bool kernel_running(rei_server *S) {
+// whether the persistent launch is still running; *err is set when the
+// launch (or the context) reported an error instead of finishing
+bool kernel_running(rei_server *S, bool *err) {
+    *err = false;
     if (!S->running) return false;
-    if (cudaEventQuery(S->kdone) == cudaSuccess) S->running = false;
-    return S->running;
+    const cudaError_t e = cudaEventQuery(S->kdone);
+    if (e == cudaErrorNotReady) return true;
+    S->running = false;
+    *err = e != cudaSuccess;
+    return false;
 }
 
 rei_status ensure_kernel(rei_server *S) {
-    if (kernel_running(S)) return REI_OK;
+    bool err = false;
+    if (kernel_running(S, &err)) return REI_OK;
+    if (err) return REI_ECUDA;
     if (launch_serve(&S->args, S->grid, S->threads, S->smem, S->kstream) != cudaSuccess) return REI_ECUDA;
     if (cudaEventRecord(S->kdone, S->kstream) != cudaSuccess) return REI_ECUDA;
     S->ctx->launches++;
