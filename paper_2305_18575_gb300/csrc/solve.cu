@@ -153,7 +153,7 @@ struct Shared {
     SegTile *tiles;          // per segment
     uint32_t *pos, *neg;     // precision masks (W words)
     const uint32_t *gt_off, *gt_pair, *len_start;
-    unsigned long long *sortbuf;  // kSortMax words: a small chunk's slot entries, or a CTA's survivor list
+    unsigned long long *sortbuf;  // kSortMax words: a small chunk's slot entries, or the append's per-CTA prefix and survivor list
     uint32_t *solo_bits;     // kSortMax / 32 words: candidates of a small chunk that hold a slot
     uint32_t *solo_pref;     // kSortMax / 32 + 4 words: survivors before each bitmap word, total
     // the search's start, while every language fits in CTA 0's shared memory
