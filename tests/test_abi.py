@@ -56,3 +56,25 @@ def test_no_cpu_fallback_without_gpu():
         return
     h = ctypes.c_void_p()
     assert rei.load().rei_ctx_create(ctypes.byref(h), 0, None, None) != rei.REI_OK
+
+
+def test_binding_constants_match_header(tmp_path):
+    """Status codes, flags, options and limits of the binding are the values
+    the C compiler sees in include/rei.h."""
+    import subprocess
+    src = open(os.path.join(ROOT, "include", "rei.h")).read()
+    names = sorted(set(re.findall(r"^#define (REI_(?:F|OPT|MAX)_[A-Z_]+)\b", src, flags=re.M)))
+    names += ["REI_NOALLOC_SCRATCH_BYTES"]
+    names += sorted(set(re.findall(r"^\s+(REI_[A-Z_]+)\s*=\s*\d+", src, flags=re.M)))  # rei_status
+    assert {"REI_OK", "REI_ETIMEOUT", "REI_OPT_YIELD_US", "REI_F_ONTHEFLY", "REI_MAX_IC"} <= set(names)
+    lines = ['#include <stdio.h>', '#include "rei.h"', "int main(void) {"]
+    lines += [f'printf("{n} %llu\\n", (unsigned long long)({n}));' for n in names]
+    lines.append("return 0; }")
+    c = tmp_path / "consts.c"
+    c.write_text("\n".join(lines))
+    exe = tmp_path / "consts"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)]).decode().splitlines())
+    for n in names:
+        assert hasattr(rei, n), n
+        assert int(got[n]) == getattr(rei, n), n
