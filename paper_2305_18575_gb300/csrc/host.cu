@@ -511,9 +511,8 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
         if ((s = ensure(c, c->bitmap, 4ull * ((chunk_words + 31) / 32)))) return s;
         if (c->bitmap.p != before || c->bitmap.bytes != before_bytes) c->table_clean = false;
     }
-    const uint32_t threads = 256;  // (the launch bounds of k_solve_fused)
-    const size_t half = c->smem_sm / 2 > 4096 ? c->smem_sm / 2 - 4096 : 0;
-    const size_t smem = std::min(half, c->smem_optin);
+    const uint32_t threads = 512;  // (the launch bounds of k_solve_fused: one 16-warp CTA per SM)
+    const size_t smem = c->smem_optin > 8192 ? c->smem_optin - 8192 : 0;  // (its static shared memory and a reserve)
     int bps = 0;
     CK(solve_fused_occupancy(threads, smem, &bps));
     if (bps < 1) return REI_EBUSY;

@@ -830,10 +830,12 @@ __device__ uint32_t emit_tree(const SolveJob &J, uint32_t op, uint32_t l, uint32
 // state, published with release / read with acquire), join the chunk's
 // phases with grid barriers, and go back to waiting.
 
-// CTAs of the plain path, two per SM: the fused launch (staging, then the
-// levels of a small or medium search, latency-bound) runs 8 warps; the
-// relaunch that takes over large levels runs 16 for more loads in flight
-constexpr uint32_t kFusedThreads = 256;
+// CTAs of the plain path, 16 warps each: the fused launch (staging, then the
+// levels of a small or medium search, latency-bound) runs one per SM, at up
+// to 128 registers and with the SM's shared memory, so that CTA 0 alone has
+// 16 warps for the small chunks; the relaunch that takes over large levels
+// runs two per SM at 64 registers for more loads in flight
+constexpr uint32_t kFusedThreads = 512;
 constexpr uint32_t kSolveThreads = 512;
 constexpr uint32_t kSortMax = 2048;  // candidates of a chunk CTA 0 runs with shared-memory bookkeeping
 static_assert(kMaxTeam < kSortMax, "the append's prefix table of per-CTA counts lives in sortbuf");
@@ -1854,7 +1856,7 @@ __device__ __forceinline__ uint64_t auto_chunk(uint32_t W) {
 // size the search from the staged problem, then search, all in one launch.
 // A problem whose staging or search the launch cannot hold (|ic| > 2048, a
 // guide table beyond the pair buffer, shared memory) ends with ST_RESTAGE.
-__global__ void __launch_bounds__(kFusedThreads, 2) k_solve_fused(const __grid_constant__ FuseArgs F) {
+__global__ void __launch_bounds__(kFusedThreads, 1) k_solve_fused(const __grid_constant__ FuseArgs F) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     __shared__ SolveJob J;
     SolveState *st = F.tmpl.st;
