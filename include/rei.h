@@ -318,7 +318,9 @@ rei_status rei_server_submit(rei_server *srv, const rei_problem *prob, uint64_t 
  * out->stats.ms_total is the time from submission to the answer.
  * REI_EBUSY when not finished in time; REI_EINVAL for a ticket that was not
  * issued or was already released; REI_EBUFSZ (ticket kept) when out's regex
- * or tree buffer is too small.  The ticket is released on success. */
+ * or tree buffer is too small.  The ticket is released on success.  Once the
+ * server's launch has failed (a CUDA error), every unanswered ticket and
+ * every later submission get REI_ECUDA. */
 rei_status rei_server_poll(rei_server *srv, uint64_t ticket, rei_result *out, int block_ms);
 
 /* Stop the server's worker (finishing queued and live problems) and free it. */
