@@ -1610,6 +1610,7 @@ rei_status server_setup(rei_server *S) {
     if (cudaHostAlloc((void **)&S->outs_h, sizeof(ServeOut) * S->ring_size, cudaHostAllocMapped) != cudaSuccess)
         return REI_ECUDA;
     if (cudaHostAlloc((void **)&S->ctl_h, 64, cudaHostAllocMapped) != cudaSuccess) return REI_ECUDA;
+    memset(S->ring_h, 0, sizeof(ServeReq) * S->ring_size);  // (sequence words 0: no job yet)
     memset(S->outs_h, 0, sizeof(ServeOut) * S->ring_size);
     memset(S->ctl_h, 0, 64);
     ServeArgs &A = S->args;
@@ -1844,6 +1845,9 @@ void server_loop(rei_server *S) {
                 fill_leaves(&req.p, &q.cmin, q.leaf_cost, q.leaf_sym);
                 memcpy(q.offs, req.offs.data(), 4ull * (n_str + 1));
                 if (total) memcpy(q.bytes, req.bytes.data(), total);
+                // the entry's sequence word last: a launch that sees it reads a whole entry
+                std::atomic_thread_fence(std::memory_order_seq_cst);
+                *(volatile unsigned long long *)&q.seq = job + 1;
                 S->live_bytes += req.footprint;
                 S->live[job] = std::move(req);
                 S->published++;
@@ -1985,6 +1989,12 @@ void rei_server_destroy(rei_server *S) {
         cudaStreamDestroy(S->kstream);
     }
     if (S->kdone) cudaEventDestroy(S->kdone);
+    if (getenv("REI_DEBUG") && S->args.head) {
+        unsigned long long h[3] = {0, 0, 0};
+        if (cudaMemcpy(h, S->args.head, sizeof h, cudaMemcpyDeviceToHost) == cudaSuccess)
+            fprintf(stderr, "rei server: %llu jobs claimed, %llu ring entries incomplete when first read, "
+                    "%llu given up\n", h[0], h[1], h[2]);
+    }
     for (DevBuf &b : S->bufs) dev_free(S->ctx, b);
     if (S->ring_h) cudaFreeHost(S->ring_h);
     if (S->outs_h) cudaFreeHost(S->outs_h);

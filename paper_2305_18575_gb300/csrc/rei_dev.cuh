@@ -253,6 +253,7 @@ constexpr uint32_t kServePairCap = 1u << 16; // guide pairs a served request may
 
 // a request in the ring (mapped host memory), written before it is published
 struct ServeReq {
+    unsigned long long seq;        // job + 1, written by the host after every other field
     uint32_t n_pos, n_neg, n_sym, total_bytes;
     uint8_t alphabet[256];
     rei_costs costs;
@@ -287,7 +288,8 @@ struct ServeArgs {
     const volatile unsigned long long *avail;  // jobs published (mapped)
     const volatile unsigned long long *stop;   // nonzero: return (mapped)
     uint64_t yield_ns;  // as BatchArgs::yield_ns
-    unsigned long long *head;                  // next job to claim (device)
+    unsigned long long *head;                  // next job to claim (device); head[1]: entries
+                                               // found incomplete when first read, head[2]: given up
     unsigned long long idle_ns;
     size_t smem_cap;
 };

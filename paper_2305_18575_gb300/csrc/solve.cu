@@ -2106,6 +2106,42 @@ __global__ void __launch_bounds__(256, 2) k_serve(const __grid_constant__ ServeA
         const uint32_t r = (uint32_t)(job % A.ring_size);
         const ServeReq &q = A.ring[r];
         ServeOut &o = A.outs[r];
+        // the entry is read only once it is whole: its sequence word names
+        // this job and its sizes are in range (waited for at most 2 ms; a
+        // request still incomplete then is answered as invalid, never read)
+        if (tid == 0) {
+            const unsigned long long t0 = globaltimer_ns();
+            uint32_t ok = 0, tries = 0;
+            for (;;) {
+                if (ld_acquire_sys_u64(&q.seq) == job + 1) {
+                    const uint32_t np = q.n_pos, nn = q.n_neg, ns = q.n_sym, tb = q.total_bytes;
+                    if (np + nn <= kServeMaxStrings && np <= kServeMaxStrings && ns <= 256 && tb <= kServeMaxBytes &&
+                        q.offs[np + nn] == tb && q.max_cost <= REI_MAX_COST) {
+                        ok = 1;
+                        break;
+                    }
+                }
+                tries++;
+                if (globaltimer_ns() - t0 > 2000000ull) break;
+                __nanosleep(256);
+            }
+            if (tries) atomicAdd(A.head + 1, 1ull);
+            if (!ok) atomicAdd(A.head + 2, 1ull);
+            s_red[1] = ok;
+        }
+        __syncthreads();
+        if (!s_red[1]) {
+            if (tid == 0) {
+                o.out = BatchOut{};
+                o.out.status = ST_BAD;
+                o.info = StageInfo{};
+                __threadfence_system();
+                *(volatile unsigned long long *)&o.done = job + 1;
+                __threadfence_system();
+            }
+            __syncthreads();
+            continue;
+        }
         // the request's offsets into this slot's buffer, then staged by this CTA
         const uint32_t n_str = q.n_pos + q.n_neg;
         uint32_t *in_o = A.in_offs + (uint64_t)slot * (kServeMaxStrings + 1);
