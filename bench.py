@@ -83,9 +83,12 @@ def measured_peaks():
 
 class ClockSampler:
     def __init__(self, device: int):
+        import tempfile
         self.p = None
         self.device = device
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device}.csv")
+        # the raw samples go to REI_CLOCKS_DIR when set (kept), else to the temp directory
+        d = os.environ.get("REI_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"rei_clocks_rank{device}_{os.getpid()}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
