@@ -6,6 +6,10 @@ package imports this module.
 
 The oracle is compiled with gcc into ``oracle/_lib/librei_oracle.so`` by
 :func:`build` (also called from ``__graft_entry__.build()``).
+
+Parity unpinned by the paper: the choice among equal-cost precise expressions
+(the fixed enumeration order) and the exact candidate counts; see the header of
+``rei_oracle.c``.
 """
 from __future__ import annotations
 

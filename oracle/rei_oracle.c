@@ -48,6 +48,13 @@
  *     the 32-bit words of a padded characteristic sequence (1 for n <= 32, 2
  *     for n <= 64, else 4*ceil(n/128)); a level whose survivors would exceed it
  *     without yielding an answer ends the search with "out of memory".
+ *
+ * Parity unpinned by the paper: which of several equal-cost precise
+ * expressions is returned (the tie-breaking order above is this project's
+ * reading; the paper's printed answers agree with it where it prints them),
+ * and the exact candidate and unique counts (the paper counts its own way).
+ * Both are pinned only by this oracle; the minimal cost, the precision of
+ * the answer and the languages themselves are pinned by the tests.
  */
 #include <stdint.h>
 #include <stdio.h>
