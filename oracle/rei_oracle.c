@@ -51,7 +51,8 @@
  *
  * Parity unpinned by the paper: which of several equal-cost precise
  * expressions is returned (the tie-breaking order above is this project's
- * reading; the paper's printed answers agree with it where it prints them),
+ * reading; the answers the paper prints for its allowed-error table agree
+ * with it for 15-50 %),
  * and the exact candidate and unique counts (the paper counts its own way).
  * Both are pinned only by this oracle; the minimal cost, the precision of
  * the answer and the languages themselves are pinned by the tests.
