@@ -1,20 +1,23 @@
 #!/usr/bin/env python
 """Benchmark of the REI search on GB300: candidate languages built+deduped/s.
 
-Workload (one step): the medium single-instance configuration -- alphabet
-{0,1}, |P| = |N| = 10, lengths 0-7, each labelled by a seeded random target of
-cost 10-14, |ic| <= 128 -- seeds 0..19, each solved under the cost vectors
-(1,1,1,1,1) and (1,1,5,1,1) with max_cost 40: 40 complete solves per step.
-Inputs are synthetic (the paper's benchmark files are not available).
+Workload (one step, the headline `value`): the medium single-instance
+configuration -- alphabet {0,1}, |P| = |N| = 10, lengths 0-7, each labelled by a
+seeded random target of cost 10-14, |ic| <= 128 -- seeds 0..19, each solved
+under the cost vectors (1,1,1,1,1) and (1,1,5,1,1) with max_cost 40: 40
+complete solves per step.  Inputs are synthetic (the paper's benchmark files
+are not available).
 
 Prints ONE JSON line (rank 0).  `value` is candidates/s measured with CUDA
 events on the library's stream over exactly --steps steps (inputs already in
 device memory); `e2e` is the same metric through rei_solve with host string
 arrays (host<->device copies inside the timed region).  The L2 cache is
-flushed (a 256 MiB write) between timed steps.
+flushed (a 256 MiB write) between timed steps.  Further legs on the same line:
+the wide configuration (multiword languages), the paper's printed instance
+(the throughput regime) and the batched form.
 
---impl reference times the CPU oracle (the slow reference arm) on a bounded
-sample of the same workload.
+--impl reference times the CPU oracle (the slow reference arm) on the same 40
+problems, each stopped after a stated number of candidates.
 """
 from __future__ import annotations
 
@@ -47,27 +50,27 @@ def problems():
     return out
 
 
-def recorded_traffic():
-    """DRAM bytes per k_solve_fused launch from the committed ncu summary, while
-    the kernel sources are the ones it was measured on (else nothing)."""
+def kernel_sources_hash() -> str:
     import hashlib
     h = hashlib.sha256()
     for f in ("solve.cu", "stage_dev.cuh", "rei_dev.cuh"):
         with open(os.path.join(ROOT, "paper_2305_18575_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    rec = {}
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes of the search kernels from the committed one-pass ncu capture
+    (profiles/dram_traffic.json), while the kernel sources are the ones it was
+    measured on (else nothing)."""
     try:
-        with open(os.path.join(ROOT, "profiles", "dram_k_solve_fused.md")) as fh:
-            for line in fh:
-                k, sep, v = line.partition(":")
-                if sep and k.strip() in ("kernel_sources_sha256_16", "medium_traffic_bytes_per_launch",
-                                         "printed_traffic_bytes_per_solve"):
-                    rec[k.strip()] = v.strip()
-    except OSError:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
         return {}
-    if rec.get("kernel_sources_sha256_16") != h.hexdigest()[:16]:
+    if rec.get("kernel_sources_sha256_16") != kernel_sources_hash():
         return {}
-    return {k: int(v) for k, v in rec.items() if k != "kernel_sources_sha256_16"}
+    return {k: v for k, v in rec.items() if isinstance(v, int)}
 
 
 def measured_peaks():
@@ -135,50 +138,60 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------
-# CPU oracle timing (the cpu_baseline leg and the reference arm)
+# CPU oracle timing (the cpu_baseline legs and the reference arm)
 
-def oracle_sample(max_candidates_each: int, seeds=SEEDS):
+def oracle_sample(probs, max_candidates_each: int, max_cost: int = 40):
+    """The oracle on (instance, costs) pairs, each stopped after
+    max_candidates_each candidates: (candidates, seconds of oracle time)."""
     import oracle
-    from workloads import make_config
     cands, secs = 0, 0.0
-    for costs in COSTS:
-        for s in seeds:
-            i = make_config("medium", s)
-            r = oracle.solve(i.alphabet, i.pos, i.neg, costs=costs, max_cost=40,
-                             mem_budget=i.mem_budget, max_candidates=max_candidates_each)
-            cands += r.candidates
-            secs += r.seconds
+    for i, costs in probs:
+        r = oracle.solve(i.alphabet, i.pos, i.neg, costs=costs, max_cost=max_cost,
+                         mem_budget=i.mem_budget, max_candidates=max_candidates_each)
+        cands += r.candidates
+        secs += r.seconds
     return cands, secs
 
 
 def cpu_baseline():
     cap = 80000
-    cands, secs = oracle_sample(cap)
+    cands, secs = oracle_sample(problems(), cap)
     return {"value": cands / secs if secs else None, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"the 40 problems of the workload, each stopped after {cap} candidates "
                       f"({cands} candidates, {secs:.1f} s, one host thread)"}
 
 
+REF_CAP = 20000  # candidates per problem and step of the reference arm
+
+
+def config_of(world: int) -> dict:
+    """The workload as both arms name it (the same problems in both)."""
+    return {"workload": WORKLOAD, "problems_per_step": len(SEEDS) * len(COSTS), "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args, rank, world):
+    """The CPU oracle on the GPU arm's 40 problems, each stopped after REF_CAP
+    candidates per step (rank 0 only)."""
     if rank != 0:
         return
-    cap = 4000
+    probs = problems()
     for _ in range(args.warmup):
-        oracle_sample(cap, seeds=SEEDS[:5])
+        oracle_sample(probs, REF_CAP)
     t0 = time.perf_counter()
     tot_c, tot_s = 0, 0.0
     for _ in range(args.steps):
-        c, s = oracle_sample(cap, seeds=SEEDS[:5])
+        c, s = oracle_sample(probs, REF_CAP)
         tot_c += c
         tot_s += s
     wall = time.perf_counter() - t0
     value = tot_c / tot_s if tot_s else None
-    sample = (f"per step: seeds 0-4 x both cost vectors, each stopped after {cap} candidates "
-              f"(oracle timing, one host thread)")
+    sample = (f"per step: the 40 problems of the workload (seeds 0-19 x both cost vectors), each stopped "
+              f"after {REF_CAP} candidates ({tot_c // max(args.steps, 1)} candidates per step; oracle timing, "
+              f"one host thread)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "none (CPU oracle)"},
+            "data": "synthetic", "config": config_of(world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -188,6 +201,7 @@ def run_reference(args, rank, world):
 # GPU arm
 
 def alu_peak(device: int):
+    """LOP3 lane-operations per second of the GPU (the integer-throughput probe)."""
     from paper_2305_18575_gb300 import build as b
     L = C.CDLL(b.build_peak())
     L.rei_peak_lop3.restype = C.c_double
@@ -208,6 +222,41 @@ def reduce_over_ranks(total_ms: float, cands: float, world: int, device: str):
     cc = torch.tensor([float(cands)], dtype=torch.float64, device=device)
     dist.all_reduce(cc)
     return float(t.item()), float(cc.item())
+
+
+def alg_work(results):
+    """Algorithmic work of a set of solves (per-candidate figures of the
+    method): bytes = a 32-byte uniqueness probe per candidate + (48 W + 17)
+    bytes per new language; bit-pair operations = G per concatenation, G* per
+    star, 32 W per symbol, ? and + candidate."""
+    bytes_ = sum(32 * r.candidates + (12 * 4 * r.words + 17) * r.unique for r in results)
+    pairs = sum(r.cand_op[3] * r.guide_pairs + r.cand_op[2] * r.star_pairs +
+                (r.cand_op[0] + r.cand_op[1] + r.cand_op[4]) * 32 * r.words for r in results)
+    return bytes_, pairs
+
+
+def roofline(results, k_ms: float, launches: int, lop3: float, kernel: str, traffic=None):
+    """Both roofs of a kernel from its algorithmic work and its CUDA-event time;
+    the better-fitting one (the larger fraction) is `bound`."""
+    peaks, peak_kind = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    alg_bytes, pair_ops = alg_work(results)
+    alu_peak_pairs = lop3 * 32 if lop3 > 0 else None  # one LOP3 = 32 bit-sliced AND-ORs
+    hbm_ach = alg_bytes / (k_ms * 1e-3) / 1e9 if k_ms > 0 else 0.0
+    alu_ach = pair_ops / (k_ms * 1e-3) if k_ms > 0 else 0.0
+    hbm_frac = hbm_ach / hbm_peak
+    alu_frac = alu_ach / alu_peak_pairs if alu_peak_pairs else 0.0
+    if alu_frac > hbm_frac:
+        roof = {"bound": "alu", "achieved": alu_ach / 1e12, "peak": alu_peak_pairs / 1e12,
+                "unit": "T bit-pair-ops/s", "frac": alu_frac}
+    else:
+        roof = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_frac}
+    roof.update({"traffic": traffic, "kernel": kernel, "launches": launches,
+                 "avg_launch_ms": k_ms / max(launches, 1), "alg_bytes_per_launch": alg_bytes / max(launches, 1),
+                 "hbm_frac": hbm_frac, "hbm_peak_gbs": hbm_peak, "hbm_peak_source": f"{peak_kind} hbm_gbs",
+                 "alu_frac": alu_frac, "lop3_lane_ops_per_s": lop3,
+                 "alu_peak_source": "LOP3 throughput probe (peak.cu) x 32 bit-slices"})
+    return roof
 
 
 def run_gpu(args, rank, world, local_rank):
@@ -278,30 +327,9 @@ def run_gpu(args, rank, world, local_rank):
 
     # roofline of the search kernel: its own device time (CUDA events on the
     # launching stream, accumulated by the library) against algorithmic work
-    k_ms = sum(r.ms_search_kernel for r in results)
-    k_launches = sum(r.search_launches for r in results)
-    pair_ops = sum(r.cand_op[3] * r.guide_pairs + r.cand_op[2] * r.star_pairs +
-                   (r.cand_op[0] + r.cand_op[1] + r.cand_op[4]) * 32 * r.words for r in results)
-    alg_bytes = sum(32 * r.candidates + (12 * 4 * r.words + 17) * r.unique for r in results)
-    peaks, peak_kind = measured_peaks()
-    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     lop3 = alu_peak(dev)
-    alu_peak_pairs = lop3 * 32 if lop3 > 0 else None  # one LOP3 = 32 bit-sliced AND-ORs
-    hbm_ach = alg_bytes / (k_ms * 1e-3) / 1e9
-    alu_ach = pair_ops / (k_ms * 1e-3)
-    hbm_frac = hbm_ach / hbm_peak
-    alu_frac = alu_ach / alu_peak_pairs if alu_peak_pairs else 0.0
-    if alu_frac >= hbm_frac:
-        roof = {"bound": "alu", "achieved": alu_ach / 1e12, "peak": alu_peak_pairs / 1e12,
-                "unit": "T bit-pair-ops/s", "frac": alu_frac, "traffic": None,
-                "peak_source": f"LOP3 throughput probe {lop3 / 1e12:.2f} T lane-ops/s x 32 bits"}
-    else:
-        roof = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": hbm_frac, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs"}
-    roof["traffic"] = recorded_traffic().get("medium_traffic_bytes_per_launch")
-    roof.update({"kernel": "k_solve_fused", "launches": k_launches, "avg_launch_ms": k_ms / max(k_launches, 1),
-                 "alg_bytes_per_launch": alg_bytes / max(k_launches, 1), "alu_frac": alu_frac,
-                 "hbm_frac": hbm_frac})
+    roof = roofline(results, sum(r.ms_search_kernel for r in results), sum(r.search_launches for r in results),
+                    lop3, "k_solve_fused", recorded_traffic().get("medium_traffic_bytes_per_launch"))
 
     # whole-job aggregation over ranks (replicas: no data-path collective)
     t_max, c_sum = reduce_over_ranks(total_ms, cands, world, f"cuda:{dev}")
@@ -314,8 +342,8 @@ def run_gpu(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded target-labelled instances; the paper's files are unavailable)",
-        "config": {"workload": WORKLOAD, "problems_per_step": len(dprobs), "l2": "flushed between steps",
-                   "parallelism": f"replicas x{world}", "grid": results[0].grid if results else None},
+        "config": config_of(world),
+        "launch": {"grid": results[0].grid if results else None, "l2": "flushed between steps (256 MiB write)"},
         "time_to_min_re_ms": {"p50": pct(0.5), "p99": pct(0.99), "mean": statistics.mean(ttm)},
         "candidates_per_step": cands / args.steps,
         "roofline": roof,
@@ -325,21 +353,71 @@ def run_gpu(args, rank, world, local_rank):
         "clocks": clocks.summary(),
         "gpu_launches": launches,
     }
+    if not args.no_wide:
+        line["wide"] = wide_leg(ctx, lop3, cpu=not args.no_cpu_baseline)
     if not args.no_paper:
-        line["paper_instance"] = paper_instance_leg(ctx, dev)
+        line["paper_instance"] = paper_instance_leg(ctx, lop3)
     if not args.no_batch:
         bprobs = batched_problems()
         line["batched"] = batched_leg(ctx, dev, bprobs)
         if not args.no_cpu_baseline:
             line["batched"]["cpu_oracle"] = cpu_batched_baseline(line["batched"]["mean_candidates"])
-        if args.served:
-            line["served"] = served_leg(dev, bprobs, args.serve_seconds)
-        else:
-            line["served"] = {"skipped": SERVED_OFF}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
 
+
+# ----------------------------------------------------------------------------
+# the wide configuration: multiword languages
+
+WIDE_WORKLOAD = ("wide single instance: alphabet {a,b,c,d}, |P|=|N|=20, lengths 1-10, target cost 12-18, "
+                 "|ic| 400-1500 (16-48 x 32-bit words); seeds 0-9, costs (1,1,1,1,1), max_cost 40, "
+                 "memory budget 64 GB")
+WIDE_SEEDS = list(range(10))
+
+
+def wide_problems():
+    from workloads import make_config
+    return [(make_config("wide", s), (1, 1, 1, 1, 1)) for s in WIDE_SEEDS]
+
+
+def wide_leg(ctx, lop3: float, cpu: bool = True, reps: int = 3):
+    """Time to the minimal regex of each wide problem (whole rei_solve_problem
+    calls, host clock, inputs in host memory), candidates/s over the search
+    kernels' CUDA-event time, and their roofline."""
+    import paper_2305_18575_gb300 as rei
+    wp = wide_problems()
+    probs = [rei.Problem(i.alphabet, i.pos, i.neg, costs=c, max_cost=40, mem_budget=i.mem_budget) for i, c in wp]
+    for p in probs:  # warm-up (the context sizes its buffers)
+        ctx.solve_problem(p)
+    res = []
+    for _ in range(reps):
+        for p in probs:
+            r = ctx.solve_problem(p)
+            if r.status != rei.REI_OK:
+                raise RuntimeError(f"wide solve failed: {r.status_name}")
+            res.append(r)
+    ttm = sorted(r.ms_total for r in res)
+    pct = lambda q: ttm[min(len(ttm) - 1, int(q * len(ttm)))]
+    k_ms = sum(r.ms_search_kernel for r in res)
+    cands = sum(r.candidates for r in res)
+    out = {"workload": WIDE_WORKLOAD, "solves": len(res), "n_ic": sorted({r.n_ic for r in res}),
+           "words": sorted({r.words for r in res}),
+           "candidates_per_s": cands / (k_ms * 1e-3) if k_ms else None,
+           "candidates_per_s_wall": cands / (sum(ttm) * 1e-3),
+           "time_to_min_re_ms": {"p50": pct(0.5), "p99": pct(0.99), "mean": statistics.mean(ttm)},
+           "roofline": roofline(res, k_ms, sum(r.search_launches for r in res), lop3, "k_solve_fused / k_solve")}
+    if cpu:
+        cap = 20000
+        c, s = oracle_sample(wp, cap)
+        out["cpu_baseline"] = {"value": c / s if s else None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"the 10 wide problems, each stopped after {cap} candidates "
+                                         f"({c} candidates, {s:.1f} s, one host thread)"}
+    return out
+
+
+# ----------------------------------------------------------------------------
+# the batched form
 
 BATCH_WORKLOAD = ("batched: 512 instances, |alphabet| 2-4, |P|,|N| uniform 2-20, lengths 0-10, |ic| 16-1024, "
                   "target cost 4-14, costs (1,1,1,1,1), max_cost 40; one rei_solve_batch call vs 512 rei_solve_problem calls")
@@ -419,16 +497,19 @@ def cpu_batched_baseline(mean_candidates: float):
                       f"candidates ({cands} candidates, {wall:.1f} s wall, {cores} processes)"}
 
 
+# ----------------------------------------------------------------------------
+# the paper's printed instance: the throughput regime
+
 PAPER_WORKLOAD = ("the specification printed in Sec. 6 (Table 1, Type 1 No 50): 10 positive and 12 negative "
                   "binary strings, |ic| = 25, costs (1,1,1,1,1), max_cost 30, minimal cost 28")
 PAPER_A100_S = 4.9512          # Table 1: the paper's A100 time for this instance (context, other hardware)
 PAPER_A100_REs = 26774099142   # Table 1: its candidate count there
 
 
-def paper_instance_leg(ctx, dev):
+def paper_instance_leg(ctx, lop3: float):
     """Time to the minimal regex on the one instance the paper prints with its
-    GPU time: a search of ~2.6e10 candidates whose uniqueness table (22 M
-    languages) lives in HBM, the regime where the search is throughput-bound."""
+    GPU time: a search of ~2.6e10 candidates whose uniqueness structures live
+    in HBM, the regime where the search is throughput-bound."""
     import paper_2305_18575_gb300 as rei
     from workloads import printed_instance
     i = printed_instance()
@@ -438,95 +519,17 @@ def paper_instance_leg(ctx, dev):
     r = min(runs, key=lambda x: x.ms_total)
     if r.status != rei.REI_OK or r.cost != 28:
         raise RuntimeError(f"printed instance: {r.status_name} cost {r.cost}")
-    peaks, kind = measured_peaks()
-    alg_bytes = 32 * r.candidates + (12 * 4 * r.words + 17) * r.unique
-    hbm = alg_bytes / (r.ms_search_kernel * 1e-3) / 1e9
+    roof = roofline([r], r.ms_search_kernel, r.search_launches, lop3, "k_solve_fused, then k_solve")
+    alg_bytes, _ = alg_work([r])
+    roof.update({"alg_bytes_per_solve": alg_bytes,
+                 "traffic_per_solve": recorded_traffic().get("printed_traffic_bytes_per_solve"),
+                 "alg_bytes": "32 B probe per candidate + (48 W + 17) B per new language"})
     return {"workload": PAPER_WORKLOAD, "regex": r.regex, "cost": r.cost, "candidates": r.candidates,
             "unique": r.unique, "time_to_min_re_s": r.ms_total / 1e3, "kernel_s": r.ms_search_kernel / 1e3,
             "candidates_per_s": r.candidates / (r.ms_total * 1e-3), "search_launches": r.search_launches,
-            "roofline": {"bound": "hbm", "achieved": hbm, "peak": float(peaks.get("hbm_gbs", 6800.0)),
-                         "unit": "GB/s", "frac": hbm / float(peaks.get("hbm_gbs", 6800.0)),
-                         "peak_source": f"{kind} hbm_gbs", "alg_bytes_per_solve": alg_bytes,
-                         "traffic_per_solve": recorded_traffic().get("printed_traffic_bytes_per_solve"),
-                         "alg_bytes": "32 B probe per candidate + (48 W + 17) B per new language",
-                         "kernels": "k_solve_fused, then k_solve for levels above 4 Mi candidates"},
+            "roofline": roof,
             "paper_a100": {"seconds": PAPER_A100_S, "candidates": PAPER_A100_REs,
                            "note": "the paper's own run on an A100 (Table 1); context, not a target"}}
-
-
-SERVE_WORKLOAD = ("served: Poisson arrivals at 50, 200 and 1000 problems/s (trace seed = rate), problems drawn in turn "
-                  "from the 512 batched-workload instances; rei_server (one persistent launch) vs a loop of "
-                  "rei_solve_problem calls taking the same arrivals in order")
-SERVE_RATES = (50, 200, 1000)
-SERVE_SECONDS = 2.0
-
-
-SERVED_OFF = ("a run of this leg raised a GPU exception in its saturated phase (512 requests at "
-              "once), cause not found; the served form's own tests still run")
-
-
-def served_leg(dev, probs, seconds=SERVE_SECONDS):
-    """Latency from arrival to answer (host clock) of the served form against a
-    plain loop that solves the same arrivals one at a time."""
-    import paper_2305_18575_gb300 as rei
-    from workloads.gen import poisson_trace
-
-    def pct(v, q):
-        v = sorted(v)
-        return v[min(len(v) - 1, int(q * len(v)))]
-
-    out = {"workload": SERVE_WORKLOAD, "seconds_per_rate": seconds, "rates": {}}
-    answers = {}
-    with rei.Context(device=dev) as sctx, rei.Server(sctx, budget_bytes=64 << 30, max_live=4096) as srv:
-        for t in [srv.submit(p) for p in probs[:64]]:  # warm-up
-            srv.result(t)
-        # saturated: all 512 problems at once, instances/s to the last answer
-        t0 = time.perf_counter()
-        tickets = [srv.submit(p) for p in probs]
-        sat = [srv.result(t) for t in tickets]
-        t_sat = time.perf_counter() - t0
-        lat = [r.ms_total for r in sat]
-        out["saturated"] = {"requests": len(probs), "instances_per_s": len(probs) / t_sat,
-                            "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99)}
-        for rate in SERVE_RATES:
-            arr = poisson_trace(rate, seconds, seed=rate)
-            tickets = []
-            t0 = time.perf_counter()
-            for k, a in enumerate(arr):
-                dt = t0 + a - time.perf_counter()
-                if dt > 0:
-                    time.sleep(dt)
-                tickets.append(srv.submit(probs[k % len(probs)]))
-            res = [srv.result(t) for t in tickets]
-            t_end = max(time.perf_counter(), t0 + seconds)
-            answers[rate] = [(r.status, r.cost, r.tree) for r in res]
-            lat = [r.ms_total for r in res]
-            out["rates"][str(rate)] = {"requests": len(arr), "served_p50_ms": pct(lat, 0.5),
-                                       "served_p99_ms": pct(lat, 0.99),
-                                       "served_throughput_per_s": len(arr) / (t_end - t0)}
-    with rei.Context(device=dev) as pctx:
-        for p in probs[:16]:
-            pctx.solve_problem(p)
-        t0 = time.perf_counter()
-        for p in probs:
-            pctx.solve_problem(p)
-        out["saturated"]["plain_instances_per_s"] = len(probs) / (time.perf_counter() - t0)
-        for rate in SERVE_RATES:
-            arr = poisson_trace(rate, seconds, seed=rate)
-            lat, got = [], []
-            t0 = time.perf_counter()
-            for k, a in enumerate(arr):
-                dt = t0 + a - time.perf_counter()
-                if dt > 0:
-                    time.sleep(dt)
-                r = pctx.solve_problem(probs[k % len(probs)])
-                lat.append(1000 * (time.perf_counter() - t0 - a))
-                got.append((r.status, r.cost, r.tree))
-            if got != answers[rate]:
-                raise RuntimeError("served and one-at-a-time answers differ")
-            o = out["rates"][str(rate)]
-            o.update({"plain_p50_ms": pct(lat, 0.5), "plain_p99_ms": pct(lat, 0.99)})
-    return out
 
 
 def main():
@@ -536,12 +539,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched and served legs")
-    ap.add_argument("--served", action="store_true",
-                    help="run the served leg (off by default: " + SERVED_OFF + ")")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched leg")
+    ap.add_argument("--no-wide", action="store_true", help="skip the wide-configuration leg")
     ap.add_argument("--no-paper", action="store_true", help="skip the printed-instance leg")
-    ap.add_argument("--serve-seconds", type=float, default=SERVE_SECONDS,
-                    help="length of each arrival trace of the served leg (the served config uses 60)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

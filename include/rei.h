@@ -346,10 +346,13 @@ void rei_server_destroy(rei_server *srv);
  *
  * Every piece of device scratch comes from one shared array of
  * REI_NOALLOC_SCRATCH_BYTES.  The first call on each device looks up the
- * array's device address (once per device; make that first call before any
- * stream capture).  The array keeps the previous call's contents; each call
- * clears on its stream what must start cleared.  Calls that overlap on the
- * GPU (other streams or host threads) race on the array: issue one at a time.
+ * array's device address (once per device).  Every call waits for its stream
+ * partway through (it reads the staged sizes back) and copies through
+ * pageable host memory, so no call may be made while its stream is being
+ * captured into a CUDA graph.  The array keeps the previous call's contents;
+ * each call clears on its stream what must start cleared.  Calls that overlap
+ * on the GPU (other streams or host threads) race on the array: issue one at
+ * a time.
  *
  * The whole language cache of the budget is resident: with W the 32-bit
  * words of a CS (see the memory rule above), cap = floor(mem_budget /
@@ -358,7 +361,11 @@ void rei_server_destroy(rei_server *srv);
  * e.g. cap up to about 1.3 million languages at W = 2).  Example bytes are
  * limited to 1 MiB, examples to 65535 and guide-table pairs to 262144.  A
  * problem beyond these limits returns REI_ESCRATCH (nothing is truncated);
- * other errors as rei_solve_problem. */
+ * other errors as rei_solve_problem (the argument rules are the same; a
+ * failed CUDA call gives REI_ECUDA in both the return value and
+ * out->status).  A regex buffer too small for the answer receives its first
+ * regex_cap - 1 bytes and a terminating NUL, with REI_EBUFSZ returned and
+ * out->regex_len set to the full length. */
 rei_status rei_solve_noalloc(const rei_problem *prob, void *stream, rei_result *out);
 
 #ifdef __cplusplus

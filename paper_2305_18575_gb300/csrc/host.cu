@@ -22,7 +22,7 @@
 
 #include "rei_dev.cuh"
 #include "stage_dev.cuh"
-#include "leaves.h"
+#include "args.h"
 
 namespace rei {
 cudaError_t launch_solve_batch(const BatchJob *jobs_dev, const BatchArgs *args, uint32_t grid, uint32_t threads,
@@ -38,6 +38,8 @@ size_t stage_smem_bytes();
 cudaError_t launch_solve(const SolveJob *job, uint32_t grid, uint32_t threads, size_t smem,
                          cudaStream_t stream);
 cudaError_t solve_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm);
+cudaError_t solve_smem_max(size_t *bytes);
+cudaError_t solve_batch_smem_max(size_t *bytes);
 cudaError_t launch_rehash(const SolveJob *job, uint32_t count, uint32_t grid, cudaStream_t stream);
 size_t solve_smem_bytes(uint32_t W, uint32_t n, uint32_t G, uint32_t max_len, uint32_t seg_cap,
                         bool gt_in_smem, uint32_t warps, uint32_t small_rows = 0);
@@ -250,31 +252,6 @@ std::string format_regex(const uint8_t *tok, uint32_t ntok, const uint8_t *alpha
 // ---------------------------------------------------------------------------
 // argument checks and input upload
 
-rei_status check_problem(const rei_problem *p) {
-    if (!p || !p->alphabet || p->n_sym == 0 || p->n_sym > 256) return REI_EINVAL;
-    const uint32_t c[5] = {p->costs.c_sym, p->costs.c_opt, p->costs.c_star, p->costs.c_cat, p->costs.c_alt};
-    for (uint32_t v : c)
-        if (v < 1 || v > REI_MAX_COST) return REI_EINVAL;
-    if (p->max_cost > REI_MAX_COST) return REI_EINVAL;
-    if (check_sym_costs(p)) return REI_EINVAL;
-    bool seen[256] = {};
-    for (uint32_t i = 0; i < p->n_sym; i++) {
-        if (seen[p->alphabet[i]]) return REI_EINVAL;
-        seen[p->alphabet[i]] = true;
-    }
-    const uint64_t n_str = (uint64_t)p->n_pos + p->n_neg;
-    if (n_str > (1u << 24)) return REI_EINVAL;
-    if (n_str && (!p->offsets || (!p->bytes && p->total_bytes))) return REI_EINVAL;
-    if (!(p->flags & REI_F_DEVICE_INPUT) && n_str) {
-        if (p->offsets[0] != 0) return REI_EINVAL;
-        for (uint64_t k = 0; k < n_str; k++) {
-            if (p->offsets[k + 1] < p->offsets[k]) return REI_EINVAL;
-            if (p->offsets[k + 1] - p->offsets[k] > REI_MAX_STRLEN) return REI_EINVAL;
-        }
-    }
-    return REI_OK;
-}
-
 struct Staged {
     StageInfo info;
     uint64_t h2d = 0, d2h = 0;
@@ -345,6 +322,7 @@ rei_status stage_problem(rei_ctx *c, const rei_problem *p, Staged &out) {
         hj->n_neg = p->n_neg;
         memcpy(hj->alphabet, p->alphabet, p->n_sym);
         hj->n_sym = p->n_sym;
+        hj->total_bytes = (uint32_t)total;
         StageJob *dj = (StageJob *)c->stage_job.p;
         hj->info = (StageInfo *)(dj + 1);
         hj->word_start = (uint32_t *)c->word_start.p;
@@ -543,6 +521,7 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
     sj.n_neg = p->n_neg;
     memcpy(sj.alphabet, p->alphabet, p->n_sym);
     sj.n_sym = p->n_sym;
+    sj.total_bytes = (uint32_t)total;
     sj.info = (StageInfo *)((uint8_t *)c->state.p + sb);
     sj.word_start = (uint32_t *)c->word_start.p;
     sj.word_len = (uint32_t *)c->word_len.p;
@@ -682,29 +661,31 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
 
     // launch shape
     const uint32_t seg_cap = 2 * max_cost + 4;
+    size_t smem_max = 0;  // dynamic shared memory a k_solve launch can take
+    CK(solve_smem_max(&smem_max));
     bool gt_smem = 4ull * (n + 1 + G + max_len + 2) <= 96 * 1024;
     uint32_t warps = 16;  // (the launch bounds of k_solve)
     size_t smem = solve_smem_bytes(W, n, G, max_len, seg_cap, gt_smem, warps);
-    while (smem > c->smem_optin && warps > 1) {
+    while (smem > smem_max && warps > 1) {
         warps /= 2;
         smem = solve_smem_bytes(W, n, G, max_len, seg_cap, gt_smem, warps);
     }
-    if (smem > c->smem_optin && gt_smem) {
+    if (smem > smem_max && gt_smem) {
         gt_smem = false;
         warps = 16;
         smem = solve_smem_bytes(W, n, G, max_len, seg_cap, gt_smem, warps);
-        while (smem > c->smem_optin && warps > 1) {
+        while (smem > smem_max && warps > 1) {
             warps /= 2;
             smem = solve_smem_bytes(W, n, G, max_len, seg_cap, gt_smem, warps);
         }
     }
-    if (smem > c->smem_optin) return REI_EINVAL;
+    if (smem > smem_max) return REI_EINVAL;
     // the search's start in CTA 0's shared memory: as many languages as keep
     // the launch at two CTAs per SM (one, if it already has only one)
     uint32_t small_rows = 0;
     if (c->opt_small_rows != 0 && W <= 8) {
         const size_t half = c->smem_sm / 2 > 4096 ? c->smem_sm / 2 - 4096 : 0;  // static smem + reserve
-        const size_t limit = smem <= half ? half : c->smem_optin;
+        const size_t limit = smem <= half ? half : smem_max;
         uint32_t r = c->opt_small_rows > 0 ? (uint32_t)c->opt_small_rows : W <= 2 ? 4096u : W <= 4 ? 2048u : 1024u;
         for (; r >= 256; r >>= 1)
             if (solve_smem_bytes(W, n, G, max_len, seg_cap, gt_smem, warps, r) <= limit) break;
@@ -1254,6 +1235,7 @@ rei_status run_batch(rei_ctx *c, const rei_problem *probs, const std::vector<uin
         j.n_neg = p.n_neg;
         memcpy(j.alphabet, p.alphabet, p.n_sym);
         j.n_sym = p.n_sym;
+        j.total_bytes = (p.n_pos + p.n_neg) ? p.offsets[p.n_pos + p.n_neg] : 0;
         j.info = (StageInfo *)c->b_sinfo.p + t;
         uint8_t *q = dst + P.off_stage[t];
         ws[t] = (uint32_t *)q;
@@ -1352,7 +1334,9 @@ rei_status run_batch(rei_ctx *c, const rei_problem *probs, const std::vector<uin
     }
     const uint32_t nl = (uint32_t)live.size();
     if (nl == 0) return REI_OK;
-    if (smem > c->smem_optin) return REI_EINVAL;
+    size_t smem_max = 0;
+    CK(solve_batch_smem_max(&smem_max));
+    if (smem > smem_max) return REI_EINVAL;
     int bps = 0;
     CK(solve_batch_occupancy(32 * warps, smem, &bps));
     if (bps < 1) return REI_ECUDA;

@@ -14,8 +14,9 @@
 // Host code cannot use the array's name as a device address (on the host it
 // names a host-side stand-in), so the first call on each device looks its
 // device address up with cudaGetSymbolAddress, with that device current, and
-// caches it; that first call should happen before any stream capture.  All
-// calls share the one array and it keeps the previous call's contents: the
+// caches it.  Every call waits for its stream partway through (to read the
+// staged sizes back), so no call can run while its stream is being captured
+// into a graph.  All calls share the one array and it keeps the previous call's contents: the
 // regions that must start cleared are cleared on the caller's stream at the
 // start of every call, and calls that overlap on the GPU (two streams, two
 // host threads) race on the array and must not be issued.
@@ -27,13 +28,14 @@
 #include <mutex>
 
 #include "rei_dev.cuh"
-#include "leaves.h"
+#include "args.h"
 
 namespace rei {
 cudaError_t launch_stage(const StageJob *jobs_dev, uint32_t n_jobs, cudaStream_t stream);
 cudaError_t launch_solve(const SolveJob *job, uint32_t grid, uint32_t threads, size_t smem,
                          cudaStream_t stream);
 cudaError_t solve_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm);
+cudaError_t solve_smem_max(size_t *bytes);
 size_t solve_smem_bytes(uint32_t W, uint32_t n, uint32_t G, uint32_t max_len, uint32_t seg_cap,
                         bool gt_in_smem, uint32_t warps, uint32_t small_rows = 0);
 }  // namespace rei
@@ -160,13 +162,27 @@ size_t format_noalloc(const uint8_t *tok, uint32_t ntok, const uint8_t *alpha, c
         if (par) put(")", 1);
         fp--;
     }
-    if (len < cap) out[len] = 0;
+    // always terminated when there is room for one byte (a string that does
+    // not fit is cut at cap - 1 bytes; the caller gets REI_EBUFSZ and the length)
+    if (cap) out[len < cap ? len : cap - 1] = 0;
     return len;
 }
 
-#define NA_CK(x)                                 \
-    do {                                         \
-        if ((x) != cudaSuccess) return REI_ECUDA; \
+// a failed CUDA call ends the call with REI_ECUDA, in the return value and
+// in out->status alike
+#define NA_CK(x)                          \
+    do {                                  \
+        if ((x) != cudaSuccess) {         \
+            out->status = REI_ECUDA;      \
+            return REI_ECUDA;             \
+        }                                 \
+    } while (0)
+
+// every early return: the same status in the return value and out->status
+#define NA_RET(st)            \
+    do {                      \
+        out->status = (st);   \
+        return (st);          \
     } while (0)
 
 }  // namespace
@@ -180,32 +196,13 @@ extern "C" rei_status rei_solve_noalloc(const rei_problem *p, void *stream_v, re
     out->regex_len = 0;
     out->tree_len = 0;
 
-    // argument checks (same rules as rei_solve_problem)
-    if (!p->alphabet || p->n_sym == 0 || p->n_sym > 256 || p->max_cost > REI_MAX_COST) return REI_EINVAL;
-    const uint32_t cc[5] = {p->costs.c_sym, p->costs.c_opt, p->costs.c_star, p->costs.c_cat, p->costs.c_alt};
-    for (uint32_t v : cc)
-        if (v < 1 || v > REI_MAX_COST) return REI_EINVAL;
-    bool seen[256] = {};
-    for (uint32_t i = 0; i < p->n_sym; i++) {
-        if (seen[p->alphabet[i]]) return REI_EINVAL;
-        seen[p->alphabet[i]] = true;
-    }
-    if (check_sym_costs(p)) return REI_EINVAL;
-    const uint32_t n_str = p->n_pos + p->n_neg;
+    // argument checks: the rules of every other entry point (args.h)
+    if (check_problem(p) != REI_OK) NA_RET(REI_EINVAL);
+    const uint32_t n_str = p->n_pos + p->n_neg;  // (at most 2^24: checked)
     const bool dev_in = (p->flags & REI_F_DEVICE_INPUT) != 0;
-    if (n_str && !p->offsets) return REI_EINVAL;
     const uint64_t total = dev_in ? p->total_bytes : (n_str ? p->offsets[n_str] : 0);
-    if (!dev_in && n_str) {
-        if (p->offsets[0] != 0) return REI_EINVAL;
-        for (uint32_t k = 0; k < n_str; k++)
-            if (p->offsets[k + 1] < p->offsets[k] || p->offsets[k + 1] - p->offsets[k] > REI_MAX_STRLEN)
-                return REI_EINVAL;
-    }
     // sizes beyond what the scratch array holds are refused, not truncated
-    if (total > kInputBytes || n_str + 1 > kMaxStrings) {
-        out->status = REI_ESCRATCH;
-        return REI_ESCRATCH;
-    }
+    if (total > kInputBytes || n_str + 1 > kMaxStrings) NA_RET(REI_ESCRATCH);
 
     int device = 0;
     NA_CK(cudaGetDevice(&device));
@@ -234,10 +231,7 @@ extern "C" rei_status rei_solve_noalloc(const rei_problem *p, void *stream_v, re
     uint32_t *d_tstack = (uint32_t *)cv.take(16ull * (REI_MAX_COST + 2));
     uint32_t *d_trace = (uint32_t *)cv.take(4ull * kMaxGrid);
     uint32_t *d_blk = (uint32_t *)cv.take(4ull * kMaxGrid);
-    if (!d_blk) {
-        out->status = REI_ESCRATCH;
-        return REI_ESCRATCH;
-    }
+    if (!d_blk) NA_RET(REI_ESCRATCH);
 
     // inputs: device inputs are read in place; host inputs are copied in
     const uint8_t *in_bytes = d_bytes;
@@ -261,6 +255,7 @@ extern "C" rei_status rei_solve_noalloc(const rei_problem *p, void *stream_v, re
     sj.n_neg = p->n_neg;
     memcpy(sj.alphabet, p->alphabet, p->n_sym);
     sj.n_sym = p->n_sym;
+    sj.total_bytes = (uint32_t)total;
     sj.info = d_si;
     sj.word_start = d_ws;
     sj.word_len = d_wl;
@@ -282,11 +277,8 @@ extern "C" rei_status rei_solve_noalloc(const rei_problem *p, void *stream_v, re
     out->stats.words = I.W;
     out->stats.max_len = I.max_len;
     out->stats.guide_pairs = I.G;
-    if (I.status == SE_PAIRS) {
-        out->status = REI_ESCRATCH;
-        return REI_ESCRATCH;
-    }
-    if (I.status != SE_OK) return REI_EINVAL;
+    if (I.status == SE_PAIRS) NA_RET(REI_ESCRATCH);
+    if (I.status != SE_OK) NA_RET(REI_EINVAL);
 
     const uint32_t n = I.n, W = I.W, G = I.G, max_len = I.max_len, max_cost = p->max_cost;
     const uint64_t per = 4ull * W + 28;
@@ -305,33 +297,33 @@ extern "C" rei_status rei_solve_noalloc(const rei_problem *p, void *stream_v, re
     uint32_t *d_l = (uint32_t *)cv.take(4ull * std::max<uint64_t>(cap, 1));
     uint32_t *d_r = (uint32_t *)cv.take(4ull * std::max<uint64_t>(cap, 1));
     uint32_t *d_used = (uint32_t *)cv.take(4ull * std::max<uint64_t>(cap, 1));
-    if (!d_used) {  // the budget's cache does not fit the array
-        out->status = REI_ESCRATCH;
-        return REI_ESCRATCH;
-    }
+    if (!d_used) NA_RET(REI_ESCRATCH);  // the budget's cache does not fit the array
 
-    // launch shape (as the allocating path chooses it)
+    // launch shape (as the allocating path chooses it), within the dynamic
+    // shared memory the search kernel can take
+    size_t smem_max = 0;
+    NA_CK(solve_smem_max(&smem_max));
     const uint32_t seg_cap = 2 * max_cost + 4;
     bool gt_smem = 4ull * (n + 1 + G + max_len + 2) <= 96 * 1024;
     uint32_t warps = 8;
     size_t smem = solve_smem_bytes(W, n, G, max_len, seg_cap, gt_smem, warps);
-    while (smem > prop.sharedMemPerBlockOptin && warps > 1) {
+    while (smem > smem_max && warps > 1) {
         warps /= 2;
         smem = solve_smem_bytes(W, n, G, max_len, seg_cap, gt_smem, warps);
     }
-    if (smem > prop.sharedMemPerBlockOptin && gt_smem) {
+    if (smem > smem_max && gt_smem) {
         gt_smem = false;
         warps = 8;
         smem = solve_smem_bytes(W, n, G, max_len, seg_cap, gt_smem, warps);
-        while (smem > prop.sharedMemPerBlockOptin && warps > 1) {
+        while (smem > smem_max && warps > 1) {
             warps /= 2;
             smem = solve_smem_bytes(W, n, G, max_len, seg_cap, gt_smem, warps);
         }
     }
-    if (smem > prop.sharedMemPerBlockOptin) return REI_EINVAL;
+    if (smem > smem_max) NA_RET(REI_EINVAL);
     int bps = 0;
     NA_CK(solve_occupancy(32 * warps, smem, &bps));
-    if (bps < 1) return REI_ECUDA;
+    if (bps < 1) NA_RET(REI_ECUDA);
     const uint32_t grid = std::min<uint32_t>(kMaxTeam, (uint32_t)(prop.multiProcessorCount * bps));
 
     // what must start cleared: table, survivor bitmap, level sizes
@@ -368,7 +360,11 @@ extern "C" rei_status rei_solve_noalloc(const rei_problem *p, void *stream_v, re
     j.n_pos_set = I.n_pos_set;
     j.pos_eps = I.pos_eps;
     j.neg_eps = I.neg_eps;
-    for (int k = 0; k < 5; k++) j.c[k] = cc[k];
+    j.c[0] = p->costs.c_sym;
+    j.c[1] = p->costs.c_opt;
+    j.c[2] = p->costs.c_star;
+    j.c[3] = p->costs.c_cat;
+    j.c[4] = p->costs.c_alt;
     fill_leaves(p, &j.cmin, j.leaf_cost, j.leaf_sym);
     j.max_cost = max_cost;
     j.max_errors = p->max_errors;
@@ -424,14 +420,19 @@ extern "C" rei_status rei_solve_noalloc(const rei_problem *p, void *stream_v, re
     }
     out->status = result;
     if (result != REI_OK) return result;
+    // the outcome stays in out->status; a buffer too small for the answer is
+    // reported by the return value (needed sizes written back), as in
+    // rei_solve_problem
     out->cost = hr.s.ans_cost;
     const uint32_t ntok = hr.s.tree_len;
     out->tree_len = 2ull * ntok;
+    rei_status ws = REI_OK;
     if (out->tree) {
-        if (out->tree_cap < out->tree_len) return REI_EBUFSZ;
-        memcpy(out->tree, hr.tree, out->tree_len);
+        if (out->tree_cap >= out->tree_len) memcpy(out->tree, hr.tree, out->tree_len);
+        else ws = REI_EBUFSZ;
     }
     out->regex_len = format_noalloc(hr.tree, ntok, p->alphabet, out->regex, out->regex ? out->regex_cap : 0);
-    if (out->regex && out->regex_cap < out->regex_len + 1) return REI_EBUFSZ;
-    return REI_OK;
+    if (out->regex && out->regex_cap < out->regex_len + 1) ws = REI_EBUFSZ;
+    else if (!out->regex && out->regex_cap) ws = REI_EINVAL;
+    return ws;
 }

@@ -50,7 +50,7 @@ enum StageErr : uint32_t {
     SE_IC_LARGE = 3,   // |ic| > REI_MAX_IC
     SE_STRLEN = 4,     // a string longer than REI_MAX_STRLEN
     SE_PAIRS = 5,      // guide table larger than the pair buffer (retry bigger)
-    SE_OFFSETS = 6,    // offsets do not start at 0 or decrease
+    SE_OFFSETS = 6,    // offsets do not start at 0, decrease, or end elsewhere than total_bytes
     SE_INTERNAL = 7,   // an infix lookup failed (never expected)
 };
 
@@ -79,6 +79,7 @@ struct StageJob {
     uint32_t n_pos, n_neg;
     uint8_t alphabet[256];
     uint32_t n_sym;
+    uint32_t total_bytes;             // = offs[n_pos + n_neg], checked on the device
     // outputs (device)
     StageInfo *info;
     uint32_t *word_start, *word_len;  // kMaxIC

@@ -2154,6 +2154,7 @@ __global__ void __launch_bounds__(256, 2) k_serve(const __grid_constant__ ServeA
             sj.n_neg = q.n_neg;
             for (uint32_t a = 0; a < q.n_sym; a++) sj.alphabet[a] = q.alphabet[a];
             sj.n_sym = q.n_sym;
+            sj.total_bytes = q.total_bytes;
             sj.info = A.sinfo + slot;
             sj.word_start = A.word_start + (uint64_t)slot * kMaxIC;
             sj.word_len = A.word_len + (uint64_t)slot * kMaxIC;
@@ -2298,6 +2299,22 @@ static cudaError_t prepare(const void *fn) {
     return cudaSuccess;
 }
 
+// the largest dynamic shared memory one launch of `fn` can take on the
+// current device: the opt-in maximum per CTA less the kernel's static shared
+// memory
+static cudaError_t smem_max_of(const void *fn, size_t *bytes) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    *bytes = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    return cudaSuccess;
+}
+
 static cudaError_t occupancy(const void *fn, uint32_t threads, size_t smem, int *bps) {
     cudaError_t e = prepare(fn);
     if (e != cudaSuccess) return e;
@@ -2341,6 +2358,10 @@ cudaError_t solve_fused_occupancy(uint32_t threads, size_t smem, int *blocks_per
 cudaError_t solve_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm) {
     return occupancy((const void *)k_solve, threads, smem, blocks_per_sm);
 }
+
+cudaError_t solve_smem_max(size_t *bytes) { return smem_max_of((const void *)k_solve, bytes); }
+
+cudaError_t solve_batch_smem_max(size_t *bytes) { return smem_max_of((const void *)k_solve_batch, bytes); }
 
 cudaError_t launch_rehash(const SolveJob *job, uint32_t count, uint32_t grid, cudaStream_t stream) {
     k_rehash<<<grid, 256, 0, stream>>>(*job, count);

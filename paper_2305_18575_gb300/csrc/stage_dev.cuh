@@ -274,9 +274,10 @@ __device__ inline void stage_run(const StageJob &J, const StageSmem &M) {
     const uint32_t total = offs[n_str];
     STAGE_MARK(0);
 
-    // offsets start at 0 and never decrease (device inputs are not checked on
-    // the host); every byte must be a symbol; strings must fit the length field
-    if (offs[0] != 0) s_err = SE_OFFSETS;
+    // offsets start at 0, never decrease and end at the declared total (device
+    // inputs are not checked on the host); every byte must be a symbol;
+    // strings must fit the length field
+    if (offs[0] != 0 || total != J.total_bytes) s_err = SE_OFFSETS;
     for (uint32_t k = tid; k < n_str; k += nt)
         if (offs[k + 1] < offs[k]) s_err = SE_OFFSETS;
     __syncthreads();
@@ -425,6 +426,13 @@ __device__ inline void stage_run(const StageJob &J, const StageSmem &M) {
     }
     const uint32_t max_len = M.wlen[n - 1];
     if (tid == 0) J.len_start[max_len + 1] = n;
+    // a failed lookup (not expected: every infix of every example is in the
+    // set) leaves no valid rank to walk the splits with: stop here
+    __syncthreads();
+    if (s_err != SE_OK) {
+        if (tid == 0) J.info->status = s_err;
+        return;
+    }
 
     // guide-table offsets: exclusive scan of |w| + 1 over words in rank order
     const uint32_t per = (n + nt - 1) / nt;

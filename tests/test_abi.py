@@ -78,3 +78,33 @@ def test_binding_constants_match_header(tmp_path):
     for n in names:
         assert hasattr(rei, n), n
         assert int(got[n]) == getattr(rei, n), n
+
+
+def _noalloc(prob):
+    buf = rei._OutBuf()
+    s = rei.rei_solve_noalloc(prob.p, None, buf.res)
+    return s, buf.res.status
+
+
+def test_noalloc_refuses_bad_arguments_before_any_launch():
+    """rei_solve_noalloc applies the argument rules of every other entry point
+    and answers REI_EINVAL, in the return value and in out->status, before it
+    makes any CUDA call (so this runs without a GPU)."""
+    # device inputs: bytes missing while total_bytes > 0
+    p = rei.Problem(b"01", [b"01"], [b"1"])
+    p.p.flags |= rei.REI_F_DEVICE_INPUT
+    p.p.bytes = None
+    p.p.total_bytes = 3
+    assert _noalloc(p) == (rei.REI_EINVAL, rei.REI_EINVAL)
+    # host inputs: bytes missing while the strings are not empty
+    p = rei.Problem(b"01", [b"01"], [b"1"])
+    p.p.bytes = None
+    assert _noalloc(p) == (rei.REI_EINVAL, rei.REI_EINVAL)
+    # example counts whose 32-bit sum wraps around: beyond the 2^24 limit
+    p = rei.Problem(b"01", [b"01"], [b"1"])
+    p.p.n_pos, p.p.n_neg = 0xFFFFFFFF, 2
+    assert _noalloc(p) == (rei.REI_EINVAL, rei.REI_EINVAL)
+    # a zero cost, a repeated symbol, max_cost beyond the limit
+    assert _noalloc(rei.Problem(b"01", [b"01"], [b"1"], costs=(1, 0, 1, 1, 1))) == (rei.REI_EINVAL, rei.REI_EINVAL)
+    assert _noalloc(rei.Problem(b"00", [b"0"], [b""])) == (rei.REI_EINVAL, rei.REI_EINVAL)
+    assert _noalloc(rei.Problem(b"01", [b"0"], [b""], max_cost=256)) == (rei.REI_EINVAL, rei.REI_EINVAL)

@@ -60,3 +60,19 @@ def test_reference_arm_prints_only_on_rank_zero(capsys):
         steps, warmup, gpus = 1, 0, 2
     bench.run_reference(A, rank=1, world=2)
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_runs_the_gpu_arms_problems(capsys):
+    """Rank 0 of the reference arm prints one line whose config is the GPU
+    arm's (the same 40 problems), with its cpu_baseline and e2e objects."""
+    import json
+
+    class A:
+        steps, warmup, gpus = 1, 0, 1
+    bench.run_reference(A, rank=0, world=1)
+    line = json.loads(capsys.readouterr().out)
+    assert line["impl"] == "reference"
+    assert line["config"] == bench.config_of(1)
+    assert line["config"]["problems_per_step"] == 40
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["value"] > 0

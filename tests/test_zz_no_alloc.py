@@ -77,3 +77,18 @@ def test_noalloc_with_per_symbol_costs():
             want = ctx.solve_problem(prob)
             assert key(noalloc(prob)) == key(want)
 
+
+
+def test_noalloc_short_regex_buffer_is_terminated():
+    """A regex buffer too small for the answer: REI_EBUFSZ, the full length
+    written back, and the buffer cut at cap - 1 bytes and NUL terminated."""
+    inst = make_config("medium", 5)
+    prob = rei.Problem(inst.alphabet, inst.pos, inst.neg, max_cost=40, mem_budget=BUDGET)
+    full = noalloc(prob)
+    assert full.status == rei.REI_OK and len(full.regex.encode()) > 4
+    buf = rei._OutBuf(regex_cap=4)
+    buf.rbuf.raw = b"\xff" * 4
+    s = rei.rei_solve_noalloc(prob.p, None, buf.res)
+    assert s == rei.REI_EBUFSZ and buf.res.status == rei.REI_OK
+    assert buf.res.regex_len == len(full.regex.encode())
+    assert buf.rbuf.raw == full.regex.encode()[:3] + b"\x00"
