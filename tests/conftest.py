@@ -41,3 +41,18 @@ def load_golden(name: str) -> dict:
 @pytest.fixture(scope="session")
 def golden():
     return load_golden
+
+
+def load_expected(name: str):
+    """Rows of a stored-oracle-results fixture (written by a script under
+    tests/golden that calls only the oracle): seed -> (status, cost,
+    candidates, unique, n_ic, tree)."""
+    rows = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            sd, st, cost, cand, uniq, n_ic, *tree = line.split()
+            rows[int(sd)] = (int(st), int(cost), int(cand), int(uniq), int(n_ic),
+                             bytes.fromhex(tree[0]) if tree else b"")
+    return rows

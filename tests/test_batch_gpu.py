@@ -8,7 +8,11 @@ import paper_2305_18575_gb300 as rei
 from workloads import make_config, type1_instance, type2_instance
 from workloads.gen import batched_instance
 
+from conftest import load_expected
+
 pytestmark = pytest.mark.gpu
+
+ST = {oracle.OK: rei.REI_OK, oracle.NOT_FOUND: rei.REI_NOT_FOUND, oracle.OOM: rei.REI_OOM}
 
 
 def key(r):
@@ -62,20 +66,26 @@ def test_batch_matches_oracle_on_small_problems():
             (rei.REI_OK, ref.cost, ref.tree, ref.candidates, ref.unique)
 
 
-def test_batch_config_with_autotuning():
-    """512 instances of the batched workload: autotuned launch shape, exact results."""
+def test_batch_config_matches_stored_oracle_results():
+    """Every one of the 512 instances of the batched configuration, solved in
+    one rei_solve_batch call with the autotuned launch shape: status, cost,
+    tree, candidate and unique counts and |ic| equal the oracle's (stored by
+    tests/golden/make_batched_expected.py, which calls only the oracle)."""
+    want = load_expected("batched_expected.txt")
+    assert sorted(want) == list(range(512))
     insts = [batched_instance(s) for s in range(512)]
     probs = [rei.Problem(i.alphabet, i.pos, i.neg, costs=(1, 1, 1, 1, 1), max_cost=40, mem_budget=1 << 30)
              for i in insts]
     with rei.Context(device=0) as ctx:
         batch = ctx.solve_batch(probs)
-        for k in range(0, 512, 17):  # a sample against the plain path
+        for k in range(0, 512, 17):  # a sample against the plain path too
             assert key(ctx.solve_problem(probs[k])) == key(batch[k]), k
-    assert all(r.status == rei.REI_OK for r in batch)
-    for i, r in zip(insts[:64], batch[:64]):
+    for s, r in enumerate(batch):
+        st, cost, cand, uniq, n_ic, tree = want[s]
+        assert r.status == ST[st], s
+        assert (r.cost, r.tree, r.candidates, r.unique, r.n_ic) == (cost, tree, cand, uniq, n_ic), s
+    for i, r in zip(insts, batch):
         assert r.cost <= i.target_cost
-        assert all(oracle.match(r.tree, i.alphabet, p) for p in i.pos)
-        assert not any(oracle.match(r.tree, i.alphabet, q) for q in i.neg)
 
 
 def test_batch_with_per_symbol_costs():

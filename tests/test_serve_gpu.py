@@ -12,7 +12,8 @@ import paper_2305_18575_gb300 as rei
 from workloads import make_config, type1_instance
 from workloads.gen import batched_instance
 
-from test_batch_gpu import key, mixed_problems
+from conftest import load_expected
+from test_batch_gpu import ST, key, mixed_problems
 
 pytestmark = pytest.mark.gpu
 
@@ -133,3 +134,21 @@ def test_serve_time_allowance_does_not_change_results(yield_us):
             got = [srv.result(t) for t in [srv.submit(p) for p in probs]]
     for k, (a, b) in enumerate(zip(plain, got)):
         assert key(a) == key(b), (k, yield_us)
+
+
+def test_served_pool_matches_stored_oracle_results():
+    """The served configuration's pool (instances 0-63, |ic| up to 2048 by
+    the recipe): every served result equals the oracle's stored result
+    (tests/golden/make_batched_expected.py, which calls only the oracle).  At
+    most eight problems are live at once."""
+    from workloads import make_config
+    want = load_expected("served_expected.txt")
+    insts = [make_config("served", s) for s in sorted(want)]
+    probs = [rei.Problem(i.alphabet, i.pos, i.neg, costs=(1, 1, 1, 1, 1), max_cost=40, mem_budget=1 << 30)
+             for i in insts]
+    with rei.Context(device=0) as ctx, rei.Server(ctx, budget_bytes=8 << 30, max_live=8) as srv:
+        got = [srv.result(t) for t in [srv.submit(p) for p in probs]]
+    for s, r in zip(sorted(want), got):
+        st, cost, cand, uniq, n_ic, tree = want[s]
+        assert r.status == ST[st], s
+        assert (r.cost, r.tree, r.candidates, r.unique, r.n_ic) == (cost, tree, cand, uniq, n_ic), s
