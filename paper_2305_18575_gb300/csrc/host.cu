@@ -84,7 +84,8 @@ struct rei_ctx {
     // search
     DevBuf cs, bp_op, bp_l, bp_r, table, minidx, tmp, pending, slotpos, bitmap, blk, lvl_start, lvl_count,
         state, solve_job, tstack, trace, used;
-    bool table_clean = false;  // the search kernel leaves the table empty after a normal end
+    DevBuf seen;               // bitmap of cached 1-word languages (2^kSeenBits bits)
+    bool table_clean = false;  // the search kernel leaves the table (and seen) empty after a normal end
     // batched form
     DevBuf b_in, b_sjobs, b_sinfo, b_stage, b_jobs, b_out, b_tree, b_queue;
     DevBuf s_cs, s_bp_op, s_bp_l, s_bp_r, s_used, s_table, s_tmp, s_pend, s_slotpos, s_bitmap, s_blk, s_lvl,
@@ -503,10 +504,15 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
     if ((s = ensure(c, c->solve_job, sizeof(SolveJob)))) return s;
     if ((s = ensure(c, c->tstack, 16ull * (max_cost + 2)))) return s;
     if ((s = ensure(c, c->trace, 4ull * grid))) return s;
+    if (c->opt_exact && !c->seen.p) {
+        if ((s = ensure(c, c->seen, (1ull << kSeenBits) / 8))) return s;
+        c->table_clean = false;
+    }
     if (!c->table_clean) {
         CK(cudaMemsetAsync(c->table.p, 0xFF, c->table.bytes, c->stream));
         CK(cudaMemsetAsync(c->minidx.p, 0xFF, c->minidx.bytes, c->stream));
         CK(cudaMemsetAsync(c->bitmap.p, 0, c->bitmap.bytes, c->stream));
+        if (c->seen.p) CK(cudaMemsetAsync(c->seen.p, 0, c->seen.bytes, c->stream));
     }
     c->table_clean = false;
     // state, answer tokens, staging report: zero (the launch fills in the rest)
@@ -584,6 +590,8 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
     F.small_opt = c->opt_small_rows < 0 ? 0xFFFFFFFFu : (uint32_t)c->opt_small_rows;
     F.smem_cap = (uint32_t)smem;
     F.handover = c->opt_handover;
+    F.seen = (uint32_t *)c->seen.p;
+    F.seen_bits = c->seen.p ? kSeenBits : 0;
 
     CK(cudaEventRecord(c->ev[0], c->stream));
     CK(launch_solve_fused(&F, grid, threads, smem, c->stream));
@@ -765,12 +773,18 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
     if ((s = ensure_pinned(c, sizeof(SolveJob) + sizeof(SolveState) + tree_bytes))) return s;
     hst = (SolveState *)(c->h_pin + sizeof(SolveJob));  // (the pinned buffer may have moved)
 
+    const bool use_seen = c->opt_exact && W == 1 && n <= kSeenBits;
+    if (use_seen && !c->seen.p) {
+        if ((s = ensure(c, c->seen, (1ull << kSeenBits) / 8))) return s;
+        CK(cudaMemsetAsync(c->seen.p, 0, c->seen.bytes, c->stream));
+    }
     if (!fused) {
         if (!c->table_clean) {
             // a new table, or the last search ended abnormally: clear it all once
             CK(cudaMemsetAsync(c->table.p, 0xFF, c->table.bytes, c->stream));
             CK(cudaMemsetAsync(c->minidx.p, 0xFF, c->minidx.bytes, c->stream));
             CK(cudaMemsetAsync(c->bitmap.p, 0, c->bitmap.bytes, c->stream));
+            if (c->seen.p) CK(cudaMemsetAsync(c->seen.p, 0, c->seen.bytes, c->stream));
         }
         c->table_clean = false;
         uint32_t hj_cmin;
@@ -827,6 +841,7 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
         hj->table = (unsigned long long *)c->table.p;
         hj->minidx = (uint32_t *)c->minidx.p;
         hj->exact = (W <= 2 && n <= 62 && c->opt_exact) ? 1u : 0u;
+        hj->seen = use_seen ? (uint32_t *)c->seen.p : nullptr;
         hj->table_mask = tslots - 1;
         hj->tmp = (uint32_t *)c->tmp.p;
         hj->pending = (uint32_t *)c->pending.p;
@@ -1024,7 +1039,7 @@ void rei_ctx_destroy(rei_ctx *c) {
                       &c->len_start, &c->gt_off, &c->gt_pair, &c->pos, &c->neg, &c->leaf, &c->cs,
                       &c->bp_op, &c->bp_l, &c->bp_r, &c->table, &c->minidx, &c->tmp, &c->pending, &c->slotpos,
                       &c->bitmap, &c->blk, &c->lvl_start, &c->lvl_count, &c->state, &c->solve_job,
-                      &c->tstack, &c->trace, &c->used, &c->b_in, &c->b_sjobs, &c->b_sinfo, &c->b_stage,
+                      &c->tstack, &c->trace, &c->used, &c->seen, &c->b_in, &c->b_sjobs, &c->b_sinfo, &c->b_stage,
                       &c->b_jobs, &c->b_out, &c->b_tree, &c->b_queue, &c->s_cs, &c->s_bp_op, &c->s_bp_l,
                       &c->s_bp_r, &c->s_used, &c->s_table, &c->s_tmp, &c->s_pend, &c->s_slotpos, &c->s_bitmap,
                       &c->s_blk, &c->s_lvl, &c->s_state, &c->s_tstack};

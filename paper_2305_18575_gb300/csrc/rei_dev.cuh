@@ -25,7 +25,9 @@ constexpr uint64_t kEmpty = ~0ull;
 constexpr uint32_t kPending = 0x80000000u;
 constexpr uint32_t kMaxTeam = 2047;  // CTAs of a plain search launch at most (the ordered append's prefix table)
 constexpr uint32_t kNoRight = 0xFFFFFFFFu;
+constexpr uint32_t kNoOperand = 0xFFFFFFFFu;  // no cache row (rows are < 2^31)
 constexpr unsigned long long kNone = ~0ull;
+constexpr uint32_t kSeenBits = 30;   // largest |ic| with a bitmap of cached languages (2^30 bits = 128 MiB)
 
 // operators of a cache entry / candidate
 enum Op : uint32_t { OP_LEAF = 0, OP_OPT = 1, OP_STAR = 2, OP_CAT = 3, OP_ALT = 4 };
@@ -173,6 +175,11 @@ struct SolveJob {
     // of the chunk with that language; 0 = fingerprint | row slots
     uint32_t exact;
     uint32_t *minidx;
+    // 1-word languages (|ic| <= kSeenBits, exact keys): bit L of seen[] is set
+    // once language L is cached, so that a candidate whose language is already
+    // cached is told by one bit instead of a table probe; nullptr = none.  All
+    // zero between searches (a search clears the words of the rows it cached).
+    uint32_t *seen;
     // leaves: the alphabet symbols ordered by (cost, alphabet order) and
     // their costs (every symbol costs c[0] unless costs are given per
     // symbol; a cost above REI_MAX_COST is stored as REI_MAX_COST + 1);
@@ -200,6 +207,8 @@ struct FuseArgs {
     uint32_t small_opt;       // languages in shared memory at the start: 0xFFFFFFFF automatic, 0 none
     uint64_t handover;        // levels above this many candidates go to the relaunch (0 = never)
     uint32_t smem_cap;        // dynamic shared memory of the launch
+    uint32_t seen_bits;       // the seen bitmap covers languages of up to this many bits (0 = none)
+    uint32_t *seen;           // 2^seen_bits bits, all zero
 };
 
 

@@ -144,8 +144,36 @@ __device__ __forceinline__ uint64_t cs_hash(const uint32_t *c, uint32_t W, uint3
 struct SegTile {
     uint64_t lo, hi;  // chunk intersected with the segment
     uint64_t r0;      // first row (binary ops)
-    uint64_t nb;      // column blocks per row, or row blocks per column (swapped)
+    uint32_t nb;      // column blocks per row, or row blocks per column (swapped)
+    uint32_t nb_mul;  // x / nb = (umulhi(nb_mul, x) + x) >> nb_shift for x < 2^31
+    uint32_t nb_shift, pad;
 };
+
+// Division by a divisor fixed for many dividends (Granlund and Montgomery,
+// "Division by invariant integers using multiplication", 1994, the round-up
+// method with a 33-bit multiplier 2^32 + m): for 1 <= d < 2^31 and x < 2^31,
+// x / d = (umulhi(m, x) + x) >> l with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1.
+__host__ __device__ inline void div_magic(uint32_t d, uint32_t &m, uint32_t &l) {
+    l = 0;
+    while ((1ull << l) < d) l++;
+    m = (uint32_t)((((1ull << l) - d) << 32) / d + 1);
+}
+
+__device__ __forceinline__ uint32_t div_by(uint32_t x, uint32_t m, uint32_t l) {
+    return (__umulhi(m, x) + x) >> l;
+}
+
+// per-warp shared memory (32-bit words): the shared operand's words, two
+// 32-candidate tiles (candidate-major and bit-sliced); for 1-word languages
+// also the nibble tables of the concatenation's shared operand and its id
+constexpr uint32_t kW1Tab = 128;   // 8 nibble tables of 16 words
+constexpr uint32_t kW1TabAt = 68;  // their offset (4 + 2 * 32 words; 16-byte aligned)
+__host__ __device__ inline uint32_t warp_words(uint32_t W) {
+    const uint32_t Ws = (W & 1u) ? W : W + 1;
+    const uint32_t base = ((W + 3) & ~3u) + 2 * 32 * Ws;
+    return W == 1 ? kW1TabAt + kW1Tab + 4 : base;
+}
 
 struct Shared {
     Seg *seg;                // level plan
@@ -242,8 +270,12 @@ __device__ void plan_level(const SolveJob &J, uint32_t c, const uint32_t *lvs, c
                 s.rbase = lvs[cr];
                 s.rcnt = lvc[cr];
                 size = (uint64_t)s.lcnt * s.rcnt;
-                // fewer than 32 right operands: bit-slice over 32 left ones instead
-                s.swap = (s.rcnt < 32 && s.lcnt > s.rcnt) ? 1u : 0u;
+                // tiles of 32 right operands per left one, or (swapped) of 32
+                // left operands per right one: whichever needs fewer tiles
+                // (fewer partly empty tiles)
+                const uint64_t t_rows = (uint64_t)s.lcnt * ((s.rcnt + 31) / 32);
+                const uint64_t t_cols = (uint64_t)s.rcnt * ((s.lcnt + 31) / 32);
+                s.swap = t_cols < t_rows ? 1u : 0u;
             } else {
                 const uint32_t cl = c1 + (uint32_t)(k - 3 - ncat), cr = (uint32_t)rem_u - cl;
                 s.op = OP_ALT;
@@ -453,6 +485,10 @@ template <uint32_t WT>
 __device__ void dedup_insert_exact(const TileCtx &T, const uint32_t *c, uint32_t xl) {
     const SolveJob &J = *T.J;
     const uint32_t W = WT ? WT : T.W;
+    // a language cached by an earlier chunk: one bit of the seen bitmap (set
+    // by the append of that chunk, visible after its grid barriers; read
+    // through L2).  Languages new in this chunk take the table protocol below.
+    if (J.seen && ((ldcg(J.seen + (c[0] >> 5)) >> (c[0] & 31u)) & 1u)) return;
     const unsigned long long key = exact_key(c, W), pk = key | kXPend;
     const uint64_t h = cs_hash(c, W, 1);
     uint64_t p = h & J.table_mask;
@@ -580,8 +616,8 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uin
         valid = x < hi;
         nrow = (uint32_t)umin64(32, hi - first);
     } else if (swapped) {
-        // (a segment's tiles in a chunk and its blocks per row fit 32 bits)
-        const uint32_t t32 = (uint32_t)tile, nb = (uint32_t)tl.nb, qt = t32 / nb;
+        // (a segment's tiles in a chunk and its blocks per row fit 31 bits)
+        const uint32_t t32 = (uint32_t)tile, nb = tl.nb, qt = div_by(t32, tl.nb_mul, tl.nb_shift);
         col = qt;
         first = (uint32_t)tl.r0 + (t32 - qt * nb) * 32;
         row = first + lane;
@@ -589,7 +625,7 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uin
         valid = row < sg.lcnt && x >= lo && x < hi;
         nrow = min(32u, sg.lcnt - first);
     } else {
-        const uint32_t t32 = (uint32_t)tile, nb = (uint32_t)tl.nb, qt = t32 / nb;
+        const uint32_t t32 = (uint32_t)tile, nb = tl.nb, qt = div_by(t32, tl.nb_mul, tl.nb_shift);
         row = (uint32_t)tl.r0 + qt;
         first = (t32 - qt * nb) * 32;
         col = first + lane;
@@ -744,6 +780,118 @@ __device__ void run_tile(const TileCtx &T, const Seg &sg, const SegTile &tl, uin
 #undef TILE_JB
 
 // ---------------------------------------------------------------------------
+// phase A for 1-word languages (|ic| <= 32): one candidate per lane, its
+// language built in a register.  A concatenation l.r with one operand shared
+// by the whole tile (l, or r when swapped) is a map of the other operand's
+// words: out = OR over the set bits b of the other operand of M[b], with M[b]
+// the words w = u v of ic with u in l and v = b (swapped: u = b and v in r),
+// read off the guide table (Alg. 2).  The map is kept as 8 nibble tables,
+// T[t][x] = OR over the set bits i of x of M[4t + i], so a candidate costs one
+// shared-memory read per 4 bits of ic; the tables are rebuilt only when the
+// tile's shared operand differs from the previous tile's.
+
+__device__ __forceinline__ void w1_tables(const Shared &S, uint32_t n, uint32_t shared_cs, bool swapped,
+                                          uint32_t *tab, uint32_t lane) {
+    // lane w: column w of M (bit b set when M[b] holds w)
+    uint32_t col = 0;
+    if (lane < n) {
+        const uint32_t p1 = S.gt_off[lane + 1];
+        for (uint32_t p = S.gt_off[lane]; p < p1; p++) {
+            const uint32_t pr = S.gt_pair[p];
+            const uint32_t u = pr & 0xFFFFu, v = pr >> 16;
+            const uint32_t have = swapped ? v : u, other = swapped ? u : v;
+            col |= ((shared_cs >> have) & 1u) << other;
+        }
+    }
+    const uint32_t m = transpose32(col, lane);  // lane b: M[b]
+    // lane 4t + q fills entries 4q .. 4q + 3 of table t
+    const uint32_t t = lane >> 2, q = lane & 3u;
+    const uint32_t m0 = __shfl_sync(0xFFFFFFFFu, m, 4 * t), m1 = __shfl_sync(0xFFFFFFFFu, m, 4 * t + 1);
+    const uint32_t m2 = __shfl_sync(0xFFFFFFFFu, m, 4 * t + 2), m3 = __shfl_sync(0xFFFFFFFFu, m, 4 * t + 3);
+    const uint32_t base = ((q & 1u) ? m2 : 0u) | ((q & 2u) ? m3 : 0u);
+    *reinterpret_cast<uint4 *>(tab + 16 * t + 4 * q) = make_uint4(base, base | m0, base | m1, base | m0 | m1);
+}
+
+__device__ __forceinline__ uint32_t w1_lookup(const uint32_t *tab, uint32_t x, uint32_t nt) {
+    uint32_t out = 0;
+#pragma unroll
+    for (uint32_t t = 0; t < 8; t++)
+        if (t < nt) out |= tab[16 * t + ((x >> (4 * t)) & 15u)];
+    return out;
+}
+
+__device__ void run_tile_w1(const TileCtx &T, const Seg &sg, const SegTile &tl, uint64_t tile, uint32_t *wm) {
+    if (sg.op == OP_STAR) {  // (few candidates: the bit-sliced fixed point)
+        run_tile<1>(T, sg, tl, tile, wm);
+        return;
+    }
+    const SolveJob &J = *T.J;
+    const Shared &S = *T.S;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t *cs = T.ops;
+    const uint64_t lo = tl.lo, hi = tl.hi;
+    // which candidate this lane holds (as run_tile)
+    uint64_t x;
+    uint32_t row = 0, col = 0, first = 0;
+    bool valid;
+    const bool swapped = sg.op == OP_CAT && sg.swap;
+    if (sg.op == OP_LEAF || sg.op == OP_OPT) {
+        first = (uint32_t)(lo + tile * 32);
+        x = (uint64_t)first + lane;
+        valid = x < hi;
+    } else if (swapped) {
+        const uint32_t t32 = (uint32_t)tile, qt = div_by(t32, tl.nb_mul, tl.nb_shift);
+        col = qt;
+        row = (uint32_t)tl.r0 + (t32 - qt * tl.nb) * 32 + lane;
+        x = (uint64_t)row * sg.rcnt + col;
+        valid = row < sg.lcnt && x >= lo && x < hi;
+    } else {
+        const uint32_t t32 = (uint32_t)tile, qt = div_by(t32, tl.nb_mul, tl.nb_shift);
+        row = (uint32_t)tl.r0 + qt;
+        col = (t32 - qt * tl.nb) * 32 + lane;
+        x = (uint64_t)row * sg.rcnt + col;
+        valid = col < sg.rcnt && x >= lo && x < hi && (!sg.tri || col > row);
+    }
+    if (__ballot_sync(0xFFFFFFFFu, valid) == 0) return;
+
+    // ---- build, in a register
+    uint32_t c;
+    if (sg.op == OP_LEAF) {
+        c = valid ? __ldg(J.leaf + (uint64_t)J.leaf_sym[sg.lbase + (uint32_t)x] * J.leaf_stride) : 0u;
+    } else if (sg.op == OP_OPT) {
+        c = (valid ? ldop(cs + sg.lbase + (uint32_t)x) : 0u) | 1u;  // eps is ic word 0
+    } else if (sg.op == OP_ALT) {
+        c = ldop(cs + sg.lbase + row) | (valid ? ldop(cs + sg.rbase + col) : 0u);
+    } else {
+        // the tables of the shared operand (its id in the word after them)
+        uint32_t *tab = wm + kW1TabAt;
+        const uint32_t sid = swapped ? (0x80000000u | (sg.rbase + col)) : (sg.lbase + row);
+        if (tab[kW1Tab] != sid) {
+            const uint32_t sh = ldop(cs + (sid & 0x7FFFFFFFu));
+            __syncwarp();  // (every lane has read the old id)
+            w1_tables(S, T.n, sh, swapped, tab, lane);
+            if (lane == 0) tab[kW1Tab] = sid;
+            __syncwarp();
+        }
+        const uint32_t o = valid ? ldop(cs + (swapped ? sg.lbase + row : sg.rbase + col)) : 0u;
+        c = w1_lookup(tab, o, (T.n + 3) >> 2);
+    }
+
+    // ---- precision and uniqueness
+    if (!valid) return;
+    const uint32_t errs = __popc(S.pos[0] & ~c) + __popc(S.neg[0] & c);
+    const uint64_t xlev = sg.start + x;
+    if (errs <= J.max_errors) atomicMin(T.found, (unsigned long long)xlev);
+    if (T.dedup) {
+        const uint32_t xl = (uint32_t)(xlev - T.chunk_start);
+        if (T.smem) dedup_insert_smem<1>(T, &c, xl);
+        else if (J.exact) dedup_insert_exact<1>(T, &c, xl);
+        else if (T.bits) dedup_insert_solo<1>(T, &c, xl);
+        else dedup_insert<1>(T, &c, xl);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // decode a level-local index into (segment, op, left, right)
 
 __device__ void decode(const Seg *seg, uint32_t nseg, const uint8_t *leaf_sym, uint64_t xlev, uint32_t &op,
@@ -850,7 +998,9 @@ __host__ __device__ size_t solve_smem_bytes(uint32_t W, uint32_t n, uint32_t G, 
     b += 2 * sizeof(uint32_t) * seg_cap;
     b += 2 * sizeof(uint32_t) * W;
     if (gt_in_smem) b += sizeof(uint32_t) * (((n + 1 + G + max_len + 2) + 3) & ~3u);
-    b += sizeof(uint32_t) * (size_t)warps * (((W + 3) & ~3u) + 2 * 32 * Ws);
+    b += 16;  // (the per-warp areas start on a 16-byte boundary)
+    b += sizeof(uint32_t) * (size_t)warps * warp_words(W);
+    (void)Ws;
     return b;
 }
 
@@ -879,13 +1029,13 @@ __device__ void tile_setup(Shared &S, uint32_t nseg, uint64_t cs0, uint64_t ce0,
             tl.lo = a;
             tl.hi = e;
             tl.r0 = 0;
-            tl.nb = 0;
+            tl.nb = 1;
             if (a < e) {
                 if (g.op == OP_CAT || g.op == OP_ALT) {
                     const uint64_t r0w = a / g.rcnt, r1 = (e - 1) / g.rcnt;
                     tl.r0 = r0w;
                     if (g.op == OP_CAT && g.swap) {
-                        tl.nb = (r1 - r0w + 1 + 31) / 32;
+                        tl.nb = (uint32_t)((r1 - r0w + 1 + 31) / 32);
                         tiles = (uint64_t)g.rcnt * tl.nb;
                     } else {
                         tl.nb = (g.rcnt + 31) / 32;
@@ -895,6 +1045,7 @@ __device__ void tile_setup(Shared &S, uint32_t nseg, uint64_t cs0, uint64_t ce0,
                     tiles = (e - a + 31) / 32;
                 }
             }
+            div_magic(tl.nb, tl.nb_mul, tl.nb_shift);
         }
         const uint64_t incl = warp_incl_scan(tiles, lane);
         if (s < nseg) S.tile_first[s] = t + incl - tiles;
@@ -1003,6 +1154,7 @@ __device__ void switch_to_global(const SolveJob &J, Shared &S, Lead *L) {
             }
             p = (p + 1) & J.table_mask;
         }
+        if (J.seen) atomicOr(J.seen + (row[0] >> 5), 1u << (row[0] & 31u));
     }
     __threadfence();
     __syncthreads();
@@ -1083,6 +1235,7 @@ __device__ void solo_append(const SolveJob &J, SolveState *st, Shared &S, const 
             if (W == 2) dst[1] = (uint32_t)(key >> 32);
             J.table[q] = key;
             J.minidx[q] = 0xFFFFFFFFu;
+            if (J.seen) atomicOr(J.seen + ((uint32_t)key >> 5), 1u << (key & 31u));
         } else {
             const uint32_t *srcp = J.tmp + (uint64_t)xl * W;
             for (uint32_t b = 0; b < W; b++) dst[b] = ldcg(srcp + b);
@@ -1154,21 +1307,24 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
         // flight while the warp works on the current one.  Else tile t goes
         // to warp t mod (warps of the team).
         const bool dyn = full && ntiles >= kDynTilesPerWarp * nw;
+        // (1-word languages: longer runs of tiles that share an operand, whose
+        // lookup tables are then built once per run)
+        const uint32_t grab = W == 1 ? 4 * kGrab : kGrab;
         uint32_t t = gw, end = ntiles, step = nw;
         uint32_t nxt = 0;
         if (dyn) {
             uint32_t cur = 0;
-            if (lane == 0) cur = atomicAdd(&st->tile_next, kGrab);
+            if (lane == 0) cur = atomicAdd(&st->tile_next, grab);
             t = __shfl_sync(0xFFFFFFFFu, cur, 0);
-            end = min(t + kGrab, ntiles);
+            end = min(t + grab, ntiles);
             step = 1;
-            if (lane == 0 && t < ntiles) nxt = atomicAdd(&st->tile_next, kGrab);
+            if (lane == 0 && t < ntiles) nxt = atomicAdd(&st->tile_next, grab);
         }
         while (t < ntiles) {
             while (s + 1 < a.nseg && S.tile_first[s + 1] <= t) s++;
             const SegTile &tl = S.tiles[s];
             if (tl.lo < tl.hi) {
-                if (W == 1) run_tile<1>(TC, S.seg[s], tl, t - S.tile_first[s], wm);
+                if (W == 1) run_tile_w1(TC, S.seg[s], tl, t - S.tile_first[s], wm);
                 else if (W == 2) run_tile<2>(TC, S.seg[s], tl, t - S.tile_first[s], wm);
                 else run_tile<0>(TC, S.seg[s], tl, t - S.tile_first[s], wm);
                 __syncwarp();
@@ -1176,8 +1332,8 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
             t += step;
             if (dyn && t >= end) {
                 t = __shfl_sync(0xFFFFFFFFu, nxt, 0);
-                end = min(t + kGrab, ntiles);
-                if (lane == 0 && t < ntiles) nxt = atomicAdd(&st->tile_next, kGrab);
+                end = min(t + grab, ntiles);
+                if (lane == 0 && t < ntiles) nxt = atomicAdd(&st->tile_next, grab);
             }
         }
     }
@@ -1383,6 +1539,7 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
                         if (W == 2) J.cs[k * W + 1] = (uint32_t)(key >> 32);
                         J.table[q[u]] = key;
                         J.minidx[q[u]] = 0xFFFFFFFFu;
+                        if (J.seen) atomicOr(J.seen + ((uint32_t)key >> 5), 1u << (key & 31u));
                     } else {
                         J.table[q[u]] = (old[u] & 0xFFFFFFFF00000000ull) | (uint32_t)k;
                     }
@@ -1470,8 +1627,13 @@ __device__ void carve_shared(const SolveJob &J, Shared &S, uint8_t *smem_raw, ui
         S.gt_pair = J.gt_pair;
         S.len_start = J.len_start;
     }
-    S.warp_words = ((W + 3) & ~3u) + 2 * 32 * Ws;
+    p = smem_raw + ((size_t)(p - smem_raw + 15) & ~size_t(15));
+    S.warp_words = warp_words(W);
     S.warp_mem = reinterpret_cast<uint32_t *>(p);
+    (void)Ws;
+    // no concatenation tables built yet (1-word languages)
+    if (W == 1)
+        for (uint32_t w = tid; w < blockDim.x / 32; w += blockDim.x) S.warp_mem[w * S.warp_words + kW1TabAt + kW1Tab] = kNoOperand;
     for (uint32_t b = tid; b < W; b += blockDim.x) {
         S.pos[b] = J.pos_mask[b];
         S.neg[b] = J.neg_mask[b];
@@ -1503,6 +1665,10 @@ __device__ void clean_table(const SolveJob &J, uint32_t rows, uint32_t npending,
                             uint32_t team_r) {
     const uint64_t t = (uint64_t)team_r * blockDim.x + threadIdx.x, nt = (uint64_t)team_n * blockDim.x;
     for (uint64_t k = t; k < rows; k += nt) J.table[ldcg(J.used + k)] = kEmpty;
+    // the seen bitmap holds bits of cached languages only: zero every word
+    // that holds one
+    if (J.seen)
+        for (uint64_t k = t; k < rows; k += nt) J.seen[ldcg(J.cs + k) >> 5] = 0u;
     for (uint64_t i = t; i < npending; i += nt) {
         const uint32_t q = ldcg(J.pending + i);
         J.table[q] = kEmpty;
@@ -1896,6 +2062,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_solve_fused(const __grid_c
                 const uint32_t W = I.W;
                 j.cap = umin64(F.mem_budget / (4ull * W + 28), 0x7FFF0000ull);
                 j.exact = F.tmpl.exact && W <= 2 && I.n <= 62 ? 1u : 0u;
+                j.seen = j.exact && W == 1 && I.n <= F.seen_bits ? F.seen : nullptr;
                 j.handover = F.handover;
                 const uint64_t tmax = F.table_slots / 2;
                 j.cache_alloc = umin64(umin64(j.cap, F.rows_alloc), umin64(F.cs_words / W, tmax / 2));
@@ -2270,6 +2437,7 @@ __global__ void k_rehash(const __grid_constant__ SolveJob J, uint32_t count) {
             }
             p = (p + 1) & J.table_mask;
         }
+        if (J.seen) atomicOr(J.seen + (c[0] >> 5), 1u << (c[0] & 31u));
     }
 }
 
