@@ -180,9 +180,11 @@ rei_status rei_ctx_create(rei_ctx **out, int device, const rei_alloc *alloc, voi
 void rei_ctx_destroy(rei_ctx *ctx);
 
 /* Tuning options (defaults chosen by the library):
- *   REI_OPT_CHUNK      candidates per dedup chunk (0 = automatic, up to
- *                      2^25; values above 2^26 are taken as 2^26); the
- *                      value only changes how a level is split into chunks
+ *   REI_OPT_CHUNK      candidates per dedup chunk (0 = automatic: up to
+ *                      2^25, or 2^27 for |ic| <= 30 with exact keys;
+ *                      larger values are taken as 2^26, or 2^27 for those);
+ *                      the value only changes how a level is split into
+ *                      chunks
  *   REI_OPT_GRID       CTAs of the search kernel (0 = all that fit)
  *   REI_OPT_KEEP_CACHE 1 = keep the cache after a solve for rei_cache_dump
  *   REI_OPT_CACHE_INIT initial cache capacity in languages (0 = automatic)

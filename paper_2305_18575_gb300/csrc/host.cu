@@ -667,6 +667,10 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
     SolveState *hst = (SolveState *)(c->h_pin + sizeof(SolveJob));
     if (!fused || hst->status == ST_NEED_MEM) {
 
+    // 1-word languages with exact keys: a bitmap of the cached languages in
+    // front of the uniqueness table
+    const bool use_seen = c->opt_exact && W == 1 && n <= kSeenBits;
+
     // launch shape
     const uint32_t seg_cap = 2 * max_cost + 4;
     size_t smem_max = 0;  // dynamic shared memory a k_solve launch can take
@@ -713,9 +717,12 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
     // large levels this launch runs take chunks of up to 32 Mi candidates
     // (at most 1 GiB of candidate rows in tmp; the chunk that holds the
     // answer still runs to its end, which bounds the size from above)
+    // (with the seen bitmap, 128 Mi: most candidates end at one bit, so
+    // chunks are quicker and their fixed barriers weigh more)
     uint64_t chunk_max = c->opt_chunk > 0 ? (uint64_t)c->opt_chunk
-                                          : std::min<uint64_t>(1ull << 25, std::max<uint64_t>(1ull << 16, (1ull << 30) / (4ull * W)));
-    chunk_max = std::min<uint64_t>(chunk_max, 1ull << 26);
+                         : use_seen      ? (1ull << 27)
+                                         : std::min<uint64_t>(1ull << 25, std::max<uint64_t>(1ull << 16, (1ull << 30) / (4ull * W)));
+    chunk_max = std::min<uint64_t>(chunk_max, use_seen ? (1ull << 27) : (1ull << 26));
     uint64_t cache_alloc = c->opt_cache_init > 0 ? (uint64_t)c->opt_cache_init : (1ull << 16);
     if (c->opt_cache_init <= 0 && c->cs.p && c->bp_l.p && c->bp_r.p && c->bp_op.p) {
         // rows a previous solve already allocated (up to 1 Mi, so that the
@@ -728,7 +735,9 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
     cache_alloc = std::max<uint64_t>(1, std::min<uint64_t>(cache_alloc, cap));
 
     auto table_slots = [&](uint64_t alloc_rows) {
-        const uint64_t need = alloc_rows + (alloc_rows >= cap ? chunk_max : 0);
+        uint64_t need = alloc_rows + (alloc_rows >= cap ? chunk_max : 0);
+        // (the table holds distinct languages: at most 2^n of them)
+        if (n < 40) need = std::min<uint64_t>(need, 1ull << n);
         return pow2_at_least(std::max<uint64_t>(2 * need, 1024));
     };
     uint64_t tslots = table_slots(cache_alloc);
@@ -773,7 +782,6 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
     if ((s = ensure_pinned(c, sizeof(SolveJob) + sizeof(SolveState) + tree_bytes))) return s;
     hst = (SolveState *)(c->h_pin + sizeof(SolveJob));  // (the pinned buffer may have moved)
 
-    const bool use_seen = c->opt_exact && W == 1 && n <= kSeenBits;
     if (use_seen && !c->seen.p) {
         if ((s = ensure(c, c->seen, (1ull << kSeenBits) / 8))) return s;
         CK(cudaMemsetAsync(c->seen.p, 0, c->seen.bytes, c->stream));

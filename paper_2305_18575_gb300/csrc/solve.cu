@@ -169,6 +169,10 @@ __device__ __forceinline__ uint32_t div_by(uint32_t x, uint32_t m, uint32_t l) {
 // also the nibble tables of the concatenation's shared operand and its id
 constexpr uint32_t kW1Tab = 128;   // 8 nibble tables of 16 words
 constexpr uint32_t kW1TabAt = 68;  // their offset (4 + 2 * 32 words; 16-byte aligned)
+// candidates per tile of a concatenation or union segment: 32 (one per lane),
+// 64 for 1-word languages (two per lane, built side by side)
+__host__ __device__ inline uint32_t bin_block(uint32_t W) { return W == 1 ? 64u : 32u; }
+
 __host__ __device__ inline uint32_t warp_words(uint32_t W) {
     const uint32_t Ws = (W & 1u) ? W : W + 1;
     const uint32_t base = ((W + 3) & ~3u) + 2 * 32 * Ws;
@@ -273,8 +277,9 @@ __device__ void plan_level(const SolveJob &J, uint32_t c, const uint32_t *lvs, c
                 // tiles of 32 right operands per left one, or (swapped) of 32
                 // left operands per right one: whichever needs fewer tiles
                 // (fewer partly empty tiles)
-                const uint64_t t_rows = (uint64_t)s.lcnt * ((s.rcnt + 31) / 32);
-                const uint64_t t_cols = (uint64_t)s.rcnt * ((s.lcnt + 31) / 32);
+                const uint32_t bw = bin_block(J.W);
+                const uint64_t t_rows = (uint64_t)s.lcnt * ((s.rcnt + bw - 1) / bw);
+                const uint64_t t_cols = (uint64_t)s.rcnt * ((s.lcnt + bw - 1) / bw);
                 s.swap = t_cols < t_rows ? 1u : 0u;
             } else {
                 const uint32_t cl = c1 + (uint32_t)(k - 3 - ncat), cr = (uint32_t)rem_u - cl;
@@ -820,6 +825,43 @@ __device__ __forceinline__ uint32_t w1_lookup(const uint32_t *tab, uint32_t x, u
     return out;
 }
 
+// precision and uniqueness of 1-word candidates c0 (lane candidate x0) and
+// c1 (x1), valid as v0 / v1: both seen-bitmap words are read before either is
+// tested, so the two reads overlap
+__device__ __forceinline__ void w1_finish(const TileCtx &T, const Seg &sg, uint32_t c0, uint64_t x0, bool v0,
+                                          uint32_t c1, uint64_t x1, bool v1) {
+    const SolveJob &J = *T.J;
+    const Shared &S = *T.S;
+    const uint32_t pos = S.pos[0], neg = S.neg[0];
+    const uint64_t xlev0 = sg.start + x0, xlev1 = sg.start + x1;
+    if (v0 && __popc(pos & ~c0) + __popc(neg & c0) <= J.max_errors) atomicMin(T.found, (unsigned long long)xlev0);
+    if (v1 && __popc(pos & ~c1) + __popc(neg & c1) <= J.max_errors) atomicMin(T.found, (unsigned long long)xlev1);
+    if (!T.dedup) return;
+    const uint32_t xl0 = (uint32_t)(xlev0 - T.chunk_start), xl1 = (uint32_t)(xlev1 - T.chunk_start);
+    if (!T.smem && J.exact && J.seen) {
+        // languages cached by earlier chunks end here (one bit each)
+        const uint32_t w0 = v0 ? ldcg(J.seen + (c0 >> 5)) : 0xFFFFFFFFu;
+        const uint32_t w1 = v1 ? ldcg(J.seen + (c1 >> 5)) : 0xFFFFFFFFu;
+        if (!((w0 >> (c0 & 31u)) & 1u)) dedup_insert_exact<1>(T, &c0, xl0);
+        if (!((w1 >> (c1 & 31u)) & 1u)) dedup_insert_exact<1>(T, &c1, xl1);
+        return;
+    }
+    if (v0) {
+        if (T.smem) dedup_insert_smem<1>(T, &c0, xl0);
+        else if (J.exact) dedup_insert_exact<1>(T, &c0, xl0);
+        else if (T.bits) dedup_insert_solo<1>(T, &c0, xl0);
+        else dedup_insert<1>(T, &c0, xl0);
+    }
+    if (v1) {
+        if (T.smem) dedup_insert_smem<1>(T, &c1, xl1);
+        else if (J.exact) dedup_insert_exact<1>(T, &c1, xl1);
+        else if (T.bits) dedup_insert_solo<1>(T, &c1, xl1);
+        else dedup_insert<1>(T, &c1, xl1);
+    }
+}
+
+// one tile of 1-word candidates: 32 of a unary segment (one per lane), or 64
+// of a binary one (two per lane, 32 apart)
 __device__ void run_tile_w1(const TileCtx &T, const Seg &sg, const SegTile &tl, uint64_t tile, uint32_t *wm) {
     if (sg.op == OP_STAR) {  // (few candidates: the bit-sliced fixed point)
         run_tile<1>(T, sg, tl, tile, wm);
@@ -830,42 +872,54 @@ __device__ void run_tile_w1(const TileCtx &T, const Seg &sg, const SegTile &tl, 
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t *cs = T.ops;
     const uint64_t lo = tl.lo, hi = tl.hi;
-    // which candidate this lane holds (as run_tile)
-    uint64_t x;
-    uint32_t row = 0, col = 0, first = 0;
-    bool valid;
-    const bool swapped = sg.op == OP_CAT && sg.swap;
     if (sg.op == OP_LEAF || sg.op == OP_OPT) {
-        first = (uint32_t)(lo + tile * 32);
-        x = (uint64_t)first + lane;
-        valid = x < hi;
-    } else if (swapped) {
-        const uint32_t t32 = (uint32_t)tile, qt = div_by(t32, tl.nb_mul, tl.nb_shift);
-        col = qt;
-        row = (uint32_t)tl.r0 + (t32 - qt * tl.nb) * 32 + lane;
-        x = (uint64_t)row * sg.rcnt + col;
-        valid = row < sg.lcnt && x >= lo && x < hi;
-    } else {
-        const uint32_t t32 = (uint32_t)tile, qt = div_by(t32, tl.nb_mul, tl.nb_shift);
-        row = (uint32_t)tl.r0 + qt;
-        col = (t32 - qt * tl.nb) * 32 + lane;
-        x = (uint64_t)row * sg.rcnt + col;
-        valid = col < sg.rcnt && x >= lo && x < hi && (!sg.tri || col > row);
+        const uint64_t x = lo + tile * 32 + lane;
+        const bool valid = x < hi;
+        if (__ballot_sync(0xFFFFFFFFu, valid) == 0) return;
+        uint32_t c = 0;
+        if (sg.op == OP_LEAF) {
+            if (valid) c = __ldg(J.leaf + (uint64_t)J.leaf_sym[sg.lbase + (uint32_t)x] * J.leaf_stride);
+        } else {
+            c = (valid ? ldop(cs + sg.lbase + (uint32_t)x) : 0u) | 1u;  // eps is ic word 0
+        }
+        w1_finish(T, sg, c, x, valid, 0u, x, false);
+        return;
     }
-    if (__ballot_sync(0xFFFFFFFFu, valid) == 0) return;
-
-    // ---- build, in a register
-    uint32_t c;
-    if (sg.op == OP_LEAF) {
-        c = valid ? __ldg(J.leaf + (uint64_t)J.leaf_sym[sg.lbase + (uint32_t)x] * J.leaf_stride) : 0u;
-    } else if (sg.op == OP_OPT) {
-        c = (valid ? ldop(cs + sg.lbase + (uint32_t)x) : 0u) | 1u;  // eps is ic word 0
-    } else if (sg.op == OP_ALT) {
-        c = ldop(cs + sg.lbase + row) | (valid ? ldop(cs + sg.rbase + col) : 0u);
+    // binary: lane holds (row, col0) and (row, col0 + 32), or, swapped,
+    // (row0, col) and (row0 + 32, col)
+    const bool swapped = sg.op == OP_CAT && sg.swap;
+    const uint32_t t32 = (uint32_t)tile, qt = div_by(t32, tl.nb_mul, tl.nb_shift);
+    const uint32_t off = (t32 - qt * tl.nb) * 64 + lane;
+    uint32_t row0, row1, col0, col1;
+    uint64_t x0, x1;
+    bool v0, v1;
+    if (swapped) {
+        col0 = col1 = qt;
+        row0 = (uint32_t)tl.r0 + off;
+        row1 = row0 + 32;
+        x0 = (uint64_t)row0 * sg.rcnt + qt;
+        x1 = x0 + 32ull * sg.rcnt;
+        v0 = row0 < sg.lcnt && x0 >= lo && x0 < hi;
+        v1 = row1 < sg.lcnt && x1 >= lo && x1 < hi;
+    } else {
+        row0 = row1 = (uint32_t)tl.r0 + qt;
+        col0 = off;
+        col1 = off + 32;
+        x0 = (uint64_t)row0 * sg.rcnt + col0;
+        x1 = x0 + 32;
+        v0 = col0 < sg.rcnt && x0 >= lo && x0 < hi && (!sg.tri || col0 > row0);
+        v1 = col1 < sg.rcnt && x1 >= lo && x1 < hi && (!sg.tri || col1 > row0);
+    }
+    if (__ballot_sync(0xFFFFFFFFu, v0 || v1) == 0) return;
+    uint32_t c0, c1;
+    if (sg.op == OP_ALT) {
+        const uint32_t l = ldop(cs + sg.lbase + row0);
+        c0 = l | (v0 ? ldop(cs + sg.rbase + col0) : 0u);
+        c1 = l | (v1 ? ldop(cs + sg.rbase + col1) : 0u);
     } else {
         // the tables of the shared operand (its id in the word after them)
         uint32_t *tab = wm + kW1TabAt;
-        const uint32_t sid = swapped ? (0x80000000u | (sg.rbase + col)) : (sg.lbase + row);
+        const uint32_t sid = swapped ? (0x80000000u | (sg.rbase + qt)) : (sg.lbase + row0);
         if (tab[kW1Tab] != sid) {
             const uint32_t sh = ldop(cs + (sid & 0x7FFFFFFFu));
             __syncwarp();  // (every lane has read the old id)
@@ -873,22 +927,14 @@ __device__ void run_tile_w1(const TileCtx &T, const Seg &sg, const SegTile &tl, 
             if (lane == 0) tab[kW1Tab] = sid;
             __syncwarp();
         }
-        const uint32_t o = valid ? ldop(cs + (swapped ? sg.lbase + row : sg.rbase + col)) : 0u;
-        c = w1_lookup(tab, o, (T.n + 3) >> 2);
+        const uint32_t *ob = cs + (swapped ? sg.lbase : sg.rbase);
+        const uint32_t o0 = v0 ? ldop(ob + (swapped ? row0 : col0)) : 0u;
+        const uint32_t o1 = v1 ? ldop(ob + (swapped ? row1 : col1)) : 0u;
+        const uint32_t nt = (T.n + 3) >> 2;
+        c0 = w1_lookup(tab, o0, nt);
+        c1 = w1_lookup(tab, o1, nt);
     }
-
-    // ---- precision and uniqueness
-    if (!valid) return;
-    const uint32_t errs = __popc(S.pos[0] & ~c) + __popc(S.neg[0] & c);
-    const uint64_t xlev = sg.start + x;
-    if (errs <= J.max_errors) atomicMin(T.found, (unsigned long long)xlev);
-    if (T.dedup) {
-        const uint32_t xl = (uint32_t)(xlev - T.chunk_start);
-        if (T.smem) dedup_insert_smem<1>(T, &c, xl);
-        else if (J.exact) dedup_insert_exact<1>(T, &c, xl);
-        else if (T.bits) dedup_insert_solo<1>(T, &c, xl);
-        else dedup_insert<1>(T, &c, xl);
-    }
+    w1_finish(T, sg, c0, x0, v0, c1, x1, v1);
 }
 
 // ---------------------------------------------------------------------------
@@ -1012,7 +1058,7 @@ struct ChunkArgs {
 };
 
 // tiles of the chunk [cs0, ce0) in every segment; run by one whole warp
-__device__ void tile_setup(Shared &S, uint32_t nseg, uint64_t cs0, uint64_t ce0, uint64_t *s_tiles) {
+__device__ void tile_setup(Shared &S, uint32_t nseg, uint64_t cs0, uint64_t ce0, uint64_t *s_tiles, uint32_t bw) {
     const uint32_t lane = threadIdx.x & 31;
     uint64_t t = 0;
     for (uint32_t r0 = 0; r0 < nseg; r0 += 32) {
@@ -1035,10 +1081,10 @@ __device__ void tile_setup(Shared &S, uint32_t nseg, uint64_t cs0, uint64_t ce0,
                     const uint64_t r0w = a / g.rcnt, r1 = (e - 1) / g.rcnt;
                     tl.r0 = r0w;
                     if (g.op == OP_CAT && g.swap) {
-                        tl.nb = (uint32_t)((r1 - r0w + 1 + 31) / 32);
+                        tl.nb = (uint32_t)((r1 - r0w + bw) / bw);
                         tiles = (uint64_t)g.rcnt * tl.nb;
                     } else {
-                        tl.nb = (g.rcnt + 31) / 32;
+                        tl.nb = (g.rcnt + bw - 1) / bw;
                         tiles = (r1 - r0w + 1) * tl.nb;
                     }
                 } else {
@@ -1280,7 +1326,7 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
     REI_TSTART();
 
     if (!tiles_ready) {
-        if (wid == 0) tile_setup(S, a.nseg, a.cs0, a.ce0, s_tiles);
+        if (wid == 0) tile_setup(S, a.nseg, a.cs0, a.ce0, s_tiles, bin_block(W));
         __syncthreads();
     }
 
@@ -1834,7 +1880,7 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
         if (C == 0) C = 1;  // unreachable with room >= 1; guards the loop
         ChunkArgs a{level, size, dedup ? 1u : 0u, nseg, pos, pos + C};
         // alone when the chunk is a few tiles per warp of this CTA
-        if (wid == 0) tile_setup(S, nseg, a.cs0, a.ce0, K.tiles);
+        if (wid == 0) tile_setup(S, nseg, a.cs0, a.ce0, K.tiles, bin_block(J.W));
         if (tid == 0) *K.found = kNone;  // a small chunk's answer slot
         __syncthreads();
         const bool team = allow_team && *K.tiles > (uint64_t)J.solo_tiles;
