@@ -619,7 +619,60 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
 // ---------------------------------------------------------------------------
 // the plain solve
 
-rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
+// A search that a batched or served CTA left in its memory slot (ST_NEED_MEM:
+// its time allowance ran out, or it outgrew the slot), continued on the whole
+// GPU from the slot's cached levels instead of solved again from level 1.
+struct SlotResume {
+    const SlotMem *m;
+    uint32_t slot;
+};
+
+// Copy a parked slot's search into the context: the state into the pinned
+// state area, the cached rows, back-pointers and level table into the
+// context's buffers; clear what the continued search needs cleared.  The
+// caller has staged the problem into the context (same |ic| and W).
+rei_status load_slot(rei_ctx *c, const rei_problem *p, const StageInfo &I, const SlotResume &rs, uint64_t &d2h) {
+    const SlotMem &m = *rs.m;
+    const uint64_t so = rs.slot;
+    const uint32_t W = I.W, max_cost = p->max_cost;
+    rei_status s;
+    if ((s = ensure_pinned(c, sizeof(SolveJob) + state_bytes(max_cost) + sizeof(StageInfo)))) return s;
+    CK(cudaStreamSynchronize(c->stream));  // pinned buffer reuse
+    SolveState *hst = (SolveState *)(c->h_pin + sizeof(SolveJob));
+    CK(cudaMemcpyAsync(hst, m.state + so, sizeof(SolveState), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    d2h += sizeof(SolveState);
+    if (hst->status != ST_NEED_MEM || W > m.cs_words / m.rows || hst->size > m.rows) return REI_ECUDA;
+    const uint64_t rows = hst->size, alloc = std::max<uint64_t>(rows, 1);
+    if ((s = ensure(c, c->cs, 4ull * W * alloc))) return s;
+    if ((s = ensure(c, c->bp_op, alloc))) return s;
+    if ((s = ensure(c, c->bp_l, 4ull * alloc))) return s;
+    if ((s = ensure(c, c->bp_r, 4ull * alloc))) return s;
+    if ((s = ensure(c, c->used, 4ull * alloc))) return s;
+    if ((s = ensure(c, c->lvl_start, 8ull * (max_cost + 2)))) return s;
+    if ((s = ensure(c, c->lvl_count, 8ull * (max_cost + 2)))) return s;
+    if (rows) {
+        CK(cudaMemcpyAsync(c->cs.p, m.cs + so * m.cs_words, 4ull * W * rows, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->bp_op.p, m.bp_op + so * m.rows, rows, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->bp_l.p, m.bp_l + so * m.rows, 4ull * rows, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->bp_r.p, m.bp_r + so * m.rows, 4ull * rows, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    const int64_t *lv = m.lvl + so * 2 * (kMaxCost + 2);
+    CK(cudaMemcpyAsync(c->lvl_start.p, lv, 8ull * (max_cost + 2), cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->lvl_count.p, lv + (kMaxCost + 2), 8ull * (max_cost + 2), cudaMemcpyDeviceToDevice,
+                       c->stream));
+    // the continued search rebuilds the table from the rows; its survivor
+    // bitmap and seen bitmap must start empty
+    // (a bitmap allocated later is cleared when it is allocated)
+    if (!c->table_clean) {
+        if (c->bitmap.p) CK(cudaMemsetAsync(c->bitmap.p, 0, c->bitmap.bytes, c->stream));
+        if (c->seen.p) CK(cudaMemsetAsync(c->seen.p, 0, c->seen.bytes, c->stream));
+    }
+    c->table_clean = false;
+    return REI_OK;
+}
+
+rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out, const SlotResume *rs = nullptr) {
     const double t0 = now_ms();
     const uint64_t l0 = c->launches;
     memset(&out->stats, 0, sizeof(out->stats));
@@ -636,9 +689,22 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
     double ms_search = 0;
     uint32_t search_launches = 0, grid = 0;
     uint64_t h2d = 0, d2h = 0;
-    // staging inside the search launch when the launch can hold the problem
+    // staging inside the search launch when the launch can hold the problem;
+    // a search continued from a memory slot stages on its own, then starts
+    // from the slot's state as if a first launch had run its first part
     bool fused = false;
-    if (c->opt_fused) {
+    if (rs) {
+        s = stage_problem(c, p, sg);
+        h2d += sg.h2d;
+        d2h += sg.d2h;
+        fill_stats(out, sg.info);
+        if (s == REI_OK) s = load_slot(c, p, sg.info, *rs, d2h);
+        if (s) {
+            out->status = s;
+            return s;
+        }
+        fused = true;
+    } else if (c->opt_fused) {
         s = run_fused(c, p, sg, ms_search, grid, h2d, d2h);
         if (s == REI_OK) {
             fused = true;
@@ -653,7 +719,7 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out) {
         h2d += sg.h2d;
         d2h += sg.d2h;
     }
-    fill_stats(out, sg.info);
+    if (!rs) fill_stats(out, sg.info);
     if (!fused && s) {
         out->status = s;
         return s;
@@ -1422,6 +1488,8 @@ rei_status run_batch(rei_ctx *c, const rei_problem *probs, const std::vector<uin
     A.yield_ns = c->opt_yield_us * 1000ull;
     CK(cudaMemcpyAsync(c->b_jobs.p, bj, sizeof(BatchJob) * nl, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemsetAsync(c->b_queue.p, 0, 16, c->stream));
+    // (a problem no CTA took keeps status 0, ST_RUNNING)
+    CK(cudaMemsetAsync(c->b_out.p, 0, sizeof(BatchOut) * nl, c->stream));
     c->slots_clean = false;
     CK(cudaEventRecord(c->ev[0], c->stream));
     tb_launch = now_ms();
@@ -1442,14 +1510,22 @@ rei_status run_batch(rei_ctx *c, const rei_problem *probs, const std::vector<uin
                 "(kernel %.3f ms), total %.3f ms\n", nb, tb_up - tb0, tb_launch - tb_up, now_ms() - tb_launch, ms,
                 now_ms() - tb0);
 
-    std::vector<uint32_t> redo;
+    // parked searches (continued from their slots, before a launch reuses the
+    // slots) and problems no CTA took (a CTA that parks a search takes no
+    // more problems): launched again
+    std::vector<std::pair<uint32_t, uint32_t>> redo;  // (problem, slot)
+    std::vector<uint32_t> again;
     for (uint32_t k = 0; k < nl; k++) {
         const uint32_t t = live[k];
         const rei_problem &p = probs[sel[t]];
         rei_result &o = outs[sel[t]];
         const BatchOut &b = bo[k];
+        if (b.status == ST_RUNNING) {
+            again.push_back(sel[t]);
+            continue;
+        }
         if (b.status == ST_NEED_MEM) {
-            redo.push_back(sel[t]);
+            redo.push_back({sel[t], b.slot});
             continue;
         }
         o.stats.candidates = b.candidates;
@@ -1474,10 +1550,13 @@ rei_status run_batch(rei_ctx *c, const rei_problem *probs, const std::vector<uin
             if (write_outputs(&o, tr + tree_bytes * k, b.tree_len, p.alphabet) != REI_OK) o.status = REI_EBUFSZ;
         }
     }
-    for (uint32_t i : redo) {
-        const rei_status r = solve_one(c, &probs[i], &outs[i]);
+    for (const auto &pr : redo) {
+        const uint32_t i = pr.first;
+        const SlotResume rs{&A.slot, pr.second};
+        const rei_status r = solve_one(c, &probs[i], &outs[i], pr.second < slots ? &rs : nullptr);
         if (r != REI_OK && r != REI_NOT_FOUND && r != REI_OOM) outs[i].status = r;
     }
+    if (!again.empty()) return run_batch(c, probs, again, outs, warps, nullptr);
     return REI_OK;
 }
 
@@ -1561,6 +1640,7 @@ struct rei_server {
         rei_problem p;
         uint64_t footprint;
         double t_submit;  // host clock, ms
+        uint32_t slot = kNoSlot;  // a search the launch left in this memory slot
     };
     struct Done {
         rei_result r;
@@ -1748,8 +1828,11 @@ void solve_alone(rei_server *S, rei_server::Req &req) {
     r.tree_cap = sizeof tbuf;
     rei_status s;
     {
+        // a search left in a memory slot continues from there (the launch is
+        // stopped, so the slot is as the search left it)
+        const SlotResume rs{&S->args.slot, req.slot};
         std::lock_guard<std::mutex> g(S->ctx->mu);
-        s = solve_one(S->ctx, &req.p, &r);
+        s = solve_one(S->ctx, &req.p, &r, req.slot < S->grid ? &rs : nullptr);
     }
     if (s != REI_OK && s != REI_NOT_FOUND && s != REI_OOM) r.status = s;
     r.stats.ms_total = now_ms() - req.t_submit;
@@ -1777,6 +1860,7 @@ void server_loop(rei_server *S) {
             progress = true;
             S->live_bytes -= req.footprint;
             if (b.status == ST_NEED_MEM) {
+                req.slot = b.slot;
                 alone.push_back(std::move(req));
                 it = S->live.erase(it);
                 continue;

@@ -237,7 +237,12 @@ struct BatchOut {
     uint64_t candidates, unique;
     uint64_t cand_op[5];
     uint64_t ns;
+    // ST_NEED_MEM from the search: the memory slot that still holds its
+    // cache, level table and state (the CTA took no more work), so that the
+    // host continues the search from there; kNoSlot = not searched here
+    uint32_t slot, pad;
 };
+constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 
 // one problem of a batch: its job (staged data, costs; memory fields are
 // filled in by the CTA that takes it), where its tree and report go

@@ -2160,8 +2160,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_solve_fused(const __grid_c
 
 // Solve the problem whose job (staged data, costs) is in shared memory J,
 // in memory slot `slot`, on this CTA alone; the report goes to *out and the
-// tree to J.tree.
-__device__ void solve_in_slot(SolveJob &J, const SlotMem &m, uint32_t slot, BatchOut *out, uint8_t *smem_raw,
+// tree to J.tree.  Returns the search's status (every thread).  With
+// ST_NEED_MEM (the time allowance ran out or the slot is too small) the slot
+// keeps the cache rows, back-pointers, level table and state for the host to
+// continue from; its uniqueness table and survivor bitmap are emptied.
+__device__ uint32_t solve_in_slot(SolveJob &J, const SlotMem &m, uint32_t slot, BatchOut *out, uint8_t *smem_raw,
                               Plan *s_plan, uint32_t *s_red, uint64_t *s_tiles, unsigned long long *s_found,
                               uint32_t *s_npend, Lead *L, uint64_t yield_ns) {
     const uint32_t tid = threadIdx.x;
@@ -2215,8 +2218,9 @@ __device__ void solve_in_slot(SolveJob &J, const SlotMem &m, uint32_t slot, Batc
     if (status == ST_FOUND || status == ST_NOT_FOUND || status == ST_OOM) {
         clean_table(J, L->smode ? 0u : L->size, st->pending_count, 1, 0);
     } else {
-        // ran out of this slot's memory: the host solves it again alone;
-        // this slot's table is rebuilt from scratch
+        // the host continues this search from the slot's rows and state (it
+        // rebuilds the table there); the slot's table and bitmap are emptied
+        // for the slot's next problem
         for (uint64_t i = tid; i <= J.table_mask; i += blockDim.x) J.table[i] = kEmpty;
         for (uint64_t i = tid; i < (J.chunk_max + 31) / 32; i += blockDim.x) J.bitmap[i] = 0;
     }
@@ -2231,8 +2235,10 @@ __device__ void solve_in_slot(SolveJob &J, const SlotMem &m, uint32_t slot, Batc
         o.levels = st->level;
         for (int k = 0; k < 5; k++) o.cand_op[k] = st->cand_op[k];
         o.ns = globaltimer_ns() - t_start;
+        o.slot = slot;
     }
     __syncthreads();
+    return status;
 }
 
 __global__ void __launch_bounds__(256, 2) k_solve_batch(const BatchJob *jobs, const __grid_constant__ BatchArgs B) {
@@ -2258,8 +2264,12 @@ __global__ void __launch_bounds__(256, 2) k_solve_batch(const BatchJob *jobs, co
             J.tree = bj.tree;
         }
         __syncthreads();
-        solve_in_slot(J, B.slot, blockIdx.x, bj.out, smem_raw, &s_plan, s_red, &s_tiles, &s_found, &s_npend, &L,
-                      B.yield_ns);
+        // a search left in this slot for the host to continue: the slot is
+        // not reused, and this CTA takes no more problems (the host launches
+        // again for any left in the queue)
+        if (solve_in_slot(J, B.slot, blockIdx.x, bj.out, smem_raw, &s_plan, s_red, &s_tiles, &s_found, &s_npend,
+                          &L, B.yield_ns) == ST_NEED_MEM)
+            return;
     }
 }
 
@@ -2450,11 +2460,13 @@ __global__ void __launch_bounds__(256, 2) k_serve(const __grid_constant__ ServeA
         __syncthreads();
         verdict = s_red[0];
         __syncthreads();
+        uint32_t status = ST_BAD;
         if (verdict == 0) {
-            solve_in_slot(J, A.slot, slot, &o.out, smem_raw, &s_plan, s_red, &s_tiles, &s_found, &s_npend, &L,
-                          A.yield_ns);
+            status = solve_in_slot(J, A.slot, slot, &o.out, smem_raw, &s_plan, s_red, &s_tiles, &s_found, &s_npend,
+                                   &L, A.yield_ns);
         } else if (tid == 0) {
             o.out.status = verdict == 1 ? ST_BAD : ST_NEED_MEM;
+            o.out.slot = kNoSlot;  // (too large for a slot: never searched here)
         }
         if (tid == 0) {
             o.info = I;
@@ -2463,6 +2475,10 @@ __global__ void __launch_bounds__(256, 2) k_serve(const __grid_constant__ ServeA
             __threadfence_system();
         }
         __syncthreads();
+        // a search left in this slot for the host to continue: the CTA takes
+        // no more requests, so the slot stays as it is until the host has
+        // copied it (the host stops the launch before it does)
+        if (status == ST_NEED_MEM) return;
     }
 }
 

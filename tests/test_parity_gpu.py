@@ -177,6 +177,38 @@ def test_wide_config_matches_stored_oracle_results(fused):
             assert (got.cost, got.tree, got.candidates, got.unique, got.n_ic) == (cost, tree, cand, uniq, n_ic), sd
 
 
+def _wide_large_expected():
+    import os
+    rows = []
+    with open(os.path.join(os.path.dirname(__file__), "golden", "wide_large_expected.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            var, sd, st, cost, cand, uniq, n_ic, tree = line.split()
+            rows.append((var, int(sd), int(st), int(cost), int(cand), int(uniq), int(n_ic), bytes.fromhex(tree)))
+    return rows
+
+
+@pytest.mark.parametrize("fused", [1, 0])
+def test_wide_large_ic_matches_stored_oracle_results(fused):
+    """Wide instances with |ic| 1000-1500 (36- and 48-word languages) at their
+    full minimal cost: answer, tree and counts equal the oracle's (stored by
+    tests/golden/make_wide_large_expected.py, which calls only the oracle)."""
+    from workloads import wide_large_instance
+    rows = _wide_large_expected()
+    assert {r[6] for r in rows} and max(r[6] for r in rows) > 1408
+    with rei.Context(device=0) as c:
+        c.set_option(rei.REI_OPT_FUSED_STAGE, fused)
+        for var, sd, st, cost, cand, uniq, n_ic, tree in rows:
+            inst = wide_large_instance(var, sd)
+            got = c.solve_problem(rei.Problem(inst.alphabet, inst.pos, inst.neg, max_cost=40,
+                                              mem_budget=inst.mem_budget))
+            assert got.status == ST[st], (var, sd)
+            assert (got.cost, got.tree, got.candidates, got.unique, got.n_ic) == (cost, tree, cand, uniq, n_ic), \
+                (var, sd)
+            assert got.words == 4 * ((n_ic + 127) // 128)  # 36 or 48 words
+
+
 @pytest.mark.parametrize("chunk", [1, 7, 100, 4099])
 @pytest.mark.parametrize("grid", [1, 3, 0])
 @pytest.mark.parametrize("solo", [-1, 0, 1 << 30])

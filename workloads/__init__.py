@@ -9,4 +9,5 @@ from .gen import (  # noqa: F401
     type2_instance,
     poisson_trace,
     printed_instance,
+    wide_large_instance,
 )

@@ -288,6 +288,19 @@ CONFIGS = {
 }
 
 
+# wide instances with |ic| of 1000-1500 words (32-48 words of 32 bits): the
+# wide recipe with every string of the longest length, and with 30 examples a
+# side for |ic| above 1408
+WIDE_LARGE = {
+    "len10": dict(len_lo=10, ic_lo=1000),
+    "30x30": dict(n_pos=30, n_neg=30, len_lo=10, ic_lo=1409),
+}
+
+
+def wide_large_instance(variant: str, seed: int) -> Instance:
+    return make_config("wide", seed, **WIDE_LARGE[variant])
+
+
 def printed_instance() -> Instance:
     """The one specification the paper prints in full (Sec. 6, the top row of
     Table 1: Type 1, No 50, cost function (1,1,1,1,1)); its minimal cost is 28
