@@ -57,7 +57,7 @@
 extern "C" {
 #endif
 
-#define REI_ABI_VERSION 1
+#define REI_ABI_VERSION 2
 
 #define REI_MAX_IC 4096      /* largest |ic(P u N)| */
 #define REI_MAX_STRLEN 4095  /* longest example string */
@@ -202,9 +202,11 @@ void rei_ctx_destroy(rei_ctx *ctx);
  *                      first (latency-shaped) launch for a relaunch shaped
  *                      for throughput (default 4 Mi; 0 = never)
  *   REI_OPT_YIELD_US   a batched or served problem still searching on its one
- *                      CTA after this many microseconds gives up there and
- *                      is solved again on the whole GPU, like a problem that
- *                      outgrows its slot (default 2000; 0 = never)
+ *                      CTA after this many microseconds stops there and
+ *                      continues on the whole GPU from the levels it has
+ *                      cached, like a problem that outgrows its slot
+ *                      (default 500; 0 = never; rei_tune.yield_us, when
+ *                      given, takes its place for a batch)
  *   REI_OPT_FUSED_STAGE 1 = stage a problem inside its search launch when the
  *                      launch can hold it (|ic| <= 2048, strings <= 8 KiB;
  *                      the default), 0 = always a separate staging launch.
@@ -273,11 +275,20 @@ rei_status rei_cache_dump(rei_ctx *ctx, uint32_t *cs, uint8_t *op, uint32_t *lef
 
 /* ---- batched form: many independent problems, one persistent launch ---- */
 
-/* Tile shape and scheduling of the batched launch (NULL = autotuned). */
+/* Shape and scheduling of the batched launch, in which each CTA solves one
+ * problem at a time in its own memory slot.  A field left 0 is chosen by the
+ * library: warps_per_cta and chunk by an autotuner that times the first parts
+ * of a batch (samples of one problem per SM each) under a few settings and
+ * keeps, for the context, the one with the most candidates per millisecond of
+ * the whole call; yield_us from the context's REI_OPT_YIELD_US.  Results never
+ * depend on any field.  NULL = every field 0.  A field out of range gives
+ * REI_EINVAL. */
 typedef struct rei_tune {
-    uint32_t ctas_per_problem;  /* CTAs cooperating on one problem */
-    uint32_t warps_per_cta;
-    uint32_t chunk;             /* candidates per dedup chunk */
+    uint32_t warps_per_cta; /* warps of each CTA: 1, 2, 4 or 8 */
+    uint32_t chunk;         /* candidates per dedup chunk in a slot: 256 .. 65536 */
+    uint32_t yield_us;      /* a problem still searching on its CTA after this
+                               many microseconds continues on the whole GPU
+                               from where it stopped (0xFFFFFFFF = never) */
 } rei_tune;
 
 /* Solve n problems.  outs[i] receives problem i's result exactly as

@@ -95,7 +95,7 @@ class rei_staged(C.Structure):
 
 
 class rei_tune(C.Structure):
-    _fields_ = [("ctas_per_problem", C.c_uint32), ("warps_per_cta", C.c_uint32), ("chunk", C.c_uint32)]
+    _fields_ = [("warps_per_cta", C.c_uint32), ("chunk", C.c_uint32), ("yield_us", C.c_uint32)]
 
 
 _lib = None
@@ -459,14 +459,15 @@ class Context:
         rows = [list(cs[i * W:(i + 1) * W]) for i in range(k)]
         return rows, list(op[:k]), list(lf[:k]), list(rt[:k]), list(ls), list(lc)
 
-    def solve_batch(self, probs: Sequence[Problem], warps_per_cta: int = 0) -> List[Result]:
+    def solve_batch(self, probs: Sequence[Problem], warps_per_cta: int = 0, chunk: int = 0,
+                    yield_us: int = 0) -> List[Result]:
         """rei_solve_batch over `probs` (one staging and one search launch);
-        warps_per_cta 0 lets the library autotune the CTA shape."""
+        a rei_tune field left 0 is chosen by the library (see include/rei.h)."""
         n = len(probs)
         arr = (rei_problem * max(n, 1))(*[p.p for p in probs])
         bufs = [_OutBuf() for _ in range(n)]
         outs = (rei_result * max(n, 1))(*[b.res for b in bufs])
-        tune = rei_tune(1, warps_per_cta, 0) if warps_per_cta else None
+        tune = rei_tune(warps_per_cta, chunk, yield_us) if (warps_per_cta or chunk or yield_us) else None
         s = rei_solve_batch(self.h, arr, n, outs, tune)
         if s != REI_OK:
             raise RuntimeError(f"rei_solve_batch: {STATUS_NAMES.get(s, s)}")

@@ -74,7 +74,7 @@ struct rei_ctx {
     int64_t opt_chunk = 0, opt_grid = 0, opt_keep = 0, opt_cache_init = 0, opt_solo_tiles = -1, opt_small_rows = -1;
     int64_t opt_fused = 1, opt_exact = 1;
     uint64_t opt_handover = 1ull << 22;  // levels of more candidates leave the fused launch
-    uint64_t opt_yield_us = 2000;        // batched / served problems longer than this go to the plain path
+    uint64_t opt_yield_us = 500;         // batched / served problems longer than this continue on the whole GPU
     size_t smem_sm = 0;  // shared memory per SM
 
     // staging
@@ -86,6 +86,7 @@ struct rei_ctx {
         state, solve_job, tstack, trace, used;
     DevBuf seen;               // bitmap of cached 1-word languages (2^kSeenBits bits)
     bool table_clean = false;  // the search kernel leaves the table (and seen) empty after a normal end
+    uint64_t table_extent = 0; // slots of the table (and minidx) that may hold entries: beyond, all empty
     // batched form
     DevBuf b_in, b_sjobs, b_sinfo, b_stage, b_jobs, b_out, b_tree, b_queue;
     DevBuf s_cs, s_bp_op, s_bp_l, s_bp_r, s_used, s_table, s_tmp, s_pend, s_slotpos, s_bitmap, s_blk, s_lvl,
@@ -93,7 +94,8 @@ struct rei_ctx {
     uint64_t slot_rows = 0, slot_cs_words = 0, slot_table = 0, slot_tmp_words = 0, slot_chunk = 0;
     uint32_t slot_count = 0;
     bool slots_clean = false;
-    int batch_warps = 0;  // autotuned warps per CTA of the batched launch (0 = not yet)
+    int batch_warps = 0;       // autotuned warps per CTA of the batched launch (0 = not yet)
+    uint32_t batch_chunk = 0;  // autotuned candidates per dedup chunk in a slot (0 = not yet)
     // pinned host scratch
     uint8_t *h_pin = nullptr;
     size_t h_pin_bytes = 0;
@@ -158,6 +160,19 @@ rei_status grow_keep(rei_ctx *c, DevBuf &b, size_t bytes, size_t keep) {
     dev_free(c, b);
     b.p = np;
     b.bytes = bytes;
+    return REI_OK;
+}
+
+// Empty the uniqueness table and its first-candidate array where they may
+// hold entries (the first max(table_extent, at_least) slots; beyond them they
+// are empty), so that a context that once solved a large problem does not
+// clear its whole table for every small one.
+rei_status clear_table(rei_ctx *c, uint64_t at_least) {
+    const uint64_t ext = std::max(c->table_extent, at_least);
+    const uint64_t t = std::min<uint64_t>(ext, c->table.bytes / 8), m = std::min<uint64_t>(ext, c->minidx.bytes / 4);
+    if (t) CK(cudaMemsetAsync(c->table.p, 0xFF, 8 * t, c->stream));
+    if (m) CK(cudaMemsetAsync(c->minidx.p, 0xFF, 4 * m, c->stream));
+    c->table_extent = 0;
     return REI_OK;
 }
 
@@ -477,8 +492,10 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
         if ((s = ensure(c, c->table, 8ull * tslots))) return s;
         if ((s = ensure(c, c->minidx, 4ull * tslots))) return s;
         if (c->table.p != before || c->table.bytes != before_bytes || c->minidx.p != mbefore ||
-            c->minidx.bytes != mbefore_bytes)
+            c->minidx.bytes != mbefore_bytes) {
             c->table_clean = false;
+            c->table_extent = std::max<uint64_t>(c->table.bytes / 8, c->minidx.bytes / 4);
+        }
     }
     const uint64_t chunk_words = c->opt_chunk > 0 ? (uint64_t)c->opt_chunk : (1ull << 22);
     if ((s = ensure(c, c->tmp, std::max<uint64_t>(4ull * 2 * chunk_words, 4ull * 64 * 4096)))) return s;
@@ -509,12 +526,12 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
         c->table_clean = false;
     }
     if (!c->table_clean) {
-        CK(cudaMemsetAsync(c->table.p, 0xFF, c->table.bytes, c->stream));
-        CK(cudaMemsetAsync(c->minidx.p, 0xFF, c->minidx.bytes, c->stream));
+        if ((s = clear_table(c, 0))) return s;
         CK(cudaMemsetAsync(c->bitmap.p, 0, c->bitmap.bytes, c->stream));
         if (c->seen.p) CK(cudaMemsetAsync(c->seen.p, 0, c->seen.bytes, c->stream));
     }
     c->table_clean = false;
+    c->table_extent = std::max(c->table_extent, tslots);
     // state, answer tokens, staging report: zero (the launch fills in the rest)
     CK(cudaMemsetAsync(c->state.p, 0, sb + sizeof(StageInfo), c->stream));
 
@@ -822,8 +839,10 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out, const Sl
         if ((s = ensure(c, c->table, 8ull * tslots))) return s;
         if ((s = ensure(c, c->minidx, 4ull * tslots))) return s;
         if (c->table.p != before || c->table.bytes != before_bytes || c->minidx.p != mbefore ||
-            c->minidx.bytes != mbefore_bytes)
+            c->minidx.bytes != mbefore_bytes) {
             c->table_clean = false;
+            c->table_extent = std::max<uint64_t>(c->table.bytes / 8, c->minidx.bytes / 4);
+        }
     }
     if ((s = ensure(c, c->tmp, 4ull * W * chunk_max))) return s;
     if ((s = ensure(c, c->pending, 4ull * chunk_max))) return s;
@@ -854,13 +873,13 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out, const Sl
     }
     if (!fused) {
         if (!c->table_clean) {
-            // a new table, or the last search ended abnormally: clear it all once
-            CK(cudaMemsetAsync(c->table.p, 0xFF, c->table.bytes, c->stream));
-            CK(cudaMemsetAsync(c->minidx.p, 0xFF, c->minidx.bytes, c->stream));
+            // a new table, or the last search ended abnormally: clear it once
+            if ((s = clear_table(c, 0))) return s;
             CK(cudaMemsetAsync(c->bitmap.p, 0, c->bitmap.bytes, c->stream));
             if (c->seen.p) CK(cudaMemsetAsync(c->seen.p, 0, c->seen.bytes, c->stream));
         }
         c->table_clean = false;
+        c->table_extent = std::max(c->table_extent, tslots);
         uint32_t hj_cmin;
         {
             uint16_t lc[256];
@@ -965,10 +984,15 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out, const Sl
         if ((s = grow_keep(c, c->used, 4ull * want, 0))) return s;
         cache_alloc = want;
         tslots = table_slots(cache_alloc);
-        if ((s = ensure(c, c->table, 8ull * tslots))) return s;
-        if ((s = ensure(c, c->minidx, 4ull * tslots))) return s;
-        CK(cudaMemsetAsync(c->table.p, 0xFF, c->table.bytes, c->stream));
-        CK(cudaMemsetAsync(c->minidx.p, 0xFF, c->minidx.bytes, c->stream));
+        {
+            const void *before = c->table.p, *mbefore = c->minidx.p;
+            if ((s = ensure(c, c->table, 8ull * tslots))) return s;
+            if ((s = ensure(c, c->minidx, 4ull * tslots))) return s;
+            if (c->table.p != before || c->minidx.p != mbefore)
+                c->table_extent = std::max<uint64_t>(c->table.bytes / 8, c->minidx.bytes / 4);
+        }
+        if ((s = clear_table(c, tslots))) return s;  // (the rehash refills it)
+        c->table_extent = tslots;
         fill_job();
         if (rows) {
             CK(launch_rehash(hj, (uint32_t)rows, (uint32_t)(c->sm_count * 8), c->stream));
@@ -1019,6 +1043,7 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out, const Sl
         for (auto &kv : hist) fprintf(stderr, "rei:   %u CTAs last passed epoch %u site %u\n", kv.second, kv.first >> 8, kv.first & 255);
     }
     c->table_clean = hst->status == ST_FOUND || hst->status == ST_NOT_FOUND || hst->status == ST_OOM;
+    if (c->table_clean) c->table_extent = 0;  // (the search emptied every slot it filled)
     c->last_valid = true;
     c->last_W = W;
     c->last_size = hst->size;
@@ -1251,9 +1276,11 @@ struct BatchPlan {
 };
 
 // Run problems `sel` of `probs` in one batched launch with `warps` warps per
-// CTA.  Problems that outgrow their slot are re-solved alone afterwards.
+// CTA, dedup chunks of `chunk` candidates in each slot and a time allowance of
+// `yield_us` per problem (~0 = none).  Searches that pass the allowance or
+// outgrow their slot continue on the whole GPU afterwards.
 rei_status run_batch(rei_ctx *c, const rei_problem *probs, const std::vector<uint32_t> &sel, rei_result *outs,
-                     uint32_t warps, double *kernel_ms) {
+                     uint32_t warps, uint32_t chunk_sz, uint32_t yield_us, double *kernel_ms) {
     const uint32_t nb = (uint32_t)sel.size();
     if (kernel_ms) *kernel_ms = 0;
     if (nb == 0) return REI_OK;
@@ -1432,7 +1459,7 @@ rei_status run_batch(rei_ctx *c, const rei_problem *probs, const std::vector<uin
     const uint32_t slots = std::min<uint32_t>(nl, (uint32_t)(c->sm_count * bps));
 
     // per-slot memory (grow-only; tables and bitmaps kept empty between uses)
-    const uint64_t rows = 1ull << 18, chunk = 1ull << 14;
+    const uint64_t rows = 1ull << 18, chunk = chunk_sz;
     const uint64_t cs_words = rows * wmax, tmp_words = chunk * wmax;
     const uint64_t tslots = pow2_at_least(2 * (rows + chunk));
     bool fresh = !c->slots_clean || c->slot_count < slots || c->slot_rows != rows || c->slot_cs_words < cs_words ||
@@ -1485,7 +1512,7 @@ rei_status run_batch(rei_ctx *c, const rei_problem *probs, const std::vector<uin
     A.slot.chunk = chunk;
     A.n = nl;
     A.queue = (uint32_t *)c->b_queue.p;
-    A.yield_ns = c->opt_yield_us * 1000ull;
+    A.yield_ns = yield_us == 0xFFFFFFFFu ? 0 : (uint64_t)yield_us * 1000ull;
     CK(cudaMemcpyAsync(c->b_jobs.p, bj, sizeof(BatchJob) * nl, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemsetAsync(c->b_queue.p, 0, 16, c->stream));
     // (a problem no CTA took keeps status 0, ST_RUNNING)
@@ -1513,7 +1540,11 @@ rei_status run_batch(rei_ctx *c, const rei_problem *probs, const std::vector<uin
     // parked searches (continued from their slots, before a launch reuses the
     // slots) and problems no CTA took (a CTA that parks a search takes no
     // more problems): launched again
-    std::vector<std::pair<uint32_t, uint32_t>> redo;  // (problem, slot)
+    struct Parked {
+        uint32_t prob, slot;
+        double ms;  // time the search spent on its CTA
+    };
+    std::vector<Parked> redo;
     std::vector<uint32_t> again;
     for (uint32_t k = 0; k < nl; k++) {
         const uint32_t t = live[k];
@@ -1525,7 +1556,7 @@ rei_status run_batch(rei_ctx *c, const rei_problem *probs, const std::vector<uin
             continue;
         }
         if (b.status == ST_NEED_MEM) {
-            redo.push_back({sel[t], b.slot});
+            redo.push_back({sel[t], b.slot, b.ns / 1e6});
             continue;
         }
         o.stats.candidates = b.candidates;
@@ -1550,13 +1581,16 @@ rei_status run_batch(rei_ctx *c, const rei_problem *probs, const std::vector<uin
             if (write_outputs(&o, tr + tree_bytes * k, b.tree_len, p.alphabet) != REI_OK) o.status = REI_EBUFSZ;
         }
     }
-    for (const auto &pr : redo) {
-        const uint32_t i = pr.first;
-        const SlotResume rs{&A.slot, pr.second};
-        const rei_status r = solve_one(c, &probs[i], &outs[i], pr.second < slots ? &rs : nullptr);
+    for (const Parked &pk : redo) {
+        const uint32_t i = pk.prob;
+        const SlotResume rs{&A.slot, pk.slot};
+        const rei_status r = solve_one(c, &probs[i], &outs[i], pk.slot < slots ? &rs : nullptr);
         if (r != REI_OK && r != REI_NOT_FOUND && r != REI_OOM) outs[i].status = r;
+        // the problem's time: on its CTA, then on the whole GPU
+        outs[i].stats.ms_total += pk.ms;
+        outs[i].stats.ms_search_kernel += pk.ms;
     }
-    if (!again.empty()) return run_batch(c, probs, again, outs, warps, nullptr);
+    if (!again.empty()) return run_batch(c, probs, again, outs, warps, chunk_sz, yield_us, nullptr);
     return REI_OK;
 }
 
@@ -1567,9 +1601,11 @@ extern "C" {
 rei_status rei_solve_batch(rei_ctx *c, const rei_problem *probs, uint32_t n, rei_result *outs,
                            const rei_tune *tune) {
     if (!c || (n && (!probs || !outs))) return REI_EINVAL;
+    if (tune && ((tune->warps_per_cta && (tune->warps_per_cta > 8 || (tune->warps_per_cta & (tune->warps_per_cta - 1)))) ||
+                 (tune->chunk && (tune->chunk < 256 || tune->chunk > 65536))))
+        return REI_EINVAL;
     std::lock_guard<std::mutex> g(c->mu);
     if (cudaSetDevice(c->device) != cudaSuccess) return REI_ECUDA;
-    const double t0 = now_ms();
     std::vector<uint32_t> sel;
     for (uint32_t i = 0; i < n; i++) {
         memset(&outs[i].stats, 0, sizeof(outs[i].stats));
@@ -1585,36 +1621,51 @@ rei_status rei_solve_batch(rei_ctx *c, const rei_problem *probs, uint32_t n, rei
         }
         sel.push_back(i);
     }
+    // the launch shape: given, else autotuned once per context on samples of
+    // the batch (each one problem per SM; every sample is solved exactly, so
+    // tuning costs no work), else the default (8 warps, chunks of 2^14)
     uint32_t warps = tune && tune->warps_per_cta ? tune->warps_per_cta : (uint32_t)c->batch_warps;
+    uint32_t chunk = tune && tune->chunk ? tune->chunk : c->batch_chunk;
+    const uint32_t yield_us = tune && tune->yield_us ? tune->yield_us
+                              : c->opt_yield_us ? (uint32_t)std::min<uint64_t>(c->opt_yield_us, 0xFFFFFFFEu) : 0xFFFFFFFFu;
     size_t done = 0;
-    if (warps == 0) {
-        // autotune the CTA shape on two samples of the batch (4 or 8 warps),
-        // each large enough to fill the GPU; results are exact either way
-        warps = 8;
+    if (warps == 0 || chunk == 0) {
+        struct Trial {
+            uint32_t warps, chunk;
+        };
+        std::vector<Trial> trials;
+        for (uint32_t w : {8u, 4u})
+            for (uint32_t ch : {1u << 14, 1u << 12, 1u << 16})
+                if ((!warps || w == warps) && (!chunk || ch == chunk)) trials.push_back({w, ch});
+        Trial best{warps ? warps : 8u, chunk ? chunk : (1u << 14)};
         const size_t sample = (size_t)std::max(1, c->sm_count);
-        if (sel.size() >= 3 * sample) {
-            double rate[2] = {0, 0};
-            const uint32_t cand[2] = {8, 4};
-            for (int k = 0; k < 2; k++) {
-                std::vector<uint32_t> part(sel.begin() + done, sel.begin() + done + sample);
-                double ms = 0;
-                const rei_status r = run_batch(c, probs, part, outs, cand[k], &ms);
-                if (r != REI_OK) return r;
-                uint64_t cands = 0;
-                for (uint32_t i : part) cands += outs[i].stats.candidates;
-                rate[k] = ms > 0 ? cands / ms : 0;
-                done += sample;
+        double best_rate = -1;
+        // (at least two samples of the batch stay untimed)
+        for (const Trial &tr : trials) {
+            if (sel.size() - done < 3 * sample) break;
+            std::vector<uint32_t> part(sel.begin() + done, sel.begin() + done + sample);
+            const double ts = now_ms();
+            const rei_status r = run_batch(c, probs, part, outs, tr.warps, tr.chunk, yield_us, nullptr);
+            if (r != REI_OK) return r;
+            const double ms = now_ms() - ts;
+            uint64_t cands = 0;
+            for (uint32_t i : part) cands += outs[i].stats.candidates;
+            const double rate = ms > 0 ? cands / ms : 0;
+            if (rate > best_rate) {
+                best_rate = rate;
+                best = tr;
             }
-            warps = rate[1] > rate[0] ? 4 : 8;
-            c->batch_warps = (int)warps;
+            done += sample;
+        }
+        warps = best.warps;
+        chunk = best.chunk;
+        if (best_rate >= 0) {
+            if (!tune || !tune->warps_per_cta) c->batch_warps = (int)warps;
+            if (!tune || !tune->chunk) c->batch_chunk = chunk;
         }
     }
     std::vector<uint32_t> rest(sel.begin() + done, sel.end());
-    const rei_status r = run_batch(c, probs, rest, outs, warps, nullptr);
-    const double t1 = now_ms();
-    (void)t0;
-    (void)t1;
-    return r;
+    return run_batch(c, probs, rest, outs, warps, chunk, yield_us, nullptr);
 }
 
 }  // extern "C"

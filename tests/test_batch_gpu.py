@@ -113,3 +113,25 @@ def test_batch_time_allowance_does_not_change_results(yield_us):
         batch = ctx.solve_batch(probs)
     for k, (a, b) in enumerate(zip(plain, batch)):
         assert key(a) == key(b), (k, yield_us)
+
+
+@pytest.mark.parametrize("warps,chunk,yield_us", [(8, 256, 0xFFFFFFFF), (4, 65536, 1), (2, 1000, 300),
+                                                  (1, 4096, 0)])
+def test_batch_tune_fields_do_not_change_results(warps, chunk, yield_us):
+    """Every rei_tune field (warps per CTA, chunk in a slot, time allowance;
+    0 = chosen by the library) leaves every result as the plain path gives it."""
+    probs = mixed_problems()
+    with rei.Context(device=0) as ctx:
+        plain = [ctx.solve_problem(p) for p in probs]
+        batch = ctx.solve_batch(probs, warps_per_cta=warps, chunk=chunk, yield_us=yield_us)
+    for k, (a, b) in enumerate(zip(plain, batch)):
+        assert key(a) == key(b), (k, warps, chunk, yield_us)
+
+
+@pytest.mark.parametrize("bad", [dict(warps_per_cta=3), dict(warps_per_cta=16), dict(chunk=100),
+                                 dict(chunk=1 << 17)])
+def test_batch_tune_out_of_range(bad):
+    probs = mixed_problems()[:3]
+    with rei.Context(device=0) as ctx:
+        with pytest.raises(RuntimeError):
+            ctx.solve_batch(probs, **bad)
