@@ -200,14 +200,27 @@ def run_reference(args, rank, world):
 # ----------------------------------------------------------------------------
 # GPU arm
 
-def alu_peak(device: int):
-    """LOP3 lane-operations per second of the GPU (the integer-throughput probe)."""
+def _peak_lib():
     from paper_2305_18575_gb300 import build as b
     L = C.CDLL(b.build_peak())
     L.rei_peak_lop3.restype = C.c_double
     L.rei_peak_lop3.argtypes = [C.c_int, C.POINTER(C.c_double)]
+    L.rei_peak_l2_random.restype = C.c_double
+    L.rei_peak_l2_random.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double)]
+    return L
+
+
+def alu_peak(device: int):
+    """LOP3 lane-operations per second of the GPU (the integer-throughput probe)."""
     ms = C.c_double()
-    return L.rei_peak_lop3(device, C.byref(ms))
+    return _peak_lib().rei_peak_lop3(device, C.byref(ms))
+
+
+def l2_peak(device: int):
+    """Bytes per second of random 32-byte sectors the L2 serves (the probe's
+    best of three runs over a 32 MiB buffer that stays resident)."""
+    ms = C.c_double()
+    return max(_peak_lib().rei_peak_l2_random(device, 32, C.byref(ms)) for _ in range(3))
 
 
 def reduce_over_ranks(total_ms: float, cands: float, world: int, device: str):
@@ -235,9 +248,19 @@ def alg_work(results):
     return bytes_, pairs
 
 
-def roofline(results, k_ms: float, launches: int, lop3: float, kernel: str, traffic=None):
-    """Both roofs of a kernel from its algorithmic work and its CUDA-event time;
-    the better-fitting one (the larger fraction) is `bound`."""
+def l2_resident(results) -> bool:
+    """Whether the uniqueness probes of these solves hit a structure that fits
+    the L2: the bitmap of cached languages of 1-word languages (2^|ic| bits,
+    at most 64 MiB for |ic| <= 29)."""
+    return bool(results) and all(r.words == 1 and r.n_ic <= 29 for r in results)
+
+
+def roofline(results, k_ms: float, launches: int, lop3: float, kernel: str, traffic=None, l2=None):
+    """The roofs of a kernel from its algorithmic work and its CUDA-event time.
+    `bound`: the L2 (random 32-byte sectors, measured) when the uniqueness
+    probes hit an L2-resident bitmap and `l2` (its peak, bytes/s) is given,
+    else the better-fitting of HBM and the integer pipes (the larger
+    fraction).  Every fraction is reported."""
     peaks, peak_kind = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     alg_bytes, pair_ops = alg_work(results)
@@ -246,7 +269,11 @@ def roofline(results, k_ms: float, launches: int, lop3: float, kernel: str, traf
     alu_ach = pair_ops / (k_ms * 1e-3) if k_ms > 0 else 0.0
     hbm_frac = hbm_ach / hbm_peak
     alu_frac = alu_ach / alu_peak_pairs if alu_peak_pairs else 0.0
-    if alu_frac > hbm_frac:
+    l2_gbs = l2 / 1e9 if l2 else None
+    l2_frac = hbm_ach / l2_gbs if l2_gbs else None
+    if l2_gbs and l2_resident(results):
+        roof = {"bound": "l2", "achieved": hbm_ach, "peak": l2_gbs, "unit": "GB/s", "frac": l2_frac}
+    elif alu_frac > hbm_frac:
         roof = {"bound": "alu", "achieved": alu_ach / 1e12, "peak": alu_peak_pairs / 1e12,
                 "unit": "T bit-pair-ops/s", "frac": alu_frac}
     else:
@@ -256,6 +283,9 @@ def roofline(results, k_ms: float, launches: int, lop3: float, kernel: str, traf
                  "hbm_frac": hbm_frac, "hbm_peak_gbs": hbm_peak, "hbm_peak_source": f"{peak_kind} hbm_gbs",
                  "alu_frac": alu_frac, "lop3_lane_ops_per_s": lop3,
                  "alu_peak_source": "LOP3 throughput probe (peak.cu) x 32 bit-slices"})
+    if l2_gbs:
+        roof.update({"l2_frac": l2_frac, "l2_random_sector_peak_gbs": l2_gbs,
+                     "l2_peak_source": "L2 random 32-byte-sector probe (peak.cu), best of 3"})
     return roof
 
 
@@ -356,7 +386,7 @@ def run_gpu(args, rank, world, local_rank):
     if not args.no_wide:
         line["wide"] = wide_leg(ctx, lop3, cpu=not args.no_cpu_baseline)
     if not args.no_paper:
-        line["paper_instance"] = paper_instance_leg(ctx, lop3)
+        line["paper_instance"] = paper_instance_leg(ctx, lop3, l2_peak(dev))
     if not args.no_batch:
         bprobs = batched_problems()
         line["batched"] = batched_leg(ctx, dev, bprobs)
@@ -506,7 +536,7 @@ PAPER_A100_S = 4.9512          # Table 1: the paper's A100 time for this instanc
 PAPER_A100_REs = 26774099142   # Table 1: its candidate count there
 
 
-def paper_instance_leg(ctx, lop3: float):
+def paper_instance_leg(ctx, lop3: float, l2: float):
     """Time to the minimal regex on the one instance the paper prints with its
     GPU time: a search of ~2.6e10 candidates whose uniqueness structures live
     in HBM, the regime where the search is throughput-bound."""
@@ -519,9 +549,9 @@ def paper_instance_leg(ctx, lop3: float):
     r = min(runs, key=lambda x: x.ms_total)
     if r.status != rei.REI_OK or r.cost != 28:
         raise RuntimeError(f"printed instance: {r.status_name} cost {r.cost}")
-    roof = roofline([r], r.ms_search_kernel, r.search_launches, lop3, "k_solve_fused, then k_solve")
+    roof = roofline([r], r.ms_search_kernel, r.search_launches, lop3, "k_solve_fused, then k_solve", l2=l2)
     alg_bytes, _ = alg_work([r])
-    roof.update({"alg_bytes_per_solve": alg_bytes,
+    roof.update({"alg_bytes_per_solve": alg_bytes, "traffic": None,
                  "traffic_per_solve": recorded_traffic().get("printed_traffic_bytes_per_solve"),
                  "alg_bytes": "32 B probe per candidate + (48 W + 17) B per new language"})
     return {"workload": PAPER_WORKLOAD, "regex": r.regex, "cost": r.cost, "candidates": r.candidates,

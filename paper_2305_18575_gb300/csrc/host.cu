@@ -753,6 +753,7 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out, const Sl
     // 1-word languages with exact keys: a bitmap of the cached languages in
     // front of the uniqueness table
     const bool use_seen = c->opt_exact && W == 1 && n <= kSeenBits;
+    const bool use_direct = c->opt_exact && W == 1 && n <= kDirectBits;
 
     // launch shape
     const uint32_t seg_cap = 2 * max_cost + 4;
@@ -808,20 +809,23 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out, const Sl
     chunk_max = std::min<uint64_t>(chunk_max, use_seen ? (1ull << 27) : (1ull << 26));
     uint64_t cache_alloc = c->opt_cache_init > 0 ? (uint64_t)c->opt_cache_init : (1ull << 16);
     if (c->opt_cache_init <= 0 && c->cs.p && c->bp_l.p && c->bp_r.p && c->bp_op.p) {
-        // rows a previous solve already allocated (up to 1 Mi, so that the
-        // table this solve clears stays small)
+        // rows a previous solve already allocated (the table is cleared only
+        // where a search filled it, so a large one costs nothing here)
         const uint64_t have = std::min<uint64_t>({(uint64_t)(c->cs.bytes / (4ull * W)), (uint64_t)(c->bp_l.bytes / 4),
                                                   (uint64_t)(c->bp_r.bytes / 4), (uint64_t)c->bp_op.bytes,
                                                   (uint64_t)(c->used.bytes / 4)});
-        cache_alloc = std::max<uint64_t>(cache_alloc, std::min<uint64_t>(have, 1ull << 20));
+        cache_alloc = std::max<uint64_t>(cache_alloc, have);
     }
     cache_alloc = std::max<uint64_t>(1, std::min<uint64_t>(cache_alloc, cap));
 
     auto table_slots = [&](uint64_t alloc_rows) {
         uint64_t need = alloc_rows + (alloc_rows >= cap ? chunk_max : 0);
-        // (the table holds distinct languages: at most 2^n of them)
+        // (the table holds distinct languages: at most 2^n of them; with
+        // 1-word exact keys up to 2^26 it has a slot for every language, the
+        // language itself, and is never probed twice)
         if (n < 40) need = std::min<uint64_t>(need, 1ull << n);
-        return pow2_at_least(std::max<uint64_t>(2 * need, 1024));
+        const uint64_t t = pow2_at_least(std::max<uint64_t>(2 * need, 1024));
+        return use_direct ? std::max<uint64_t>(t, 1ull << n) : t;
     };
     uint64_t tslots = table_slots(cache_alloc);
     // after a fused launch the cache holds its rows: grow keeping them
@@ -935,6 +939,7 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out, const Sl
         hj->minidx = (uint32_t *)c->minidx.p;
         hj->exact = (W <= 2 && n <= 62 && c->opt_exact) ? 1u : 0u;
         hj->seen = use_seen ? (uint32_t *)c->seen.p : nullptr;
+        hj->direct = use_direct && tslots >= (1ull << n) ? 1u : 0u;
         hj->table_mask = tslots - 1;
         hj->tmp = (uint32_t *)c->tmp.p;
         hj->pending = (uint32_t *)c->pending.p;
@@ -975,7 +980,11 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out, const Sl
         }
         if (hst->status != ST_NEED_MEM) break;
         // grow the cache (keeping its rows) and rebuild the table
-        const uint64_t want = std::min<uint64_t>(cap, std::max<uint64_t>(cache_alloc * 4, hst->need_rows));
+        // (a search handed over by a first launch, or continued from a memory
+        // slot, may already fit: then only the table is rebuilt at this size)
+        const uint64_t want = hst->need_rows > cache_alloc
+                                  ? std::min<uint64_t>(cap, std::max<uint64_t>(cache_alloc * 4, hst->need_rows))
+                                  : cache_alloc;
         const uint64_t rows = hst->size;
         if ((s = grow_keep(c, c->cs, 4ull * W * want, 4ull * W * rows))) return s;
         if ((s = grow_keep(c, c->bp_op, want, rows))) return s;

@@ -28,6 +28,7 @@ constexpr uint32_t kNoRight = 0xFFFFFFFFu;
 constexpr uint32_t kNoOperand = 0xFFFFFFFFu;  // no cache row (rows are < 2^31)
 constexpr unsigned long long kNone = ~0ull;
 constexpr uint32_t kSeenBits = 30;   // largest |ic| with a bitmap of cached languages (2^30 bits = 128 MiB)
+constexpr uint32_t kDirectBits = 26; // largest |ic| whose table has a slot per language (2^26 x 12 bytes)
 
 // operators of a cache entry / candidate
 enum Op : uint32_t { OP_LEAF = 0, OP_OPT = 1, OP_STAR = 2, OP_CAT = 3, OP_ALT = 4 };
@@ -180,6 +181,9 @@ struct SolveJob {
     // cached is told by one bit instead of a table probe; nullptr = none.  All
     // zero between searches (a search clears the words of the rows it cached).
     uint32_t *seen;
+    // exact keys with a table of at least 2^|ic| slots: the slot of a
+    // language is the language itself (no hash, never a second probe)
+    uint32_t direct, direct_pad;
     // leaves: the alphabet symbols ordered by (cost, alphabet order) and
     // their costs (every symbol costs c[0] unless costs are given per
     // symbol; a cost above REI_MAX_COST is stored as REI_MAX_COST + 1);

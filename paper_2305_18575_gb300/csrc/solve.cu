@@ -278,8 +278,14 @@ __device__ void plan_level(const SolveJob &J, uint32_t c, const uint32_t *lvs, c
                 // left operands per right one: whichever needs fewer tiles
                 // (fewer partly empty tiles)
                 const uint32_t bw = bin_block(J.W);
-                const uint64_t t_rows = (uint64_t)s.lcnt * ((s.rcnt + bw - 1) / bw);
-                const uint64_t t_cols = (uint64_t)s.rcnt * ((s.lcnt + bw - 1) / bw);
+                uint64_t t_rows = (uint64_t)s.lcnt * ((s.rcnt + bw - 1) / bw);
+                uint64_t t_cols = (uint64_t)s.rcnt * ((s.lcnt + bw - 1) / bw);
+                if (J.W == 1) {
+                    // (and the lookup tables of each shared operand, about
+                    // one and a half tiles' work each)
+                    t_rows += s.lcnt + s.lcnt / 2;
+                    t_cols += s.rcnt + s.rcnt / 2;
+                }
                 s.swap = t_cols < t_rows ? 1u : 0u;
             } else {
                 const uint32_t cl = c1 + (uint32_t)(k - 3 - ncat), cr = (uint32_t)rem_u - cl;
@@ -495,8 +501,7 @@ __device__ void dedup_insert_exact(const TileCtx &T, const uint32_t *c, uint32_t
     // through L2).  Languages new in this chunk take the table protocol below.
     if (J.seen && ((ldcg(J.seen + (c[0] >> 5)) >> (c[0] & 31u)) & 1u)) return;
     const unsigned long long key = exact_key(c, W), pk = key | kXPend;
-    const uint64_t h = cs_hash(c, W, 1);
-    uint64_t p = h & J.table_mask;
+    uint64_t p = J.direct ? key : cs_hash(c, W, 1) & J.table_mask;
     for (uint64_t probe = 0; probe <= J.table_mask; probe++) {
         unsigned long long v = ld_relaxed_u64(&J.table[p]);
         if (v == kEmpty) {
@@ -1192,7 +1197,7 @@ __device__ void switch_to_global(const SolveJob &J, Shared &S, Lead *L) {
         const uint32_t *row = S.sm_rows + (uint64_t)k * W;
         const uint64_t h = cs_hash(row, W, 1);
         const unsigned long long v = J.exact ? exact_key(row, W) : ((uint64_t)(uint32_t)(h >> 32) << 32) | k;
-        uint64_t p = h & J.table_mask;
+        uint64_t p = J.direct ? v : h & J.table_mask;
         for (uint64_t probe = 0; probe <= J.table_mask; probe++) {
             if (atomicCAS(&J.table[p], kEmpty, v) == kEmpty) {
                 J.used[k] = (uint32_t)p;
@@ -2109,6 +2114,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_solve_fused(const __grid_c
                 j.cap = umin64(F.mem_budget / (4ull * W + 28), 0x7FFF0000ull);
                 j.exact = F.tmpl.exact && W <= 2 && I.n <= 62 ? 1u : 0u;
                 j.seen = j.exact && W == 1 && I.n <= F.seen_bits ? F.seen : nullptr;
+                j.direct = j.exact && W == 1 && (1ull << I.n) <= F.table_slots ? 1u : 0u;
                 j.handover = F.handover;
                 const uint64_t tmax = F.table_slots / 2;
                 j.cache_alloc = umin64(umin64(j.cap, F.rows_alloc), umin64(F.cs_words / W, tmax / 2));
@@ -2491,7 +2497,7 @@ __global__ void k_rehash(const __grid_constant__ SolveJob J, uint32_t count) {
         const uint64_t h = cs_hash(c, W, 1);
         const unsigned long long v =
             J.exact ? exact_key(c, W) : ((uint64_t)(uint32_t)(h >> 32) << 32) | (uint32_t)k;
-        uint64_t p = h & J.table_mask;
+        uint64_t p = J.direct ? v : h & J.table_mask;
         for (uint64_t probe = 0; probe <= J.table_mask; probe++) {
             if (atomicCAS(&J.table[p], kEmpty, v) == kEmpty) {
                 J.used[k] = (uint32_t)p;
