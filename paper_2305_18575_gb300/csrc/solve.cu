@@ -170,8 +170,9 @@ __device__ __forceinline__ uint32_t div_by(uint32_t x, uint32_t m, uint32_t l) {
 constexpr uint32_t kW1Tab = 128;   // 8 nibble tables of 16 words
 constexpr uint32_t kW1TabAt = 68;  // their offset (4 + 2 * 32 words; 16-byte aligned)
 // candidates per tile of a concatenation or union segment: 32 (one per lane),
-// 64 for 1-word languages (two per lane, built side by side)
-__host__ __device__ inline uint32_t bin_block(uint32_t W) { return W == 1 ? 64u : 32u; }
+// or for 1-word languages 32 * kW1Per (kW1Per per lane, built side by side)
+constexpr uint32_t kW1Per = 4;
+__host__ __device__ inline uint32_t bin_block(uint32_t W) { return W == 1 ? 32u * kW1Per : 32u; }
 
 __host__ __device__ inline uint32_t warp_words(uint32_t W) {
     const uint32_t Ws = (W & 1u) ? W : W + 1;
@@ -830,43 +831,48 @@ __device__ __forceinline__ uint32_t w1_lookup(const uint32_t *tab, uint32_t x, u
     return out;
 }
 
-// precision and uniqueness of 1-word candidates c0 (lane candidate x0) and
-// c1 (x1), valid as v0 / v1: both seen-bitmap words are read before either is
-// tested, so the two reads overlap
-__device__ __forceinline__ void w1_finish(const TileCtx &T, const Seg &sg, uint32_t c0, uint64_t x0, bool v0,
-                                          uint32_t c1, uint64_t x1, bool v1) {
+// precision and uniqueness of a lane's kW1Per 1-word candidates c[k]
+// (level-segment indices x0 + k * dx, valid where bit k of vb is set): every
+// seen-bitmap word is read before any is tested, so the reads overlap
+template <uint32_t K>
+__device__ __forceinline__ void w1_finish(const TileCtx &T, const Seg &sg, uint32_t (&c)[K], uint64_t x0, uint64_t dx,
+                                          uint32_t vb) {
     const SolveJob &J = *T.J;
     const Shared &S = *T.S;
     const uint32_t pos = S.pos[0], neg = S.neg[0];
-    const uint64_t xlev0 = sg.start + x0, xlev1 = sg.start + x1;
-    if (v0 && __popc(pos & ~c0) + __popc(neg & c0) <= J.max_errors) atomicMin(T.found, (unsigned long long)xlev0);
-    if (v1 && __popc(pos & ~c1) + __popc(neg & c1) <= J.max_errors) atomicMin(T.found, (unsigned long long)xlev1);
-    if (!T.dedup) return;
-    const uint32_t xl0 = (uint32_t)(xlev0 - T.chunk_start), xl1 = (uint32_t)(xlev1 - T.chunk_start);
-    if (!T.smem && J.exact && J.seen) {
-        // languages cached by earlier chunks end here (one bit each)
-        const uint32_t w0 = v0 ? ldcg(J.seen + (c0 >> 5)) : 0xFFFFFFFFu;
-        const uint32_t w1 = v1 ? ldcg(J.seen + (c1 >> 5)) : 0xFFFFFFFFu;
-        if (!((w0 >> (c0 & 31u)) & 1u)) dedup_insert_exact<1>(T, &c0, xl0);
-        if (!((w1 >> (c1 & 31u)) & 1u)) dedup_insert_exact<1>(T, &c1, xl1);
+    const uint64_t xlev0 = sg.start + x0;
+    if (T.dedup && !T.smem && J.exact && J.seen) {
+        // Languages cached by earlier chunks end here, at one bit each, and
+        // need no precision test: a cached language was tested when its
+        // first candidate was, and a precise one would have ended the search.
+        uint32_t w[K];
+#pragma unroll
+        for (uint32_t k = 0; k < K; k++) w[k] = ((vb >> k) & 1u) ? ldcg(J.seen + (c[k] >> 5)) : 0xFFFFFFFFu;
+#pragma unroll
+        for (uint32_t k = 0; k < K; k++) {
+            if ((w[k] >> (c[k] & 31u)) & 1u) continue;
+            const uint64_t xlev = xlev0 + k * dx;
+            if (__popc(pos & ~c[k]) + __popc(neg & c[k]) <= J.max_errors) atomicMin(T.found, (unsigned long long)xlev);
+            dedup_insert_exact<1>(T, &c[k], (uint32_t)(xlev - T.chunk_start));
+        }
         return;
     }
-    if (v0) {
-        if (T.smem) dedup_insert_smem<1>(T, &c0, xl0);
-        else if (J.exact) dedup_insert_exact<1>(T, &c0, xl0);
-        else if (T.bits) dedup_insert_solo<1>(T, &c0, xl0);
-        else dedup_insert<1>(T, &c0, xl0);
-    }
-    if (v1) {
-        if (T.smem) dedup_insert_smem<1>(T, &c1, xl1);
-        else if (J.exact) dedup_insert_exact<1>(T, &c1, xl1);
-        else if (T.bits) dedup_insert_solo<1>(T, &c1, xl1);
-        else dedup_insert<1>(T, &c1, xl1);
+#pragma unroll
+    for (uint32_t k = 0; k < K; k++) {
+        if (!((vb >> k) & 1u)) continue;
+        const uint64_t xlev = xlev0 + k * dx;
+        if (__popc(pos & ~c[k]) + __popc(neg & c[k]) <= J.max_errors) atomicMin(T.found, (unsigned long long)xlev);
+        if (!T.dedup) continue;
+        const uint32_t xl = (uint32_t)(xlev - T.chunk_start);
+        if (T.smem) dedup_insert_smem<1>(T, &c[k], xl);
+        else if (J.exact) dedup_insert_exact<1>(T, &c[k], xl);
+        else if (T.bits) dedup_insert_solo<1>(T, &c[k], xl);
+        else dedup_insert<1>(T, &c[k], xl);
     }
 }
 
-// one tile of 1-word candidates: 32 of a unary segment (one per lane), or 64
-// of a binary one (two per lane, 32 apart)
+// one tile of 1-word candidates: 32 of a unary segment (one per lane), or
+// 32 * kW1Per of a binary one (kW1Per per lane, 32 apart)
 __device__ void run_tile_w1(const TileCtx &T, const Seg &sg, const SegTile &tl, uint64_t tile, uint32_t *wm) {
     if (sg.op == OP_STAR) {  // (few candidates: the bit-sliced fixed point)
         run_tile<1>(T, sg, tl, tile, wm);
@@ -881,50 +887,59 @@ __device__ void run_tile_w1(const TileCtx &T, const Seg &sg, const SegTile &tl, 
         const uint64_t x = lo + tile * 32 + lane;
         const bool valid = x < hi;
         if (__ballot_sync(0xFFFFFFFFu, valid) == 0) return;
-        uint32_t c = 0;
+        uint32_t c[1] = {0u};
         if (sg.op == OP_LEAF) {
-            if (valid) c = __ldg(J.leaf + (uint64_t)J.leaf_sym[sg.lbase + (uint32_t)x] * J.leaf_stride);
+            if (valid) c[0] = __ldg(J.leaf + (uint64_t)J.leaf_sym[sg.lbase + (uint32_t)x] * J.leaf_stride);
         } else {
-            c = (valid ? ldop(cs + sg.lbase + (uint32_t)x) : 0u) | 1u;  // eps is ic word 0
+            c[0] = (valid ? ldop(cs + sg.lbase + (uint32_t)x) : 0u) | 1u;  // eps is ic word 0
         }
-        w1_finish(T, sg, c, x, valid, 0u, x, false);
+        w1_finish<1>(T, sg, c, x, 0, valid ? 1u : 0u);
         return;
     }
-    // binary: lane holds (row, col0) and (row, col0 + 32), or, swapped,
-    // (row0, col) and (row0 + 32, col)
+    // binary: candidate k of the lane is (row, col0 + 32 k), or, swapped,
+    // (row0 + 32 k, col)
+    constexpr uint32_t K = kW1Per;
     const bool swapped = sg.op == OP_CAT && sg.swap;
     const uint32_t t32 = (uint32_t)tile, qt = div_by(t32, tl.nb_mul, tl.nb_shift);
-    const uint32_t off = (t32 - qt * tl.nb) * 64 + lane;
-    uint32_t row0, row1, col0, col1;
-    uint64_t x0, x1;
-    bool v0, v1;
+    const uint32_t off = (t32 - qt * tl.nb) * (32 * K) + lane;
+    uint32_t row, col;  // of candidate 0
+    uint64_t x0, dx;
+    uint32_t vb = 0;
     if (swapped) {
-        col0 = col1 = qt;
-        row0 = (uint32_t)tl.r0 + off;
-        row1 = row0 + 32;
-        x0 = (uint64_t)row0 * sg.rcnt + qt;
-        x1 = x0 + 32ull * sg.rcnt;
-        v0 = row0 < sg.lcnt && x0 >= lo && x0 < hi;
-        v1 = row1 < sg.lcnt && x1 >= lo && x1 < hi;
+        col = qt;
+        row = (uint32_t)tl.r0 + off;
+        x0 = (uint64_t)row * sg.rcnt + col;
+        dx = 32ull * sg.rcnt;
+#pragma unroll
+        for (uint32_t k = 0; k < K; k++) {
+            const uint64_t x = x0 + k * dx;
+            if (row + 32 * k < sg.lcnt && x >= lo && x < hi) vb |= 1u << k;
+        }
     } else {
-        row0 = row1 = (uint32_t)tl.r0 + qt;
-        col0 = off;
-        col1 = off + 32;
-        x0 = (uint64_t)row0 * sg.rcnt + col0;
-        x1 = x0 + 32;
-        v0 = col0 < sg.rcnt && x0 >= lo && x0 < hi && (!sg.tri || col0 > row0);
-        v1 = col1 < sg.rcnt && x1 >= lo && x1 < hi && (!sg.tri || col1 > row0);
+        row = (uint32_t)tl.r0 + qt;
+        col = off;
+        x0 = (uint64_t)row * sg.rcnt + col;
+        dx = 32;
+#pragma unroll
+        for (uint32_t k = 0; k < K; k++) {
+            const uint64_t x = x0 + 32 * k;
+            const uint32_t ck = col + 32 * k;
+            if (ck < sg.rcnt && x >= lo && x < hi && (!sg.tri || ck > row)) vb |= 1u << k;
+        }
     }
-    if (__ballot_sync(0xFFFFFFFFu, v0 || v1) == 0) return;
-    uint32_t c0, c1;
+    if (__ballot_sync(0xFFFFFFFFu, vb != 0) == 0) return;
+    uint32_t c[K];
     if (sg.op == OP_ALT) {
-        const uint32_t l = ldop(cs + sg.lbase + row0);
-        c0 = l | (v0 ? ldop(cs + sg.rbase + col0) : 0u);
-        c1 = l | (v1 ? ldop(cs + sg.rbase + col1) : 0u);
+        const uint32_t l = ldop(cs + sg.lbase + row);
+        uint32_t r[K];
+#pragma unroll
+        for (uint32_t k = 0; k < K; k++) r[k] = ((vb >> k) & 1u) ? ldop(cs + sg.rbase + col + 32 * k) : 0u;
+#pragma unroll
+        for (uint32_t k = 0; k < K; k++) c[k] = l | r[k];
     } else {
         // the tables of the shared operand (its id in the word after them)
         uint32_t *tab = wm + kW1TabAt;
-        const uint32_t sid = swapped ? (0x80000000u | (sg.rbase + qt)) : (sg.lbase + row0);
+        const uint32_t sid = swapped ? (0x80000000u | (sg.rbase + col)) : (sg.lbase + row);
         if (tab[kW1Tab] != sid) {
             const uint32_t sh = ldop(cs + (sid & 0x7FFFFFFFu));
             __syncwarp();  // (every lane has read the old id)
@@ -932,14 +947,15 @@ __device__ void run_tile_w1(const TileCtx &T, const Seg &sg, const SegTile &tl, 
             if (lane == 0) tab[kW1Tab] = sid;
             __syncwarp();
         }
-        const uint32_t *ob = cs + (swapped ? sg.lbase : sg.rbase);
-        const uint32_t o0 = v0 ? ldop(ob + (swapped ? row0 : col0)) : 0u;
-        const uint32_t o1 = v1 ? ldop(ob + (swapped ? row1 : col1)) : 0u;
+        const uint32_t *ob = swapped ? cs + sg.lbase + row : cs + sg.rbase + col;
+        uint32_t o[K];
+#pragma unroll
+        for (uint32_t k = 0; k < K; k++) o[k] = ((vb >> k) & 1u) ? ldop(ob + 32 * k) : 0u;
         const uint32_t nt = (T.n + 3) >> 2;
-        c0 = w1_lookup(tab, o0, nt);
-        c1 = w1_lookup(tab, o1, nt);
+#pragma unroll
+        for (uint32_t k = 0; k < K; k++) c[k] = w1_lookup(tab, o[k], nt);
     }
-    w1_finish(T, sg, c0, x0, v0, c1, x1, v1);
+    w1_finish<K>(T, sg, c, x0, dx, vb);
 }
 
 // ---------------------------------------------------------------------------
