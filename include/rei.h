@@ -181,8 +181,8 @@ void rei_ctx_destroy(rei_ctx *ctx);
 
 /* Tuning options (defaults chosen by the library):
  *   REI_OPT_CHUNK      candidates per dedup chunk (0 = automatic: up to
- *                      2^25, or 2^27 for |ic| <= 30 with exact keys;
- *                      larger values are taken as 2^26, or 2^27 for those);
+ *                      2^25, or 2^28 for |ic| <= 30 with exact keys;
+ *                      larger values are taken as 2^26, or 2^28 for those);
  *                      the value only changes how a level is split into
  *                      chunks
  *   REI_OPT_GRID       CTAs of the search kernel (0 = all that fit)

@@ -801,12 +801,12 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out, const Sl
     // large levels this launch runs take chunks of up to 32 Mi candidates
     // (at most 1 GiB of candidate rows in tmp; the chunk that holds the
     // answer still runs to its end, which bounds the size from above)
-    // (with the seen bitmap, 128 Mi: most candidates end at one bit, so
-    // chunks are quicker and their fixed barriers weigh more)
+    // (with the seen bitmap, 256 Mi: most candidates end at one bit, so
+    // chunks are quicker and their fixed phases and barriers weigh more)
     uint64_t chunk_max = c->opt_chunk > 0 ? (uint64_t)c->opt_chunk
-                         : use_seen      ? (1ull << 27)
+                         : use_seen      ? (1ull << 28)
                                          : std::min<uint64_t>(1ull << 25, std::max<uint64_t>(1ull << 16, (1ull << 30) / (4ull * W)));
-    chunk_max = std::min<uint64_t>(chunk_max, use_seen ? (1ull << 27) : (1ull << 26));
+    chunk_max = std::min<uint64_t>(chunk_max, use_seen ? (1ull << 28) : (1ull << 26));
     uint64_t cache_alloc = c->opt_cache_init > 0 ? (uint64_t)c->opt_cache_init : (1ull << 16);
     if (c->opt_cache_init <= 0 && c->cs.p && c->bp_l.p && c->bp_r.p && c->bp_op.p) {
         // rows a previous solve already allocated (the table is cleared only
@@ -816,7 +816,9 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out, const Sl
                                                   (uint64_t)(c->used.bytes / 4)});
         cache_alloc = std::max<uint64_t>(cache_alloc, have);
     }
-    cache_alloc = std::max<uint64_t>(1, std::min<uint64_t>(cache_alloc, cap));
+    // (no more than 2^n distinct languages exist: rows beyond that are never used)
+    const uint64_t cap_rows = n < 63 ? std::min<uint64_t>(cap, 1ull << n) : cap;
+    cache_alloc = std::max<uint64_t>(1, std::min<uint64_t>(cache_alloc, cap_rows));
 
     auto table_slots = [&](uint64_t alloc_rows) {
         uint64_t need = alloc_rows + (alloc_rows >= cap ? chunk_max : 0);
@@ -848,7 +850,9 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out, const Sl
             c->table_extent = std::max<uint64_t>(c->table.bytes / 8, c->minidx.bytes / 4);
         }
     }
-    if ((s = ensure(c, c->tmp, 4ull * W * chunk_max))) return s;
+    // (candidate rows wait in tmp only when the keys are fingerprints)
+    const bool exact_keys = W <= 2 && n <= 62 && c->opt_exact;
+    if ((s = ensure(c, c->tmp, exact_keys ? 4096 : 4ull * W * chunk_max))) return s;
     if ((s = ensure(c, c->pending, 4ull * chunk_max))) return s;
     if ((s = ensure(c, c->slotpos, 4ull * chunk_max))) return s;
     {
@@ -983,7 +987,7 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out, const Sl
         // (a search handed over by a first launch, or continued from a memory
         // slot, may already fit: then only the table is rebuilt at this size)
         const uint64_t want = hst->need_rows > cache_alloc
-                                  ? std::min<uint64_t>(cap, std::max<uint64_t>(cache_alloc * 4, hst->need_rows))
+                                  ? std::min<uint64_t>(cap_rows, std::max<uint64_t>(cache_alloc * 4, hst->need_rows))
                                   : cache_alloc;
         const uint64_t rows = hst->size;
         if ((s = grow_keep(c, c->cs, 4ull * W * want, 4ull * W * rows))) return s;

@@ -1465,23 +1465,21 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
     // counted, then listed in order into pending[] over the CTA's own range
     // of candidates (phase B has read the pending list; the k-th survivor of
     // a range starting at candidate w0 * 32 is a candidate >= w0 * 32 + k, so
-    // the lists stay inside their ranges); the bitmap is cleared on the way
+    // the lists stay inside their ranges); the bitmap is cleared on the way.
+    // Each warp takes a contiguous part of the CTA's range and reads it 32
+    // consecutive words at a time: counted first, then listed with a warp scan.
     const uint64_t nwords = (C + 31) / 32;
     const uint64_t per_cta = (nwords + team_n - 1) / team_n;
     const uint64_t w0 = umin64(nwords, team_r * per_cta);
     const uint64_t w1 = umin64(nwords, w0 + per_cta);
-    const uint64_t per_thr = (w1 - w0 + blockDim.x - 1) / blockDim.x;
-    const uint64_t t0 = umin64(w1, w0 + tid * per_thr);
-    const uint64_t t1 = umin64(w1, t0 + per_thr);
-    uint32_t mycnt = 0;
-    for (uint64_t w = t0; w < t1; w++) mycnt += __popc(ldcg(J.bitmap + w));
     {
-        uint32_t x = mycnt;
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
-            if (lane >= (uint32_t)d) x += y;
-        }
-        if (lane == 31) s_red[wid] = x;
+        const uint64_t per_warp = (w1 - w0 + nwarps - 1) / nwarps;
+        const uint64_t a0 = umin64(w1, w0 + wid * per_warp), a1 = umin64(w1, a0 + per_warp);
+        uint32_t wcnt = 0;
+        for (uint64_t w = a0 + lane; w < a1; w += 32) wcnt += __popc(ldcg(J.bitmap + w));
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) wcnt += __shfl_xor_sync(0xFFFFFFFFu, wcnt, d);
+        if (lane == 0) s_red[wid] = wcnt;
         __syncthreads();
         uint32_t wbefore = 0, cta_cnt = 0;
         for (uint32_t k = 0; k < nwarps; k++) {
@@ -1489,15 +1487,26 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
             cta_cnt += s_red[k];
         }
         uint32_t *out = J.pending + w0 * 32;
-        uint32_t pos = wbefore + x - mycnt;
-        for (uint64_t w = t0; w < t1 && mycnt; w++) {
-            uint32_t bits = ldcg(J.bitmap + w);
-            if (!bits) continue;
-            J.bitmap[w] = 0;
-            while (bits) {
-                out[pos++] = (uint32_t)(w * 32 + (__ffs(bits) - 1));
-                bits &= bits - 1;
+        uint32_t pos = wbefore;
+        for (uint64_t base = a0; base < a1 && wcnt; base += 32) {
+            const uint64_t w = base + lane;
+            uint32_t bits = w < a1 ? ldcg(J.bitmap + w) : 0u;
+            const uint32_t cnt = __popc(bits);
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+                if (lane >= (uint32_t)d) incl += y;
             }
+            if (bits) {
+                J.bitmap[w] = 0;
+                uint32_t p = pos + incl - cnt;
+                while (bits) {
+                    out[p++] = (uint32_t)(w * 32 + (__ffs(bits) - 1));
+                    bits &= bits - 1;
+                }
+            }
+            pos += __shfl_sync(0xFFFFFFFFu, incl, 31);
         }
         if (tid == 0) J.blk[team_r] = cta_cnt;
         __syncthreads();
@@ -1881,7 +1890,10 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
         const bool dedup = !full && !otf;
         uint64_t C = T - pos;
         if (C > J.chunk_max) C = J.chunk_max;
-        if (dedup && J.cache_alloc < J.cap) {
+        // (no more than 2^|ic| distinct languages exist: a cache that holds
+        // that many, or the budget's cap, never runs out of room in a chunk)
+        const uint64_t ceil_rows = J.n < 63 ? umin64(J.cap, 1ull << J.n) : J.cap;
+        if (dedup && J.cache_alloc < ceil_rows) {
             const uint64_t room = J.cache_alloc - size;
             if (room < C) {
                 if (room * 4 >= J.chunk_max || room >= T - pos) {
@@ -1890,7 +1902,7 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
                     // the next launch continues from the global tables
                     if (L.smode) switch_to_global(J, S, &L);
                     if (tid == 0) {
-                        st->need_rows = (uint32_t)umin64(J.cap, (uint64_t)size + C);
+                        st->need_rows = (uint32_t)umin64(ceil_rows, (uint64_t)size + C);
                         L.status = ST_NEED_MEM;
                     }
                     __syncthreads();
