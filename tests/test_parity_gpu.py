@@ -454,6 +454,39 @@ def test_cache_contents_match_oracle(ctx):
             assert (ls[c], lc[c]) == run.level(c), c
 
 
+@pytest.mark.parametrize("chunk,solo,exact,handover", [(0, 0, 1, 0), (777, 0, 1, 0), (0, 1 << 30, 1, 0),
+                                                         (0, 0, 0, 0), (0, 0, 1, 1000), (777, 64, 1, 1000)])
+def test_one_word_cache_matches_oracle(chunk, solo, exact, handover):
+    """The 1-word path (|ic| = 25: candidates built in registers through nibble
+    tables, the bitmap of cached languages, a table slot per language) row by
+    row against the oracle: the printed specification searched to cost 14
+    (796 K candidates, 88.8 K languages), every chunk on the whole grid (solo 0)
+    or on one CTA, chunks split small and ragged (777), with fingerprint keys
+    instead of exact ones, and with levels above 1000 candidates handed from
+    the fused launch to the relaunched search kernel."""
+    run = oracle.Run()
+    ref = run.solve(A01, PIN_P, PIN_N, max_cost=14)
+    assert ref.status == oracle.NOT_FOUND
+    with rei.Context(device=0) as c:
+        c.set_option(rei.REI_OPT_CHUNK, chunk)
+        c.set_option(rei.REI_OPT_SOLO_TILES, solo)
+        c.set_option(rei.REI_OPT_EXACT_KEYS, exact)
+        if handover:
+            c.set_option(rei.REI_OPT_HANDOVER, handover)
+        got = c.solve_keep(rei.Problem(A01, PIN_P, PIN_N, max_cost=14, mem_budget=1 << 30))
+        check_same(got, ref, (chunk, solo, exact, handover))
+        assert got.words == 1 and got.n_ic == 25
+        rows, op, left, right, ls, lc = c.cache_dump(15)
+    assert len(rows) == ref.unique
+    for k in range(ref.unique):
+        lang, oop, ol, orr = run.cache_entry(k, 25)
+        assert bytes((rows[k][0] >> w) & 1 for w in range(25)) == lang, k
+        assert rows[k][0] >> 25 == 0, k  # padding bits stay zero
+        assert (op[k], left[k], right[k]) == (oop, ol, orr if orr >= 0 else 0xFFFFFFFF), k
+    for cst in range(1, 15):
+        assert (ls[cst], lc[cst]) == run.level(cst), cst
+
+
 def test_dynamic_tile_handout_keeps_results_and_cache():
     """A chunk of at least 32 tiles per warp of the grid hands its tiles out
     from a counter, in an order that varies from run to run; the order must not
