@@ -83,7 +83,7 @@ struct rei_ctx {
     uint32_t pair_cap = 1u << 16;
     // search
     DevBuf cs, bp_op, bp_l, bp_r, table, minidx, tmp, pending, slotpos, bitmap, blk, lvl_start, lvl_count,
-        state, solve_job, tstack, trace, used;
+        state, solve_job, tstack, trace, used, plan;
     DevBuf seen;               // bitmap of cached 1-word languages (2^kSeenBits bits)
     bool table_clean = false;  // the search kernel leaves the table (and seen) empty after a normal end
     uint64_t table_extent = 0; // slots of the table (and minidx) that may hold entries: beyond, all empty
@@ -521,6 +521,7 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
     if ((s = ensure(c, c->solve_job, sizeof(SolveJob)))) return s;
     if ((s = ensure(c, c->tstack, 16ull * (max_cost + 2)))) return s;
     if ((s = ensure(c, c->trace, 4ull * grid))) return s;
+    if ((s = ensure(c, c->plan, 8 * plan_words(2 * max_cost + 4)))) return s;
     if (c->opt_exact && !c->seen.p) {
         if ((s = ensure(c, c->seen, (1ull << kSeenBits) / 8))) return s;
         c->table_clean = false;
@@ -590,6 +591,7 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
     j.lvl_start = (int64_t *)c->lvl_start.p;
     j.lvl_count = (int64_t *)c->lvl_count.p;
     j.seg_cap = 2 * max_cost + 4;
+    j.plan = (uint64_t *)c->plan.p;
     j.st = (SolveState *)c->state.p;
     j.tree = (uint8_t *)c->state.p + sizeof(SolveState);
     j.tstack = (uint32_t *)c->tstack.p;
@@ -872,6 +874,7 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out, const Sl
     if ((s = ensure(c, c->solve_job, sizeof(SolveJob)))) return s;
     if ((s = ensure(c, c->tstack, 16ull * (max_cost + 2)))) return s;
     if ((s = ensure(c, c->trace, 4ull * grid))) return s;
+    if ((s = ensure(c, c->plan, 8 * plan_words(seg_cap)))) return s;
     if ((s = ensure_pinned(c, sizeof(SolveJob) + sizeof(SolveState) + tree_bytes))) return s;
     hst = (SolveState *)(c->h_pin + sizeof(SolveJob));  // (the pinned buffer may have moved)
 
@@ -954,6 +957,7 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out, const Sl
         hj->lvl_start = (int64_t *)c->lvl_start.p;
         hj->lvl_count = (int64_t *)c->lvl_count.p;
         hj->seg_cap = seg_cap;
+        hj->plan = (uint64_t *)c->plan.p;
         hj->st = (SolveState *)c->state.p;
         hj->tree = (uint8_t *)c->state.p + sizeof(SolveState);
         hj->tstack = (uint32_t *)c->tstack.p;
@@ -1043,6 +1047,15 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out, const Sl
                 "count+barrier %.1f us, append+barrier %.1f us; leader appends: keys %.1f sort %.1f copy %.1f us\n",
                 hst->t_sub[12] / 1e3, hst->t_sub[13] / 1e3, hst->t_sub[14] / 1e3, hst->t_sub[15] / 1e3,
                 hst->t_sub[3] / 1e3, hst->t_sub[4] / 1e3, hst->t_sub[5] / 1e3);
+        fprintf(stderr, "rei CTA 0 spans (timing builds): staging run %.1f us, lead init %.1f us, plan_level %.1f us, "
+                "tile_setup %.1f us, to global %.1f us, answer %.1f us, cleanup %.1f us\n", hst->t_sub[22] / 1e3,
+                hst->t_sub[17] / 1e3, hst->t_sub[18] / 1e3, hst->t_sub[19] / 1e3, hst->t_sub[16] / 1e3,
+                hst->t_sub[20] / 1e3, hst->t_sub[21] / 1e3);
+        fprintf(stderr, "rei solo chunks (timing builds): tile loop slowest warp %.1f us, tiles %.0f count, "
+                "before loop %.1f us\n", hst->t_sub[23] / 1e3, (double)hst->t_sub[24], hst->t_sub[25] / 1e3);
+        for (int k = 0; k < 5; k++)
+            fprintf(stderr, "rei solo tiles op%d (timing builds): %.1f us, %.0f count\n", k, hst->t_sub[26 + k] / 1e3,
+                    (double)hst->t_sub[32 + k]);
     }
     if (hst->status == ST_TIMEOUT && getenv("REI_DEBUG")) {
         std::vector<uint32_t> tr(grid);
@@ -1151,7 +1164,7 @@ void rei_ctx_destroy(rei_ctx *c) {
                       &c->len_start, &c->gt_off, &c->gt_pair, &c->pos, &c->neg, &c->leaf, &c->cs,
                       &c->bp_op, &c->bp_l, &c->bp_r, &c->table, &c->minidx, &c->tmp, &c->pending, &c->slotpos,
                       &c->bitmap, &c->blk, &c->lvl_start, &c->lvl_count, &c->state, &c->solve_job,
-                      &c->tstack, &c->trace, &c->used, &c->seen, &c->b_in, &c->b_sjobs, &c->b_sinfo, &c->b_stage,
+                      &c->tstack, &c->trace, &c->used, &c->plan, &c->seen, &c->b_in, &c->b_sjobs, &c->b_sinfo, &c->b_stage,
                       &c->b_jobs, &c->b_out, &c->b_tree, &c->b_queue, &c->s_cs, &c->s_bp_op, &c->s_bp_l,
                       &c->s_bp_r, &c->s_used, &c->s_table, &c->s_tmp, &c->s_pend, &c->s_slotpos, &c->s_bitmap,
                       &c->s_blk, &c->s_lvl, &c->s_state, &c->s_tstack};
@@ -1824,11 +1837,17 @@ rei_status server_setup(rei_server *S) {
     if (oom) return REI_OOM;
     if (cudaStreamCreateWithFlags(&S->kstream, cudaStreamNonBlocking) != cudaSuccess) return REI_ECUDA;
     if (cudaEventCreateWithFlags(&S->kdone, cudaEventDisableTiming) != cudaSuccess) return REI_ECUDA;
-    // allocations from the context allocator are stream-ordered on its stream
+    // allocations from the context allocator are stream-ordered on its stream.
+    // The slot tables, bitmaps and queue heads are emptied on the launch's own
+    // stream and waited for: both streams are non-blocking, so a plain
+    // cudaMemset (legacy default stream) would not be ordered before the
+    // first launch, which could then read the memory's previous contents as
+    // table entries (row indices from another allocation).
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return REI_ECUDA;
-    if (cudaMemset(m.table, 0xFF, 8 * slots * tslots) != cudaSuccess) return REI_ECUDA;
-    if (cudaMemset(m.bitmap, 0, 4 * slots * ((chunk + 31) / 32)) != cudaSuccess) return REI_ECUDA;
-    if (cudaMemset(A.head, 0, 64) != cudaSuccess) return REI_ECUDA;
+    if (cudaMemsetAsync(m.table, 0xFF, 8 * slots * tslots, S->kstream) != cudaSuccess) return REI_ECUDA;
+    if (cudaMemsetAsync(m.bitmap, 0, 4 * slots * ((chunk + 31) / 32), S->kstream) != cudaSuccess) return REI_ECUDA;
+    if (cudaMemsetAsync(A.head, 0, 64, S->kstream) != cudaSuccess) return REI_ECUDA;
+    if (cudaStreamSynchronize(S->kstream) != cudaSuccess) return REI_ECUDA;
     return REI_OK;
 }
 

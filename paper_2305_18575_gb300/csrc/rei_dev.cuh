@@ -105,6 +105,12 @@ struct Seg {
     uint32_t pad;
 };
 
+// words of a published chunk plan: nseg, tiles, then the segments, their
+// tiles in the chunk and the first tile of each (nseg + 1)
+__host__ __device__ inline size_t plan_words(uint32_t seg_cap) {
+    return 2 + (size_t)seg_cap * ((sizeof(Seg) + sizeof(uint64_t) * 5) / 8 + 1) + 1;
+}
+
 struct SolveState {
     uint32_t status;          // DevStatus
     uint32_t level;           // current cost level
@@ -134,7 +140,7 @@ struct SolveState {
     // level ends; and how many solo chunks, team chunks, levels
     uint64_t t_phase[4];
     uint64_t n_phase[3];
-    uint64_t t_sub[16];  // steps of CTA 0's chunks and launch (timing builds only)
+    uint64_t t_sub[40];  // steps of CTA 0's chunks and launch (timing builds only)
     uint32_t tile_next;  // the next tile of a team chunk handed out dynamically
     uint32_t pad;
 };
@@ -162,7 +168,7 @@ struct SolveJob {
     uint64_t chunk_max;
     // bookkeeping
     int64_t *lvl_start, *lvl_count;  // max_cost + 1 entries
-    Seg *segs;                       // per-CTA copies are in shared memory; this is spare
+    uint64_t *plan;                  // a team chunk's plan as CTA 0 publishes it (plan_words(seg_cap)); null: every CTA plans
     uint32_t seg_cap;
     SolveState *st;
     uint8_t *tree;                   // 2 * (max_cost + 1) bytes

@@ -31,7 +31,17 @@
 
 namespace rei {
 
-constexpr long long kSpinLimit = 10000000;  // x >= 100 ns sleeps: a wait gives up after >= 1 s
+constexpr long long kSpinLimit = 100000000;             // polls of a grid barrier, at most
+constexpr unsigned long long kBarrierWaitNs = 2000000000ull;  // a grid barrier gives up after 2 s
+#ifndef REI_BAR_NAP
+#define REI_BAR_NAP 100  // ns between polls of a grid barrier
+#endif
+#ifndef REI_X_FENCE
+#define REI_X_FENCE 0
+#endif
+#ifndef REI_CMD_NAP
+#define REI_CMD_NAP 1024  // longest back-off (ns) of an idle CTA between polls for work
+#endif
 
 // ---------------------------------------------------------------------------
 // memory helpers: data written during the launch by other CTAs is read through
@@ -60,6 +70,12 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const void *p) {
 
 __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
 // ---------------------------------------------------------------------------
 // bounded grid barrier: a monotonic 64-bit arrival counter (never reset during
 // a launch); barrier number e of a launch completes when the counter reaches
@@ -68,21 +84,27 @@ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < 
 
 __device__ bool grid_barrier(SolveState *st, uint32_t &epoch, uint32_t site, uint32_t *trace) {
     __shared__ int s_ok;
+#if !REI_X_FENCE
     // every thread publishes its own global writes and reductions (atomicMin
     // of the answer, atomicOr of survivors, table and cache stores) before the
     // CTA arrives
     __threadfence();
+#endif
     __syncthreads();
     epoch++;
     if (threadIdx.x == 0) {
         int ok = 1;
         const unsigned long long target = (unsigned long long)epoch * gridDim.x;
+#if REI_X_FENCE
+        __threadfence();
+#endif
         atomicAdd(&st->bar_arrive, 1ull);
         unsigned long long seen;
         long long spins = 0;
+        const unsigned long long t0 = globaltimer_ns();
         while ((seen = ld_acquire_u64(&st->bar_arrive)) < target) {
-            __nanosleep(100);
-            if (++spins > kSpinLimit) {
+            if (REI_BAR_NAP) __nanosleep(REI_BAR_NAP);
+            if (++spins > kSpinLimit || globaltimer_ns() - t0 > kBarrierWaitNs) {
                 ok = 0;
                 break;
             }
@@ -102,7 +124,9 @@ __device__ bool grid_barrier(SolveState *st, uint32_t &epoch, uint32_t site, uin
         s_ok = ok;
     }
     __syncthreads();
+#if !REI_X_FENCE
     __threadfence();
+#endif
     return s_ok != 0;
 }
 
@@ -344,12 +368,6 @@ __device__ int max_operand_level(const SolveJob &J, int c) {
 // ---------------------------------------------------------------------------
 // phase A: one warp tile of up to 32 candidates
 
-__device__ __forceinline__ unsigned long long globaltimer_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-
 // step timing of CTA 0's chunks alone, compiled in with -DREI_TIMING only
 #ifdef REI_TIMING
 #define REI_TMARK(cond, k)                                          \
@@ -361,7 +379,19 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
         }                                                           \
     } while (0)
 #define REI_TSTART() const unsigned long long t_mark0 = globaltimer_ns(); unsigned long long t_mark = t_mark0
+// a span of CTA 0's thread 0, added to t_sub[k]
+#define REI_TSPAN_BEGIN(v) const unsigned long long v = globaltimer_ns()
+#define REI_TSPAN_END(st_, v, k)                                                                   \
+    do {                                                                                           \
+        if (blockIdx.x == 0 && threadIdx.x == 0) (st_)->t_sub[k] += globaltimer_ns() - (v); \
+    } while (0)
 #else
+#define REI_TSPAN_BEGIN(v) \
+    do {                   \
+    } while (0)
+#define REI_TSPAN_END(st_, v, k) \
+    do {                         \
+    } while (0)
 #define REI_TMARK(cond, k) \
     do {                   \
     } while (0)
@@ -437,6 +467,20 @@ __device__ void dedup_insert_smem(const TileCtx &T, const uint32_t *c, uint32_t 
     atomicExch(&T.st->err, 2u);  // table full: cannot happen with load <= 1/2
 }
 
+// A fingerprint entry names a cached row (below the cache's rows) or, marked
+// pending, a candidate of the current chunk (below the chunk size).  Any other
+// value was not written by this search (memory not emptied before the search
+// began): the search is stopped with an error and nothing is read through it.
+__device__ __forceinline__ bool entry_ok(const TileCtx &T, uint32_t idx) {
+    const SolveJob &J = *T.J;
+    const bool ok = (idx & kPending) ? (idx & ~kPending) < J.chunk_max : idx < J.cache_alloc;
+    if (!ok) {
+        atomicCAS(&T.st->err, 0u, 6u);
+        atomicExch(&T.st->status, (uint32_t)ST_TIMEOUT);
+    }
+    return ok;
+}
+
 // uniqueness insert of candidate xl of a small chunk that CTA 0 runs alone
 // (no other CTA touches the table meanwhile).  The candidate's row goes to
 // tmp first, then the slot is claimed with one CAS whose result doubles as
@@ -461,7 +505,7 @@ __device__ void dedup_insert_solo(const TileCtx &T, const uint32_t *c, uint32_t 
             atomicOr(&T.bits[xl >> 5], 1u << (xl & 31));
             return;
         }
-        if ((uint32_t)(v >> 32) == fp) {
+        if ((uint32_t)(v >> 32) == fp && entry_ok(T, (uint32_t)v)) {
             __threadfence_block();
             const uint32_t idx = (uint32_t)v;
             const uint32_t *src = (idx & kPending) ? J.tmp + (uint64_t)(idx & ~kPending) * W
@@ -574,7 +618,7 @@ __device__ void dedup_insert(const TileCtx &T, const uint32_t *c, uint32_t xl) {
             v = old;
             __threadfence();
         }
-        if ((uint32_t)(v >> 32) == fp) {
+        if ((uint32_t)(v >> 32) == fp && entry_ok(T, (uint32_t)v)) {
             const uint32_t idx = (uint32_t)v;
             const uint32_t *src = (idx & kPending) ? J.tmp + (uint64_t)(idx & ~kPending) * W
                                                    : J.cs + (uint64_t)idx * W;
@@ -1035,6 +1079,143 @@ __device__ uint32_t emit_tree(const SolveJob &J, uint32_t op, uint32_t l, uint32
     return nt;
 }
 
+// The same postfix tokens, by one whole warp, in a few rounds of loads
+// instead of one per node: the tree is gathered breadth first (every node of
+// a depth fetches its children's back-pointers at once), subtree sizes are
+// summed bottom-up and postfix positions handed down top-down, depth by depth,
+// in shared scratch (`scr`, kTreeScratchWords words).  Returns the token count
+// (in every lane), or falls back to emit_tree when the tree does not fit.
+constexpr uint32_t kTreeNodes = 480;  // nodes the scratch holds (7 arrays + depth starts)
+constexpr uint32_t kTreeScratchWords = 7 * kTreeNodes + kTreeNodes + 1;
+__device__ uint32_t emit_tree_warp(const SolveJob &J, uint32_t op, uint32_t l, uint32_t r, uint32_t *scr) {
+    const uint32_t lane = threadIdx.x & 31;
+    uint32_t *nop = scr, *na = nop + kTreeNodes, *nb = na + kTreeNodes, *c0 = nb + kTreeNodes;
+    uint32_t *c1 = c0 + kTreeNodes, *sz = c1 + kTreeNodes, *pos = sz + kTreeNodes, *dep = pos + kTreeNodes;
+    if (lane == 0) {
+        nop[0] = op;
+        na[0] = l;
+        nb[0] = r;
+        dep[0] = 0;
+        dep[1] = 1;
+    }
+    __syncwarp();
+    // ---- gather, one depth per round: node v's children are appended in
+    // order (left, right) at the positions a warp scan of the child counts gives
+    uint32_t nd = 1, f0 = 0, f1 = 1;  // depths, current frontier [f0, f1)
+    bool fits = true;
+    while (f0 < f1) {
+        uint32_t next = f1;
+        for (uint32_t b0 = f0; b0 < f1; b0 += 32) {
+            const uint32_t v = b0 + lane;
+            uint32_t k = 0, o = 0;
+            if (v < f1) {
+                o = nop[v];
+                k = (o == OP_CAT || o == OP_ALT) ? 2u : (o == OP_OPT || o == OP_STAR) ? 1u : 0u;
+            }
+            uint32_t incl = k;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+                if (lane >= (uint32_t)d) incl += y;
+            }
+            const uint32_t at = next + incl - k, tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+            if (next + tot > kTreeNodes) {
+                fits = false;
+                break;
+            }
+            if (k) {
+                const uint32_t e0 = na[v];
+                uint32_t op0 = *(volatile const uint8_t *)(J.bp_op + e0), l0 = ldcg(J.bp_l + e0), r0 = ldcg(J.bp_r + e0);
+                uint32_t op1 = 0, l1 = 0, r1 = 0;
+                if (k == 2) {
+                    const uint32_t e1 = nb[v];
+                    op1 = *(volatile const uint8_t *)(J.bp_op + e1);
+                    l1 = ldcg(J.bp_l + e1);
+                    r1 = ldcg(J.bp_r + e1);
+                }
+                nop[at] = op0;
+                na[at] = l0;
+                nb[at] = r0;
+                c0[v] = at;
+                if (k == 2) {
+                    nop[at + 1] = op1;
+                    na[at + 1] = l1;
+                    nb[at + 1] = r1;
+                    c1[v] = at + 1;
+                }
+            }
+            next += tot;
+        }
+        fits = __all_sync(0xFFFFFFFFu, fits);
+        if (!fits) break;
+        __syncwarp();
+        f0 = f1;
+        f1 = next;
+        if (f0 < f1) {
+            if (nd + 1 > kTreeNodes) {
+                fits = false;
+                break;
+            }
+            nd++;
+            if (lane == 0) dep[nd] = f1;
+        }
+        __syncwarp();
+    }
+    if (!fits) {
+        uint32_t nt = 0;
+        if (lane == 0) nt = emit_tree(J, op, l, r);
+        return __shfl_sync(0xFFFFFFFFu, nt, 0);
+    }
+    const uint32_t nodes = f1;
+    // ---- subtree sizes, deepest depth first
+    for (int d = (int)nd - 1; d >= 0; d--) {
+        for (uint32_t v = dep[d] + lane; v < dep[d + 1]; v += 32) {
+            const uint32_t o = nop[v];
+            uint32_t t = 1;
+            if (o == OP_CAT || o == OP_ALT) t += sz[c0[v]] + sz[c1[v]];
+            else if (o == OP_OPT || o == OP_STAR) t += sz[c0[v]];
+            sz[v] = t;
+        }
+        __syncwarp();
+    }
+    // ---- postfix positions, from the root down: a node is last in its
+    // subtree, its left subtree first, then its right one
+    if (lane == 0) pos[0] = sz[0] - 1;
+    __syncwarp();
+    for (uint32_t d = 0; d < nd; d++) {
+        for (uint32_t v = dep[d] + lane; v < dep[d + 1]; v += 32) {
+            const uint32_t o = nop[v], p = pos[v];
+            if (o == OP_CAT || o == OP_ALT) {
+                const uint32_t start = p + 1 - sz[v];
+                pos[c0[v]] = start + sz[c0[v]] - 1;
+                pos[c1[v]] = p - 1;
+            } else if (o == OP_OPT || o == OP_STAR) {
+                pos[c0[v]] = p - 1;
+            }
+        }
+        __syncwarp();
+    }
+    // ---- tokens
+    const uint32_t cap = J.max_cost + 1;
+    for (uint32_t v = lane; v < nodes; v += 32) {
+        const uint32_t o = nop[v], p = pos[v];
+        uint8_t k = '+', a = 0;
+        switch (o) {
+        case OP_LEAF: k = 'a'; a = (uint8_t)na[v]; break;
+        case OP_OPT: k = '?'; break;
+        case OP_STAR: k = '*'; break;
+        case OP_CAT: k = '.'; break;
+        default: break;
+        }
+        if (p < cap) {
+            J.tree[2 * p] = k;
+            J.tree[2 * p + 1] = a;
+        }
+    }
+    __syncwarp();
+    return nodes;
+}
+
 // ---------------------------------------------------------------------------
 // the persistent search kernel
 //
@@ -1054,6 +1235,7 @@ constexpr uint32_t kFusedThreads = 512;
 constexpr uint32_t kSolveThreads = 512;
 constexpr uint32_t kSortMax = 2048;  // candidates of a chunk CTA 0 runs with shared-memory bookkeeping
 static_assert(kMaxTeam < kSortMax, "the append's prefix table of per-CTA counts lives in sortbuf");
+static_assert(kTreeScratchWords <= 2 * kSortMax, "the answer's tree is gathered in sortbuf");
 
 __host__ __device__ size_t solve_smem_bytes(uint32_t W, uint32_t n, uint32_t G, uint32_t max_len,
                                             uint32_t seg_cap, bool gt_in_smem, uint32_t warps, uint32_t small_rows) {
@@ -1099,7 +1281,10 @@ __device__ void tile_setup(Shared &S, uint32_t nseg, uint64_t cs0, uint64_t ce0,
             tl.nb = 1;
             if (a < e) {
                 if (g.op == OP_CAT || g.op == OP_ALT) {
-                    const uint64_t r0w = a / g.rcnt, r1 = (e - 1) / g.rcnt;
+                    // (32-bit division when the chunk's indices fit)
+                    const bool narrow = e <= 0xFFFFFFFFull;
+                    const uint64_t r0w = narrow ? (uint64_t)((uint32_t)a / g.rcnt) : a / g.rcnt;
+                    const uint64_t r1 = narrow ? (uint64_t)((uint32_t)(e - 1) / g.rcnt) : (e - 1) / g.rcnt;
                     tl.r0 = r0w;
                     if (g.op == OP_CAT && g.swap) {
                         tl.nb = (uint32_t)((r1 - r0w + bw) / bw);
@@ -1112,7 +1297,8 @@ __device__ void tile_setup(Shared &S, uint32_t nseg, uint64_t cs0, uint64_t ce0,
                     tiles = (e - a + 31) / 32;
                 }
             }
-            div_magic(tl.nb, tl.nb_mul, tl.nb_shift);
+            if (tl.nb > 1) div_magic(tl.nb, tl.nb_mul, tl.nb_shift);
+            else tl.nb_mul = 1, tl.nb_shift = 0;  // (x / 1 = (umulhi(1, x) + x) >> 0)
         }
         const uint64_t incl = warp_incl_scan(tiles, lane);
         if (s < nseg) S.tile_first[s] = t + incl - tiles;
@@ -1209,6 +1395,7 @@ __device__ void smem_append(const SolveJob &J, Shared &S, const ChunkArgs &a, ui
 // and the table cleanup see them
 __device__ void switch_to_global(const SolveJob &J, Shared &S, Lead *L) {
     const uint32_t W = J.W, rows = L->size;
+    REI_TSPAN_BEGIN(t_sw);
     for (uint32_t k = threadIdx.x; k < rows; k += blockDim.x) {
         const uint32_t *row = S.sm_rows + (uint64_t)k * W;
         const uint64_t h = cs_hash(row, W, 1);
@@ -1227,6 +1414,7 @@ __device__ void switch_to_global(const SolveJob &J, Shared &S, Lead *L) {
     __syncthreads();
     if (threadIdx.x == 0) L->smode = 0;
     __syncthreads();
+    REI_TSPAN_END(J.st, t_sw, 16);
 }
 
 // survivors of a small chunk CTA 0 ran alone, appended in candidate order: a
@@ -1379,6 +1567,14 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
         const uint32_t grab = W == 1 ? 4 * kGrab : kGrab;
         uint32_t t = gw, end = ntiles, step = nw;
         uint32_t nxt = 0;
+#ifdef REI_TIMING
+        __shared__ unsigned long long s_wmax;
+        if (tid == 0) s_wmax = 0;
+        __syncthreads();
+        const unsigned long long t_loop0 = globaltimer_ns();
+        if (!full && tid == 0) st->t_sub[25] += t_loop0 - t_mark0;
+        if (!full && tid == 0) st->t_sub[24] += ntiles;
+#endif
         if (dyn) {
             uint32_t cur = 0;
             if (lane == 0) cur = atomicAdd(&st->tile_next, grab);
@@ -1391,10 +1587,19 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
             while (s + 1 < a.nseg && S.tile_first[s + 1] <= t) s++;
             const SegTile &tl = S.tiles[s];
             if (tl.lo < tl.hi) {
+#ifdef REI_TIMING
+                const unsigned long long t_tile0 = globaltimer_ns();
+#endif
                 if (W == 1) run_tile_w1(TC, S.seg[s], tl, t - S.tile_first[s], wm);
                 else if (W == 2) run_tile<2>(TC, S.seg[s], tl, t - S.tile_first[s], wm);
                 else run_tile<0>(TC, S.seg[s], tl, t - S.tile_first[s], wm);
                 __syncwarp();
+#ifdef REI_TIMING
+                if (!full && lane == 0) {
+                    atomicAdd((unsigned long long *)&st->t_sub[26 + S.seg[s].op], globaltimer_ns() - t_tile0);
+                    atomicAdd((unsigned long long *)&st->t_sub[32 + S.seg[s].op], 1ull);
+                }
+#endif
             }
             t += step;
             if (dyn && t >= end) {
@@ -1403,6 +1608,11 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
                 if (lane == 0 && t < ntiles) nxt = atomicAdd(&st->tile_next, grab);
             }
         }
+#ifdef REI_TIMING
+        if (lane == 0) atomicMax(&s_wmax, globaltimer_ns() - t_loop0);
+        __syncthreads();
+        if (!full && tid == 0) st->t_sub[23] += s_wmax;
+#endif
     }
     if (!team_barrier(full, st, bar_epoch, 5, J.trace)) return -1;
     REI_TMARK(!full, 0);
@@ -1638,11 +1848,48 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
     return 0;
 }
 
+// a team chunk's plan (segments, their tiles in the chunk, first tiles), as
+// CTA 0 made it, for the other CTAs: written before the command that names
+// the chunk, read with it
+static_assert(sizeof(Seg) % 8 == 0 && sizeof(SegTile) == 40, "plan words");
+__device__ void write_plan(const SolveJob &J, const Shared &S, uint32_t nseg, uint64_t ntiles) {
+    const uint32_t sw = sizeof(Seg) / 8, tw = sizeof(SegTile) / 8;
+    uint64_t *P = J.plan;
+    if (threadIdx.x == 0) {
+        P[0] = nseg;
+        P[1] = ntiles;
+    }
+    const uint64_t *seg = reinterpret_cast<const uint64_t *>(S.seg);
+    const uint64_t *til = reinterpret_cast<const uint64_t *>(S.tiles);
+    for (uint32_t i = threadIdx.x; i < nseg * sw; i += blockDim.x) P[2 + i] = seg[i];
+    for (uint32_t i = threadIdx.x; i < nseg * tw; i += blockDim.x) P[2 + J.seg_cap * sw + i] = til[i];
+    for (uint32_t i = threadIdx.x; i <= nseg; i += blockDim.x) P[2 + J.seg_cap * (sw + tw) + i] = S.tile_first[i];
+}
+
+__device__ void read_plan(const SolveJob &J, Shared &S, uint64_t *s_tiles, uint32_t *s_nseg) {
+    const uint32_t sw = sizeof(Seg) / 8, tw = sizeof(SegTile) / 8, cap = J.seg_cap;
+    const uint64_t *P = J.plan;
+    uint64_t *seg = reinterpret_cast<uint64_t *>(S.seg);
+    uint64_t *til = reinterpret_cast<uint64_t *>(S.tiles);
+    if (threadIdx.x == 0) {
+        *s_nseg = (uint32_t)ld_relaxed_u64(P);
+        *s_tiles = ld_relaxed_u64(P + 1);
+    }
+    for (uint32_t i = threadIdx.x; i < cap * sw; i += blockDim.x) seg[i] = ld_relaxed_u64(P + 2 + i);
+    for (uint32_t i = threadIdx.x; i < cap * tw; i += blockDim.x) til[i] = ld_relaxed_u64(P + 2 + cap * sw + i);
+    for (uint32_t i = threadIdx.x; i <= cap; i += blockDim.x) S.tile_first[i] = ld_relaxed_u64(P + 2 + cap * (sw + tw) + i);
+}
+
 // CTA 0 publishes a command (release); the workers pick it up (acquire)
 __device__ void publish(SolveState *st, uint32_t cmd) {
+#if !REI_X_FENCE
     __threadfence();
+#endif
     __syncthreads();
     if (threadIdx.x == 0) {
+#if REI_X_FENCE
+        __threadfence();
+#endif
         st->cmd = cmd;
         __threadfence();
         atomicAdd(&st->cmd_seq, 1u);
@@ -1762,6 +2009,7 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
     const uint32_t tid = threadIdx.x, wid = tid >> 5;
     Lead &L = *K.L;
     Plan &s_plan = *K.plan;
+    REI_TSPAN_BEGIN(t_init);
     if (tid == 0) {
         L.status = st->status;
         L.level = st->level;
@@ -1794,6 +2042,7 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
     if (L.smode)
         for (uint32_t i = tid; i < 2 * J.small_rows; i += blockDim.x) S.sm_table[i] = kSmEmpty;
     __syncthreads();
+    REI_TSPAN_END(st, t_init, 17);
 
     bool found = false;
     uint32_t planned = 0xFFFFFFFFu;  // the level whose plan is in S.seg / s_plan
@@ -1852,9 +2101,11 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
         }
         // a level's plan depends on lower levels only: once per level
         if (level != planned) {
+            REI_TSPAN_BEGIN(t_pl);
             if (wid == 0) plan_level(J, level, S.lvs, S.lvc, S.seg, s_plan);
             __syncthreads();
             planned = level;
+            REI_TSPAN_END(st, t_pl, 18);
         }
         const uint32_t nseg = s_plan.nseg;
         const uint64_t T = s_plan.total;
@@ -1913,9 +2164,11 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
         if (C == 0) C = 1;  // unreachable with room >= 1; guards the loop
         ChunkArgs a{level, size, dedup ? 1u : 0u, nseg, pos, pos + C};
         // alone when the chunk is a few tiles per warp of this CTA
+        REI_TSPAN_BEGIN(t_ts);
         if (wid == 0) tile_setup(S, nseg, a.cs0, a.ce0, K.tiles, bin_block(J.W));
         if (tid == 0) *K.found = kNone;  // a small chunk's answer slot
         __syncthreads();
+        REI_TSPAN_END(st, t_ts, 19);
         const bool team = allow_team && *K.tiles > (uint64_t)J.solo_tiles;
         // the shared-memory start ends before a chunk it cannot hold
         if (L.smode && (team || !dedup || C > kSortMax || (uint64_t)size + C > J.small_rows))
@@ -1931,6 +2184,7 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
                 st->c_cs0 = a.cs0;
                 st->c_ce0 = a.ce0;
             }
+            if (J.plan) write_plan(J, S, nseg, *K.tiles);
             publish(st, CMD_CHUNK);
         }
         const int r = process_chunk(J, st, S, a, team, true, bar_epoch, K.tiles, K.red, K.found, K.npend, K.wm, &L);
@@ -1951,27 +2205,43 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
     }
 
     // ---- answer: back-pointers of the first precise candidate, then its tree
-    if (found && tid == 0) {
-        const unsigned long long f = ld_relaxed_u64(&st->found);
-        if (L.status == ST_RUNNING && f != kNone) {
-            uint32_t op, l, r;
-            decode(S.seg, s_plan.nseg, J.leaf_sym, f, op, l, r);
-            st->ans_op = op;
-            st->ans_l = l;
-            st->ans_r = r;
-            st->ans_cost = L.level;
-            uint64_t cnt = 0;
-            for (uint32_t s = 0; s < s_plan.nseg; s++) {
-                const Seg &g = S.seg[s];
-                uint64_t v = 0;
-                if (g.start + g.size <= f) v = valid_count(g);
-                else if (g.start <= f) v = valid_upto(g, f - g.start);
-                cnt += v;
-                L.cand_op[g.op] += v;
+    REI_TSPAN_BEGIN(t_ans);
+    // (warp 0: thread 0 decodes, the warp gathers the tree)
+    if (found && wid == 0) {
+        const uint32_t lane = tid & 31;
+        uint32_t op = 0, l = 0, r = 0, ok = 0;
+        if (lane == 0) {
+            const unsigned long long f = ld_relaxed_u64(&st->found);
+            if (L.status == ST_RUNNING && f != kNone) {
+                ok = 1;
+                decode(S.seg, s_plan.nseg, J.leaf_sym, f, op, l, r);
+                st->ans_op = op;
+                st->ans_l = l;
+                st->ans_r = r;
+                st->ans_cost = L.level;
+                uint64_t cnt = 0;
+                for (uint32_t s = 0; s < s_plan.nseg; s++) {
+                    const Seg &g = S.seg[s];
+                    uint64_t v = 0;
+                    if (g.start + g.size <= f) v = valid_count(g);
+                    else if (g.start <= f) v = valid_upto(g, f - g.start);
+                    cnt += v;
+                    L.cand_op[g.op] += v;
+                }
+                L.candidates += cnt;
             }
-            L.candidates += cnt;
-            st->tree_len = emit_tree(J, op, l, r);
-            L.status = ST_FOUND;
+        }
+        ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+        if (ok) {
+            op = __shfl_sync(0xFFFFFFFFu, op, 0);
+            l = __shfl_sync(0xFFFFFFFFu, l, 0);
+            r = __shfl_sync(0xFFFFFFFFu, r, 0);
+            // (the chunk's shared scratch is free once its answer is known)
+            const uint32_t nt = emit_tree_warp(J, op, l, r, reinterpret_cast<uint32_t *>(S.sortbuf));
+            if (lane == 0) {
+                st->tree_len = nt;
+                L.status = ST_FOUND;
+            }
         }
     }
     // the state the host reads, and a later launch of this search resumes from
@@ -1990,6 +2260,7 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
         for (int k = 0; k < 3; k++) st->n_phase[k] += tcnt[k];
     }
     __syncthreads();
+    REI_TSPAN_END(st, t_ans, 20);
     return 0;
 }
 
@@ -2023,25 +2294,34 @@ __device__ __forceinline__ void solve_body(const SolveJob &J, uint32_t &bar_epoc
                 uint32_t seq, nap = 64;
                 while ((seq = ld_relaxed_u32(&st->cmd_seq)) == seen) {
                     __nanosleep(nap);
-                    if (nap < 1024) nap <<= 1;
+                    if (nap < REI_CMD_NAP) nap <<= 1;
                     if (globaltimer_ns() - t0 > kWorkerWaitNs) break;
                 }
                 __threadfence();
+                s_ctl[4] = seq != seen;
                 if (seq == seen) {
                     atomicCAS(&st->err, 0u, 3u);
                     atomicExch(&st->status, (uint32_t)ST_TIMEOUT);
-                    s_ctl[0] = CMD_EXIT;
-                } else {
-                    s_ctl[0] = ld_relaxed_u32(&st->cmd);
-                    s_ctl[1] = ld_relaxed_u32(&st->c_level);
-                    s_ctl[2] = ld_relaxed_u32(&st->c_size);
-                    s_ctl[3] = ld_relaxed_u32(&st->c_dedup);
-                    s_pos[0] = ld_relaxed_u64(&st->c_cs0);
-                    s_pos[1] = ld_relaxed_u64(&st->c_ce0);
                 }
             }
             __syncthreads();
+#if !REI_X_FENCE
             __threadfence();
+#endif
+            if (!s_ctl[4]) return;
+            // the command, and the plan of a chunk CTA 0 published with it,
+            // read at once (the plan of the largest level fits; entries past
+            // the chunk's segments are not used)
+            if (tid == 0) {
+                s_ctl[0] = ld_relaxed_u32(&st->cmd);
+                s_ctl[1] = ld_relaxed_u32(&st->c_level);
+                s_ctl[2] = ld_relaxed_u32(&st->c_size);
+                s_ctl[3] = ld_relaxed_u32(&st->c_dedup);
+                s_pos[0] = ld_relaxed_u64(&st->c_cs0);
+                s_pos[1] = ld_relaxed_u64(&st->c_ce0);
+            }
+            if (J.plan) read_plan(J, S, &s_tiles, &s_ctl[5]);
+            __syncthreads();
             seen++;
             if (s_ctl[0] == CMD_CLEAN) {
                 clean_table(J, s_ctl[1], s_ctl[2], gridDim.x, blockIdx.x);
@@ -2049,23 +2329,28 @@ __device__ __forceinline__ void solve_body(const SolveJob &J, uint32_t &bar_epoc
             }
             if (s_ctl[0] != CMD_CHUNK) return;
             ChunkArgs a{s_ctl[1], s_ctl[2], s_ctl[3], 0, s_pos[0], s_pos[1]};
-            // the level table up to this level, as CTA 0 published it
-            for (uint32_t c = tid; c <= a.level; c += blockDim.x) {
-                S.lvs[c] = (uint32_t)ld_relaxed_u64(&J.lvl_start[c]);
-                S.lvc[c] = (uint32_t)ld_relaxed_u64(&J.lvl_count[c]);
+            if (J.plan) {
+                a.nseg = s_ctl[5];
+            } else {
+                // the level table up to this level, as CTA 0 published it
+                for (uint32_t c = tid; c <= a.level; c += blockDim.x) {
+                    S.lvs[c] = (uint32_t)ld_relaxed_u64(&J.lvl_start[c]);
+                    S.lvc[c] = (uint32_t)ld_relaxed_u64(&J.lvl_count[c]);
+                }
+                __syncthreads();
+                if ((tid >> 5) == 0) plan_level(J, a.level, S.lvs, S.lvc, S.seg, s_plan);
+                __syncthreads();
+                a.nseg = s_plan.nseg;
             }
-            __syncthreads();
-            if ((tid >> 5) == 0) plan_level(J, a.level, S.lvs, S.lvc, S.seg, s_plan);
-            __syncthreads();
-            a.nseg = s_plan.nseg;
-            if (process_chunk(J, st, S, a, true, false, bar_epoch, &s_tiles, s_red, &s_found, &s_npend, wm,
-                              nullptr) < 0)
+            if (process_chunk(J, st, S, a, true, J.plan != nullptr, bar_epoch, &s_tiles, s_red, &s_found, &s_npend,
+                              wm, nullptr) < 0)
                 return;
         }
     }
 
     // ---- CTA 0 leads
     if (lead_search(J, st, S, K, true, bar_epoch) < 0) return;
+    REI_TSPAN_BEGIN(t_cl);
     const uint32_t status = ld_relaxed_u32(&st->status);
     if (status == ST_FOUND || status == ST_NOT_FOUND || status == ST_OOM) {
         // every CTA empties its share of the slots this search filled
@@ -2082,6 +2367,7 @@ __device__ __forceinline__ void solve_body(const SolveJob &J, uint32_t &bar_epoc
     } else {
         publish(st, CMD_EXIT);
     }
+    REI_TSPAN_END(st, t_cl, 21);
 }
 
 __global__ void __launch_bounds__(kSolveThreads, 2) k_solve(const __grid_constant__ SolveJob J) {
@@ -2121,9 +2407,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_solve_fused(const __grid_c
             F.tmpl.lvl_count[c] = 0;
         }
         {
+            REI_TSPAN_BEGIN(t_sr);
             StageSmem M;
             stage_layout(kServeMaxIC, kServeMaxBytes, smem_raw, &M);
             stage_run(F.sj, M);
+            __syncthreads();
+            REI_TSPAN_END(st, t_sr, 22);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
