@@ -264,23 +264,26 @@ class _OutBuf:
     def __init__(self, regex_cap: int = 8192, tree_cap: int = 2 * (REI_MAX_COST + 1)):
         self.rbuf = C.create_string_buffer(regex_cap)
         self.tbuf = C.create_string_buffer(tree_cap)
+        self.raddr = C.addressof(self.rbuf)
+        self.taddr = C.addressof(self.tbuf)
         self.res = rei_result()
         self.reset()
 
     def reset(self):
         r = self.res
-        r.regex = C.cast(self.rbuf, C.c_void_p)
+        r.regex = self.raddr
         r.regex_cap = len(self.rbuf)
-        r.tree = C.cast(self.tbuf, C.c_void_p)
+        r.tree = self.taddr
         r.tree_cap = len(self.tbuf)
 
     def result(self, status: int) -> Result:
         r = self.res
         ok = status == REI_OK
         st = r.stats
+        # (only the bytes written are copied out of the buffers)
         return Result(status, r.cost if ok else 0,
-                      self.rbuf.raw[: r.regex_len].decode("utf-8") if ok else None,
-                      self.tbuf.raw[: r.tree_len] if ok else None, st.candidates, st.unique,
+                      C.string_at(self.raddr, r.regex_len).decode("utf-8") if ok else None,
+                      C.string_at(self.taddr, r.tree_len) if ok else None, st.candidates, st.unique,
                       st.levels, st.n_ic, st.words, st.guide_pairs, st.ms_stage, st.ms_total,
                       st.launches, st.bytes_h2d, st.bytes_d2h, tuple(st.cand_op), st.star_pairs,
                       st.ms_search_kernel, st.ms_stage_kernel, st.search_launches, st.grid)

@@ -75,6 +75,7 @@ struct rei_ctx {
     int64_t opt_fused = 1, opt_exact = 1;
     uint64_t opt_handover = 1ull << 22;  // levels of more candidates leave the fused launch
     uint64_t opt_yield_us = 500;         // batched / served problems longer than this continue on the whole GPU
+    bool phases = getenv("REI_PHASES") != nullptr;  // per-solve timing report on stderr (diagnostics)
     size_t smem_sm = 0;  // shared memory per SM
 
     // staging
@@ -423,6 +424,7 @@ size_t state_bytes(uint32_t max_cost) {
 rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_search, uint32_t &grid_out,
                      uint64_t &h2d, uint64_t &d2h) {
     rei_status s;
+    const double th0 = now_ms();
     const uint32_t n_str = p->n_pos + p->n_neg, max_cost = p->max_cost;
     const bool dev_in = (p->flags & REI_F_DEVICE_INPUT) != 0;
     const uint64_t total = dev_in ? p->total_bytes : (n_str ? p->offsets[n_str] : 0);
@@ -612,13 +614,19 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
     F.seen = (uint32_t *)c->seen.p;
     F.seen_bits = c->seen.p ? kSeenBits : 0;
 
+    const double th1 = now_ms();
     CK(cudaEventRecord(c->ev[0], c->stream));
     CK(launch_solve_fused(&F, grid, threads, smem, c->stream));
     CK(cudaEventRecord(c->ev[1], c->stream));
+    const double th2 = now_ms();
     c->launches++;
     uint8_t *hs = c->h_pin + sizeof(SolveJob);
     CK(cudaMemcpyAsync(hs, c->state.p, sb + sizeof(StageInfo), cudaMemcpyDeviceToHost, c->stream));
+    const double th3 = now_ms();
     CK(cudaStreamSynchronize(c->stream));
+    if (c->phases)
+        fprintf(stderr, "rei host (fused): setup %.1f us, launch %.1f us, read-back issue %.1f us, wait %.1f us\n",
+                (th1 - th0) * 1e3, (th2 - th1) * 1e3, (th3 - th2) * 1e3, (now_ms() - th3) * 1e3);
     c->pin_clean = true;
     d2h += sb + sizeof(StageInfo);
     float ms = 0;
@@ -1026,7 +1034,7 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out, const Sl
     }
     }
 
-    if (getenv("REI_PHASES")) {
+    if (c->phases) {
         fprintf(stderr, "rei phases: plan %.1f us, solo %.1f us (%llu chunks), team %.1f us (%llu chunks), "
                 "level-end %.1f us (%llu levels); search kernel %.1f us\n", hst->t_phase[0] / 1e3,
                 hst->t_phase[1] / 1e3, (unsigned long long)hst->n_phase[0], hst->t_phase[2] / 1e3,
@@ -1053,6 +1061,12 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out, const Sl
                 hst->t_sub[20] / 1e3, hst->t_sub[21] / 1e3);
         fprintf(stderr, "rei solo chunks (timing builds): tile loop slowest warp %.1f us, tiles %.0f count, "
                 "before loop %.1f us\n", hst->t_sub[23] / 1e3, (double)hst->t_sub[24], hst->t_sub[25] / 1e3);
+        fprintf(stderr, "rei team phase A (timing builds): publish %.1f us, last CTA starts tiles %.1f us, "
+                "slowest tile loop %.1f us, last arrival %.1f us, CTA 0 leaves barrier %.1f us, CTA 0 tile loop %.1f us "
+                "(after publish, summed over team chunks)\n", hst->t_sub[40] / 1e3, hst->t_sub[41] / 1e3,
+                hst->t_sub[42] / 1e3, hst->t_sub[43] / 1e3, hst->t_sub[39] / 1e3, hst->t_sub[37] / 1e3);
+        fprintf(stderr, "rei CTA 0 clock (timing builds): %.0f MHz\n",
+                hst->t_sub[11] ? 1e3 * (double)hst->t_sub[38] / (double)hst->t_sub[11] : 0.0);
         for (int k = 0; k < 5; k++)
             fprintf(stderr, "rei solo tiles op%d (timing builds): %.1f us, %.0f count\n", k, hst->t_sub[26 + k] / 1e3,
                     (double)hst->t_sub[32 + k]);
@@ -1096,6 +1110,8 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out, const Sl
     const double t1 = now_ms();
     out->stats.ms_stage = t_stage - t0;
     out->stats.ms_total = t1 - t0;
+    if (c->phases) fprintf(stderr, "rei host: solve call %.1f us (after the search %.1f us)\n", (t1 - t0) * 1e3,
+                           (t1 - t_stage) * 1e3);
     out->stats.launches = c->launches - l0;
     out->stats.bytes_h2d = h2d;
     out->stats.bytes_d2h = d2h;
@@ -1558,7 +1574,7 @@ rei_status run_batch(rei_ctx *c, const rei_problem *probs, const std::vector<uin
     float ms = 0;
     CK(cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
     if (kernel_ms) *kernel_ms = ms;
-    if (getenv("REI_PHASES"))
+    if (c->phases)
         fprintf(stderr, "rei batch of %u: upload %.3f ms, staging+jobs %.3f ms, search launch to answers %.3f ms "
                 "(kernel %.3f ms), total %.3f ms\n", nb, tb_up - tb0, tb_launch - tb_up, now_ms() - tb_launch, ms,
                 now_ms() - tb0);

@@ -140,7 +140,7 @@ struct SolveState {
     // level ends; and how many solo chunks, team chunks, levels
     uint64_t t_phase[4];
     uint64_t n_phase[3];
-    uint64_t t_sub[40];  // steps of CTA 0's chunks and launch (timing builds only)
+    uint64_t t_sub[48];  // steps of CTA 0's chunks and launch (timing builds only)
     uint32_t tile_next;  // the next tile of a team chunk handed out dynamically
     uint32_t pad;
 };

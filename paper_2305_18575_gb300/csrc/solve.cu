@@ -36,9 +36,6 @@ constexpr unsigned long long kBarrierWaitNs = 2000000000ull;  // a grid barrier 
 #ifndef REI_BAR_NAP
 #define REI_BAR_NAP 100  // ns between polls of a grid barrier
 #endif
-#ifndef REI_X_FENCE
-#define REI_X_FENCE 0
-#endif
 #ifndef REI_CMD_NAP
 #define REI_CMD_NAP 1024  // longest back-off (ns) of an idle CTA between polls for work
 #endif
@@ -84,20 +81,18 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 
 __device__ bool grid_barrier(SolveState *st, uint32_t &epoch, uint32_t site, uint32_t *trace) {
     __shared__ int s_ok;
-#if !REI_X_FENCE
-    // every thread publishes its own global writes and reductions (atomicMin
-    // of the answer, atomicOr of survivors, table and cache stores) before the
-    // CTA arrives
-    __threadfence();
-#endif
+    // the CTA's threads have finished their global writes and reductions
+    // (atomicMin of the answer, atomicOr of survivors, table and cache stores)
+    // when they pass __syncthreads; thread 0's fence then orders all of them
+    // (the barrier makes them visible to it) before its arrival, and its fence
+    // after the wait orders what the other CTAs wrote before every thread's
+    // later reads (the same pattern as a cooperative-groups grid sync)
     __syncthreads();
     epoch++;
     if (threadIdx.x == 0) {
         int ok = 1;
         const unsigned long long target = (unsigned long long)epoch * gridDim.x;
-#if REI_X_FENCE
         __threadfence();
-#endif
         atomicAdd(&st->bar_arrive, 1ull);
         unsigned long long seen;
         long long spins = 0;
@@ -124,9 +119,6 @@ __device__ bool grid_barrier(SolveState *st, uint32_t &epoch, uint32_t site, uin
         s_ok = ok;
     }
     __syncthreads();
-#if !REI_X_FENCE
-    __threadfence();
-#endif
     return s_ok != 0;
 }
 
@@ -1574,6 +1566,7 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
         const unsigned long long t_loop0 = globaltimer_ns();
         if (!full && tid == 0) st->t_sub[25] += t_loop0 - t_mark0;
         if (!full && tid == 0) st->t_sub[24] += ntiles;
+        if (full && tid == 0) atomicMax((unsigned long long *)&st->t_sub[45], t_loop0 - ld_relaxed_u64(&st->t_sub[47]));
 #endif
         if (dyn) {
             uint32_t cur = 0;
@@ -1612,9 +1605,23 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
         if (lane == 0) atomicMax(&s_wmax, globaltimer_ns() - t_loop0);
         __syncthreads();
         if (!full && tid == 0) st->t_sub[23] += s_wmax;
+        if (full && tid == 0) {
+            atomicMax((unsigned long long *)&st->t_sub[46], s_wmax);
+            atomicMax((unsigned long long *)&st->t_sub[44], globaltimer_ns() - ld_relaxed_u64(&st->t_sub[47]));
+            if (blockIdx.x == 0) st->t_sub[37] += s_wmax;
+        }
 #endif
     }
     if (!team_barrier(full, st, bar_epoch, 5, J.trace)) return -1;
+#ifdef REI_TIMING
+    if (full && blockIdx.x == 0 && tid == 0) {
+        st->t_sub[39] += globaltimer_ns() - ld_relaxed_u64(&st->t_sub[47]);
+        st->t_sub[41] += ld_relaxed_u64(&st->t_sub[45]);
+        st->t_sub[42] += ld_relaxed_u64(&st->t_sub[46]);
+        st->t_sub[43] += ld_relaxed_u64(&st->t_sub[44]);
+        st->t_sub[44] = st->t_sub[45] = st->t_sub[46] = 0;
+    }
+#endif
     REI_TMARK(!full, 0);
     REI_TMARK(full && blockIdx.x == 0, 12);
     if (small) {
@@ -1882,14 +1889,9 @@ __device__ void read_plan(const SolveJob &J, Shared &S, uint64_t *s_tiles, uint3
 
 // CTA 0 publishes a command (release); the workers pick it up (acquire)
 __device__ void publish(SolveState *st, uint32_t cmd) {
-#if !REI_X_FENCE
-    __threadfence();
-#endif
     __syncthreads();
     if (threadIdx.x == 0) {
-#if REI_X_FENCE
-        __threadfence();
-#endif
+        __threadfence();  // (after the barrier: covers every thread's writes)
         st->cmd = cmd;
         __threadfence();
         atomicAdd(&st->cmd_seq, 1u);
@@ -2184,8 +2186,14 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
                 st->c_cs0 = a.cs0;
                 st->c_ce0 = a.ce0;
             }
+#ifdef REI_TIMING
+            if (tid == 0) st->t_sub[47] = globaltimer_ns();
+#endif
             if (J.plan) write_plan(J, S, nseg, *K.tiles);
             publish(st, CMD_CHUNK);
+#ifdef REI_TIMING
+            if (tid == 0) st->t_sub[40] += globaltimer_ns() - st->t_sub[47];
+#endif
         }
         const int r = process_chunk(J, st, S, a, team, true, bar_epoch, K.tiles, K.red, K.found, K.npend, K.wm, &L);
         if (r < 0) return -1;
@@ -2305,9 +2313,6 @@ __device__ __forceinline__ void solve_body(const SolveJob &J, uint32_t &bar_epoc
                 }
             }
             __syncthreads();
-#if !REI_X_FENCE
-            __threadfence();
-#endif
             if (!s_ctl[4]) return;
             // the command, and the plan of a chunk CTA 0 published with it,
             // read at once (the plan of the largest level fits; entries past
@@ -2394,6 +2399,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_solve_fused(const __grid_c
     uint32_t bar_epoch = 0;
 #ifdef REI_TIMING
     const unsigned long long t_begin = globaltimer_ns();
+    const long long c_begin = clock64();
 #endif
     if (blockIdx.x == 0) {
         // the search state and the level table start empty
@@ -2472,7 +2478,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_solve_fused(const __grid_c
 #endif
     solve_body(J, bar_epoch);
 #ifdef REI_TIMING
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->t_sub[11] = globaltimer_ns() - t_begin;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->t_sub[11] = globaltimer_ns() - t_begin;
+        st->t_sub[38] = (unsigned long long)(clock64() - c_begin);
+    }
 #endif
 }
 
