@@ -1073,7 +1073,8 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out, const Sl
     }
     if (hst->status == ST_TIMEOUT && getenv("REI_DEBUG")) {
         std::vector<uint32_t> tr(grid);
-        cudaMemcpy(tr.data(), c->trace.p, 4ull * grid, cudaMemcpyDeviceToHost);
+        cudaMemcpyAsync(tr.data(), c->trace.p, 4ull * grid, cudaMemcpyDeviceToHost, c->stream);
+        cudaStreamSynchronize(c->stream);
         std::map<uint32_t, uint32_t> hist;
         for (uint32_t v : tr) hist[v]++;
         fprintf(stderr, "rei: barrier wait ran out: cta %u epoch %u site %u seen %u (grid %u); "
@@ -1855,8 +1856,8 @@ rei_status server_setup(rei_server *S) {
     if (cudaEventCreateWithFlags(&S->kdone, cudaEventDisableTiming) != cudaSuccess) return REI_ECUDA;
     // allocations from the context allocator are stream-ordered on its stream.
     // The slot tables, bitmaps and queue heads are emptied on the launch's own
-    // stream and waited for: both streams are non-blocking, so a plain
-    // cudaMemset (legacy default stream) would not be ordered before the
+    // stream and waited for: both streams are non-blocking, so a memset
+    // without a stream (legacy default stream) would not be ordered before the
     // first launch, which could then read the memory's previous contents as
     // table entries (row indices from another allocation).
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return REI_ECUDA;
@@ -2181,7 +2182,8 @@ void rei_server_destroy(rei_server *S) {
     if (S->kdone) cudaEventDestroy(S->kdone);
     if (getenv("REI_DEBUG") && S->args.head) {
         unsigned long long h[3] = {0, 0, 0};
-        if (cudaMemcpy(h, S->args.head, sizeof h, cudaMemcpyDeviceToHost) == cudaSuccess)
+        if (cudaMemcpyAsync(h, S->args.head, sizeof h, cudaMemcpyDeviceToHost, S->ctx->stream) == cudaSuccess &&
+            cudaStreamSynchronize(S->ctx->stream) == cudaSuccess)
             fprintf(stderr, "rei server: %llu jobs claimed, %llu ring entries incomplete when first read, "
                     "%llu given up\n", h[0], h[1], h[2]);
     }

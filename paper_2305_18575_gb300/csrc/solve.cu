@@ -34,10 +34,10 @@ namespace rei {
 constexpr long long kSpinLimit = 100000000;             // polls of a grid barrier, at most
 constexpr unsigned long long kBarrierWaitNs = 2000000000ull;  // a grid barrier gives up after 2 s
 #ifndef REI_BAR_NAP
-#define REI_BAR_NAP 100  // ns between polls of a grid barrier
+#define REI_BAR_NAP 32  // ns between polls of a grid barrier
 #endif
 #ifndef REI_CMD_NAP
-#define REI_CMD_NAP 1024  // longest back-off (ns) of an idle CTA between polls for work
+#define REI_CMD_NAP 256  // longest back-off (ns) of an idle CTA between polls for work
 #endif
 
 // ---------------------------------------------------------------------------
@@ -2296,8 +2296,8 @@ __device__ __forceinline__ void solve_body(const SolveJob &J, uint32_t &bar_epoc
         uint32_t seen = 0;
         for (;;) {
             if (tid == 0) {
-                // back off up to 1 us between polls: hundreds of idle CTAs
-                // must not crowd the L2 while CTA 0 works alone
+                // back off up to REI_CMD_NAP ns between polls: hundreds of
+                // idle CTAs must not crowd the L2 while CTA 0 works alone
                 const unsigned long long t0 = globaltimer_ns();
                 uint32_t seq, nap = 64;
                 while ((seq = ld_relaxed_u32(&st->cmd_seq)) == seen) {

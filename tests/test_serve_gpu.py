@@ -152,3 +152,20 @@ def test_served_pool_matches_stored_oracle_results():
         st, cost, cand, uniq, n_ic, tree = want[s]
         assert r.status == ST[st], s
         assert (r.cost, r.tree, r.candidates, r.unique, r.n_ic) == (cost, tree, cand, uniq, n_ic), s
+
+
+def test_serve_sessions_on_one_context_match_plain():
+    """Servers created one after another on one context reuse memory the
+    earlier ones (and the plain solves) freed; every session's first searches
+    must still start from empty slot tables.  Three sessions, with and without
+    a time allowance, each result against the problem solved alone."""
+    probs = mixed_problems()
+    with rei.Context(device=0) as ctx:
+        plain = [ctx.solve_problem(p) for p in probs]
+        for rep in range(3):
+            for yield_us in (0, 300):
+                ctx.set_option(rei.REI_OPT_YIELD_US, yield_us)
+                with rei.Server(ctx) as srv:
+                    got = [srv.result(t) for t in [srv.submit(p) for p in probs]]
+                for k, (a, b) in enumerate(zip(plain, got)):
+                    assert key(a) == key(b), (rep, yield_us, k)
