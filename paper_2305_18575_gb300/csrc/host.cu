@@ -76,6 +76,7 @@ struct rei_ctx {
     uint64_t opt_handover = 1ull << 22;  // levels of more candidates leave the fused launch
     uint64_t opt_yield_us = 500;         // batched / served problems longer than this continue on the whole GPU
     bool phases = getenv("REI_PHASES") != nullptr;  // per-solve timing report on stderr (diagnostics)
+    unsigned long long fused_launch_id = 0;         // ids of this context's fused launches (only grow)
     size_t smem_sm = 0;  // shared memory per SM
 
     // staging
@@ -519,7 +520,13 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
     if ((s = ensure(c, c->blk, 4ull * grid))) return s;
     if ((s = ensure(c, c->lvl_start, 8ull * (max_cost + 2)))) return s;
     if ((s = ensure(c, c->lvl_count, 8ull * (max_cost + 2)))) return s;
-    if ((s = ensure(c, c->state, sb + sizeof(StageInfo)))) return s;
+    {
+        // a new state buffer starts zeroed: the launch id it holds is then
+        // always below the next launch's (the launch resets the rest itself)
+        const void *before = c->state.p;
+        if ((s = ensure(c, c->state, sb + sizeof(StageInfo)))) return s;
+        if (c->state.p != before) CK(cudaMemsetAsync(c->state.p, 0, c->state.bytes, c->stream));
+    }
     if ((s = ensure(c, c->solve_job, sizeof(SolveJob)))) return s;
     if ((s = ensure(c, c->tstack, 16ull * (max_cost + 2)))) return s;
     if ((s = ensure(c, c->trace, 4ull * grid))) return s;
@@ -535,8 +542,6 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
     }
     c->table_clean = false;
     c->table_extent = std::max(c->table_extent, tslots);
-    // state, answer tokens, staging report: zero (the launch fills in the rest)
-    CK(cudaMemsetAsync(c->state.p, 0, sb + sizeof(StageInfo), c->stream));
 
     FuseArgs F;
     memset(&F, 0, sizeof F);
@@ -613,6 +618,7 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
     F.handover = c->opt_handover;
     F.seen = (uint32_t *)c->seen.p;
     F.seen_bits = c->seen.p ? kSeenBits : 0;
+    F.launch_id = ++c->fused_launch_id;
 
     const double th1 = now_ms();
     CK(cudaEventRecord(c->ev[0], c->stream));
@@ -878,7 +884,11 @@ rei_status solve_one(rei_ctx *c, const rei_problem *p, rei_result *out, const Sl
     if ((s = ensure(c, c->blk, 4ull * grid))) return s;
     if ((s = ensure(c, c->lvl_start, 8ull * (max_cost + 2)))) return s;
     if ((s = ensure(c, c->lvl_count, 8ull * (max_cost + 2)))) return s;
-    if ((s = ensure(c, c->state, sizeof(SolveState) + tree_bytes))) return s;
+    {
+        const void *before = c->state.p;  // (a new state buffer starts zeroed, as in run_fused)
+        if ((s = ensure(c, c->state, sizeof(SolveState) + tree_bytes))) return s;
+        if (c->state.p != before) CK(cudaMemsetAsync(c->state.p, 0, c->state.bytes, c->stream));
+    }
     if ((s = ensure(c, c->solve_job, sizeof(SolveJob)))) return s;
     if ((s = ensure(c, c->tstack, 16ull * (max_cost + 2)))) return s;
     if ((s = ensure(c, c->trace, 4ull * grid))) return s;

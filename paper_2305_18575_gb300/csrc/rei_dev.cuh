@@ -143,6 +143,9 @@ struct SolveState {
     uint64_t t_sub[48];  // steps of CTA 0's chunks and launch (timing builds only)
     uint32_t tile_next;  // the next tile of a team chunk handed out dynamically
     uint32_t pad;
+    // the fused launch that owns this state: CTA 0 resets the state, stages,
+    // then writes its launch id here; the other CTAs start once it names theirs
+    unsigned long long launch;
 };
 
 struct SolveJob {
@@ -219,6 +222,7 @@ struct FuseArgs {
     uint32_t smem_cap;        // dynamic shared memory of the launch
     uint32_t seen_bits;       // the seen bitmap covers languages of up to this many bits (0 = none)
     uint32_t *seen;           // 2^seen_bits bits, all zero
+    unsigned long long launch_id;  // larger than any id the state buffer can hold
 };
 
 

@@ -22,6 +22,7 @@
 //      temporary storage -> language cache copy of Sec. 3, "GPU language
 //      cache implementation"), and make their table slots point at the cache.
 #include <cstdint>
+#include <cstddef>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -2392,9 +2393,11 @@ __device__ __forceinline__ uint64_t auto_chunk(uint32_t W) {
 // size the search from the staged problem, then search, all in one launch.
 // A problem whose staging or search the launch cannot hold (|ic| > 2048, a
 // guide table beyond the pair buffer, shared memory) ends with ST_RESTAGE.
+static_assert(sizeof(StageInfo) % 8 == 0 && offsetof(SolveState, launch) % 8 == 0, "state reset by 8-byte words");
 __global__ void __launch_bounds__(kFusedThreads, 1) k_solve_fused(const __grid_constant__ FuseArgs F) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     __shared__ SolveJob J;
+    __shared__ uint32_t s_go;
     SolveState *st = F.tmpl.st;
     uint32_t bar_epoch = 0;
 #ifdef REI_TIMING
@@ -2402,18 +2405,29 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_solve_fused(const __grid_c
     const long long c_begin = clock64();
 #endif
     if (blockIdx.x == 0) {
-        // the search state and the level table start empty
-        if (threadIdx.x == 0) {
-            st->level = F.tmpl.cmin;
-            st->found = kNone;
-            st->partial_level = F.tmpl.max_cost + 1;
+        // this launch's state starts from zero (the state buffer holds the
+        // previous launch's; the other CTAs read none of it before the release
+        // below), and so does the level table
+        {
+            unsigned long long *w = reinterpret_cast<unsigned long long *>(st);
+            for (uint32_t i = threadIdx.x; i < offsetof(SolveState, launch) / 8; i += blockDim.x) w[i] = 0;
+            unsigned long long *si = reinterpret_cast<unsigned long long *>(F.sj.info);
+            for (uint32_t i = threadIdx.x; i < sizeof(StageInfo) / 8; i += blockDim.x) si[i] = 0;
         }
         for (uint32_t c = threadIdx.x; c < F.tmpl.max_cost + 2; c += blockDim.x) {
             F.tmpl.lvl_start[c] = 0;
             F.tmpl.lvl_count[c] = 0;
         }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            st->level = F.tmpl.cmin;
+            st->found = kNone;
+            st->partial_level = F.tmpl.max_cost + 1;
+        }
         {
+#ifdef REI_TIMING
             REI_TSPAN_BEGIN(t_sr);
+#endif
             StageSmem M;
             stage_layout(kServeMaxIC, kServeMaxBytes, smem_raw, &M);
             stage_run(F.sj, M);
@@ -2462,11 +2476,40 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_solve_fused(const __grid_c
             }
             *F.job = j;
             if (!ok) st->status = ST_RESTAGE;
+            // release: the job and the fresh state are in place
+            __threadfence();
+            atomicExch(&st->launch, F.launch_id);
+            s_go = ok ? 1u : 0u;
         }
+        __syncthreads();
+        if (!s_go) return;
+    } else {
+        // the other CTAs wait for CTA 0's release of this launch (a stale id
+        // in the state is always smaller: ids only grow), then take the job
+        if (threadIdx.x == 0) {
+            const unsigned long long t0 = globaltimer_ns();
+            uint32_t nap = 64, go = 0;
+            for (;;) {
+                if (ld_acquire_u64(&st->launch) == F.launch_id) {
+                    go = 1;
+                    break;
+                }
+                if (globaltimer_ns() - t0 > kBarrierWaitNs) break;
+                __nanosleep(nap);
+                if (nap < REI_CMD_NAP) nap <<= 1;
+            }
+            __threadfence();
+            if (go && ld_relaxed_u32(&st->status) != ST_RUNNING) go = 0;
+            if (!go && ld_acquire_u64(&st->launch) != F.launch_id) {
+                // (never released: the launch ends with an error for the host)
+                atomicCAS(&st->err, 0u, 4u);
+                atomicExch(&st->status, (uint32_t)ST_TIMEOUT);
+            }
+            s_go = go;
+        }
+        __syncthreads();
+        if (!s_go) return;
     }
-    // every CTA waits for the staging, then takes the job into shared memory
-    if (!grid_barrier(st, bar_epoch, 1, F.tmpl.trace)) return;
-    if (ld_relaxed_u32(&st->status) != ST_RUNNING) return;
     {
         const unsigned long long *src = reinterpret_cast<const unsigned long long *>(F.job);
         unsigned long long *dst = reinterpret_cast<unsigned long long *>(&J);
