@@ -277,16 +277,62 @@ class _OutBuf:
         r.tree_cap = len(self.tbuf)
 
     def result(self, status: int) -> Result:
-        r = self.res
-        ok = status == REI_OK
-        st = r.stats
-        # (only the bytes written are copied out of the buffers)
-        return Result(status, r.cost if ok else 0,
-                      C.string_at(self.raddr, r.regex_len).decode("utf-8") if ok else None,
-                      C.string_at(self.taddr, r.tree_len) if ok else None, st.candidates, st.unique,
-                      st.levels, st.n_ic, st.words, st.guide_pairs, st.ms_stage, st.ms_total,
-                      st.launches, st.bytes_h2d, st.bytes_d2h, tuple(st.cand_op), st.star_pairs,
-                      st.ms_search_kernel, st.ms_stage_kernel, st.search_launches, st.grid)
+        return _result(self.res, status, self.raddr, self.taddr)
+
+
+def _result(r: "rei_result", status: int, raddr: int, taddr: int) -> Result:
+    ok = status == REI_OK
+    st = r.stats
+    # (only the bytes written are copied out of the buffers)
+    return Result(status, r.cost if ok else 0,
+                  C.string_at(raddr, r.regex_len).decode("utf-8") if ok else None,
+                  C.string_at(taddr, r.tree_len) if ok else None, st.candidates, st.unique,
+                  st.levels, st.n_ic, st.words, st.guide_pairs, st.ms_stage, st.ms_total,
+                  st.launches, st.bytes_h2d, st.bytes_d2h, tuple(st.cand_op), st.star_pairs,
+                  st.ms_search_kernel, st.ms_stage_kernel, st.search_launches, st.grid)
+
+
+class _BatchBufs:
+    """Caller-owned outputs of a batch of n problems: one rei_result array and
+    one regex and one tree buffer for all of them (the pointers are set once;
+    the library writes only lengths, statistics and the text)."""
+
+    def __init__(self, n: int, regex_cap: int = 8192, tree_cap: int = 2 * (REI_MAX_COST + 1)):
+        self.n = n
+        self.rbuf = C.create_string_buffer(regex_cap * max(n, 1))
+        self.tbuf = C.create_string_buffer(tree_cap * max(n, 1))
+        self.outs = (rei_result * max(n, 1))()
+        ra, ta = C.addressof(self.rbuf), C.addressof(self.tbuf)
+        self.raddr = [ra + i * regex_cap for i in range(n)]
+        self.taddr = [ta + i * tree_cap for i in range(n)]
+        for i in range(n):
+            o = self.outs[i]
+            o.regex = self.raddr[i]
+            o.regex_cap = regex_cap
+            o.tree = self.taddr[i]
+            o.tree_cap = tree_cap
+
+    def results(self) -> List[Result]:
+        # every record unpacked at once (field by field through ctypes would
+        # cost more than the batch's search)
+        raw = C.string_at(C.addressof(self.outs), _RESULT_SIZE * self.n)
+        res = []
+        for i, f in enumerate(_RESULT_FMT.iter_unpack(raw)):
+            (status, cost, _, _, rlen, _, _, tlen, cand, uniq, levels, n_ic, words, _max_len, gp, ms_stage,
+             ms_total, launches, h2d, d2h, o0, o1, o2, o3, o4, star, ms_sk, ms_stk, s_l, grid) = f
+            ok = status == REI_OK
+            res.append(Result(status, cost if ok else 0,
+                              C.string_at(self.raddr[i], rlen).decode("utf-8") if ok else None,
+                              C.string_at(self.taddr[i], tlen) if ok else None, cand, uniq, levels, n_ic, words,
+                              gp, ms_stage, ms_total, launches, h2d, d2h, (o0, o1, o2, o3, o4), star, ms_sk,
+                              ms_stk, s_l, grid))
+        return res
+
+
+# rei_result as stored (x86-64 and aarch64 alike: natural alignment, no padding)
+_RESULT_FMT = struct.Struct("=iIQQQQQQ" "QQIIIIQddQQQ5QQddII")
+_RESULT_SIZE = _RESULT_FMT.size
+assert _RESULT_SIZE == C.sizeof(rei_result), (_RESULT_SIZE, C.sizeof(rei_result))
 
 
 def pack(pos: Sequence[bytes], neg: Sequence[bytes]):
@@ -467,18 +513,20 @@ class Context:
         """rei_solve_batch over `probs` (one staging and one search launch);
         a rei_tune field left 0 is chosen by the library (see include/rei.h)."""
         n = len(probs)
-        arr = (rei_problem * max(n, 1))(*[p.p for p in probs])
-        bufs = [_OutBuf() for _ in range(n)]
-        outs = (rei_result * max(n, 1))(*[b.res for b in bufs])
+        # the packed problems and the output buffers of the last batch are
+        # kept for a batch of the same problems (the same objects, in order)
+        key = tuple(map(id, probs))
+        if getattr(self, "_batch_key", None) != key:
+            self._batch_probs = list(probs)  # (keeps the objects, so their ids stay theirs)
+            self._batch_arr = (rei_problem * max(n, 1))(*[p.p for p in probs])
+            self._batch_key = key
+        if getattr(self, "_batch_bufs", None) is None or self._batch_bufs.n != n:
+            self._batch_bufs = _BatchBufs(n)
         tune = rei_tune(warps_per_cta, chunk, yield_us) if (warps_per_cta or chunk or yield_us) else None
-        s = rei_solve_batch(self.h, arr, n, outs, tune)
+        s = rei_solve_batch(self.h, self._batch_arr, n, self._batch_bufs.outs, tune)
         if s != REI_OK:
             raise RuntimeError(f"rei_solve_batch: {STATUS_NAMES.get(s, s)}")
-        res = []
-        for b, o in zip(bufs, outs):
-            b.res = o
-            res.append(b.result(o.status))
-        return res
+        return self._batch_bufs.results()
 
     def solve_keep(self, prob: Problem) -> Result:
         """solve_problem with the cache kept for cache_dump()."""

@@ -40,6 +40,10 @@ cudaError_t launch_solve(const SolveJob *job, uint32_t grid, uint32_t threads, s
 cudaError_t solve_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm);
 cudaError_t solve_smem_max(size_t *bytes);
 cudaError_t solve_batch_smem_max(size_t *bytes);
+cudaError_t launch_solve_groups(const BatchJob *jobs_dev, const GroupArgs *args, uint32_t grid, uint32_t threads,
+                                size_t smem, cudaStream_t stream);
+cudaError_t solve_groups_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm);
+cudaError_t solve_groups_smem_max(size_t *bytes);
 cudaError_t launch_rehash(const SolveJob *job, uint32_t count, uint32_t grid, cudaStream_t stream);
 size_t solve_smem_bytes(uint32_t W, uint32_t n, uint32_t G, uint32_t max_len, uint32_t seg_cap,
                         bool gt_in_smem, uint32_t warps, uint32_t small_rows = 0);
@@ -93,6 +97,7 @@ struct rei_ctx {
     DevBuf b_in, b_sjobs, b_sinfo, b_stage, b_jobs, b_out, b_tree, b_queue;
     DevBuf s_cs, s_bp_op, s_bp_l, s_bp_r, s_used, s_table, s_tmp, s_pend, s_slotpos, s_bitmap, s_blk, s_lvl,
         s_state, s_tstack;
+    DevBuf g_idx, g_blk, g_plan, g_tmp, g_pend, g_slotpos, g_bitmap;  // parked searches continued in their slots
     uint64_t slot_rows = 0, slot_cs_words = 0, slot_table = 0, slot_tmp_words = 0, slot_chunk = 0;
     uint32_t slot_count = 0;
     bool slots_clean = false;
@@ -106,6 +111,10 @@ struct rei_ctx {
     // last solve (for rei_cache_dump)
     bool last_valid = false;
     uint32_t last_W = 0, last_size = 0, last_max_cost = 0;
+
+    // contexts of its own (streams, buffers) on which a batch continues its
+    // parked searches side by side, each launch on a share of the GPU
+    std::vector<rei_ctx *> helpers;
 
     cudaEvent_t ev[2] = {nullptr, nullptr};
     std::mutex mu;
@@ -660,6 +669,8 @@ struct SlotResume {
     uint32_t slot;
 };
 
+constexpr uint32_t kBatchHelpers = 8;  // parked searches of a batch continued side by side, at most
+
 // Copy a parked slot's search into the context: the state into the pinned
 // state area, the cached rows, back-pointers and level table into the
 // context's buffers; clear what the continued search needs cleared.  The
@@ -1185,6 +1196,8 @@ rei_status rei_ctx_create(rei_ctx **out, int device, const rei_alloc *alloc, voi
 
 void rei_ctx_destroy(rei_ctx *c) {
     if (!c) return;
+    for (rei_ctx *h : c->helpers) rei_ctx_destroy(h);
+    c->helpers.clear();
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     DevBuf *bufs[] = {&c->in_bytes, &c->in_offs, &c->stage_job, &c->stage_info, &c->word_start, &c->word_len,
@@ -1194,7 +1207,8 @@ void rei_ctx_destroy(rei_ctx *c) {
                       &c->tstack, &c->trace, &c->used, &c->plan, &c->seen, &c->b_in, &c->b_sjobs, &c->b_sinfo, &c->b_stage,
                       &c->b_jobs, &c->b_out, &c->b_tree, &c->b_queue, &c->s_cs, &c->s_bp_op, &c->s_bp_l,
                       &c->s_bp_r, &c->s_used, &c->s_table, &c->s_tmp, &c->s_pend, &c->s_slotpos, &c->s_bitmap,
-                      &c->s_blk, &c->s_lvl, &c->s_state, &c->s_tstack};
+                      &c->s_blk, &c->s_lvl, &c->s_state, &c->s_tstack, &c->g_idx, &c->g_blk, &c->g_plan,
+                      &c->g_tmp, &c->g_pend, &c->g_slotpos, &c->g_bitmap};
     for (DevBuf *b : bufs) dev_free(c, *b);
     cudaStreamSynchronize(c->stream);
     if (c->h_pin) cudaFreeHost(c->h_pin);
@@ -1376,7 +1390,7 @@ rei_status run_batch(rei_ctx *c, const rei_problem *probs, const std::vector<uin
     if ((s = ensure(c, c->b_tree, tree_bytes * nb))) return s;
     if ((s = ensure(c, c->b_queue, 16))) return s;
     const size_t host_bytes = std::max(P.in_bytes, std::max(sizeof(StageJob), sizeof(BatchJob)) * nb) +
-                              (sizeof(StageInfo) + sizeof(BatchOut) + tree_bytes) * nb + 4096;
+                              (sizeof(StageInfo) + sizeof(BatchOut) + tree_bytes + 8) * nb + 4096;
     if ((s = ensure_pinned(c, host_bytes))) return s;
     CK(cudaStreamSynchronize(c->stream));
     uint8_t *hp = c->h_pin;
@@ -1595,32 +1609,26 @@ rei_status run_batch(rei_ctx *c, const rei_problem *probs, const std::vector<uin
     // more problems): launched again
     struct Parked {
         uint32_t prob, slot;
-        double ms;  // time the search spent on its CTA
+        double ms;           // time the search spent on its CTA (and in its slot group)
+        uint32_t k;          // its entry among the launch's problems
+        uint32_t need_rows;  // 0: parked at its time allowance
     };
     std::vector<Parked> redo;
     std::vector<uint32_t> again;
-    for (uint32_t k = 0; k < nl; k++) {
+    // a finished search's report into its result
+    auto finish = [&](uint32_t k, const BatchOut &b, double ms) {
         const uint32_t t = live[k];
         const rei_problem &p = probs[sel[t]];
         rei_result &o = outs[sel[t]];
-        const BatchOut &b = bo[k];
-        if (b.status == ST_RUNNING) {
-            again.push_back(sel[t]);
-            continue;
-        }
-        if (b.status == ST_NEED_MEM) {
-            redo.push_back({sel[t], b.slot, b.ns / 1e6});
-            continue;
-        }
         o.stats.candidates = b.candidates;
         o.stats.unique = b.unique;
         o.stats.levels = b.levels;
         for (int q = 0; q < 5; q++) o.stats.cand_op[q] = b.cand_op[q];
         o.stats.star_pairs = o.stats.guide_pairs - o.stats.n_ic;
-        o.stats.ms_search_kernel = b.ns / 1e6;
-        o.stats.ms_total = b.ns / 1e6;
-        o.stats.launches = 2;
-        o.stats.search_launches = 1;
+        o.stats.ms_search_kernel = ms;
+        o.stats.ms_total = ms;
+        o.stats.launches += 2;
+        o.stats.search_launches += 1;
         o.stats.grid = slots;
         switch (b.status) {
         case ST_FOUND: o.status = REI_OK; break;
@@ -1633,15 +1641,166 @@ rei_status run_batch(rei_ctx *c, const rei_problem *probs, const std::vector<uin
             o.cost = b.cost;
             if (write_outputs(&o, tr + tree_bytes * k, b.tree_len, p.alphabet) != REI_OK) o.status = REI_EBUFSZ;
         }
+    };
+    for (uint32_t k = 0; k < nl; k++) {
+        const uint32_t t = live[k];
+        const BatchOut &b = bo[k];
+        if (b.status == ST_RUNNING) {
+            again.push_back(sel[t]);
+            continue;
+        }
+        if (b.status == ST_NEED_MEM) {
+            redo.push_back({sel[t], b.slot, b.ns / 1e6, k, b.need_rows});
+            continue;
+        }
+        finish(k, b, b.ns / 1e6);
     }
-    for (const Parked &pk : redo) {
+
+    // searches parked at their time allowance (their slot holds their cache
+    // and table): continued side by side in one launch, a group of CTAs per
+    // search in its slot
+    std::vector<Parked> rest;
+    {
+        std::vector<Parked> grp;
+        for (const Parked &pk : redo) (pk.slot < slots && pk.need_rows == 0 ? grp : rest).push_back(pk);
+        const uint32_t threads_g = 256;
+        size_t smem_g = 0, smem_gmax = 0;
+        uint32_t seg_cap_g = 0, wmax_g = 1;
+        for (const Parked &pk : grp) {
+            const SolveJob &J = bj[pk.k].job;
+            smem_g = std::max(smem_g, solve_smem_bytes(J.W, J.n, J.G, J.max_len, J.seg_cap, J.gt_in_smem, threads_g / 32));
+            seg_cap_g = std::max(seg_cap_g, J.seg_cap);
+            wmax_g = std::max(wmax_g, J.W);
+        }
+        int bps_g = 0;
+        if (!grp.empty()) {
+            CK(solve_groups_smem_max(&smem_gmax));
+            if (smem_g <= smem_gmax) CK(solve_groups_occupancy(threads_g, smem_g, &bps_g));
+        }
+        const uint32_t cap = (uint32_t)std::max(0, bps_g) * (uint32_t)c->sm_count;
+        const uint32_t ng = (uint32_t)std::min<size_t>(grp.size(), cap / 2);
+        for (uint32_t q = ng; q < grp.size(); q++) rest.push_back(grp[q]);
+        if (ng > 0) {
+            const uint32_t gctas = std::min<uint32_t>(cap / ng, kMaxTeam);
+            const uint64_t pstride = plan_words(seg_cap_g);
+            if ((s = ensure(c, c->g_idx, 8ull * ng))) return s;
+            if ((s = ensure(c, c->g_blk, 4ull * ng * gctas))) return s;
+            if ((s = ensure(c, c->g_plan, 8ull * ng * pstride))) return s;
+            // chunks of up to 2^18 candidates (the slot tables' room), rows of
+            // the widest group's languages; about 1 GiB of rows at most
+            uint64_t chunk_g = 1ull << 18;
+            while (chunk_g > 4096 && chunk_g * wmax_g * ng > (1ull << 28)) chunk_g >>= 1;
+            const uint64_t tmp_g = chunk_g * wmax_g, bmw_g = (chunk_g + 31) / 32;
+            if ((s = ensure(c, c->g_tmp, 4ull * ng * tmp_g))) return s;
+            if ((s = ensure(c, c->g_pend, 4ull * ng * chunk_g))) return s;
+            if ((s = ensure(c, c->g_slotpos, 4ull * ng * chunk_g))) return s;
+            if ((s = ensure(c, c->g_bitmap, 4ull * ng * bmw_g))) return s;
+            CK(cudaMemsetAsync(c->g_bitmap.p, 0, 4ull * ng * bmw_g, c->stream));
+            uint32_t *gidx = (uint32_t *)(((uintptr_t)(tr + tree_bytes * nb) + 7) & ~(uintptr_t)7);
+            for (uint32_t g = 0; g < ng; g++) {
+                gidx[g] = grp[g].k;
+                gidx[ng + g] = grp[g].slot;
+            }
+            CK(cudaMemcpyAsync(c->g_idx.p, gidx, 8ull * ng, cudaMemcpyHostToDevice, c->stream));
+            GroupArgs G{};
+            G.slot = A.slot;
+            G.prob = (const uint32_t *)c->g_idx.p;
+            G.slot_of = (const uint32_t *)c->g_idx.p + ng;
+            G.groups = ng;
+            G.group_ctas = gctas;
+            G.blk = (uint32_t *)c->g_blk.p;
+            G.plan = (uint64_t *)c->g_plan.p;
+            G.plan_stride = pstride;
+            G.tmp = (uint32_t *)c->g_tmp.p;
+            G.pending = (uint32_t *)c->g_pend.p;
+            G.slotpos = (uint32_t *)c->g_slotpos.p;
+            G.bitmap = (uint32_t *)c->g_bitmap.p;
+            G.chunk = chunk_g;
+            G.tmp_words = tmp_g;
+            c->slots_clean = false;
+            CK(launch_solve_groups((const BatchJob *)c->b_jobs.p, &G, ng * gctas, threads_g, smem_g, c->stream));
+            c->launches++;
+            CK(cudaMemcpyAsync(bo, c->b_out.p, sizeof(BatchOut) * nl, cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaMemcpyAsync(tr, c->b_tree.p, tree_bytes * nl, cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            if (c->phases)
+                fprintf(stderr, "rei batch: %u parked searches continued in their slots, %u CTAs each\n", ng, gctas);
+            for (uint32_t g = 0; g < ng; g++) {
+                Parked pk = grp[g];
+                const BatchOut &b = bo[pk.k];
+                pk.ms += b.ns / 1e6;
+                if (b.status == ST_FOUND || b.status == ST_NOT_FOUND || b.status == ST_OOM) {
+                    finish(pk.k, b, pk.ms);
+                    outs[pk.prob].stats.launches += 1;
+                    outs[pk.prob].stats.search_launches += 1;
+                } else {
+                    // (outgrew its slot again, or failed: continued on the whole GPU)
+                    pk.need_rows = b.status == ST_NEED_MEM ? b.need_rows : 1u;
+                    rest.push_back(pk);
+                }
+            }
+        }
+    }
+    // the rest continue on the whole GPU from their slots' rows (the table is
+    // rebuilt there, so the slots' tables and chunk bitmaps are emptied for
+    // later problems); then every slot is empty again
+    const uint64_t bm_words = (chunk + 31) / 32;
+    for (const Parked &pk : rest)
+        if (pk.slot < slots) {
+            CK(cudaMemsetAsync((unsigned long long *)c->s_table.p + (uint64_t)pk.slot * tslots, 0xFF, 8 * tslots,
+                               c->stream));
+            CK(cudaMemsetAsync((uint32_t *)c->s_bitmap.p + (uint64_t)pk.slot * bm_words, 0, 4 * bm_words, c->stream));
+        }
+    c->slots_clean = true;
+
+    // each such search continues from its slot: one after another on this
+    // context's whole GPU when there is one, else side by side on helper
+    // contexts (own streams and buffers), each launch on an equal share of
+    // the SMs (the searches are latency-bound; together they fill the GPU)
+    auto continue_one = [&](rei_ctx *h, const Parked &pk) {
         const uint32_t i = pk.prob;
         const SlotResume rs{&A.slot, pk.slot};
-        const rei_status r = solve_one(c, &probs[i], &outs[i], pk.slot < slots ? &rs : nullptr);
+        const rei_status r = solve_one(h, &probs[i], &outs[i], pk.slot < slots ? &rs : nullptr);
         if (r != REI_OK && r != REI_NOT_FOUND && r != REI_OOM) outs[i].status = r;
-        // the problem's time: on its CTA, then on the whole GPU
+        // the problem's time: on its CTA (and group), then on its share of the GPU
         outs[i].stats.ms_total += pk.ms;
         outs[i].stats.ms_search_kernel += pk.ms;
+    };
+    redo = rest;
+    const uint32_t nh = (uint32_t)std::min<size_t>(redo.size(), kBatchHelpers);
+    if (nh <= 1) {
+        for (const Parked &pk : redo) continue_one(c, pk);
+    } else {
+        while (c->helpers.size() < nh) {
+            rei_ctx *h = nullptr;
+            if (rei_ctx_create(&h, c->device, nullptr, nullptr) != REI_OK) break;
+            c->helpers.push_back(h);
+        }
+        const uint32_t nuse = (uint32_t)std::min<size_t>(nh, c->helpers.size());
+        std::atomic<size_t> next{0};
+        std::vector<uint64_t> l0(nuse);
+        std::vector<std::thread> th;
+        for (uint32_t k = 0; k < nuse; k++) {
+            rei_ctx *h = c->helpers[k];
+            h->opt_chunk = c->opt_chunk;
+            h->opt_cache_init = c->opt_cache_init;
+            h->opt_solo_tiles = c->opt_solo_tiles;
+            h->opt_small_rows = c->opt_small_rows;
+            h->opt_fused = c->opt_fused;
+            h->opt_exact = c->opt_exact;
+            h->opt_handover = c->opt_handover;
+            const int64_t share = std::max<int64_t>(1, (int64_t)c->sm_count * 2 / nuse);  // (k_solve: 2 CTAs per SM)
+            h->opt_grid = c->opt_grid > 0 ? std::min<int64_t>(c->opt_grid, share) : share;
+            l0[k] = h->launches;
+            th.emplace_back([&, h] {
+                cudaSetDevice(h->device);
+                for (size_t q; (q = next.fetch_add(1)) < redo.size();) continue_one(h, redo[q]);
+            });
+        }
+        if (nuse == 0)
+            for (const Parked &pk : redo) continue_one(c, pk);
+        for (std::thread &t : th) t.join();
+        for (uint32_t k = 0; k < nuse; k++) c->launches += c->helpers[k]->launches - l0[k];
     }
     if (!again.empty()) return run_batch(c, probs, again, outs, warps, chunk_sz, yield_us, nullptr);
     return REI_OK;

@@ -202,6 +202,9 @@ struct SolveJob {
     // a search on one CTA of the batched or served form gives up (and is
     // solved again on the whole GPU) after yield_ns from t_start (0 = never)
     uint64_t yield_ns, t_start;
+    // the CTAs that search this problem: team_size of them from team_base on
+    // (0, 0: every CTA of the launch); the first of them leads
+    uint32_t team_base, team_size;
     uint16_t leaf_cost[256];
     uint8_t leaf_sym[256];
 };
@@ -252,9 +255,11 @@ struct BatchOut {
     uint64_t cand_op[5];
     uint64_t ns;
     // ST_NEED_MEM from the search: the memory slot that still holds its
-    // cache, level table and state (the CTA took no more work), so that the
-    // host continues the search from there; kNoSlot = not searched here
-    uint32_t slot, pad;
+    // cache, uniqueness table, level table and state (the CTA took no more
+    // work), so that the search continues from there; kNoSlot = not searched
+    // here.  need_rows: the cache rows the search asked for (0: it stopped at
+    // its time allowance, and fits its slot)
+    uint32_t slot, need_rows;
 };
 constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
 
@@ -264,6 +269,22 @@ struct BatchJob {
     SolveJob job;
     uint8_t *tree;
     BatchOut *out;
+};
+
+// searches a batch left in their slots at their time allowance, continued
+// side by side in one launch: group g (group_ctas CTAs from g * group_ctas on)
+// continues problem prob[g] in slot slot[g], in the slot's memory
+struct GroupArgs {
+    SlotMem slot;
+    const uint32_t *prob, *slot_of;  // per group
+    uint32_t groups, group_ctas;
+    uint32_t *blk;                   // groups * group_ctas
+    uint64_t *plan;                  // groups * plan_stride words
+    uint64_t plan_stride;
+    // chunk workspace of each group (larger chunks than a slot's): `chunk`
+    // candidates, tmp_words words of candidate rows; the bitmaps start zeroed
+    uint32_t *tmp, *pending, *slotpos, *bitmap;
+    uint64_t chunk, tmp_words;
 };
 
 struct BatchArgs {

@@ -80,7 +80,13 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // e * gridDim.x.  A wait that runs out records where it gave up, marks the
 // launch ST_TIMEOUT and returns false so every CTA leaves the kernel.
 
-__device__ bool grid_barrier(SolveState *st, uint32_t &epoch, uint32_t site, uint32_t *trace) {
+// the CTAs that search a problem (SolveJob::team_base/team_size; 0 = the
+// whole launch) and this CTA's rank among them; rank 0 leads
+__device__ __forceinline__ uint32_t team_size_of(const SolveJob &J) { return J.team_size ? J.team_size : gridDim.x; }
+__device__ __forceinline__ uint32_t team_rank_of(const SolveJob &J) { return blockIdx.x - J.team_base; }
+
+__device__ bool grid_barrier(SolveState *st, uint32_t &epoch, uint32_t site, uint32_t *trace, uint32_t team_n,
+                             uint32_t team_r) {
     __shared__ int s_ok;
     // the CTA's threads have finished their global writes and reductions
     // (atomicMin of the answer, atomicOr of survivors, table and cache stores)
@@ -92,7 +98,7 @@ __device__ bool grid_barrier(SolveState *st, uint32_t &epoch, uint32_t site, uin
     epoch++;
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned long long target = (unsigned long long)epoch * gridDim.x;
+        const unsigned long long target = (unsigned long long)epoch * team_n;
         __threadfence();
         atomicAdd(&st->bar_arrive, 1ull);
         unsigned long long seen;
@@ -106,10 +112,10 @@ __device__ bool grid_barrier(SolveState *st, uint32_t &epoch, uint32_t site, uin
             }
         }
         __threadfence();
-        if (trace) trace[blockIdx.x] = (epoch << 8) | site;
+        if (trace) trace[team_r] = (epoch << 8) | site;
         if (!ok) {
             if (atomicCAS(&st->err, 0u, 1u) == 0u) {
-                st->dbg_cta = blockIdx.x;
+                st->dbg_cta = team_r;
                 st->dbg_epoch = epoch;
                 st->dbg_site = site;
                 st->dbg_seen = (uint32_t)seen;
@@ -1308,8 +1314,8 @@ __device__ void tile_setup(Shared &S, uint32_t nseg, uint64_t cs0, uint64_t ce0,
 // __syncthreads when CTA 0 works alone (global writes of a CTA are visible
 // to its own threads after __syncthreads)
 __device__ __forceinline__ bool team_barrier(bool full, SolveState *st, uint32_t &epoch, uint32_t site,
-                                             uint32_t *trace) {
-    if (full) return grid_barrier(st, epoch, site, trace);
+                                             uint32_t *trace, uint32_t team_n, uint32_t team_r) {
+    if (full) return grid_barrier(st, epoch, site, trace, team_n, team_r);
     __syncthreads();
     return true;
 }
@@ -1523,7 +1529,7 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
     const uint32_t Ws = (W & 1u) ? W : W + 1;
     const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const uint32_t nwarps = blockDim.x >> 5;
-    const uint32_t team_n = full ? gridDim.x : 1, team_r = full ? blockIdx.x : 0;
+    const uint32_t team_n = full ? team_size_of(J) : 1, team_r = full ? team_rank_of(J) : 0;
     const bool dedup = a.dedup != 0;
     REI_TSTART();
 
@@ -1613,7 +1619,7 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
         }
 #endif
     }
-    if (!team_barrier(full, st, bar_epoch, 5, J.trace)) return -1;
+    if (!team_barrier(full, st, bar_epoch, 5, J.trace, team_n, team_r)) return -1;
 #ifdef REI_TIMING
     if (full && blockIdx.x == 0 && tid == 0) {
         st->t_sub[39] += globaltimer_ns() - ld_relaxed_u64(&st->t_sub[47]);
@@ -1676,7 +1682,7 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
             J.slotpos[j] = q;
         }
     }
-    if (!team_barrier(full, st, bar_epoch, 7, J.trace)) return -1;
+    if (!team_barrier(full, st, bar_epoch, 7, J.trace, team_n, team_r)) return -1;
     REI_TMARK(full && blockIdx.x == 0, 13);
 
     // ---- phase C: survivors per CTA (contiguous word ranges of the bitmap),
@@ -1730,7 +1736,7 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
         __syncthreads();
     }
     if (team_r == 0 && tid == 0) st->pending_count = 0;
-    if (!team_barrier(full, st, bar_epoch, 8, J.trace)) return -1;
+    if (!team_barrier(full, st, bar_epoch, 8, J.trace, team_n, team_r)) return -1;
     REI_TMARK(full && blockIdx.x == 0, 14);
 
     // ---- phase D: append survivors in candidate order.  Survivor g (of all
@@ -1851,7 +1857,7 @@ __device__ int process_chunk(const SolveJob &J, SolveState *st, Shared &S, const
             J.lvl_count[a.level] = S.lvc[a.level];
         }
     }
-    if (!team_barrier(full, st, bar_epoch, 9, J.trace)) return -1;
+    if (!team_barrier(full, st, bar_epoch, 9, J.trace, team_n, team_r)) return -1;
     REI_TMARK(full && blockIdx.x == 0, 15);
     return 0;
 }
@@ -2292,8 +2298,8 @@ __device__ __forceinline__ void solve_body(const SolveJob &J, uint32_t &bar_epoc
     carve_shared(J, S, smem_raw, &wm);
     const Cta K{&s_plan, s_red, &s_tiles, &s_found, &s_npend, &L, wm};
 
-    if (blockIdx.x != 0) {
-        // ---- worker: run the chunks CTA 0 hands out, until told to stop
+    if (team_rank_of(J) != 0) {
+        // ---- worker: run the chunks the leader hands out, until told to stop
         uint32_t seen = 0;
         for (;;) {
             if (tid == 0) {
@@ -2330,7 +2336,7 @@ __device__ __forceinline__ void solve_body(const SolveJob &J, uint32_t &bar_epoc
             __syncthreads();
             seen++;
             if (s_ctl[0] == CMD_CLEAN) {
-                clean_table(J, s_ctl[1], s_ctl[2], gridDim.x, blockIdx.x);
+                clean_table(J, s_ctl[1], s_ctl[2], team_size_of(J), team_rank_of(J));
                 return;
             }
             if (s_ctl[0] != CMD_CHUNK) return;
@@ -2367,7 +2373,7 @@ __device__ __forceinline__ void solve_body(const SolveJob &J, uint32_t &bar_epoc
             st->c_size = npending;
         }
         publish(st, CMD_CLEAN);
-        clean_table(J, rows, npending, gridDim.x, 0);
+        clean_table(J, rows, npending, team_size_of(J), 0);
         __syncthreads();
         if (tid == 0) st->pending_count = 0;
     } else {
@@ -2539,35 +2545,61 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_solve_fused(const __grid_c
 // ST_NEED_MEM (the time allowance ran out or the slot is too small) the slot
 // keeps the cache rows, back-pointers, level table and state for the host to
 // continue from; its uniqueness table and survivor bitmap are emptied.
+// a problem's search in memory slot `slot`: its cache, table, chunk
+// workspace, level table, state and answer-walk stack (one CTA's share)
+__device__ void bind_slot(SolveJob &J, const SlotMem &m, uint32_t slot) {
+    const uint64_t so = slot;
+    J.cs = m.cs + so * m.cs_words;
+    J.bp_op = m.bp_op + so * m.rows;
+    J.bp_l = m.bp_l + so * m.rows;
+    J.bp_r = m.bp_r + so * m.rows;
+    J.used = m.used + so * m.rows;
+    J.cache_alloc = umin64(J.cap, m.cs_words / J.W < m.rows ? m.cs_words / J.W : m.rows);
+    J.table = m.table + so * m.table_slots;
+    J.table_mask = m.table_slots - 1;
+    J.tmp = m.tmp + so * m.tmp_words;
+    J.chunk_max = umin64(m.chunk, m.tmp_words / J.W);
+    J.pending = m.pending + so * m.chunk;
+    J.slotpos = m.slotpos + so * m.chunk;
+    J.bitmap = m.bitmap + so * ((m.chunk + 31) / 32);
+    J.blk = m.blk + so;
+    J.lvl_start = m.lvl + so * 2 * (kMaxCost + 2);
+    J.lvl_count = J.lvl_start + (kMaxCost + 2);
+    J.st = m.state + so;
+    J.tstack = m.tstack + so * 4 * (kMaxCost + 2);
+    J.trace = nullptr;
+}
+
+// a slot search's report (thread 0)
+__device__ void report_slot(const SolveJob &J, uint32_t status, uint32_t slot, unsigned long long ns, BatchOut &o) {
+    const SolveState *st = J.st;
+    o.status = status;
+    o.cost = st->ans_cost;
+    o.tree_len = st->tree_len;
+    o.candidates = st->candidates;
+    o.unique = st->unique_done;
+    o.levels = st->level;
+    for (int k = 0; k < 5; k++) o.cand_op[k] = st->cand_op[k];
+    o.ns = ns;
+    o.slot = slot;
+    o.need_rows = status == ST_NEED_MEM ? st->need_rows : 0u;
+}
+
+// keep_table: a search that parks leaves its uniqueness table in the slot
+// (the batch continues it there, or empties the table when it continues
+// elsewhere); else the table is emptied for the slot's next problem
 __device__ uint32_t solve_in_slot(SolveJob &J, const SlotMem &m, uint32_t slot, BatchOut *out, uint8_t *smem_raw,
                               Plan *s_plan, uint32_t *s_red, uint64_t *s_tiles, unsigned long long *s_found,
-                              uint32_t *s_npend, Lead *L, uint64_t yield_ns) {
+                              uint32_t *s_npend, Lead *L, uint64_t yield_ns, bool keep_table) {
     const uint32_t tid = threadIdx.x;
     const unsigned long long t_start = globaltimer_ns();
     if (tid == 0) {
         J.yield_ns = yield_ns;
         J.t_start = t_start;
-        const uint64_t so = slot;
-        J.cs = m.cs + so * m.cs_words;
-        J.bp_op = m.bp_op + so * m.rows;
-        J.bp_l = m.bp_l + so * m.rows;
-        J.bp_r = m.bp_r + so * m.rows;
-        J.used = m.used + so * m.rows;
-        J.cache_alloc = umin64(J.cap, m.cs_words / J.W < m.rows ? m.cs_words / J.W : m.rows);
-        J.table = m.table + so * m.table_slots;
-        J.table_mask = m.table_slots - 1;
-        J.tmp = m.tmp + so * m.tmp_words;
-        J.chunk_max = umin64(m.chunk, m.tmp_words / J.W);
-        J.pending = m.pending + so * m.chunk;
-        J.slotpos = m.slotpos + so * m.chunk;
-        J.bitmap = m.bitmap + so * ((m.chunk + 31) / 32);
-        J.blk = m.blk + so;
-        J.lvl_start = m.lvl + so * 2 * (kMaxCost + 2);
-        J.lvl_count = J.lvl_start + (kMaxCost + 2);
-        J.st = m.state + so;
-        J.tstack = m.tstack + so * 4 * (kMaxCost + 2);
-        J.trace = nullptr;
+        bind_slot(J, m, slot);
         J.solo_tiles = 0xFFFFFFFFu;
+        J.team_base = blockIdx.x;
+        J.team_size = 1;
     }
     __syncthreads();
     SolveState *st = J.st;
@@ -2593,25 +2625,14 @@ __device__ uint32_t solve_in_slot(SolveJob &J, const SlotMem &m, uint32_t slot, 
     if (status == ST_FOUND || status == ST_NOT_FOUND || status == ST_OOM) {
         clean_table(J, L->smode ? 0u : L->size, st->pending_count, 1, 0);
     } else {
-        // the host continues this search from the slot's rows and state (it
-        // rebuilds the table there); the slot's table and bitmap are emptied
-        // for the slot's next problem
-        for (uint64_t i = tid; i <= J.table_mask; i += blockDim.x) J.table[i] = kEmpty;
+        // the search continues from the slot's rows and state (in the slot,
+        // or on the whole GPU, where the table is rebuilt from the rows)
+        if (!keep_table)
+            for (uint64_t i = tid; i <= J.table_mask; i += blockDim.x) J.table[i] = kEmpty;
         for (uint64_t i = tid; i < (J.chunk_max + 31) / 32; i += blockDim.x) J.bitmap[i] = 0;
     }
     __syncthreads();
-    if (tid == 0) {
-        BatchOut &o = *out;
-        o.status = status;
-        o.cost = st->ans_cost;
-        o.tree_len = st->tree_len;
-        o.candidates = st->candidates;
-        o.unique = st->unique_done;
-        o.levels = st->level;
-        for (int k = 0; k < 5; k++) o.cand_op[k] = st->cand_op[k];
-        o.ns = globaltimer_ns() - t_start;
-        o.slot = slot;
-    }
+    if (tid == 0) report_slot(J, status, slot, globaltimer_ns() - t_start, *out);
     __syncthreads();
     return status;
 }
@@ -2643,9 +2664,62 @@ __global__ void __launch_bounds__(256, 2) k_solve_batch(const BatchJob *jobs, co
         // not reused, and this CTA takes no more problems (the host launches
         // again for any left in the queue)
         if (solve_in_slot(J, B.slot, blockIdx.x, bj.out, smem_raw, &s_plan, s_red, &s_tiles, &s_found, &s_npend,
-                          &L, B.yield_ns) == ST_NEED_MEM)
+                          &L, B.yield_ns, true) == ST_NEED_MEM)
             return;
     }
+}
+
+// ---------------------------------------------------------------------------
+// searches a batch left in their slots at their time allowance, continued side
+// by side: group g of G.group_ctas CTAs takes problem G.prob[g] in its slot and
+// runs the plain search there (its first CTA leads, the others take the team
+// chunks), with the slot's cache, uniqueness table and state as the batch CTA
+// left them.  The leader writes the problem's report like a batch CTA.
+__global__ void __launch_bounds__(256, 2) k_solve_groups(const BatchJob *jobs, const __grid_constant__ GroupArgs G) {
+    __shared__ SolveJob J;
+    __shared__ unsigned long long s_t0;
+    const uint32_t g = blockIdx.x / G.group_ctas;
+    if (g >= G.groups) return;
+    const uint32_t slot = G.slot_of[g];
+    const BatchJob &bj = jobs[G.prob[g]];
+    if (threadIdx.x == 0) {
+        J = bj.job;
+        J.tree = bj.tree;
+        bind_slot(J, G.slot, slot);
+        J.blk = G.blk + (uint64_t)g * G.group_ctas;
+        J.plan = G.plan + (uint64_t)g * G.plan_stride;
+        J.tmp = G.tmp + (uint64_t)g * G.tmp_words;
+        J.pending = G.pending + (uint64_t)g * G.chunk;
+        J.slotpos = G.slotpos + (uint64_t)g * G.chunk;
+        J.bitmap = G.bitmap + (uint64_t)g * ((G.chunk + 31) / 32);
+        // (new languages of a chunk and the cached ones keep the slot's
+        // table at most half full)
+        J.chunk_max = umin64(umin64(G.chunk, G.tmp_words / J.W), (J.table_mask + 1) / 2 - J.cache_alloc);
+        J.team_base = g * G.group_ctas;
+        J.team_size = G.group_ctas;
+        J.yield_ns = 0;
+        J.solo_tiles = 64;
+        J.small_rows = 0;
+        J.handover = 0;
+        s_t0 = globaltimer_ns();
+        // (the leader continues the parked search; the other CTAs read no
+        // state before its first command)
+        if (team_rank_of(J) == 0) {
+            SolveState *st = J.st;
+            st->status = ST_RUNNING;
+            st->need_rows = 0;
+            st->pending_count = 0;
+            st->bar_arrive = 0;
+            st->cmd = 0;
+            st->cmd_seq = 0;
+            st->err = 0;
+        }
+    }
+    __syncthreads();
+    uint32_t epoch = 0;
+    solve_body(J, epoch);
+    if (team_rank_of(J) == 0 && threadIdx.x == 0)
+        report_slot(J, ld_relaxed_u32(&J.st->status), slot, globaltimer_ns() - s_t0, *bj.out);
 }
 
 // ---------------------------------------------------------------------------
@@ -2838,7 +2912,7 @@ __global__ void __launch_bounds__(256, 2) k_serve(const __grid_constant__ ServeA
         uint32_t status = ST_BAD;
         if (verdict == 0) {
             status = solve_in_slot(J, A.slot, slot, &o.out, smem_raw, &s_plan, s_red, &s_tiles, &s_found, &s_npend,
-                                   &L, A.yield_ns);
+                                   &L, A.yield_ns, false);
         } else if (tid == 0) {
             o.out.status = verdict == 1 ? ST_BAD : ST_NEED_MEM;
             o.out.slot = kNoSlot;  // (too large for a slot: never searched here)
@@ -2984,6 +3058,20 @@ cudaError_t launch_solve_batch(const BatchJob *jobs_dev, const BatchArgs *args, 
 cudaError_t solve_batch_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm) {
     return occupancy((const void *)k_solve_batch, threads, smem, blocks_per_sm);
 }
+
+cudaError_t launch_solve_groups(const BatchJob *jobs_dev, const GroupArgs *args, uint32_t grid, uint32_t threads,
+                                size_t smem, cudaStream_t stream) {
+    cudaError_t e = prepare((const void *)k_solve_groups);
+    if (e != cudaSuccess) return e;
+    void *args_[] = {(void *)&jobs_dev, (void *)args};
+    return cudaLaunchCooperativeKernel((const void *)k_solve_groups, dim3(grid), dim3(threads), args_, smem, stream);
+}
+
+cudaError_t solve_groups_occupancy(uint32_t threads, size_t smem, int *blocks_per_sm) {
+    return occupancy((const void *)k_solve_groups, threads, smem, blocks_per_sm);
+}
+
+cudaError_t solve_groups_smem_max(size_t *bytes) { return smem_max_of((const void *)k_solve_groups, bytes); }
 
 cudaError_t launch_serve(const ServeArgs *args, uint32_t grid, uint32_t threads, size_t smem, cudaStream_t stream) {
     cudaError_t e = prepare((const void *)k_serve);
