@@ -203,10 +203,12 @@ void rei_ctx_destroy(rei_ctx *ctx);
  *                      for throughput (default 4 Mi; 0 = never)
  *   REI_OPT_YIELD_US   a batched or served problem still searching on its one
  *                      CTA after this many microseconds stops there and
- *                      continues on the whole GPU from the levels it has
- *                      cached, like a problem that outgrows its slot
- *                      (default 500; 0 = never; rei_tune.yield_us, when
- *                      given, takes its place for a batch)
+ *                      continues from the levels it has cached: in a batch,
+ *                      in its slot on a group of CTAs beside the other such
+ *                      problems; served, or once it outgrows its slot, on
+ *                      the whole GPU (default 500; 0 = never;
+ *                      rei_tune.yield_us, when given, takes its place for a
+ *                      batch)
  *   REI_OPT_FUSED_STAGE 1 = stage a problem inside its search launch when the
  *                      launch can hold it (|ic| <= 2048, strings <= 8 KiB;
  *                      the default), 0 = always a separate staging launch.
@@ -287,8 +289,10 @@ typedef struct rei_tune {
     uint32_t warps_per_cta; /* warps of each CTA: 1, 2, 4 or 8 */
     uint32_t chunk;         /* candidates per dedup chunk in a slot: 256 .. 65536 */
     uint32_t yield_us;      /* a problem still searching on its CTA after this
-                               many microseconds continues on the whole GPU
-                               from where it stopped (0xFFFFFFFF = never) */
+                               many microseconds continues from where it
+                               stopped, in its slot on a group of CTAs beside
+                               the other such problems, or on the whole GPU
+                               once it outgrows its slot (0xFFFFFFFF = never) */
 } rei_tune;
 
 /* Solve n problems.  outs[i] receives problem i's result exactly as
