@@ -77,8 +77,9 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // ---------------------------------------------------------------------------
 // bounded grid barrier: a monotonic 64-bit arrival counter (never reset during
 // a launch); barrier number e of a launch completes when the counter reaches
-// e * gridDim.x.  A wait that runs out records where it gave up, marks the
-// launch ST_TIMEOUT and returns false so every CTA leaves the kernel.
+// e times the team's CTAs.  A wait that runs out records where it gave up,
+// marks the search ST_TIMEOUT and returns false so every CTA of the team
+// leaves the kernel.
 
 // the CTAs that search a problem (SolveJob::team_base/team_size; 0 = the
 // whole launch) and this CTA's rank among them; rank 0 leads
@@ -1218,12 +1219,14 @@ __device__ uint32_t emit_tree_warp(const SolveJob &J, uint32_t op, uint32_t l, u
 // ---------------------------------------------------------------------------
 // the persistent search kernel
 //
-// CTA 0 leads: it plans levels, moves from level to level and decides, chunk by
-// chunk, whether to process the chunk alone (small chunks: its own warps,
-// __syncthreads between phases, no grid-wide wait) or with every CTA.  The
-// other CTAs wait for a command (a sequence number and parameters in the
-// state, published with release / read with acquire), join the chunk's
-// phases with grid barriers, and go back to waiting.
+// The team's first CTA (CTA 0 of a plain launch) leads: it plans levels, moves
+// from level to level and decides, chunk by chunk, whether to process the
+// chunk alone (small chunks: its own warps, __syncthreads between phases, no
+// grid-wide wait) or with the whole team.  The other CTAs wait for a command
+// (a sequence number and parameters in the state, published with release /
+// read with acquire), join the chunk's phases with grid barriers, and go back
+// to waiting.  A team is every CTA of the launch, or (continued batch
+// searches) a group of them per problem.
 
 // CTAs of the plain path, 16 warps each: the fused launch (staging, then the
 // levels of a small or medium search, latency-bound) runs one per SM, at up
@@ -2279,7 +2282,7 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
     return 0;
 }
 
-// the search of one problem by every CTA of the launch (CTA 0 leads)
+// the search of one problem by its team of CTAs (the first one leads)
 __device__ __forceinline__ void solve_body(const SolveJob &J, uint32_t &bar_epoch) {
     SolveState *st = J.st;
     extern __shared__ __align__(16) uint8_t smem_raw[];
