@@ -88,6 +88,24 @@ def test_batch_config_matches_stored_oracle_results():
         assert r.cost <= i.target_cost
 
 
+@pytest.mark.parametrize("yield_us,chunk", [(1, 0), (50, 4096)])
+def test_batch_config_parked_everywhere_matches_stored_oracle_results(yield_us, chunk):
+    """The 512 batched instances with a time allowance so short that nearly
+    every search parks on its CTA: more parked searches than the GPU has CTA
+    pairs, so some continue in slot groups and the rest on helper contexts
+    from their slots; every result still equals the oracle's."""
+    want = load_expected("batched_expected.txt")
+    insts = [batched_instance(s) for s in range(512)]
+    probs = [rei.Problem(i.alphabet, i.pos, i.neg, costs=(1, 1, 1, 1, 1), max_cost=40, mem_budget=1 << 30)
+             for i in insts]
+    with rei.Context(device=0) as ctx:
+        batch = ctx.solve_batch(probs, warps_per_cta=8, chunk=chunk, yield_us=yield_us)
+    for s, r in enumerate(batch):
+        st, cost, cand, uniq, n_ic, tree = want[s]
+        assert r.status == ST[st], s
+        assert (r.cost, r.tree, r.candidates, r.unique, r.n_ic) == (cost, tree, cand, uniq, n_ic), s
+
+
 def test_batch_with_per_symbol_costs():
     insts = [make_config("small", s) for s in range(12)] + [batched_instance(s) for s in range(12)]
     probs = []
