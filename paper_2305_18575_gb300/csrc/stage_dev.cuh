@@ -301,10 +301,17 @@ __device__ inline void stage_run(const StageJob &J, const StageSmem &M) {
     STAGE_MARK(1);
 
     // every occurrence (start p, length len) of every string goes into the
-    // set; the first occurrence of each word also records its slot
+    // set; the first occurrence of each word also records its slot.  The
+    // lengths from one start are split into up to four runs of consecutive
+    // lengths, one thread each (a run hashes its start's shorter prefix
+    // first), so that no thread inserts more than a quarter of a string's
+    // infixes from one start
     if (s_err == SE_OK) {
         const uint32_t mask = M.hcap - 1;
-        for (uint32_t p = tid; p < total; p += nt) {
+        const uint32_t nb = s_maxlen < 8 ? (s_maxlen + 1) / 2 : 4u;  // runs per start (0 when every string is empty)
+        const uint32_t run = nb ? (s_maxlen + nb - 1) / nb : 1u;     // lengths per run
+        for (uint64_t item = tid; item < (uint64_t)total * nb; item += nt) {
+            const uint32_t p = (uint32_t)(item / nb), b = (uint32_t)(item - (uint64_t)p * nb);
             // string k with offs[k] <= p < offs[k+1] (strings may be empty)
             uint32_t lo = 0, hi = n_str;  // invariant: offs[lo] <= p < offs[hi]
             while (hi - lo > 1) {
@@ -313,8 +320,11 @@ __device__ inline void stage_run(const StageJob &J, const StageSmem &M) {
                 else hi = mid;
             }
             const uint32_t end = offs[lo + 1];
+            const uint32_t e0 = p + b * run, e1 = min(end, e0 + run);  // this run's lengths: e0 - p + 1 .. e1 - p
+            if (e0 >= end) continue;
             uint64_t h = kH0;
-            for (uint32_t e = p + 1; e <= end; e++) {
+            for (uint32_t e = p + 1; e <= e0; e++) h = stage_mix(h, (uint32_t)rank_tab[bytes[e - 1]]);
+            for (uint32_t e = e0 + 1; e <= e1; e++) {
                 const uint32_t len = e - p;
                 h = stage_mix(h, (uint32_t)rank_tab[bytes[e - 1]]);
                 const uint64_t f = stage_final(h, len);
@@ -451,19 +461,22 @@ __device__ inline void stage_run(const StageJob &J, const StageSmem &M) {
         return;
     }
     // pairs of word r: split k is (prefix of length k, the rest); prefixes by
-    // dropping last symbols from r, suffixes by dropping first symbols
+    // dropping last symbols from r, suffixes by dropping first symbols.  Each
+    // half of a pair word is stored on its own (16-bit stores: the halves
+    // are written, never read back from global memory)
     for (uint32_t r = r0; r < r1; r++) {
         J.gt_off[r] = off;
         const uint32_t len = M.wlen[r];
-        uint32_t *out = J.gt_pair + off;
+        // (little-endian words: pair k's low half, the prefix, is out[2k])
+        uint16_t *out = reinterpret_cast<uint16_t *>(J.gt_pair + off);
         uint32_t v = r;
         for (uint32_t k = 0; k <= len; k++) {
-            out[k] = v << 16;
+            out[2 * k + 1] = (uint16_t)v;
             v = M.dfirst[v];
         }
         uint32_t u = r;
         for (uint32_t k = len + 1; k-- > 0;) {
-            out[k] |= u;
+            out[2 * k] = (uint16_t)u;
             u = M.dlast[u];
         }
         off += len + 1;
