@@ -2483,14 +2483,23 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_solve_fused(const __grid_c
                      solve_smem_bytes(W, I.n, I.G, I.max_len, j.seg_cap, j.gt_in_smem, warps, j.small_rows) <=
                          F.smem_cap;
             }
-            *F.job = j;
+            J = j;  // (CTA 0 keeps the job in shared memory)
             if (!ok) st->status = ST_RESTAGE;
-            // release: the job and the fresh state are in place
-            __threadfence();
-            atomicExch(&st->launch, F.launch_id);
             s_go = ok ? 1u : 0u;
         }
         __syncthreads();
+        // the job for the other CTAs, written by every thread; then the
+        // release: the job and the fresh state are in place
+        {
+            const unsigned long long *src = reinterpret_cast<const unsigned long long *>(&J);
+            unsigned long long *dst = reinterpret_cast<unsigned long long *>(F.job);
+            for (uint32_t i = threadIdx.x; i < sizeof(SolveJob) / 8; i += blockDim.x) dst[i] = src[i];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicExch(&st->launch, F.launch_id);
+        }
         if (!s_go) return;
     } else {
         // the other CTAs wait for CTA 0's release of this launch (a stale id
@@ -2518,13 +2527,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_solve_fused(const __grid_c
         }
         __syncthreads();
         if (!s_go) return;
-    }
-    {
         const unsigned long long *src = reinterpret_cast<const unsigned long long *>(F.job);
         unsigned long long *dst = reinterpret_cast<unsigned long long *>(&J);
         for (uint32_t i = threadIdx.x; i < sizeof(SolveJob) / 8; i += blockDim.x) dst[i] = ld_relaxed_u64(src + i);
+        __syncthreads();
     }
-    __syncthreads();
 #ifdef REI_TIMING
     if (blockIdx.x == 0 && threadIdx.x == 0) st->t_sub[10] = globaltimer_ns() - t_begin;
 #endif
