@@ -1904,6 +1904,9 @@ struct rei_server {
         uint64_t footprint;
         double t_submit;  // host clock, ms
         uint32_t slot = kNoSlot;  // a search the launch left in this memory slot
+        uint32_t need_rows = 0;   // the rows it asked for (0: it stopped at its time allowance)
+        uint64_t job = 0;         // its ring job (its report is in outs[job % ring_size])
+        double ms_slot = 0;       // time its search spent in the slot
     };
     struct Done {
         rei_result r;
@@ -2020,6 +2023,7 @@ rei_status server_setup(rei_server *S) {
     A.leaf = (uint32_t *)take(4 * slots * kMaxWords * 256);
     A.sinfo = (StageInfo *)take(sizeof(StageInfo) * slots);
     A.head = (unsigned long long *)take(64);
+    A.parked = (BatchJob *)take(sizeof(BatchJob) * slots);
     if (oom) return REI_OOM;
     if (cudaStreamCreateWithFlags(&S->kstream, cudaStreamNonBlocking) != cudaSuccess) return REI_ECUDA;
     if (cudaEventCreateWithFlags(&S->kdone, cudaEventDisableTiming) != cudaSuccess) return REI_ECUDA;
@@ -2083,6 +2087,139 @@ void finish(rei_server *S, uint64_t ticket, const rei_result &r, const char *reg
     S->done_cv.notify_all();
 }
 
+// a served search's report (from its slot, or its slot group) as its result
+void finish_served(rei_server *S, const rei_server::Req &req, const ServeOut &o, const BatchOut &b, double ms,
+                   uint32_t launches) {
+    rei_result r{};
+    r.stats.n_ic = o.info.n;
+    r.stats.words = o.info.W;
+    r.stats.max_len = o.info.max_len;
+    r.stats.guide_pairs = o.info.G;
+    r.stats.candidates = b.candidates;
+    r.stats.unique = b.unique;
+    r.stats.levels = b.levels;
+    for (int k = 0; k < 5; k++) r.stats.cand_op[k] = b.cand_op[k];
+    r.stats.ms_search_kernel = ms;
+    r.stats.ms_total = now_ms() - req.t_submit;
+    r.stats.search_launches = launches;
+    switch (b.status) {
+    case ST_FOUND: r.status = REI_OK; break;
+    case ST_NOT_FOUND: r.status = REI_NOT_FOUND; break;
+    case ST_OOM: r.status = REI_OOM; break;
+    case ST_BAD: r.status = REI_EINVAL; break;
+    default: r.status = REI_ECUDA; break;
+    }
+    std::string text;
+    uint32_t ntok = 0;
+    if (r.status == REI_OK) {
+        r.cost = b.cost;
+        ntok = b.tree_len;
+        text = format_regex(o.tree, ntok, req.alphabet.data());
+    }
+    r.regex_len = text.size();
+    r.tree_len = 2ull * ntok;
+    finish(S, req.ticket, r, text.data(), text.size(), o.tree, 2ull * ntok);
+}
+
+// a slot whose search continues elsewhere: its table and chunk bitmap are
+// emptied for its next request (ordered before the next launch)
+void empty_slot(rei_server *S, uint32_t slot) {
+    const SlotMem &m = S->args.slot;
+    const uint64_t bmw = (m.chunk + 31) / 32;
+    cudaMemsetAsync(m.table + (uint64_t)slot * m.table_slots, 0xFF, 8 * m.table_slots, S->kstream);
+    cudaMemsetAsync(m.bitmap + (uint64_t)slot * bmw, 0, 4 * bmw, S->kstream);
+}
+
+// the searches in `alone` that stopped at their time allowance continue in
+// their slots, side by side in one launch (a group of CTAs each, as in the
+// batched form); those that finish are answered and leave `alone`
+void continue_in_slots(rei_server *S, std::vector<rei_server::Req> &alone) {
+    rei_ctx *c = S->ctx;
+    std::vector<size_t> gi;
+    for (size_t i = 0; i < alone.size(); i++)
+        if (alone[i].slot < S->grid && alone[i].need_rows == 0) gi.push_back(i);
+    if (gi.empty()) return;
+    const uint32_t threads_g = 256;
+    size_t smem_g = 0, smem_gmax = 0;
+    uint32_t seg_cap_g = 0, wmax_g = 1;
+    for (size_t i : gi) {
+        const StageInfo &I = S->outs_h[alone[i].job % S->ring_size].info;
+        const uint32_t seg_cap = 2 * alone[i].p.max_cost + 4;
+        // (the guide table in shared memory as the served CTA decided it)
+        const bool gt = solve_smem_bytes(I.W, I.n, I.G, I.max_len, seg_cap, true, threads_g / 32) <= S->smem;
+        smem_g = std::max(smem_g, solve_smem_bytes(I.W, I.n, I.G, I.max_len, seg_cap, gt, threads_g / 32));
+        seg_cap_g = std::max(seg_cap_g, seg_cap);
+        wmax_g = std::max(wmax_g, I.W);
+    }
+    if (solve_groups_smem_max(&smem_gmax) != cudaSuccess || smem_g > smem_gmax) return;
+    int bps = 0;
+    if (solve_groups_occupancy(threads_g, smem_g, &bps) != cudaSuccess || bps < 1) return;
+    const uint32_t cap = (uint32_t)bps * (uint32_t)c->sm_count;
+    const uint32_t ng = (uint32_t)std::min<size_t>(gi.size(), cap / 2);
+    if (ng == 0) return;
+    const uint32_t gctas = std::min<uint32_t>(cap / ng, kMaxTeam);
+    const uint64_t pstride = plan_words(seg_cap_g);
+    uint64_t chunk_g = 1ull << 18;
+    while (chunk_g > 4096 && chunk_g * wmax_g * ng > (1ull << 28)) chunk_g >>= 1;
+    const uint64_t tmp_g = chunk_g * wmax_g, bmw_g = (chunk_g + 31) / 32;
+    if (ensure(c, c->g_idx, 8ull * ng) || ensure(c, c->g_blk, 4ull * ng * gctas) ||
+        ensure(c, c->g_plan, 8ull * ng * pstride) || ensure(c, c->g_tmp, 4ull * ng * tmp_g) ||
+        ensure(c, c->g_pend, 4ull * ng * chunk_g) || ensure(c, c->g_slotpos, 4ull * ng * chunk_g) ||
+        ensure(c, c->g_bitmap, 4ull * ng * bmw_g) || ensure_pinned(c, 8ull * ng))
+        return;
+    // (allocations on the context's stream; and no copy uses the pinned buffer)
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return;
+    uint32_t *gidx = (uint32_t *)c->h_pin;
+    for (uint32_t g = 0; g < ng; g++) gidx[g] = gidx[ng + g] = alone[gi[g]].slot;
+    GroupArgs G{};
+    G.slot = S->args.slot;
+    G.prob = (const uint32_t *)c->g_idx.p;
+    G.slot_of = (const uint32_t *)c->g_idx.p + ng;
+    G.groups = ng;
+    G.group_ctas = gctas;
+    G.blk = (uint32_t *)c->g_blk.p;
+    G.plan = (uint64_t *)c->g_plan.p;
+    G.plan_stride = pstride;
+    G.tmp = (uint32_t *)c->g_tmp.p;
+    G.pending = (uint32_t *)c->g_pend.p;
+    G.slotpos = (uint32_t *)c->g_slotpos.p;
+    G.bitmap = (uint32_t *)c->g_bitmap.p;
+    G.chunk = chunk_g;
+    G.tmp_words = tmp_g;
+    if (cudaMemcpyAsync(c->g_idx.p, gidx, 8ull * ng, cudaMemcpyHostToDevice, S->kstream) != cudaSuccess ||
+        cudaMemsetAsync(c->g_bitmap.p, 0, 4ull * ng * bmw_g, S->kstream) != cudaSuccess ||
+        launch_solve_groups(S->args.parked, &G, ng * gctas, threads_g, smem_g, S->kstream) != cudaSuccess ||
+        cudaStreamSynchronize(S->kstream) != cudaSuccess) {
+        // (nothing was answered: every search continues alone, from its slot)
+        return;
+    }
+    c->launches++;
+    c->pin_clean = true;
+    std::vector<rei_server::Req> rest;
+    std::vector<bool> grouped(alone.size(), false);
+    for (uint32_t g = 0; g < ng; g++) grouped[gi[g]] = true;
+    for (size_t i = 0; i < alone.size(); i++) {
+        rei_server::Req &req = alone[i];
+        if (!grouped[i]) {
+            rest.push_back(std::move(req));
+            continue;
+        }
+        const ServeOut &o = S->outs_h[req.job % S->ring_size];
+        std::atomic_thread_fence(std::memory_order_acquire);  // (the launch has finished: its writes are in)
+        const BatchOut b = o.out;
+        const double ms = req.ms_slot + b.ns / 1e6;
+        if (b.status == ST_FOUND || b.status == ST_NOT_FOUND || b.status == ST_OOM) {
+            finish_served(S, req, o, b, ms, 2);
+        } else {
+            // (outgrew its slot in the group, or failed there: continued alone)
+            req.need_rows = b.status == ST_NEED_MEM ? std::max<uint32_t>(1, b.need_rows) : 1u;
+            req.ms_slot = ms;
+            rest.push_back(std::move(req));
+        }
+    }
+    alone.swap(rest);
+}
+
 void solve_alone(rei_server *S, rei_server::Req &req) {
     req.p.alphabet = req.alphabet.data();
     req.p.bytes = req.bytes.data();
@@ -2130,45 +2267,27 @@ void server_loop(rei_server *S) {
             S->live_bytes -= req.footprint;
             if (b.status == ST_NEED_MEM) {
                 req.slot = b.slot;
+                req.need_rows = b.need_rows;
+                req.job = job;
+                req.ms_slot = b.ns / 1e6;
                 alone.push_back(std::move(req));
                 it = S->live.erase(it);
                 continue;
             }
-            rei_result r{};
-            r.stats.n_ic = o.info.n;
-            r.stats.words = o.info.W;
-            r.stats.max_len = o.info.max_len;
-            r.stats.guide_pairs = o.info.G;
-            r.stats.candidates = b.candidates;
-            r.stats.unique = b.unique;
-            r.stats.levels = b.levels;
-            for (int k = 0; k < 5; k++) r.stats.cand_op[k] = b.cand_op[k];
-            r.stats.ms_search_kernel = b.ns / 1e6;
-            r.stats.ms_total = now_ms() - req.t_submit;
-            r.stats.search_launches = 1;
-            switch (b.status) {
-            case ST_FOUND: r.status = REI_OK; break;
-            case ST_NOT_FOUND: r.status = REI_NOT_FOUND; break;
-            case ST_OOM: r.status = REI_OOM; break;
-            case ST_BAD: r.status = REI_EINVAL; break;
-            default: r.status = REI_ECUDA; break;
-            }
-            std::string text;
-            uint32_t ntok = 0;
-            if (r.status == REI_OK) {
-                r.cost = b.cost;
-                ntok = b.tree_len;
-                text = format_regex(o.tree, ntok, req.alphabet.data());
-            }
-            r.regex_len = text.size();
-            r.tree_len = 2ull * ntok;
-            finish(S, req.ticket, r, text.data(), text.size(), o.tree, 2ull * ntok);
+            finish_served(S, req, o, b, b.ns / 1e6, 1);
             it = S->live.erase(it);
         }
-        // 2. requests too large for a slot: solved alone while the launch is stopped
+        // 2. searches the launch left in their slots, and requests too large
+        // for a slot, while the launch is stopped: those that stopped at their
+        // time allowance continue side by side in their slots, the others
+        // (and any that outgrow their slot there) alone on the whole GPU
         if (!alone.empty()) {
             stop_kernel(S);
-            for (auto &req : alone) solve_alone(S, req);
+            continue_in_slots(S, alone);
+            for (auto &req : alone) {
+                if (req.slot < S->grid) empty_slot(S, req.slot);
+                solve_alone(S, req);
+            }
             alone.clear();
             progress = true;
         }

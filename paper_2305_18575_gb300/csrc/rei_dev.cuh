@@ -342,6 +342,9 @@ struct ServeArgs {
                                                // found incomplete when first read, head[2]: given up
     unsigned long long idle_ns;
     size_t smem_cap;
+    // per slot: the job of a request whose search parked there (its time
+    // allowance ran out or it outgrew the slot), for its continuation
+    BatchJob *parked;
 };
 
 }  // namespace rei

@@ -2922,7 +2922,15 @@ __global__ void __launch_bounds__(256, 2) k_serve(const __grid_constant__ ServeA
         uint32_t status = ST_BAD;
         if (verdict == 0) {
             status = solve_in_slot(J, A.slot, slot, &o.out, smem_raw, &s_plan, s_red, &s_tiles, &s_found, &s_npend,
-                                   &L, A.yield_ns, false);
+                                   &L, A.yield_ns, true);
+            // a parked search's job, for its continuation (in its slot, or on
+            // the whole GPU from the slot's rows)
+            if (status == ST_NEED_MEM && threadIdx.x == 0) {
+                BatchJob &pj = A.parked[slot];
+                pj.job = J;
+                pj.tree = o.tree;
+                pj.out = &o.out;
+            }
         } else if (tid == 0) {
             o.out.status = verdict == 1 ? ST_BAD : ST_NEED_MEM;
             o.out.slot = kNoSlot;  // (too large for a slot: never searched here)
