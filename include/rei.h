@@ -203,12 +203,11 @@ void rei_ctx_destroy(rei_ctx *ctx);
  *                      for throughput (default 4 Mi; 0 = never)
  *   REI_OPT_YIELD_US   a batched or served problem still searching on its one
  *                      CTA after this many microseconds stops there and
- *                      continues from the levels it has cached: in a batch,
- *                      in its slot on a group of CTAs beside the other such
- *                      problems; served, or once it outgrows its slot, on
- *                      the whole GPU (default 500; 0 = never;
- *                      rei_tune.yield_us, when given, takes its place for a
- *                      batch)
+ *                      continues from the levels it has cached, in its
+ *                      slot on a group of CTAs beside the other such
+ *                      problems (on the whole GPU once it outgrows its
+ *                      slot) (default 500; 0 = never; rei_tune.yield_us,
+ *                      when given, takes its place for a batch)
  *   REI_OPT_FUSED_STAGE 1 = stage a problem inside its search launch when the
  *                      launch can hold it (|ic| <= 2048, strings <= 8 KiB;
  *                      the default), 0 = always a separate staging launch.
@@ -312,7 +311,9 @@ rei_status rei_solve_batch(rei_ctx *ctx, const rei_problem *probs, uint32_t n, r
  * ring, reads answers back and relaunches the search when it returned after
  * going idle.  Problems with more than 255 strings or 8192 bytes, or whose
  * search outgrows a slot (2^17 languages, |ic| <= 2048), are solved alone by
- * rei_solve_problem while the launch is stopped.  Every result equals
+ * rei_solve_problem while the launch is stopped; searches past their time
+ * allowance (REI_OPT_YIELD_US) continue meanwhile in their slots, side by
+ * side on groups of CTAs.  Every result equals
  * rei_solve_problem's for the problem alone.  The server owns its context's
  * device while it lives: make no other call
  * on that context until rei_server_destroy. */
