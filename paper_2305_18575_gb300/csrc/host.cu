@@ -2250,9 +2250,10 @@ void server_loop(rei_server *S) {
     cudaSetDevice(S->ctx->device);
     volatile unsigned long long *ctl = S->ctl_h;
     std::vector<rei_server::Req> alone;
-    for (;;) {
-        bool progress = false;
-        // 1. completions
+    // completions of the live requests: answered ones are finished, parked
+    // ones move to `alone`
+    auto collect = [&]() {
+        bool any = false;
         for (auto it = S->live.begin(); it != S->live.end();) {
             const uint64_t job = it->first;
             ServeOut &o = S->outs_h[job % S->ring_size];
@@ -2263,7 +2264,7 @@ void server_loop(rei_server *S) {
             std::atomic_thread_fence(std::memory_order_acquire);
             rei_server::Req &req = it->second;
             const BatchOut b = o.out;
-            progress = true;
+            any = true;
             S->live_bytes -= req.footprint;
             if (b.status == ST_NEED_MEM) {
                 req.slot = b.slot;
@@ -2277,18 +2278,30 @@ void server_loop(rei_server *S) {
             finish_served(S, req, o, b, b.ns / 1e6, 1);
             it = S->live.erase(it);
         }
-        // 2. searches the launch left in their slots, and requests too large
-        // for a slot, while the launch is stopped: those that stopped at their
-        // time allowance continue side by side in their slots, the others
-        // (and any that outgrow their slot there) alone on the whole GPU
+        return any;
+    };
+    // searches a launch left in their slots, and requests too large for a
+    // slot, once the launch has ended (and every search it parked is in
+    // `alone`: a slot is reused only by a later launch): those that stopped
+    // at their time allowance continue side by side in their slots, the
+    // others (and any that outgrow their slot there) alone on the whole GPU
+    auto handle_alone = [&]() {
+        stop_kernel(S);
+        collect();  // (searches parked while the launch was stopping)
+        continue_in_slots(S, alone);
+        for (auto &req : alone) {
+            if (req.slot < S->grid) empty_slot(S, req.slot);
+            solve_alone(S, req);
+        }
+        alone.clear();
+    };
+    for (;;) {
+        bool progress = false;
+        // 1. completions
+        if (collect()) progress = true;
+        // 2. parked searches and requests too large for a slot
         if (!alone.empty()) {
-            stop_kernel(S);
-            continue_in_slots(S, alone);
-            for (auto &req : alone) {
-                if (req.slot < S->grid) empty_slot(S, req.slot);
-                solve_alone(S, req);
-            }
-            alone.clear();
+            handle_alone();
             progress = true;
         }
         // 3. admissions into the ring, then one publication
@@ -2339,8 +2352,20 @@ void server_loop(rei_server *S) {
             std::atomic_thread_fence(std::memory_order_seq_cst);
             progress = true;
         }
-        // 4. a launch must be running while published requests wait
+        // 4. a launch must be running while published requests wait; before
+        // a new launch reuses the slots, every search the last one parked is
+        // continued (its completion may have arrived after step 1)
         if (!S->live.empty()) {
+            bool kerr = false;
+            const bool running = kernel_running(S, &kerr);
+            if (kerr) {
+                server_fail(S, REI_ECUDA);
+                return;
+            }
+            if (!running) {
+                collect();
+                if (!alone.empty()) handle_alone();
+            }
             const rei_status s = ensure_kernel(S);
             if (s != REI_OK) {
                 server_fail(S, s);
