@@ -513,17 +513,12 @@ class Context:
         """rei_solve_batch over `probs` (one staging and one search launch);
         a rei_tune field left 0 is chosen by the library (see include/rei.h)."""
         n = len(probs)
-        # the packed problems and the output buffers of the last batch are
-        # kept for a batch of the same problems (the same objects, in order)
-        key = tuple(map(id, probs))
-        if getattr(self, "_batch_key", None) != key:
-            self._batch_probs = list(probs)  # (keeps the objects, so their ids stay theirs)
-            self._batch_arr = (rei_problem * max(n, 1))(*[p.p for p in probs])
-            self._batch_key = key
+        arr = (rei_problem * max(n, 1))(*[p.p for p in probs])
+        # (the output buffers of a batch of the same size are reused)
         if getattr(self, "_batch_bufs", None) is None or self._batch_bufs.n != n:
             self._batch_bufs = _BatchBufs(n)
         tune = rei_tune(warps_per_cta, chunk, yield_us) if (warps_per_cta or chunk or yield_us) else None
-        s = rei_solve_batch(self.h, self._batch_arr, n, self._batch_bufs.outs, tune)
+        s = rei_solve_batch(self.h, arr, n, self._batch_bufs.outs, tune)
         if s != REI_OK:
             raise RuntimeError(f"rei_solve_batch: {STATUS_NAMES.get(s, s)}")
         return self._batch_bufs.results()
