@@ -103,8 +103,8 @@ struct rei_ctx {
     bool slots_clean = false;
     int batch_warps = 0;       // autotuned warps per CTA of the batched launch (0 = not yet)
     uint32_t batch_chunk = 0;  // autotuned candidates per dedup chunk in a slot (0 = not yet)
-    // pinned host scratch
-    uint8_t *h_pin = nullptr;
+    // pinned host scratch (and its device address, or null)
+    uint8_t *h_pin = nullptr, *h_pin_dev = nullptr;
     size_t h_pin_bytes = 0;
     bool pin_clean = false;  // no copy from or to h_pin is in flight (the last user synchronised)
 
@@ -198,6 +198,10 @@ rei_status ensure_pinned(rei_ctx *c, size_t bytes) {
     size_t want = std::max<size_t>(bytes, 1 << 16);
     if (cudaMallocHost((void **)&c->h_pin, want) != cudaSuccess) return REI_ECUDA;
     c->h_pin_bytes = want;
+    // (the device's address of the buffer, for kernels that write results there)
+    void *dev = nullptr;
+    c->h_pin_dev = cudaHostGetDevicePointer(&dev, c->h_pin, 0) == cudaSuccess ? (uint8_t *)dev : nullptr;
+    if (!c->h_pin_dev) cudaGetLastError();
     return REI_OK;
 }
 
@@ -628,6 +632,9 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
     F.seen = (uint32_t *)c->seen.p;
     F.seen_bits = c->seen.p ? kSeenBits : 0;
     F.launch_id = ++c->fused_launch_id;
+    // the launch writes its final state into the pinned buffer itself
+    F.host_out = c->h_pin_dev ? (unsigned long long *)(c->h_pin_dev + sizeof(SolveJob)) : nullptr;
+    F.out_words = (sb + sizeof(StageInfo)) / 8;
 
     const double th1 = now_ms();
     CK(cudaEventRecord(c->ev[0], c->stream));
@@ -636,7 +643,7 @@ rei_status run_fused(rei_ctx *c, const rei_problem *p, Staged &sg, double &ms_se
     const double th2 = now_ms();
     c->launches++;
     uint8_t *hs = c->h_pin + sizeof(SolveJob);
-    CK(cudaMemcpyAsync(hs, c->state.p, sb + sizeof(StageInfo), cudaMemcpyDeviceToHost, c->stream));
+    if (!F.host_out) CK(cudaMemcpyAsync(hs, c->state.p, sb + sizeof(StageInfo), cudaMemcpyDeviceToHost, c->stream));
     const double th3 = now_ms();
     CK(cudaStreamSynchronize(c->stream));
     if (c->phases)

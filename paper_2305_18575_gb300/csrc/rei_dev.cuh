@@ -226,6 +226,11 @@ struct FuseArgs {
     uint32_t seen_bits;       // the seen bitmap covers languages of up to this many bits (0 = none)
     uint32_t *seen;           // 2^seen_bits bits, all zero
     unsigned long long launch_id;  // larger than any id the state buffer can hold
+    // where CTA 0 writes the final state, the answer's tokens and the staging
+    // report (out_words 8-byte words, the state buffer's layout) for the host,
+    // in mapped pinned memory; null: the host copies them itself
+    unsigned long long *host_out;
+    uint64_t out_words;
 };
 
 

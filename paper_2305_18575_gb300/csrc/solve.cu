@@ -227,6 +227,9 @@ struct Shared {
 struct Lead {
     uint32_t status, level, size, full, otf, partial_level;
     uint32_t smode;  // languages and their uniqueness table live in shared memory
+    // the answer was found and the other CTAs were told to empty the table
+    // (rows and pending slots given) while the leader writes out the answer
+    uint32_t cleaned, clean_rows, clean_pend;
     uint64_t chunk_pos, candidates, unique_done;
     uint64_t cand_op[5];
 };
@@ -2023,6 +2026,7 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
     Plan &s_plan = *K.plan;
     REI_TSPAN_BEGIN(t_init);
     if (tid == 0) {
+        L.cleaned = 0;
         L.status = st->status;
         L.level = st->level;
         L.size = st->size;
@@ -2222,7 +2226,19 @@ __device__ int lead_search(const SolveJob &J, SolveState *st, Shared &S, const C
         __syncthreads();
     }
 
-    // ---- answer: back-pointers of the first precise candidate, then its tree
+    // ---- answer: back-pointers of the first precise candidate, then its tree.
+    // With a team, its other CTAs empty the table meanwhile (the walk reads
+    // back-pointers only)
+    if (found && allow_team) {
+        if (tid == 0) {
+            L.cleaned = 1;
+            L.clean_rows = L.smode ? 0u : L.size;
+            L.clean_pend = ld_relaxed_u32(&st->pending_count);
+            st->c_level = L.clean_rows;
+            st->c_size = L.clean_pend;
+        }
+        publish(st, CMD_CLEAN);
+    }
     REI_TSPAN_BEGIN(t_ans);
     // (warp 0: thread 0 decodes, the warp gathers the tree)
     if (found && wid == 0) {
@@ -2367,7 +2383,12 @@ __device__ __forceinline__ void solve_body(const SolveJob &J, uint32_t &bar_epoc
     if (lead_search(J, st, S, K, true, bar_epoch) < 0) return;
     REI_TSPAN_BEGIN(t_cl);
     const uint32_t status = ld_relaxed_u32(&st->status);
-    if (status == ST_FOUND || status == ST_NOT_FOUND || status == ST_OOM) {
+    if (L.cleaned) {
+        // (the other CTAs were told while the answer was written out)
+        clean_table(J, L.clean_rows, L.clean_pend, team_size_of(J), 0);
+        __syncthreads();
+        if (tid == 0) st->pending_count = 0;
+    } else if (status == ST_FOUND || status == ST_NOT_FOUND || status == ST_OOM) {
         // every CTA empties its share of the slots this search filled
         // (languages that never left shared memory are in no global slot)
         const uint32_t rows = L.smode ? 0u : L.size, npending = ld_relaxed_u32(&st->pending_count);
@@ -2403,6 +2424,16 @@ __device__ __forceinline__ uint64_t auto_chunk(uint32_t W) {
 // A problem whose staging or search the launch cannot hold (|ic| > 2048, a
 // guide table beyond the pair buffer, shared memory) ends with ST_RESTAGE.
 static_assert(sizeof(StageInfo) % 8 == 0 && offsetof(SolveState, launch) % 8 == 0, "state reset by 8-byte words");
+
+// CTA 0's last step: the final state, tokens and staging report to the host
+__device__ void state_out(const FuseArgs &F) {
+    if (!F.host_out) return;
+    __syncthreads();
+    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(F.tmpl.st);
+    for (uint64_t i = threadIdx.x; i < F.out_words; i += blockDim.x) F.host_out[i] = ld_relaxed_u64(src + i);
+    __threadfence_system();
+}
+
 __global__ void __launch_bounds__(kFusedThreads, 1) k_solve_fused(const __grid_constant__ FuseArgs F) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     __shared__ SolveJob J;
@@ -2500,7 +2531,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_solve_fused(const __grid_c
             __threadfence();
             atomicExch(&st->launch, F.launch_id);
         }
-        if (!s_go) return;
+        if (!s_go) {
+            state_out(F);
+            return;
+        }
     } else {
         // the other CTAs wait for CTA 0's release of this launch (a stale id
         // in the state is always smaller: ids only grow), then take the job
@@ -2542,6 +2576,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_solve_fused(const __grid_c
         st->t_sub[38] = (unsigned long long)(clock64() - c_begin);
     }
 #endif
+    if (blockIdx.x == 0) state_out(F);
 }
 
 // ---------------------------------------------------------------------------
