@@ -295,10 +295,13 @@ def _result(r: "rei_result", status: int, raddr: int, taddr: int) -> Result:
 class _BatchBufs:
     """Caller-owned outputs of a batch of n problems: one rei_result array and
     one regex and one tree buffer for all of them (the pointers are set once;
-    the library writes only lengths, statistics and the text)."""
+    the library writes only lengths, statistics and the text).  A regex of at
+    most REI_MAX_COST + 1 nodes prints at most 3 bytes per node (a symbol or
+    an operator, and its parentheses), so 1024 bytes hold any of them."""
 
-    def __init__(self, n: int, regex_cap: int = 8192, tree_cap: int = 2 * (REI_MAX_COST + 1)):
+    def __init__(self, n: int, regex_cap: int = 1024, tree_cap: int = 2 * (REI_MAX_COST + 1)):
         self.n = n
+        self.rcap, self.tcap = regex_cap, tree_cap
         self.rbuf = C.create_string_buffer(regex_cap * max(n, 1))
         self.tbuf = C.create_string_buffer(tree_cap * max(n, 1))
         self.outs = (rei_result * max(n, 1))()
@@ -316,14 +319,17 @@ class _BatchBufs:
         # every record unpacked at once (field by field through ctypes would
         # cost more than the batch's search)
         raw = C.string_at(C.addressof(self.outs), _RESULT_SIZE * self.n)
+        rtext = C.string_at(self.raddr[0], self.rcap * self.n) if self.n else b""
+        ttext = C.string_at(self.taddr[0], self.tcap * self.n) if self.n else b""
         res = []
         for i, f in enumerate(_RESULT_FMT.iter_unpack(raw)):
             (status, cost, _, _, rlen, _, _, tlen, cand, uniq, levels, n_ic, words, _max_len, gp, ms_stage,
              ms_total, launches, h2d, d2h, o0, o1, o2, o3, o4, star, ms_sk, ms_stk, s_l, grid) = f
             ok = status == REI_OK
+            r0, t0 = i * self.rcap, i * self.tcap
             res.append(Result(status, cost if ok else 0,
-                              C.string_at(self.raddr[i], rlen).decode("utf-8") if ok else None,
-                              C.string_at(self.taddr[i], tlen) if ok else None, cand, uniq, levels, n_ic, words,
+                              rtext[r0:r0 + rlen].decode("utf-8") if ok else None,
+                              ttext[t0:t0 + tlen] if ok else None, cand, uniq, levels, n_ic, words,
                               gp, ms_stage, ms_total, launches, h2d, d2h, (o0, o1, o2, o3, o4), star, ms_sk,
                               ms_stk, s_l, grid))
         return res
