@@ -108,3 +108,35 @@ def test_noalloc_refuses_bad_arguments_before_any_launch():
     assert _noalloc(rei.Problem(b"01", [b"01"], [b"1"], costs=(1, 0, 1, 1, 1))) == (rei.REI_EINVAL, rei.REI_EINVAL)
     assert _noalloc(rei.Problem(b"00", [b"0"], [b""])) == (rei.REI_EINVAL, rei.REI_EINVAL)
     assert _noalloc(rei.Problem(b"01", [b"0"], [b""], max_cost=256)) == (rei.REI_EINVAL, rei.REI_EINVAL)
+
+
+def test_batch_results_unpack_every_field():
+    """The batch binding reads all rei_result records with one unpack (a packed
+    format of the struct): every field of every record, and each record's own
+    regex and tree bytes, come out as field-by-field reading gives them."""
+    import ctypes as C
+    n = 37
+    b = rei._BatchBufs(n)
+    for i in range(n):
+        o = b.outs[i]
+        o.status = rei.REI_OK if i % 3 else rei.REI_NOT_FOUND
+        o.cost = 5 + i
+        text = b"0*(1%d)?" % i
+        o.regex_len = len(text)
+        C.memmove(b.raddr[i], text, len(text))
+        tree = bytes((i + k) & 255 for k in range(2 * (i % 7 + 1)))
+        o.tree_len = len(tree)
+        C.memmove(b.taddr[i], tree, len(tree))
+        st = o.stats
+        st.candidates, st.unique, st.levels, st.n_ic, st.words = 1000 + i, 100 + i, 9, 40 + i, 2
+        st.guide_pairs, st.ms_stage, st.ms_total, st.launches = 300 + i, 0.25 * i, 0.5 * i, i
+        st.bytes_h2d, st.bytes_d2h, st.star_pairs = 7 * i, 11 * i, 3 * i
+        for k in range(5):
+            st.cand_op[k] = i * 10 + k
+        st.ms_search_kernel, st.ms_stage_kernel, st.search_launches, st.grid = 0.125 * i, 0.0625 * i, 1 + i % 2, 152
+    got = b.results()
+    assert len(got) == n
+    for i in range(n):
+        want = rei._result(b.outs[i], b.outs[i].status, b.raddr[i], b.taddr[i])
+        assert got[i] == want, i
+    assert got[4].regex == "0*(14)?" and got[3].regex is None
